@@ -1,0 +1,476 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test names the part of the oracle it pins and the source of the expected
+value (an equation of arXiv 2501.04920, a printed number under tests/golden/, a
+closed form or an independent library routine).  None of them recomputes the
+oracle's own formula; each is chosen so that a dropped term, a wrong sign or a
+transposed operand in that part fails it.
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, special
+
+import oracle as O
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+CX9 = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+CY9 = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+CX5 = CX9[:5]
+CY5 = CY9[:5]
+W5 = np.array([1 / 3] + [1 / 6] * 4)
+CS2 = 1.0 / 3.0
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "printed_values.txt")
+
+# a quiet lattice: no droplet, no ions, no field (used by several pins)
+QUIET = dict(R=-100.0, k_d=0.0, k_r=0.0, c0=0.0, onsager_form=2, Kq=0.0,
+             eps_r=1.0, psi_anode=0.0, psi_cathode=0.0, freeze_E=1,
+             sweeps_min=0, sweeps_max=0, init_sweeps_fixed=0)
+
+
+# ---- P1: moment matrices (Eq. 28, Eq. 46) ---------------------------------
+
+def _inv1d(c):
+    # 1D basis {1, c, c^2} on velocities {0, 1, -1}: rows of the inverse
+    return {0: (1.0, 0.0, -1.0), 1: (0.0, 0.5, 0.5), -1: (0.0, -0.5, 0.5)}[c]
+
+
+def test_p1_matrices_are_the_natural_moment_basis_and_invert():
+    M, Mi, N, Ni = O.matrices()
+    mono9 = [(0, 0), (1, 0), (0, 1), (2, 0), (0, 2), (1, 1), (1, 2), (2, 1), (2, 2)]
+    Mt = np.array([[cx**a * cy**b for cx, cy in zip(CX9, CY9)] for a, b in mono9], float)
+    assert np.array_equal(M, Mt)
+    # tensor-product closed form of the inverse: Minv[i, (a,b)] = psi_a(cx_i) psi_b(cy_i)
+    Mit = np.array([[_inv1d(cx)[a] * _inv1d(cy)[b] for (a, b) in mono9]
+                    for cx, cy in zip(CX9, CY9)])
+    np.testing.assert_allclose(Mi, Mit, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(M @ Mi, np.eye(9), rtol=0, atol=1e-15)
+    mono5 = [(0, 0), (1, 0), (0, 1), (2, 0), (0, 2)]
+    Nt = np.array([[cx**a * cy**b for cx, cy in zip(CX5, CY5)] for a, b in mono5], float)
+    assert np.array_equal(N, Nt)
+    # D2Q5: g0 = m0 - m3 - m4, g(+-1,0) = (m3 +- m1)/2, g(0,+-1) = (m4 +- m2)/2
+    Nit = np.array([[1, 0, 0, -1, -1], [0, .5, 0, .5, 0], [0, 0, .5, 0, .5],
+                    [0, -.5, 0, .5, 0], [0, 0, -.5, 0, .5]])
+    np.testing.assert_allclose(Ni, Nit, rtol=0, atol=1e-15)
+
+
+# ---- P2: equilibria (Eq. 31, 38, 45, 52-53, 57) ----------------------------
+
+def test_p2_equilibrium_moments():
+    rng = np.random.default_rng(2)
+    for _ in range(25):
+        p, rho = rng.uniform(-1e-2, 1e-2), rng.uniform(0.5, 2.0)
+        ux, uy = rng.uniform(-0.1, 0.1, 2)
+        fe = O.feq(p, rho, ux, uy)
+        # zero-mass incompressible form: sum f_eq = 0, first moment rho u,
+        # momentum flux p I + rho u u
+        assert abs(fe.sum()) < 1e-15
+        np.testing.assert_allclose([CX9 @ fe, CY9 @ fe], [rho * ux, rho * uy], atol=1e-15)
+        np.testing.assert_allclose(
+            [(CX9**2) @ fe, (CY9**2) @ fe, (CX9 * CY9) @ fe],
+            [p + rho * ux * ux, p + rho * uy * uy, rho * ux * uy], atol=1e-15)
+        # Eq. 57 returns p from f_eq (grad rho = 0): sum_{i>0} f_eq = (1-w0) p/cs2 - rho r_0
+        r0 = -W9[0] * (ux * ux + uy * uy) / (2 * CS2)
+        p_back = CS2 / (1 - W9[0]) * (fe[1:].sum() + rho * r0)
+        assert abs(p_back - p) < 1e-15
+        phi = rng.uniform(0, 1)
+        he = O.heq(phi, ux, uy)
+        np.testing.assert_allclose(
+            [he.sum(), CX9 @ he, CY9 @ he, (CX9**2) @ he, (CX9 * CY9) @ he],
+            [phi, phi * ux, phi * uy, phi * CS2, 0.0], atol=1e-15)
+        c = rng.uniform(0, 2)
+        ie = O.ion_eq(c, ux, uy)
+        np.testing.assert_allclose([ie.sum(), CX5 @ ie, CY5 @ ie],
+                                   [c, c * ux, c * uy], atol=1e-15)
+        psi = rng.uniform(-2, 2)
+        ge = O.geq(psi)
+        assert abs(ge.sum()) < 1e-15
+        assert abs(ge[1:].sum() / (1 - W5[0]) - psi) < 1e-15   # Eq. 49
+
+
+# ---- P3: MRT with one rate is BGK -------------------------------------------
+
+def test_p3_uniform_rates_reduce_to_bgk():
+    rng = np.random.default_rng(3)
+    for Q in (9, 5):
+        for _ in range(20):
+            tau = rng.uniform(0.51, 2.0)
+            x, xeq, src = (rng.normal(size=Q) for _ in range(3))
+            out = O.mrt(np.full(Q, 1 / tau), x, xeq, src)
+            ref = x - (x - xeq) / tau + (1 - 1 / (2 * tau)) * src
+            np.testing.assert_allclose(out, ref, rtol=0, atol=1e-14)
+
+
+# ---- P4: conserved-moment sources, independent of the free rates -------------
+
+def test_p4_momentum_and_ion_sources_exact_for_any_rates():
+    rng = np.random.default_rng(4)
+    for _ in range(25):
+        f = rng.normal(scale=1e-2, size=9)
+        F = rng.normal(scale=1e-3, size=2)
+        gr = rng.normal(scale=1e-2, size=2)
+        rho, p = rng.uniform(0.5, 2), rng.normal(scale=1e-3)
+        ux, uy = (np.array([CX9 @ f, CY9 @ f]) + 0.5 * F) / rho    # Eq. 56
+        fe = O.feq(p, rho, ux, uy)
+        Fi = O.forcing_f(ux, uy, F[0], F[1], gr[0], gr[1])
+        # the forcing term carries exactly the force in its first moment
+        np.testing.assert_allclose([CX9 @ Fi, CY9 @ Fi], F, atol=1e-16)
+        out = O.mrt(rng.uniform(0.2, 1.9, 9), f, fe, Fi)
+        np.testing.assert_allclose([CX9 @ out, CY9 @ out],
+                                   [CX9 @ f + F[0], CY9 @ f + F[1]], atol=1e-15)
+        # ions: with c = sum p + R/2 (Eq. 41) the zeroth moment gains exactly R
+        pp = rng.uniform(0, 0.5, 5)
+        R = rng.normal(scale=0.1)
+        c = pp.sum() + 0.5 * R
+        out5 = O.mrt(rng.uniform(0.2, 1.9, 5), pp, O.ion_eq(c, ux, uy), W5 * R)
+        assert abs(out5.sum() - (pp.sum() + R)) < 1e-15
+        # Allen-Cahn: phi = sum h is conserved by the collision
+        h = rng.uniform(0, 0.3, 9)
+        phi = h.sum()
+        Hs = O.Hsrc(phi, 4.0, *rng.normal(scale=1e-3, size=2), *rng.normal(size=2))
+        outh = O.mrt(rng.uniform(0.2, 1.9, 9), h, O.heq(phi, ux, uy), Hs)
+        assert abs(outh.sum() - phi) < 1e-15
+
+
+# ---- P5: isotropic stencils (Eq. 59 and the Laplacian) ---------------------
+
+def test_p5_stencil_exact_on_low_degree_polynomials():
+    ny, nx = 10, 12
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    inner = (slice(1, ny - 1), slice(1, nx - 1))
+    rng = np.random.default_rng(5)
+    a = rng.normal(size=10)
+    chi = (a[0] + a[1] * x + a[2] * y + a[3] * x * x + a[4] * x * y + a[5] * y * y)
+    gx, gy, lap = O.stencil(chi)
+    np.testing.assert_allclose(gx[inner], (a[1] + 2 * a[3] * x + a[4] * y)[inner], atol=1e-11)
+    np.testing.assert_allclose(gy[inner], (a[2] + a[4] * x + 2 * a[5] * y)[inner], atol=1e-11)
+    np.testing.assert_allclose(lap[inner], np.full((ny - 2, nx - 2), 2 * a[3] + 2 * a[5]), atol=1e-10)
+    cub = a[6] * x**3 + a[7] * x * x * y + a[8] * x * y * y + a[9] * y**3
+    _, _, lap3 = O.stencil(cub)
+    ref3 = 6 * a[6] * x + 2 * a[7] * y + 2 * a[8] * x + 6 * a[9] * y
+    np.testing.assert_allclose(lap3[inner], ref3[inner], atol=1e-9)
+
+
+def test_p5_stencil_periodic_x_and_mirror_rows():
+    ny, nx = 6, 16
+    k = 2 * np.pi / nx
+    x = np.arange(nx)
+    chi = np.tile(np.sin(k * x), (ny, 1))
+    gx, gy, _ = O.stencil(chi)
+    # on a Fourier mode the gradient stencil returns sin(k) cos(kx) at every x,
+    # including the periodic wrap
+    np.testing.assert_allclose(gx, np.tile(np.sin(k) * np.cos(k * x), (ny, 1)), atol=1e-14)
+    np.testing.assert_allclose(gy, 0.0, atol=1e-15)
+    # a field linear in y: the ghost row below y = 0 mirrors row 0, so the
+    # one-sided gradient there is half the slope
+    chi = np.tile(np.arange(ny, dtype=float)[:, None], (1, nx))
+    _, gy, _ = O.stencil(chi)
+    np.testing.assert_allclose(gy[0], 0.5, atol=1e-15)
+    np.testing.assert_allclose(gy[ny - 1], 0.5, atol=1e-15)
+    np.testing.assert_allclose(gy[1:-1], 1.0, atol=1e-14)
+
+
+# ---- P6: Onsager function -------------------------------------------------------
+
+def test_p6_onsager_full_form_matches_bessel_i1():
+    for b in np.logspace(-6, 1.3, 60):
+        ref = special.i1(4 * b) / (2 * b)
+        assert abs(O.onsager(b, 0) - ref) <= 1e-14 * ref, b
+    assert O.onsager(0.0, 0) == 1.0
+    for b in (1e-4, 1e-3):
+        assert abs(O.onsager(b, 0) - (1 + 2 * b * b + 4 / 3 * b**4)) < 1e-15
+    # the linear form of Eq. 6 is the first two series terms
+    for b in (0.0, 0.3, 1.7):
+        assert O.onsager(b, 1) == 1 + 2 * b * b
+
+
+# ---- P7: implicit reaction (Eq. 41-43) --------------------------------------
+
+def test_p7_reaction_satisfies_eq41_with_eq5():
+    rng = np.random.default_rng(7)
+    cases = [(rng.uniform(0, 3), rng.uniform(0, 3), rng.uniform(0.1, 5),
+              rng.uniform(0.1, 5), rng.uniform(1, 3)) for _ in range(200)]
+    cases += [(10.0, 0.0, 1.0, 1.0, 1.0), (0.0, 10.0, 1.0, 2.0, 1.5)]  # both branches
+    for sp, sn, kd, kr, F in cases:
+        cp, cm, R = O.reaction(sp, sn, kd, kr, F)
+        assert cp >= 0.0 and cm >= 0.0
+        # Eq. 41 with R = k_d F - k_r c+ c- (Eq. 5): the system the quadratic solves
+        assert abs(R - (kd * F - kr * cp * cm)) <= 1e-14 * max(1.0, kd * F)
+        assert abs(cp - (sp + 0.5 * R)) <= 1e-14 * max(1.0, cp)
+        assert abs(cm - (sn + 0.5 * R)) <= 1e-14 * max(1.0, cm)
+    # uniform n_eq = sqrt(k_d F / k_r) is a fixed point (R = 0)
+    kd, kr, F = 1.3, 0.7, 1.9
+    neq = np.sqrt(kd * F / kr)
+    cp, cm, R = O.reaction(neq, neq, kd, kr, F)
+    assert abs(cp - neq) < 1e-15 and abs(cm - neq) < 1e-15 and abs(R) < 1e-14
+
+
+# ---- mapping of Sec. 3 pinned by the printed numbers ------------------------
+
+def _golden():
+    rows = []
+    for line in open(GOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        parts = line.split()
+        kv = dict(p.split("=") for p in parts[1:] if "=" in p)
+        val = float([p for p in parts[1:] if "=" not in p][0])
+        rows.append((parts[0], {k: float(v) for k, v in kv.items()}, val))
+    return rows
+
+
+def test_mapping_reproduces_printed_W0_and_beta():
+    ny = 128
+    for name, cond, val in _golden():
+        d = cond["d_mm"]
+        P = O.params_from_physical(128, ny, d, cond.get("dpsi_kV", 1.0), 0.5, 5.0)
+        dpsi = cond.get("dpsi_kV", 1.0)
+        if name == "W0":
+            W0 = P["Kq"] * ny * ny / dpsi
+            assert abs(W0 / val - 1) < 2e-5, (d, W0, val)
+        else:
+            beta = np.sqrt(P["onsager_cb"] ** 2 * P["Kq"] * ny)  # beta^2 = O W0
+            assert abs(beta / val - 1) < 2e-4, (d, beta, val)
+
+
+# ---- P8: conservation of sum phi --------------------------------------------
+
+def test_p8_sum_phi_conserved_with_electrodes_and_walls():
+    o = O.Oracle(32, 32, dict(xc=15.5, yc=15.5, R=8.0, Kq=5.6893 / 32**2,
+                              sweeps_max=30, init_sweeps_max=20000))
+    s0 = o.sum_phi()
+    o.step(120)
+    assert abs(o.sum_phi() - s0) <= 1e-13 * s0
+    f = o.fields()
+    # charge layers of the right sign: anions at the anode (bottom), cations
+    # at the cathode (top)
+    assert f["q"][0].mean() < -0.05 and f["q"][-1].mean() > 0.05
+
+
+# ---- P9, P10: potential (Eq. 44-50) --------------------------------------------
+
+def test_p9_linear_potential_between_electrodes():
+    ny = 32
+    o = O.Oracle(4, ny, dict(QUIET, freeze_E=0, psi_anode=1.0, psi_cathode=0.0,
+                             init_psi_zero=1, init_sweeps_fixed=-1,
+                             init_sweeps_max=400000, sweep_tol=1e-13))
+    f = o.fields()
+    j = np.arange(ny)
+    ref = 1.0 - (j + 0.5) / ny
+    np.testing.assert_allclose(f["psi"], np.tile(ref[:, None], (1, 4)), atol=1e-9)
+    np.testing.assert_allclose(f["Ey"], 1.0 / ny, atol=1e-9)
+    np.testing.assert_allclose(f["Ex"], 0.0, atol=1e-12)
+
+
+def _parabola_error(ny, kq):
+    o = O.Oracle(4, ny, dict(QUIET, freeze_E=0, Kq=kq, sweeps_min=1,
+                             sweeps_max=4000000, sweep_tol=1e-14))
+    s = o.state()
+    s[:, :, 18:23] = W5          # cations with sum p = 1, no anions: q = 1
+    o.set_state(s)
+    o.step(1)
+    f = o.fields()
+    y = np.arange(ny)
+    ref = 0.5 * kq * (y + 0.5) * (ny - 0.5 - y)
+    Eref = kq * (y - (ny - 1) / 2)
+    return (np.max(np.abs(f["psi"][:, 0] - ref)) / ref.max(),
+            np.max(np.abs(f["Ey"][:, 0] - Eref)) / Eref.max())
+
+
+def test_p9_uniform_charge_gives_the_poisson_parabola():
+    # lap psi = -Kq q (Eq. 7 with eps = 1) between grounded half-way electrodes:
+    # psi = Kq q (y + 1/2)(ny - 1/2 - y) / 2 and E = -psi'.  The source of
+    # Eq. 44 carries the 1/(1 - w0) that makes its steady state this equation
+    # (without it the parabola comes out 2/3 as high); the scheme is second
+    # order, so the relative error must fall 4x per doubling of ny.
+    e32, E32 = _parabola_error(32, 1e-3)
+    e64, E64 = _parabola_error(64, 2.5e-4)
+    assert e32 < 5e-3 and E32 < 1e-6, (e32, E32)
+    assert e64 < e32 / 3.5, (e32, e64)
+
+
+def _two_layer_error(ny, W, R, eps_r):
+    yc = (ny - 1) / 2
+    o = O.Oracle(4, ny, dict(QUIET, freeze_E=0, init_shape=1, W=W, R=R, yc=yc,
+                             eps_r=eps_r, psi_anode=1.0, psi_cathode=0.0,
+                             init_sweeps_fixed=-1, init_sweeps_max=2000000,
+                             sweep_tol=1e-13))
+    psi = o.fields()["psi"][:, 0]
+    eps = lambda y: 1 + (eps_r - 1) * 0.5 * (1 + np.tanh(2 * (R - abs(y - yc)) / W))
+    yy = np.linspace(-0.5, ny - 0.5, 200 * ny + 1)
+    inv = 1.0 / eps(yy)
+    cum = np.concatenate([[0.0], np.cumsum(0.5 * (inv[1:] + inv[:-1]) * np.diff(yy))])
+    ref = 1.0 - np.interp(np.arange(ny), yy, cum) / cum[-1]
+    # bulk field ratio of the series capacitor: E_outside / E_inside = eps_r
+    f = o.fields()
+    Ey = f["Ey"][:, 0]
+    return np.max(np.abs(psi - ref)), Ey[2] / Ey[int(yc)]
+
+
+@pytest.mark.slow
+def test_p10_two_layer_potential_converges_second_order():
+    e1, ratio = _two_layer_error(64, 4.0, 16.0, 4.0)
+    e2, _ = _two_layer_error(128, 8.0, 32.0, 4.0)
+    assert e1 < 3e-3, e1
+    assert e2 < e1 / 3.0, (e1, e2)
+    assert abs(ratio - 4.0) < 0.1, ratio
+
+
+# ---- P11: flat interface relaxes to the tanh profile (Eq. 1-2) -----------------
+
+def _flat_interface_error(ny, W, R, steps):
+    yc = (ny - 1) / 2
+    o = O.Oracle(4, ny, dict(QUIET, init_shape=1, W=W, W_init=2 * W, R=R, yc=yc,
+                             M_phi=0.05))
+    o.step(steps)
+    phi = o.fields()["phi"][:, 0]
+    y = np.arange(ny)
+    ref = 0.5 * (1 + np.tanh(2 * (R - np.abs(y - yc)) / W))
+    return np.max(np.abs(phi - ref))
+
+
+@pytest.mark.slow
+def test_p11_flat_interface_relaxes_to_tanh():
+    e1 = _flat_interface_error(48, 4.0, 12.0, 3000)
+    e2 = _flat_interface_error(96, 8.0, 24.0, 9000)
+    assert e1 < 1e-2, e1
+    assert e2 < e1 / 3.0, (e1, e2)
+
+
+# ---- P12: Laplace law (Eq. 12-13, 56-57) ---------------------------------------
+
+@pytest.mark.slow
+def test_p12_static_droplet_obeys_laplace_law():
+    n, sigma = 48, 0.01
+    invR, dp = [], []
+    for R in (8.0, 10.0, 12.0, 14.0):
+        o = O.Oracle(n, n, dict(QUIET, R=R, xc=(n - 1) / 2, yc=(n - 1) / 2, sigma=sigma))
+        o.step(1500)
+        f = o.fields()
+        c = n // 2
+        dp.append(f["p"][c - 1:c + 1, c - 1:c + 1].mean() - f["p"][n // 2, 1:3].mean())
+        invR.append(1.0 / R)
+        umax = np.max(np.hypot(f["ux"], f["uy"]))
+        assert umax < 1e-4, umax
+    slope = np.polyfit(invR, dp, 1)[0]
+    assert abs(slope / sigma - 1) < 0.05, slope
+
+
+# ---- P13: dissociation-recombination equilibrium (Eq. 5) ---------------------
+
+@pytest.mark.parametrize("scale", [0.0, 2.0])
+def test_p13_uniform_field_reaches_n_eq(scale):
+    E0, cb = 0.3, 1.0
+    o = O.Oracle(8, 8, dict(QUIET, onsager_form=0, k_d=1.0, k_r=1.0, onsager_cb=cb,
+                            ion_bc=2, E_frozen_x=E0, c_init_scale=scale))
+    o.step(200)
+    f = o.fields()
+    neq = np.sqrt(special.i1(4 * cb * np.sqrt(E0)) / (2 * cb * np.sqrt(E0)))
+    np.testing.assert_allclose(f["cp"], neq, rtol=1e-12)
+    np.testing.assert_allclose(f["cm"], neq, rtol=1e-12)
+
+
+# ---- ion drift (Eq. 34-35, 40): sign and speed -------------------------------
+
+def test_ion_drift_moves_the_centroid_at_mobility_times_field():
+    nx, ny, E0, mu, m = 64, 4, 0.02, 1.0, 0.5
+    o = O.Oracle(nx, ny, dict(QUIET, ion_bc=2, E_frozen_x=E0, mu_v=mu, m=m,
+                              einstein_D=0))
+    s = o.state()
+    x = np.arange(nx)
+    bump = np.exp(-0.5 * ((x - 24.0) / 3.0) ** 2)
+    s[:, :, 18:23] += W5[None, None, :] * bump[None, :, None]   # cations
+    s[:, :, 23:28] += W5[None, None, :] * bump[None, :, None]   # anions
+    o.set_state(s)
+    N = 200
+    o.step(N)
+    st = o.state()
+    cp = st[:, :, 18:23].sum(-1).sum(0)
+    cm = st[:, :, 23:28].sum(-1).sum(0)
+    x0 = (bump * x).sum() / bump.sum()
+    s_p = 1 / (0.5 + 0.01 / CS2)           # first-moment rate, Eq. 37
+    lag = (1 - s_p) * (1 - (1 - s_p) ** N) / s_p
+    assert abs((cp * x).sum() / cp.sum() - x0 - mu * E0 * (N - lag)) < 1e-8
+    assert abs((cm * x).sum() / cm.sum() - x0 + m * mu * E0 * (N - lag)) < 1e-8
+
+
+# ---- viscosity (Eq. 51, 55 and the viscous rates) ------------------------------
+
+def test_shear_wave_decays_at_the_viscosity_of_tau_f():
+    ny, tau = 32, 0.8
+    o = O.Oracle(4, ny, dict(QUIET, tau_f=tau))
+    s = o.state()
+    y = np.arange(ny)
+    k = np.pi / ny
+    mode = np.cos(k * (y + 0.5 - ny / 2))     # zero at the half-way walls
+    for j in range(ny):
+        fe = O.feq(0.0, 1.0, 1e-3 * mode[j], 0.0)
+        s[j, :, 0:9] = fe
+    o.set_state(s)
+    amp = []
+    for n in (100, 400):
+        o.step(n - o.t)
+        ux = o.fields()["ux"][:, 0]
+        amp.append(ux @ mode / (mode @ mode))
+    nu = CS2 * (tau - 0.5)
+    rate = -np.log(amp[1] / amp[0]) / 300
+    assert abs(rate / (nu * k * k) - 1) < 0.01, (rate, nu * k * k)
+
+
+# ---- polarization force (Eq. 14) on a flat dielectric layer ---------------------
+
+@pytest.mark.slow
+def test_polarization_force_sets_the_pressure_jump():
+    # sign and factor 1/2 of the polarization force: at rest, dp/dy balances
+    # -1/2 E^2 deps/dy with E = D / eps, so the pressure inside a dielectric
+    # layer differs from outside by D^2 (1/eps_r - 1) / 2 (no surface tension;
+    # tau_f = 2 damps the acoustic sloshing of the 1D column)
+    ny, eps_r = 64, 4.0
+    yc = (ny - 1) / 2
+    o = O.Oracle(4, ny, dict(QUIET, freeze_E=0, init_shape=1, R=16.0, W=4.0, yc=yc,
+                             sigma=0.0, tau_f=2.0, eps_r=eps_r, psi_anode=1.0,
+                             init_sweeps_fixed=-1, init_sweeps_max=4000000,
+                             sweep_tol=1e-13))
+    o.step(4000)
+    f = o.fields()
+    psi = f["psi"][:, 0]
+    D = (psi[2] - psi[6]) / 4.0       # displacement from the outer potential drop
+    p = f["p"][:, 0]
+    jump = p[int(yc)] - 0.5 * (p[4] + p[ny - 5])
+    ref = 0.5 * D * D * (1 / eps_r - 1)
+    assert abs(jump / ref - 1) < 0.03, (jump, ref)
+    assert np.max(np.abs(f["uy"])) < 1e-6
+
+
+# ---- Coulomb force (Eq. 14) in a 1D column with heterocharge layers ----------
+
+@pytest.mark.slow
+def test_coulomb_force_balances_the_pressure_gradient():
+    # no droplet, uniform eps: once the ions have formed their layers at the
+    # electrodes the column is at rest and dp/dy = Kq q E_y (Eq. 11, 14)
+    ny = 32
+    kq = 4 * 5.6893 / ny**2
+    o = O.Oracle(4, ny, dict(R=-100.0, Kq=kq, eps_r=1.0, tau_f=2.0, sweeps_min=1,
+                             sweeps_max=100, sweep_tol=1e-11, init_sweeps_max=400000))
+    o.step(1000)
+    f = o.fields()
+    p = f["p"][:, 0]
+    F = kq * f["q"][:, 0] * f["Ey"][:, 0]
+    cum = np.concatenate([[0.0], np.cumsum(0.5 * (F[1:] + F[:-1]))])
+    assert np.max(np.abs(cum)) > 1e-4          # the layers carry a real force
+    err = np.max(np.abs((p - p[0]) - cum)) / np.max(np.abs(cum))
+    assert err < 2e-3, err
+
+
+# ---- deformation factor (Eq. 63) ------------------------------------------------
+
+def test_deformation_factor_of_ellipses():
+    n = 96
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    for a, b in ((20.0, 20.0), (24.0, 16.0), (15.0, 22.0)):   # a along y, b along x
+        r = np.sqrt(((x - 47.5) / b) ** 2 + ((y - 47.5) / a) ** 2)
+        phi = 0.5 * (1 + np.tanh(2 * (1 - r) * min(a, b) / 4.0))
+        assert abs(O.deformation(phi) - (a - b) / (a + b)) < 2e-3
