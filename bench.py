@@ -1,0 +1,277 @@
+"""Throughput benchmark of the EHD lattice Boltzmann solver on GB300.
+
+One step = one time step of all five lattice Boltzmann equations (with its 20
+potential sweeps) on the 2048 x 2048 FP32 droplet case.  The state (~1.35 GB)
+is larger than L2, so no flush is needed between steps.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the method has no cross-lattice exchange here, so N > 1 runs N
+independent replicas (one lattice per rank, weak scaling, no collective on
+the data path); value is the sum over ranks of node updates / the slowest
+rank's time.  ``--impl reference`` times the FP64 CPU oracle on a 256 x 256
+copy of the case (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS over 5 LB fields, % HBM roofline; served cases/h vs plain, p99 latency"
+N = 2048
+SWEEPS = 20
+SAMPLE_N = 256          # oracle sample: a 256^2 copy of the case (R = 32)
+SWEEP_BYTES_PER_NODE = 40   # FP32: 4 populations read + 4 written, phi and q read
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.lines: list[str] = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def oracle_rate(n: int, steps: int, budget_s: float):
+    """FP64 oracle on an n x n copy of the case: (MLUPS, steps run, seconds, threads)."""
+    import oracle
+    from paper_2501_04920_gb300 import workloads
+    o = oracle.Oracle(n, n, workloads.droplet(n))
+    done, t0 = 0, time.perf_counter()
+    while done < steps:
+        o.step(1)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return n * n * done / dt / 1e6, done, dt, threads
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    # warm-up steps, then the timed steps, each one oracle time step on the sample
+    import oracle
+    from paper_2501_04920_gb300 import workloads
+    n = SAMPLE_N
+    o = oracle.Oracle(n, n, workloads.droplet(n))
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    value = n * n * args.steps / dt / 1e6
+    sample = (f"FP64 CPU oracle, {n}x{n} copy of the 2048^2 droplet case (R = {n // 8}, "
+              f"{SWEEPS} sweeps/step), {args.steps} timed steps after {args.warmup} warm-up")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"droplet {n}x{n} (sample of the 2048x2048 case)", "nx": n, "ny": n,
+                   "sweeps_per_step": SWEEPS},
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2501_04920_gb300 import ehdlb, workloads
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    prm = workloads.droplet(N)
+    lat = ehdlb.Lattice(N, N, prm, precision=ehdlb.FP32, cuda_stream=stream.cuda_stream)
+    nn = N * N
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up
+    lat.step(args.warmup)
+    ehdlb.ehdlb_set_timing(lat.ctx, True)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        status, st = lat.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = nn * args.steps * world / (ms / 1e3) / 1e6
+    sweep_launch_ms = st.ms_sweeps / (args.steps * SWEEPS)
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    achieved = SWEEP_BYTES_PER_NODE * nn / (sweep_launch_ms / 1e3) / 1e9
+    launches = int(st.launches)
+    ehdlb.ehdlb_set_timing(lat.ctx, False)
+
+    # end to end through the public API with host buffers: every step one
+    # ehdlb_step call (its control words go host -> device, its counters
+    # device -> host) and the phi field of the step read into pinned memory
+    host_phi = torch.empty(nn, dtype=torch.float64).pin_memory()
+    phi_np = host_phi.numpy()
+    e2e_steps = max(10, args.steps // 3)
+    torch.cuda.synchronize(dev)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lat.step(1)
+        ehdlb.ehdlb_get_fields(lat.ctx, 1 << 0, phi_np)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = nn * e2e_steps * world / e2e_s / 1e6
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        rate, done, dt, threads = oracle_rate(SAMPLE_N, 1000, 12.0)
+        cpu = {"value": round(rate, 4), "unit": "MLUPS", "cores": threads, "kind": "oracle",
+               "sample": f"FP64 CPU oracle, {SAMPLE_N}x{SAMPLE_N} copy of the case "
+                         f"(R = {SAMPLE_N // 8}, {SWEEPS} sweeps/step), {done} steps in {dt:.1f} s"}
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "droplet 2048x2048 FP32, 20 potential sweeps per step "
+                               "(R = 256, eps_r = 4, mu_r = 2, dpsi = 2)",
+                   "nx": N, "ny": N, "sweeps_per_step": SWEEPS,
+                   "l2": "inputs larger than L2 (state ~1.35 GB), no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "kernel": "k_sweep (potential sweep)",
+                     "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "peak_source": peak_kind,
+                     "traffic": None, "bytes_per_launch": SWEEP_BYTES_PER_NODE * nn,
+                     "launch_ms": sweep_launch_ms},
+        "gpu_launches": launches,
+        "kernel_ms": {"prep": st.ms_prep / args.steps, "sweeps": st.ms_sweeps / args.steps,
+                      "main": st.ms_main / args.steps},
+        "clocks": clk.summary(),
+        "status": ehdlb.STATUS_NAMES.get(status, status),
+        "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS", "steps": e2e_steps,
+                "h2d_bytes_per_step": 16, "d2h_bytes_per_step": 8 * nn + 104},
+    }
+    if cpu:
+        out["cpu_baseline"] = cpu
+    print(json.dumps(out), flush=True)
+    lat.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

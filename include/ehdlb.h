@@ -1,0 +1,212 @@
+/*
+ * ehdlb.h -- C ABI of the GB300 (sm_103a) solver for the phase-field lattice
+ * Boltzmann method for two-phase electrohydrodynamic flow driven by the
+ * Onsager-Wien effect (Zheng, Wang, Xiong, Huang, Luo, arXiv 2501.04920).
+ *
+ * One time step advances five coupled lattice Boltzmann equations on a 2D
+ * lattice (Sec. 4): the conservative Allen-Cahn equation (D2Q9, Eq. 27-33),
+ * the cation and anion Nernst-Planck equations with field-enhanced
+ * dissociation and recombination (D2Q5, Eq. 34-43), the electric potential
+ * in pseudo-time (D2Q5, Eq. 44-50, swept inside every step) and the
+ * incompressible Navier-Stokes equations with surface-tension and electric
+ * forces (D2Q9, Eq. 51-57).  All compute runs in CUDA kernels; there is no
+ * CPU path behind this interface.
+ *
+ * Conventions for every entry point:
+ *  - Lattice units (dx = dt = 1).  Node (x, y), x in [0, nx) periodic,
+ *    y in [0, ny).  The anode (psi_anode) lies half a spacing below row 0,
+ *    the cathode (psi_cathode) half a spacing above row ny - 1 (Eq. 64).
+ *  - Host arrays are row-major [ny][nx] (x fastest), FP64, caller-owned and
+ *    only borrowed for the duration of the call.  The context owns all device
+ *    memory; nothing returned points into it.
+ *  - Every call returns an ehdlb_status; none aborts the process.  On an
+ *    error, ehdlb_last_error() describes it.  A context is used by one host
+ *    thread at a time.
+ */
+#ifndef EHDLB_H
+#define EHDLB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EHDLB_ABI_VERSION 1
+
+typedef struct ehdlb_ctx ehdlb_ctx;
+
+typedef enum ehdlb_status {
+    EHDLB_OK = 0,
+    EHDLB_WNOTCONV = 1,   /* warning: a step hit sweeps_max above sweep_tol */
+    EHDLB_EINVAL = -1,    /* invalid argument or parameter */
+    EHDLB_ENOMEM = -2,    /* device or host allocation failed */
+    EHDLB_ECUDA = -3,     /* a CUDA call failed */
+    EHDLB_EUNSTABLE = -4, /* NaN or Inf in the fields */
+    EHDLB_ESTATE = -5     /* call out of order (e.g. step before set_params) */
+} ehdlb_status;
+
+typedef enum ehdlb_precision {
+    EHDLB_FP64 = 0,       /* populations and arithmetic in double */
+    EHDLB_FP32 = 1        /* populations and arithmetic in float; residual and
+                             global sums in double */
+} ehdlb_precision;
+
+/* Snapshot fields (bit i of a field mask selects field i). */
+typedef enum ehdlb_field {
+    EHDLB_PHI = 0,  /* order parameter, Eq. 33 */
+    EHDLB_UX,       /* velocity, Eq. 56 */
+    EHDLB_UY,
+    EHDLB_P,        /* hydrodynamic pressure, Eq. 57 */
+    EHDLB_PSI,      /* electric potential, Eq. 49 */
+    EHDLB_EX,       /* electric field, Eq. 50 */
+    EHDLB_EY,
+    EHDLB_CP,       /* cation concentration, Eq. 42 */
+    EHDLB_CM,       /* anion concentration, Eq. 42 */
+    EHDLB_Q,        /* net charge c+ - c- */
+    EHDLB_NFIELDS
+} ehdlb_field;
+
+/* Problem statement in lattice units.  Fill with ehdlb_params_default() or
+ * ehdlb_params_from_physical(), then edit; size must equal
+ * sizeof(ehdlb_params). */
+typedef struct ehdlb_params {
+    size_t size;
+    /* incompressible NS (Eq. 51-57, 60-61) */
+    double tau_f;        /* relaxation time of the outer phase (phi = 0), > 0.5 */
+    double rho_ratio;    /* rho_l / rho_v, rho_v = 1 */
+    double eta_ratio;    /* eta_l / eta_v */
+    /* interface (Eq. 1-2, 12-13, 27-33) */
+    double sigma;        /* surface tension */
+    double W;            /* interface thickness, > 0 */
+    double W_init;       /* thickness of the initial profile (<= 0: W) */
+    double M_phi;        /* Allen-Cahn mobility, > 0 */
+    /* initial droplet: phi = (1 + tanh(2 (R - r) / W_init)) / 2 */
+    double xc, yc, R;    /* centre and radius; for the slab, half-width */
+    int init_shape;      /* 0 disc, 1 horizontal slab |y - yc| < R */
+    /* ions (Eq. 3-6, 34-43) */
+    double D;            /* ion diffusivity in the outer phase, > 0 */
+    double mu_v;         /* cation mobility in the outer phase, > 0 */
+    double mu_r;         /* mobility ratio mu_l / mu_v */
+    double m;            /* anion / cation mobility ratio */
+    double k_d;          /* dissociation rate delta c0^2 (Eq. 5), >= 0 */
+    double k_r;          /* recombination rate delta (Eq. 5), >= 0 */
+    double onsager_cb;   /* b = onsager_cb * sqrt(|E|) */
+    int onsager_form;    /* 0: F = I1(4b) / (2b); 1: F = 1 + 2 b^2 (Eq. 6);
+                            2: no reaction, R = 0 (Sec. 5.2) */
+    int ion_bc;          /* 0: Eq. 64 (repelled species c = 0, attracted
+                            species zero gradient); 1: c = 0 at both
+                            electrodes; 2: zero flux */
+    int einstein_D;      /* 1: D_pm = D mu_pm / mu_v (Sec. 2.2) */
+    int ion_L_term;      /* 1: keep the source L_i of Eq. 39 */
+    double c_init_scale; /* initial c_pm = c_init_scale * n_eq(E) */
+    double c0;           /* initial c_pm when k_r = 0 or onsager_form = 2 */
+    /* potential (Eq. 7-9, 44-50) */
+    double eps_r;        /* permittivity ratio eps_l / eps_v, > 0 */
+    double Kq;           /* charge coupling: lap psi = -Kq (c+ - c-) / eps */
+    double vartheta;     /* artificial diffusion (Eq. 47), > 0 */
+    int psi_src_literal; /* 1: Eq. 44 source as printed; 0 (default): divided
+                            by (1 - w0) so that the steady state is Eq. 7 */
+    double psi_anode, psi_cathode;
+    int sweeps_min, sweeps_max;  /* pseudo-time sweeps per step, min <= max */
+    double sweep_tol;            /* stop on ||psi^k - psi^(k-1)|| / ||psi^k|| */
+    int init_sweeps_max;         /* cap of the initial potential solve */
+    int init_sweeps_fixed;       /* >= 0: exactly this many initial sweeps */
+    int init_psi_zero;           /* 1: start the potential from psi = 0 */
+    int freeze_E;                /* 1: no potential sweeps, E = E_frozen */
+    double E_frozen_x, E_frozen_y;
+    /* collision */
+    double s_free;       /* the free MRT rates, in (0, 2); 1.0 in Sec. 6 */
+    int bgk;             /* 1: all rates equal the hydrodynamic one */
+} ehdlb_params;
+
+/* Counters of one ehdlb_step() call. */
+typedef struct ehdlb_stats {
+    long long steps;          /* steps advanced by the call */
+    long long t;              /* time steps since set_params */
+    long long sweeps_total;   /* potential sweeps in the call */
+    int sweeps_max;           /* most sweeps in one step */
+    int not_converged;        /* steps that hit sweeps_max above sweep_tol */
+    double last_residual;     /* residual of the last sweep (NaN: none) */
+    double sum_phi, sum_q;    /* FP64 sums of phi and q of the last snapshot */
+    double seconds;           /* wall time of the call */
+    double mlups;             /* nx ny steps / seconds / 1e6 */
+    double ms_prep, ms_sweeps, ms_main;  /* device time per kernel class when
+                                            timing is on (ehdlb_set_timing) */
+    long long launches;       /* kernels launched by the call */
+} ehdlb_stats;
+
+/* ABI version of the loaded library (EHDLB_ABI_VERSION). */
+int ehdlb_version(void);
+
+/* Lattice values of the plain 64x64 droplet case: tau_f 0.8, sigma 0.01,
+ * W 4, M_phi 0.02, R 12, D 0.01, k_d = k_r = 1, eps_r 2, vartheta 0.3 (Sec. 4.2),
+ * Kq = 5.6893 / 64^2, sweeps 1..200 to 1e-8.  Returns EHDLB_EINVAL on NULL. */
+int ehdlb_params_default(ehdlb_params *p);
+
+/* Physical problem of Sec. 6 -> lattice values (Sec. 3): reference length
+ * d_mm (electrode gap), applied voltage dpsi_kV, eps_r and mu_r.
+ *   W0 = 1.42233 d^2 / dpsi (Eq. 23, value printed with Fig. 10),
+ *   beta = 0.5643 (d / 2)^(1/2) (Eq. 24, values printed in Sec. 6),
+ *   O = beta^2 / W0, Kq = W0 dpsi / ny^2 (Eq. 20), onsager_cb = (O ny / dpsi)^(1/2)
+ *   (b^2 = O |E*|, Eq. 17), psi_anode = dpsi, R = nx / 5; other values as
+ * ehdlb_params_default, 20 sweeps per step, no initial solve. */
+int ehdlb_params_from_physical(ehdlb_params *p, int nx, int ny, double d_mm,
+                               double dpsi_kV, double eps_r, double mu_r);
+
+/* Allocate a solver for an nx x ny lattice (nx, ny >= 4) in the given
+ * precision.  cuda_stream: a cudaStream_t to launch on, or NULL for a stream
+ * the context creates.  The device is the current one.  *out receives the
+ * context; EHDLB_ENOMEM if device memory runs out. */
+int ehdlb_create(ehdlb_ctx **out, int nx, int ny, int precision,
+                 void *cuda_stream);
+
+/* Validate p and (re)initialise the lattice at t = 0 (Sec. 6 set-up): the
+ * droplet profile, u = p = 0, the linear potential with its initial solve
+ * (q = 0), ions at n_eq of the resulting field, populations at equilibrium.
+ * EHDLB_EINVAL on a relaxation time <= 0.5 or any other invalid value. */
+int ehdlb_set_params(ehdlb_ctx *c, const ehdlb_params *p);
+
+/* Replay given sweep counts: step t (counted from the last set_params)
+ * takes exactly counts[t] sweeps for t < n; later steps follow the stop rule.
+ * n = 0 clears the schedule.  Used to compare with a run whose sweep counts
+ * were decided elsewhere. */
+int ehdlb_set_sweep_schedule(ehdlb_ctx *c, const int *counts, int n);
+
+/* Advance nsteps time steps.  Blocks until the device has finished.  out
+ * (nullable) receives the counters.  Returns EHDLB_WNOTCONV if a step hit
+ * sweeps_max above sweep_tol, EHDLB_EUNSTABLE on NaN/Inf. */
+int ehdlb_step(ehdlb_ctx *c, int nsteps, ehdlb_stats *out);
+
+/* Copy snapshot fields to the host: the fields of the last step, at the
+ * time t of that step (before its collision), with psi and E after its
+ * sweeps; before any step, the initial fields.  mask selects fields (bit
+ * EHDLB_PHI ...); they are written in increasing field order, each
+ * [ny][nx], into dst of dst_len doubles (>= popcount(mask) nx ny). */
+int ehdlb_get_fields(ehdlb_ctx *c, unsigned mask, double *dst,
+                     size_t dst_len);
+
+/* Sweep counts of the steps of the last ehdlb_step call, n <= its nsteps. */
+int ehdlb_get_sweep_counts(ehdlb_ctx *c, int *dst, int n);
+
+/* Raw state as 35 doubles per node, node-major [ny][nx][35]: f0..f8, h0..h8,
+ * p0..p4, n0..n4, g0..g4 (Eq. 25-26 order), (phi u)(t-1) x and y.  The
+ * library does not store f0 and g0 (no other quantity depends on them):
+ * get_state writes 0 there and set_state ignores them.  len in doubles. */
+size_t ehdlb_state_len(const ehdlb_ctx *c);
+int ehdlb_get_state(ehdlb_ctx *c, double *dst, size_t len);
+int ehdlb_set_state(ehdlb_ctx *c, const double *src, size_t len);
+
+/* Record device time per kernel class in ehdlb_stats (1) or not (0). */
+int ehdlb_set_timing(ehdlb_ctx *c, int on);
+
+/* Free all device memory of the context (NULL is a no-op). */
+void ehdlb_destroy(ehdlb_ctx *c);
+
+/* Text of the last error on c (empty if none); valid until the next call. */
+const char *ehdlb_last_error(const ehdlb_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,233 @@
+// ehdlb_api.cu -- the extern "C" boundary declared in include/ehdlb.h:
+// argument checks, parameter validation, error codes and messages.  All
+// compute is delegated to the CUDA solver; there is no host fallback.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "ehdlb.h"
+#include "ehdlb_solver_base.h"
+
+struct ehdlb_ctx {
+    ehdlb::SolverBase *solver = nullptr;
+    int nx = 0, ny = 0, precision = 0;
+    bool has_params = false;
+    std::string err;
+};
+
+namespace {
+
+int fail(ehdlb_ctx *c, int status, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return status;
+}
+
+bool finite_all(const ehdlb_params *p)
+{
+    const double v[] = {p->tau_f, p->rho_ratio, p->eta_ratio, p->sigma, p->W, p->W_init, p->M_phi,
+                        p->xc, p->yc, p->R, p->D, p->mu_v, p->mu_r, p->m, p->k_d, p->k_r,
+                        p->onsager_cb, p->c_init_scale, p->c0, p->eps_r, p->Kq, p->vartheta,
+                        p->psi_anode, p->psi_cathode, p->sweep_tol, p->E_frozen_x, p->E_frozen_y,
+                        p->s_free};
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+// Returns an empty string if p is acceptable for an nx x ny lattice.
+std::string validate(const ehdlb_params *p)
+{
+    if (p->size != sizeof(ehdlb_params)) return "params.size != sizeof(ehdlb_params)";
+    if (!finite_all(p)) return "a parameter is NaN or Inf";
+    if (!(p->tau_f > 0.5)) return "tau_f must be > 0.5";
+    if (!(p->rho_ratio > 0.0) || !(p->eta_ratio > 0.0)) return "rho_ratio and eta_ratio must be > 0";
+    // the local NS relaxation time (Eq. 55 with Eq. 61) must stay > 0.5 in both phases
+    if (!(p->eta_ratio / p->rho_ratio * (p->tau_f - 0.5) > 0.0)) return "tau_f of the inner phase <= 0.5";
+    if (!(p->W > 0.0)) return "W must be > 0";
+    if (!(p->M_phi > 0.0)) return "M_phi must be > 0 (tau_h > 0.5)";
+    if (!(p->sigma >= 0.0)) return "sigma must be >= 0";
+    if (!(p->D > 0.0)) return "D must be > 0 (ion tau > 0.5)";
+    if (!(p->mu_v > 0.0) || !(p->mu_r > 0.0) || !(p->m > 0.0)) return "mobilities must be > 0";
+    if (!(p->k_d >= 0.0) || !(p->k_r >= 0.0)) return "k_d and k_r must be >= 0";
+    if (!(p->onsager_cb >= 0.0)) return "onsager_cb must be >= 0";
+    if (p->onsager_form < 0 || p->onsager_form > 2) return "onsager_form must be 0, 1 or 2";
+    if (p->ion_bc < 0 || p->ion_bc > 2) return "ion_bc must be 0, 1 or 2";
+    if (!(p->eps_r > 0.0)) return "eps_r must be > 0";
+    if (!(p->vartheta > 0.0)) return "vartheta must be > 0 (tau_g > 0.5)";
+    if (p->sweeps_min < 0 || p->sweeps_max < p->sweeps_min) return "need 0 <= sweeps_min <= sweeps_max";
+    if (p->sweeps_max > 1000000) return "sweeps_max above 1e6";
+    if (!(p->sweep_tol >= 0.0)) return "sweep_tol must be >= 0";
+    if (p->init_sweeps_max < 0 || p->init_sweeps_max > 100000000) return "init_sweeps_max out of range";
+    if (p->init_sweeps_fixed > 100000000) return "init_sweeps_fixed out of range";
+    if (!(p->s_free > 0.0 && p->s_free < 2.0)) return "s_free must lie in (0, 2)";
+    if (!(p->c_init_scale >= 0.0) || !(p->c0 >= 0.0)) return "initial concentrations must be >= 0";
+    return "";
+}
+
+}  // namespace
+
+extern "C" {
+
+int ehdlb_version(void) { return EHDLB_ABI_VERSION; }
+
+int ehdlb_params_default(ehdlb_params *p)
+{
+    if (!p) return EHDLB_EINVAL;
+    std::memset(p, 0, sizeof *p);
+    p->size = sizeof *p;
+    p->tau_f = 0.8; p->rho_ratio = 1.0; p->eta_ratio = 1.0;
+    p->sigma = 0.01; p->W = 4.0; p->W_init = 0.0; p->M_phi = 0.02;
+    p->xc = 31.5; p->yc = 31.5; p->R = 12.0; p->init_shape = 0;
+    p->D = 0.01; p->mu_v = 1.0; p->mu_r = 1.0; p->m = 1.0;
+    p->k_d = 1.0; p->k_r = 1.0; p->onsager_cb = 1.0;
+    p->onsager_form = 0; p->ion_bc = 0; p->einstein_D = 1; p->ion_L_term = 1;
+    p->c_init_scale = 1.0; p->c0 = 1.0;
+    p->eps_r = 2.0; p->Kq = 5.6893 / (64.0 * 64.0); p->vartheta = 0.3; p->psi_src_literal = 0;
+    p->psi_anode = 1.0; p->psi_cathode = 0.0;
+    p->sweeps_min = 1; p->sweeps_max = 200; p->sweep_tol = 1e-8;
+    p->init_sweeps_max = 100000; p->init_sweeps_fixed = -1; p->init_psi_zero = 0;
+    p->freeze_E = 0; p->E_frozen_x = 0.0; p->E_frozen_y = 0.0;
+    p->s_free = 1.0; p->bgk = 0;
+    return EHDLB_OK;
+}
+
+int ehdlb_params_from_physical(ehdlb_params *p, int nx, int ny, double d_mm, double dpsi_kV,
+                               double eps_r, double mu_r)
+{
+    if (!p || nx < 4 || ny < 4 || !(d_mm > 0.0) || !(dpsi_kV > 0.0) || !(eps_r > 0.0) || !(mu_r > 0.0))
+        return EHDLB_EINVAL;
+    ehdlb_params_default(p);
+    const double W0 = 1.42233 * d_mm * d_mm / dpsi_kV;   // Eq. 23, Fig. 10 caption
+    const double beta = 0.5643 * std::sqrt(d_mm / 2.0);  // Eq. 24, Sec. 6
+    const double O = beta * beta / W0;                   // Eq. 24
+    p->xc = 0.5 * (nx - 1);
+    p->yc = 0.5 * (ny - 1);
+    p->R = nx / 5.0;
+    p->mu_r = mu_r;
+    p->eps_r = eps_r;
+    p->Kq = W0 * dpsi_kV / ((double)ny * ny);            // Eq. 20
+    p->onsager_cb = std::sqrt(O * ny / dpsi_kV);         // b^2 = O |E*| (Eq. 17)
+    p->psi_anode = dpsi_kV;
+    p->psi_cathode = 0.0;
+    p->sweeps_min = 20;
+    p->sweeps_max = 20;
+    p->init_sweeps_max = 0;
+    p->init_sweeps_fixed = 0;
+    return EHDLB_OK;
+}
+
+int ehdlb_create(ehdlb_ctx **out, int nx, int ny, int precision, void *cuda_stream)
+{
+    if (!out) return EHDLB_EINVAL;
+    *out = nullptr;
+    if (nx < 4 || ny < 4) return EHDLB_EINVAL;
+    if ((long long)nx * ny > (1LL << 31)) return EHDLB_EINVAL;
+    if (precision != EHDLB_FP64 && precision != EHDLB_FP32) return EHDLB_EINVAL;
+    ehdlb_ctx *c = new (std::nothrow) ehdlb_ctx;
+    if (!c) return EHDLB_ENOMEM;
+    c->nx = nx;
+    c->ny = ny;
+    c->precision = precision;
+    int status = EHDLB_OK;
+    std::string err;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    c->solver = precision == EHDLB_FP64 ? ehdlb::make_solver_fp64(nx, ny, s, &status, err)
+                                        : ehdlb::make_solver_fp32(nx, ny, s, &status, err);
+    if (!c->solver) {
+        delete c;
+        return status != EHDLB_OK ? status : EHDLB_ENOMEM;
+    }
+    *out = c;
+    return EHDLB_OK;
+}
+
+int ehdlb_set_params(ehdlb_ctx *c, const ehdlb_params *p)
+{
+    if (!c) return EHDLB_EINVAL;
+    if (!p) return fail(c, EHDLB_EINVAL, "params is NULL");
+    const std::string why = validate(p);
+    if (!why.empty()) return fail(c, EHDLB_EINVAL, why);
+    c->has_params = false;
+    const int st = c->solver->set_params(*p, c->err);
+    if (st == EHDLB_OK) c->has_params = true;
+    return st;
+}
+
+int ehdlb_set_sweep_schedule(ehdlb_ctx *c, const int *counts, int n)
+{
+    if (!c) return EHDLB_EINVAL;
+    if (n < 0 || (n > 0 && !counts)) return fail(c, EHDLB_EINVAL, "bad schedule");
+    for (int i = 0; i < n; ++i)
+        if (counts[i] < 0 || counts[i] > 1000000) return fail(c, EHDLB_EINVAL, "schedule entry out of range");
+    c->solver->set_schedule(counts, n);
+    return EHDLB_OK;
+}
+
+int ehdlb_step(ehdlb_ctx *c, int nsteps, ehdlb_stats *out)
+{
+    if (!c) return EHDLB_EINVAL;
+    if (!c->has_params) return fail(c, EHDLB_ESTATE, "ehdlb_set_params must come before ehdlb_step");
+    if (nsteps < 0) return fail(c, EHDLB_EINVAL, "nsteps < 0");
+    if (out) std::memset(out, 0, sizeof *out);
+    if (nsteps == 0) return EHDLB_OK;
+    return c->solver->step(nsteps, out, c->err);
+}
+
+int ehdlb_get_fields(ehdlb_ctx *c, unsigned mask, double *dst, size_t dst_len)
+{
+    if (!c) return EHDLB_EINVAL;
+    if (!c->has_params) return fail(c, EHDLB_ESTATE, "no fields before ehdlb_set_params");
+    if (mask == 0 || (mask >> EHDLB_NFIELDS) != 0) return fail(c, EHDLB_EINVAL, "bad field mask");
+    int nf = 0;
+    for (int f = 0; f < EHDLB_NFIELDS; ++f) nf += (mask >> f) & 1;
+    if (!dst || dst_len < (size_t)nf * c->nx * c->ny) return fail(c, EHDLB_EINVAL, "dst too small");
+    return c->solver->get_fields(mask, dst, c->err);
+}
+
+int ehdlb_get_sweep_counts(ehdlb_ctx *c, int *dst, int n)
+{
+    if (!c) return EHDLB_EINVAL;
+    if (n < 0 || n > c->solver->last_nsteps || (n > 0 && !dst))
+        return fail(c, EHDLB_EINVAL, "n exceeds the steps of the last call");
+    return c->solver->get_counts(dst, n, c->err);
+}
+
+size_t ehdlb_state_len(const ehdlb_ctx *c) { return c ? (size_t)35 * c->nx * c->ny : 0; }
+
+int ehdlb_get_state(ehdlb_ctx *c, double *dst, size_t len)
+{
+    if (!c) return EHDLB_EINVAL;
+    if (!c->has_params) return fail(c, EHDLB_ESTATE, "no state before ehdlb_set_params");
+    if (!dst || len < ehdlb_state_len(c)) return fail(c, EHDLB_EINVAL, "dst too small");
+    return c->solver->get_state(dst, c->err);
+}
+
+int ehdlb_set_state(ehdlb_ctx *c, const double *src, size_t len)
+{
+    if (!c) return EHDLB_EINVAL;
+    if (!c->has_params) return fail(c, EHDLB_ESTATE, "ehdlb_set_params must come before ehdlb_set_state");
+    if (!src || len < ehdlb_state_len(c)) return fail(c, EHDLB_EINVAL, "src too small");
+    return c->solver->set_state(src, c->err);
+}
+
+int ehdlb_set_timing(ehdlb_ctx *c, int on)
+{
+    if (!c) return EHDLB_EINVAL;
+    c->solver->set_timing(on);
+    return EHDLB_OK;
+}
+
+void ehdlb_destroy(ehdlb_ctx *c)
+{
+    if (!c) return;
+    delete c->solver;
+    delete c;
+}
+
+const char *ehdlb_last_error(const ehdlb_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

@@ -1,0 +1,737 @@
+// ehdlb_kernels.cuh -- sm_103a kernels of one time step of the phase-field
+// lattice Boltzmann EHD method (arXiv 2501.04920, Sec. 4).
+//
+// Storage (structure of arrays, one plane of nx*ny values per population):
+//   f  : 8 planes, f1..f8 of Eq. 25.  f0 is never stored: with the zero-mass
+//        equilibrium of Eq. 52 the rest population only feeds the zeroth moment
+//        sum f, and neither u (Eq. 56), p (Eq. 57) nor any other population
+//        depends on that moment (the moment basis of Eq. 28 is a tensor product
+//        of {1, c, c^2}, so only f0 reads m00).
+//   h  : 9 planes (Eq. 27), p, n : 5 planes each (Eq. 34-35, D2Q5).
+//   g  : 4 planes, g1..g4 of Eq. 44, stored as g_i - w_i psi_lin(y) where
+//        psi_lin is the linear profile between the electrodes; g0 is not
+//        stored (psi (Eq. 49) and E (Eq. 50) do not read it, and the diagonal
+//        relaxation of N (Eq. 46) keeps the other moments free of it).  The
+//        shift keeps the small first moment that carries E (Eq. 50) from
+//        drowning in the rounding of psi ~ 1.
+//   f, h, p, n are double-buffered by time step and g by sweep; every
+//   kernel reads its node's own populations and pushes post-collision values
+//   to the neighbours (x periodic, walls half-way below row 0 and above row
+//   ny - 1).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace ehdlb {
+
+// ---- lattice constants (Eq. 25, Eq. 26) -----------------------------------
+
+__host__ __device__ constexpr int cx9(int i)
+{
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy9(int i)
+{
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp9(int i)
+{
+    return i == 0 ? 0 : (i < 5 ? ((i + 1) % 4) + 1 : ((i - 5 + 2) % 4) + 5);
+}
+template <typename T> __host__ __device__ constexpr T w9(int i)
+{
+    return i == 0 ? T(4) / T(9) : (i < 5 ? T(1) / T(9) : T(1) / T(36));
+}
+
+// Device-side problem constants, derived once on the host (kernel argument).
+template <typename T> struct DevP {
+    int nx, ny;
+    long long nn;
+    int onsager_form, ion_bc, einstein_D, ion_L_term, bgk, freeze_E;
+    T tau_g, s_g, s_free_g;        // potential rates
+    T src_norm;                    // vartheta (Eq. 44) times 1 or 1/(1 - w0)
+    T Kq, er1;                     // Kq, eps_r - 1
+    T psi_a, psi_c, G, wG;         // electrodes; G = (psi_c - psi_a) / ny, wG = G / 6
+    T rho1, eta_v, eta1;           // rho_r - 1, eta_v, eta_r - 1
+    T beta, kappa, W, tau_h;       // Eq. 13, Eq. 30
+    T mu_v, mu1, m, D;             // ions
+    T k_d, k_r, cb;
+    T s_free;
+    T Ex_frozen, Ey_frozen;
+};
+
+// Per-run control block in device memory (all kernels of a step read it).
+struct Control {
+    int cur0;          // g buffer that holds the state at the start of the step
+    int done;          // converge mode: no further sweeps this step
+    int K;             // sweeps taken by this step
+    int kmin, kmax;
+    int early;         // stopped on the residual; r_last already set
+    int unstable;      // NaN or Inf seen
+    int notconv;       // steps of the current call that hit kmax above tol
+    int sweeps_max;    // most sweeps in one step of the current call
+    int converge;      // 1: stop rule active
+    long long t;       // steps since set_params
+    long long tloc;    // step index within the current call
+    long long sweeps_total;
+    double tol;
+    double r_last;
+    double r_step;     // residual of the last finished step
+    double sum_phi, sum_q;
+};
+
+template <typename T> struct Pops {
+    T *f;   // 8 planes
+    T *h;   // 9 planes
+    T *p;   // 5 planes
+    T *n;   // 5 planes
+};
+
+// ---- small helpers ------------------------------------------------------------
+
+template <typename T> __device__ __forceinline__ T dsqrt(T v);
+template <> __device__ __forceinline__ double dsqrt<double>(double v) { return sqrt(v); }
+template <> __device__ __forceinline__ float dsqrt<float>(float v) { return sqrtf(v); }
+
+template <typename T> __device__ __forceinline__ T bessel_i1(T v);
+template <> __device__ __forceinline__ double bessel_i1<double>(double v) { return cyl_bessel_i1(v); }
+template <> __device__ __forceinline__ float bessel_i1<float>(float v) { return cyl_bessel_i1f(v); }
+
+// Onsager function F(b) = I1(4b) / (2b) with F(0) = 1 (north of b = 1e-4 the
+// CUDA Bessel function, below it the series 1 + 2 b^2, whose next term
+// (4/3) b^4 is under 2e-16); form 1 is Eq. 6 with b^2 = gamma E.
+template <typename T> __device__ __forceinline__ T onsager(T b, int form)
+{
+    if (form == 1) return T(1) + T(2) * b * b;
+    if (b < T(1e-4)) return T(1) + T(2) * b * b;
+    return bessel_i1<T>(T(4) * b) / (T(2) * b);
+}
+
+__device__ __forceinline__ int wrapx(int x, int nx)
+{
+    return x < 0 ? x + nx : (x >= nx ? x - nx : x);
+}
+
+template <typename T> __device__ __forceinline__ T psi_lin(const DevP<T> &P, int y)
+{
+    return P.psi_a + P.G * (T(y) + T(0.5));
+}
+
+// Deterministic block sum of NV doubles (fixed tree order), written by
+// thread 0 to out[NV * block].  blockDim must be a multiple of 32, <= 1024.
+template <int NV> __device__ __forceinline__ void block_sum_store(double (&v)[NV], double *out)
+{
+    __shared__ double red[32][NV];
+    const int lane = (threadIdx.x + threadIdx.y * blockDim.x) & 31;
+    const int warp = (threadIdx.x + threadIdx.y * blockDim.x) >> 5;
+    const int nwarp = (blockDim.x * blockDim.y) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double s = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) red[warp][k] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = lane < nwarp ? red[lane][k] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) out[(size_t)NV * (blockIdx.x + (size_t)blockIdx.y * gridDim.x) + k] = s;
+        }
+    }
+}
+
+// Sum NV-wide partials of nb blocks in a fixed order (one block of 256).
+template <int NV> __device__ __forceinline__ void sum_partials(const double *part, long long nb,
+                                                              double (&tot)[NV])
+{
+    __shared__ double red[256][NV];
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (long long b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] += part[NV * b + k];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) red[threadIdx.x][k] += red[threadIdx.x + s][k];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = red[0][k];
+}
+
+// ---- D2Q9 natural moments (Eq. 28) by the tensor product of {1, c, c^2} ------
+// Moment order as the rows of Eq. 28: m00 m10 m01 m20 m02 m11 m12 m21 m22
+// (first index: power of cx).
+
+template <typename T> __device__ __forceinline__ void moments9(const T (&v)[9], T (&m)[9])
+{
+    // x-transform of the rows cy = 0, +1, -1
+    T a0 = v[3] + v[0] + v[1], a1 = v[1] - v[3], a2 = v[1] + v[3];
+    T b0 = v[6] + v[2] + v[5], b1 = v[5] - v[6], b2 = v[5] + v[6];
+    T c0 = v[7] + v[4] + v[8], c1 = v[8] - v[7], c2 = v[8] + v[7];
+    m[0] = a0 + b0 + c0;
+    m[1] = a1 + b1 + c1;
+    m[2] = b0 - c0;
+    m[3] = a2 + b2 + c2;
+    m[4] = b0 + c0;
+    m[5] = b1 - c1;
+    m[6] = b1 + c1;
+    m[7] = b2 - c2;
+    m[8] = b2 + c2;
+}
+
+template <typename T> __device__ __forceinline__ void inverse9(const T (&m)[9], T (&v)[9])
+{
+    // y-inverse for each x-moment k: row cy=+1 (b), cy=-1 (c), cy=0 (a)
+    const T h = T(0.5);
+    T b0 = h * (m[2] + m[4]), c0 = h * (m[4] - m[2]), a0 = m[0] - m[4];
+    T b1 = h * (m[5] + m[6]), c1 = h * (m[6] - m[5]), a1 = m[1] - m[6];
+    T b2 = h * (m[7] + m[8]), c2 = h * (m[8] - m[7]), a2 = m[3] - m[8];
+    v[0] = a0 - a2; v[1] = h * (a1 + a2); v[3] = h * (a2 - a1);
+    v[2] = b0 - b2; v[5] = h * (b1 + b2); v[6] = h * (b2 - b1);
+    v[4] = c0 - c2; v[8] = h * (c1 + c2); v[7] = h * (c2 - c1);
+}
+
+// ---- kernels -----------------------------------------------------------------
+
+// phi = sum h (Eq. 33) with mirrored ghost rows, q = sum p - sum n.  With
+// init_ctl the first thread also opens the step in the control block.
+template <typename T>
+__global__ void __launch_bounds__(256) k_prep(const DevP<T> P, const T *__restrict__ h,
+                                              const T *__restrict__ p, const T *__restrict__ n,
+                                              T *__restrict__ phig, T *__restrict__ q,
+                                              Control *ctl, int fixedK, int kmin, int kmax)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        if (fixedK >= 0) {
+            ctl->K = fixedK; ctl->done = 1; ctl->converge = 0;
+        } else {
+            ctl->K = 0; ctl->done = (kmax <= 0); ctl->converge = 1;
+        }
+        ctl->kmin = kmin; ctl->kmax = kmax; ctl->early = 0; ctl->r_last = nan("");
+    }
+    if (x >= P.nx || y >= P.ny) return;
+    const long long nn = P.nn, k = (long long)y * P.nx + x;
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) s += h[i * nn + k];
+    T sp = T(0), sn = T(0);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) { sp += p[i * nn + k]; sn += n[i * nn + k]; }
+    phig[(long long)(y + 1) * P.nx + x] = s;
+    if (y == 0) phig[x] = s;
+    if (y == P.ny - 1) phig[(long long)(P.ny + 1) * P.nx + x] = s;
+    q[k] = sp - sn;
+}
+
+// One pseudo-time sweep of the potential (Eq. 44-50) at every node: E and
+// psi from the node's own populations, the variable-permittivity source
+// (Kq q - grad eps . E) / eps, MRT collision with N (Eq. 46), push to the
+// neighbours with anti-bounce-back to the electrode potentials.
+//   WRITE_PSI: store psi (shifted) for the residual of the next sweep/main.
+//   RESID    : partial sums of (psi - psi_prev)^2 and psi^2 (FP64).
+//   CTRL     : converge mode; skip if the step is done, parity from K.
+template <typename T, bool WRITE_PSI, bool RESID, bool CTRL>
+__global__ void __launch_bounds__(256) k_sweep(const DevP<T> P, T *__restrict__ gA,
+                                               T *__restrict__ gB, const T *__restrict__ phig,
+                                               const T *__restrict__ q, T *__restrict__ psi_prev,
+                                               double *__restrict__ part, const Control *__restrict__ ctl,
+                                               int j)
+{
+    if (CTRL && ctl->done) return;
+    const int par = (ctl->cur0 + j - 1) & 1;
+    const T *__restrict__ src = par ? gB : gA;
+    T *__restrict__ dst = par ? gA : gB;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    double red[2] = {0.0, 0.0};
+    if (x < P.nx && y < P.ny) {
+        const int nx = P.nx;
+        const long long nn = P.nn, k = (long long)y * nx + x;
+        const T g1 = src[k], g2 = src[nn + k], g3 = src[2 * nn + k], g4 = src[3 * nn + k];
+        const T psit = T(1.5) * ((g1 + g3) + (g2 + g4));      // Eq. 49, minus psi_lin
+        if (RESID) {
+            const double d = (double)psit - (double)psi_prev[k];
+            const double ps = (double)psit + (double)psi_lin(P, y);
+            red[0] = d * d;
+            red[1] = ps * ps;
+        }
+        if (WRITE_PSI) psi_prev[k] = psit;
+        // grad phi by Eq. 59 (only grad eps enters the potential)
+        const int xm = wrapx(x - 1, nx), xp = wrapx(x + 1, nx);
+        const T *r0 = phig + (long long)y * nx, *r1 = r0 + nx, *r2 = r1 + nx;
+        const T phi = r1[x];
+        const T gx = (r1[xp] - r1[xm]) * T(1.0 / 3.0) +
+                     ((r2[xp] - r2[xm]) + (r0[xp] - r0[xm])) * T(1.0 / 12.0);
+        const T gy = (r2[x] - r0[x]) * T(1.0 / 3.0) +
+                     ((r2[xp] + r2[xm]) - (r0[xp] + r0[xm])) * T(1.0 / 12.0);
+        const T m1 = g1 - g3, m2 = g2 - g4;
+        const T Ex = T(3) * m1 / P.tau_g, Ey = T(3) * m2 / P.tau_g;  // Eq. 50
+        const T eps = T(1) + P.er1 * phi;
+        const T rt = (P.Kq * q[k] - P.er1 * (gx * Ex + gy * Ey)) / eps;
+        const T X3 = P.src_norm * rt * T(1.0 / 3.0);                // w_i source, 2nd moments
+        const T eq = psit * T(1.0 / 3.0);
+        const T m3 = g1 + g3, m4 = g2 + g4;
+        const T n1 = (T(1) - P.s_g) * m1, n2 = (T(1) - P.s_g) * m2;
+        const T n3 = m3 - P.s_free_g * (m3 - eq) + X3;
+        const T n4 = m4 - P.s_free_g * (m4 - eq) + X3;
+        const T o1 = T(0.5) * (n3 + n1), o3 = T(0.5) * (n3 - n1);
+        const T o2 = T(0.5) * (n4 + n2), o4 = T(0.5) * (n4 - n2);
+        dst[(long long)y * nx + xp] = o1;
+        dst[2 * nn + (long long)y * nx + xm] = o3;
+        if (y + 1 < P.ny) dst[nn + k + nx] = o2 - P.wG;
+        else dst[3 * nn + k] = -o2 + P.wG;          // cathode: ABB to psi_c
+        if (y > 0) dst[3 * nn + k - nx] = o4 + P.wG;
+        else dst[nn + k] = -o4 - P.wG;              // anode: ABB to psi_a
+    }
+    if (RESID) block_sum_store<2>(red, part);
+}
+
+// Converge mode, after sweep j (one block of 256): r_{j-1} from the partials
+// of sweep j, then the stop rule k >= kmin and (r_k < tol or k = kmax).
+static __global__ void __launch_bounds__(256) k_sweep_decide(const double *__restrict__ part, long long nb,
+                                                      Control *ctl, int j)
+{
+    if (ctl->done) return;
+    double tot[2] = {0.0, 0.0};
+    if (j >= 2) sum_partials<2>(part, nb, tot);
+    if (threadIdx.x != 0) return;
+    if (j >= 2) {
+        const double r = tot[1] > 0.0 ? sqrt(tot[0] / tot[1]) : sqrt(tot[0]);
+        if (j - 1 >= ctl->kmin && r < ctl->tol) {
+            ctl->K = j - 1; ctl->done = 1; ctl->early = 1; ctl->r_last = r;
+            return;
+        }
+    }
+    ctl->K = j;
+    if (j >= ctl->kmax) ctl->done = 1;
+}
+
+// The rest of the step at every node (O5-O11): reaction (Eq. 42-43), forces
+// (Eq. 12-14), u and p (Eq. 56-57), MRT collisions of f (Eq. 51), h (Eq. 27),
+// p and n (Eq. 34-35), push with the wall rules (Eq. 64).
+//   SNAP  : write the macroscopic snapshot.   FROZEN: E from DevP.
+//   RESID : residual of the last sweep against psi_prev.
+template <typename T, bool SNAP, bool FROZEN, bool RESID>
+__global__ void __launch_bounds__(256, 2) k_main(const DevP<T> P, const Pops<T> src, const Pops<T> dst,
+                                                 const T *__restrict__ gA, const T *__restrict__ gB,
+                                                 const Control *__restrict__ ctl, const T *__restrict__ phig,
+                                                 T *__restrict__ phiu, const T *__restrict__ psi_prev,
+                                                 T *__restrict__ snap, double *__restrict__ part)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    double red[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (x < P.nx && y < P.ny) {
+        const int nx = P.nx, ny = P.ny;
+        const long long nn = P.nn, k = (long long)y * nx + x;
+        const T third = T(1.0 / 3.0);
+
+        // ---- O1-O2: phi, properties (Eq. 61), stencils (Eq. 59) ----
+        const int xm = wrapx(x - 1, nx), xp = wrapx(x + 1, nx);
+        const T *r0 = phig + (long long)y * nx, *r1 = r0 + nx, *r2 = r1 + nx;
+        const T phi = r1[x];
+        const T pE = r1[xp], pW = r1[xm], pN = r2[x], pS = r0[x];
+        const T pNE = r2[xp], pNW = r2[xm], pSW = r0[xm], pSE = r0[xp];
+        const T gx = (pE - pW) * third + ((pNE - pNW) + (pSE - pSW)) * T(1.0 / 12.0);
+        const T gy = (pN - pS) * third + ((pNE + pNW) - (pSE + pSW)) * T(1.0 / 12.0);
+        const T lap = T(2.0 / 3.0) * ((pE + pN + pW + pS) - T(4) * phi) +
+                      T(1.0 / 6.0) * ((pNE + pNW + pSW + pSE) - T(4) * phi);
+        const T rho = T(1) + P.rho1 * phi;
+        const T eta = P.eta_v * (T(1) + P.eta1 * phi);
+        const T tau_f = T(0.5) + T(3) * eta / rho;
+        const T mup = P.mu_v * (T(1) + P.mu1 * phi);
+        const T mum = P.m * mup;
+        const T Dp = P.einstein_D ? P.D * mup / P.mu_v : P.D;
+        const T Dm = P.einstein_D ? P.D * mum / P.mu_v : P.D;
+        const T grx = P.rho1 * gx, gry = P.rho1 * gy;
+        const T dex = P.er1 * gx, dey = P.er1 * gy;
+
+        // ---- O4 result: psi, E from the last sweep (Eq. 49-50) ----
+        const int K = ctl->K;
+        const T *__restrict__ g = ((ctl->cur0 + K) & 1) ? gB : gA;
+        const T g1 = g[k], g2 = g[nn + k], g3 = g[2 * nn + k], g4 = g[3 * nn + k];
+        const T psit = T(1.5) * ((g1 + g3) + (g2 + g4));
+        const T psi = psit + psi_lin(P, y);
+        T Ex, Ey;
+        if (FROZEN) { Ex = P.Ex_frozen; Ey = P.Ey_frozen; }
+        else { Ex = T(3) * (g1 - g3) / P.tau_g; Ey = T(3) * (g2 - g4) / P.tau_g; }
+        if (RESID) {
+            const double d = (double)psit - (double)psi_prev[k];
+            red[2] = d * d;
+            red[3] = (double)psi * (double)psi;
+        }
+
+        // ---- O5: Onsager dissociation and the implicit reaction (Eq. 5, 42-43) ----
+        T pv[5], nv[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) { pv[i] = src.p[i * nn + k]; nv[i] = src.n[i * nn + k]; }
+        const T sp = (((pv[0] + pv[1]) + pv[2]) + pv[3]) + pv[4];
+        const T sn = (((nv[0] + nv[1]) + nv[2]) + nv[3]) + nv[4];
+        const T q = sp - sn;
+        T cp, cm, R;
+        if (P.onsager_form == 2) {
+            cp = sp; cm = sn; R = T(0);
+        } else {
+            const T b = P.cb * dsqrt<T>(dsqrt<T>(Ex * Ex + Ey * Ey));
+            const T F = onsager<T>(b, P.onsager_form);
+            const T cbp = sp + T(0.5) * P.k_d * F, cbm = sn + T(0.5) * P.k_d * F;
+            const T lam0 = T(0.5) * P.k_r;
+            const T B = T(1) - lam0 * cbp + lam0 * cbm;
+            const T disc = dsqrt<T>(B * B + T(4) * lam0 * cbp);
+            if (B >= T(0)) cp = (B + disc > T(0)) ? T(2) * cbp / (B + disc) : T(0);
+            else cp = (-B + disc) / (T(2) * lam0);
+            cm = cp - cbp + cbm;
+            R = P.k_d * F - P.k_r * cp * cm;
+        }
+
+        // ---- O6: forces (Eq. 12-14) ----
+        const T mu_phi = T(4) * P.beta * phi * (phi - T(1)) * (phi - T(0.5)) - P.kappa * lap;
+        const T E2 = Ex * Ex + Ey * Ey;
+        const T Fx = mu_phi * gx + P.Kq * q * Ex - T(0.5) * E2 * dex;
+        const T Fy = mu_phi * gy + P.Kq * q * Ey - T(0.5) * E2 * dey;
+
+        // ---- O7: u and p (Eq. 56-57) ----
+        T fv[9];
+        fv[0] = T(0);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) fv[i] = src.f[(i - 1) * nn + k];
+        const T jx = ((fv[1] - fv[3]) + (fv[5] - fv[6])) + (fv[8] - fv[7]);
+        const T jy = ((fv[2] - fv[4]) + (fv[5] + fv[6])) - (fv[7] + fv[8]);
+        const T ux = (jx + T(0.5) * Fx) / rho;
+        const T uy = (jy + T(0.5) * Fy) / rho;
+        const T uu = ux * ux + uy * uy;
+        T sne0 = T(0);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) sne0 += fv[i];
+        const T ugr = ux * grx + uy * gry;
+        const T pr = T(0.6) * (sne0 + T(0.5) * ugr - rho * T(2.0 / 3.0) * uu);
+
+        // ---- O8: f collision (Eq. 51-55) ----
+        {
+            T d[9], Fi[9], md[9], mF[9], mc[9], dl[9];
+            d[0] = T(0); Fi[0] = T(0);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const T cu = T(cx9(i)) * ux + T(cy9(i)) * uy;
+                const T cF = T(cx9(i)) * Fx + T(cy9(i)) * Fy;
+                const T cg = T(cx9(i)) * grx + T(cy9(i)) * gry;
+                const T feq = w9<T>(i) * (T(3) * pr + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
+                d[i] = fv[i] - feq;
+                Fi[i] = w9<T>(i) * T(3) * (cF + cu * cg);   // Eq. 54 (its u.grad rho terms cancel)
+            }
+            moments9<T>(d, md);
+            moments9<T>(Fi, mF);
+            const T sv = T(1) / tau_f;
+            const T sfree = P.bgk ? sv : P.s_free;
+#pragma unroll
+            for (int kk = 0; kk < 9; ++kk) {
+                const T s = (kk >= 1 && kk <= 5) ? sv : sfree;
+                mc[kk] = s * md[kk] - (T(1) - T(0.5) * s) * mF[kk];
+            }
+            inverse9<T>(mc, dl);
+            // push with half-way bounce-back (f0 not stored)
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const T v = fv[i] - dl[i];
+                const int yd = y + cy9(i);
+                if (yd >= 0 && yd < ny)
+                    dst.f[(i - 1) * nn + (long long)yd * nx + wrapx(x + cx9(i), nx)] = v;
+                else
+                    dst.f[(opp9(i) - 1) * nn + k] = v;
+            }
+        }
+
+        // ---- O9: h collision (Eq. 27-33, Eq. 58) ----
+        {
+            T hv[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) hv[i] = src.h[i * nn + k];
+            const T pux = phi * ux, puy = phi * uy;
+            const T dpx = pux - phiu[k], dpy = puy - phiu[nn + k];
+            phiu[k] = pux;
+            phiu[nn + k] = puy;
+            const T mag = dsqrt<T>(gx * gx + gy * gy);
+            T nhx = T(0), nhy = T(0);
+            if (mag >= T(1e-12)) { nhx = gx / mag; nhy = gy / mag; }
+            const T lam = T(4) * phi * (T(1) - phi) / P.W;
+            const T Vx = dpx + third * lam * nhx, Vy = dpy + third * lam * nhy;
+            T d[9], Hi[9], md[9], mH[9], mc[9], dl[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const T cu = T(cx9(i)) * ux + T(cy9(i)) * uy;
+                const T cV = T(cx9(i)) * Vx + T(cy9(i)) * Vy;
+                d[i] = hv[i] - w9<T>(i) * phi * (T(1) + T(3) * cu);
+                Hi[i] = w9<T>(i) * T(3) * cV;
+            }
+            moments9<T>(d, md);
+            moments9<T>(Hi, mH);
+            const T sv = T(1) / P.tau_h;
+            const T sfree = P.bgk ? sv : P.s_free;
+#pragma unroll
+            for (int kk = 0; kk < 9; ++kk) {
+                const T s = (kk == 1 || kk == 2) ? sv : sfree;
+                mc[kk] = s * md[kk] - (T(1) - T(0.5) * s) * mH[kk];
+            }
+            inverse9<T>(mc, dl);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const T v = hv[i] - dl[i];
+                const int yd = y + cy9(i);
+                if (yd >= 0 && yd < ny)
+                    dst.h[i * nn + (long long)yd * nx + wrapx(x + cx9(i), nx)] = v;
+                else
+                    dst.h[opp9(i) * nn + k] = v;
+            }
+        }
+
+        // ---- O10-O11: ions (Eq. 34-40) on D2Q5, push with Eq. 64 ----
+        {
+            const T sv_p = T(1) / (T(0.5) + T(3) * Dp);
+            const T sv_n = T(1) / (T(0.5) + T(3) * Dm);
+            const T fp = P.bgk ? sv_p : P.s_free, fn = P.bgk ? sv_n : P.s_free;
+            const T Lx = P.ion_L_term ? Fx : T(0), Ly = P.ion_L_term ? Fy : T(0);
+            // cations: moments of (p - p_eq) + G and of R_i + L_i
+            T mc0 = fp * (sp - cp) - (T(1) - T(0.5) * fp) * R;
+            T mc1 = sv_p * ((pv[1] - pv[3]) - cp * ux - mup * cp * Ex) - (T(1) - T(0.5) * sv_p) * cp * Lx;
+            T mc2 = sv_p * ((pv[2] - pv[4]) - cp * uy - mup * cp * Ey) - (T(1) - T(0.5) * sv_p) * cp * Ly;
+            T mc3 = fp * ((pv[1] + pv[3]) - cp * third) - (T(1) - T(0.5) * fp) * R * third;
+            T mc4 = fp * ((pv[2] + pv[4]) - cp * third) - (T(1) - T(0.5) * fp) * R * third;
+            T po[5];
+            po[0] = pv[0] - (mc0 - mc3 - mc4);
+            po[1] = pv[1] - T(0.5) * (mc3 + mc1);
+            po[3] = pv[3] - T(0.5) * (mc3 - mc1);
+            po[2] = pv[2] - T(0.5) * (mc4 + mc2);
+            po[4] = pv[4] - T(0.5) * (mc4 - mc2);
+            // anions: (n - n_eq) - G_bar
+            mc0 = fn * (sn - cm) - (T(1) - T(0.5) * fn) * R;
+            mc1 = sv_n * ((nv[1] - nv[3]) - cm * ux + mum * cm * Ex) - (T(1) - T(0.5) * sv_n) * cm * Lx;
+            mc2 = sv_n * ((nv[2] - nv[4]) - cm * uy + mum * cm * Ey) - (T(1) - T(0.5) * sv_n) * cm * Ly;
+            mc3 = fn * ((nv[1] + nv[3]) - cm * third) - (T(1) - T(0.5) * fn) * R * third;
+            mc4 = fn * ((nv[2] + nv[4]) - cm * third) - (T(1) - T(0.5) * fn) * R * third;
+            T no[5];
+            no[0] = nv[0] - (mc0 - mc3 - mc4);
+            no[1] = nv[1] - T(0.5) * (mc3 + mc1);
+            no[3] = nv[3] - T(0.5) * (mc3 - mc1);
+            no[2] = nv[2] - T(0.5) * (mc4 + mc2);
+            no[4] = nv[4] - T(0.5) * (mc4 - mc2);
+
+            const long long row = (long long)y * nx;
+            dst.p[k] = po[0];
+            dst.n[k] = no[0];
+            dst.p[nn + row + xp] = po[1];
+            dst.n[nn + row + xp] = no[1];
+            dst.p[3 * nn + row + xm] = po[3];
+            dst.n[3 * nn + row + xm] = no[3];
+            const T w = T(1) / T(6);
+            if (y + 1 < ny) {
+                dst.p[2 * nn + k + nx] = po[2];
+                dst.n[2 * nn + k + nx] = no[2];
+            } else {  // cathode: attracts cations (zero gradient), repels anions
+                const T cwp = P.ion_bc == 0 ? cp : T(0);
+                dst.p[4 * nn + k] = P.ion_bc == 2 ? po[2] : -po[2] + T(2) * w * cwp;
+                dst.n[4 * nn + k] = P.ion_bc == 2 ? no[2] : -no[2];
+            }
+            if (y > 0) {
+                dst.p[4 * nn + k - nx] = po[4];
+                dst.n[4 * nn + k - nx] = no[4];
+            } else {  // anode: repels cations, attracts anions
+                const T cwm = P.ion_bc == 0 ? cm : T(0);
+                dst.p[2 * nn + k] = P.ion_bc == 2 ? po[4] : -po[4];
+                dst.n[2 * nn + k] = P.ion_bc == 2 ? no[4] : -no[4] + T(2) * w * cwm;
+            }
+        }
+
+        if (SNAP) {
+            snap[k] = phi;
+            snap[nn + k] = ux;
+            snap[2 * nn + k] = uy;
+            snap[3 * nn + k] = pr;
+            snap[4 * nn + k] = psi;
+            snap[5 * nn + k] = Ex;
+            snap[6 * nn + k] = Ey;
+            snap[7 * nn + k] = cp;
+            snap[8 * nn + k] = cm;
+            snap[9 * nn + k] = q;
+        }
+        red[0] = (double)phi;
+        red[1] = (double)q;
+        const T chk = ux + uy + pr + psi + cp + cm;
+        red[4] = isfinite((double)chk) ? 0.0 : 1.0;
+    }
+    block_sum_store<5>(red, part);
+}
+
+// End of step (one block of 256): global sums of the main kernel, the step's
+// residual, counters, the next step's g parity.
+static __global__ void __launch_bounds__(256) k_step_end(const double *__restrict__ part, long long nb,
+                                                  Control *ctl, int *counts, int resid)
+{
+    double tot[5];
+    sum_partials<5>(part, nb, tot);
+    if (threadIdx.x != 0) return;
+    const int K = ctl->K;
+    double r = ctl->r_last;
+    if (!ctl->early) {
+        if (resid && K >= 1) r = tot[3] > 0.0 ? sqrt(tot[2] / tot[3]) : sqrt(tot[2]);
+        else r = nan("");
+    }
+    ctl->r_step = r;
+    ctl->sum_phi = tot[0];
+    ctl->sum_q = tot[1];
+    if (tot[4] > 0.0) ctl->unstable = 1;
+    if (counts) counts[ctl->tloc] = K;
+    ctl->sweeps_total += K;
+    if (K > ctl->sweeps_max) ctl->sweeps_max = K;
+    if (ctl->converge && ctl->kmax > ctl->kmin && K >= ctl->kmax && !(r < ctl->tol)) ctl->notconv += 1;
+    ctl->cur0 = (ctl->cur0 + K) & 1;
+    ctl->t += 1;
+    ctl->tloc += 1;
+}
+
+// ---- initial state (Sec. 6 set-up) ------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_init_state(const DevP<T> P, Pops<T> pops, T *__restrict__ g,
+                                                    T *__restrict__ phiu, double xc, double yc, double R,
+                                                    double Wi, int shape, int psi_zero)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const long long nn = P.nn, k = (long long)y * P.nx + x;
+    const double r = shape == 1 ? fabs(y - yc) : sqrt((x - xc) * (x - xc) + (y - yc) * (y - yc));
+    const T phi0 = (T)(0.5 * (1.0 + tanh(2.0 * (R - r) / Wi)));
+#pragma unroll
+    for (int i = 0; i < 9; ++i) pops.h[i * nn + k] = w9<T>(i) * phi0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) pops.f[i * nn + k] = T(0);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) { pops.p[i * nn + k] = T(0); pops.n[i * nn + k] = T(0); }
+    phiu[k] = T(0);
+    phiu[nn + k] = T(0);
+    const T w = T(1) / T(6);
+    if (psi_zero) {
+        const T v = -w * psi_lin(P, y);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) g[i * nn + k] = v;
+    } else {  // linear profile with the non-equilibrium part giving E = -grad psi
+        g[k] = T(0);
+        g[nn + k] = -P.tau_g * w * P.G;
+        g[2 * nn + k] = T(0);
+        g[3 * nn + k] = P.tau_g * w * P.G;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_init_ions(const DevP<T> P, Pops<T> pops, const T *__restrict__ gA,
+                                                   const T *__restrict__ gB, const Control *__restrict__ ctl,
+                                                   const T *__restrict__ phig, T *__restrict__ snap,
+                                                   double c_scale, double c0)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const long long nn = P.nn, k = (long long)y * P.nx + x;
+    const T *__restrict__ g = ((ctl->cur0 + ctl->K) & 1) ? gB : gA;
+    const T g1 = g[k], g2 = g[nn + k], g3 = g[2 * nn + k], g4 = g[3 * nn + k];
+    const T psi = T(1.5) * ((g1 + g3) + (g2 + g4)) + psi_lin(P, y);
+    T Ex, Ey;
+    if (P.freeze_E) { Ex = P.Ex_frozen; Ey = P.Ey_frozen; }
+    else { Ex = T(3) * (g1 - g3) / P.tau_g; Ey = T(3) * (g2 - g4) / P.tau_g; }
+    T ceq;
+    if (P.k_r > T(0) && P.onsager_form != 2) {
+        const T b = P.cb * dsqrt<T>(dsqrt<T>(Ex * Ex + Ey * Ey));
+        ceq = dsqrt<T>(P.k_d * onsager<T>(b, P.onsager_form) / P.k_r);
+    } else {
+        ceq = (T)c0;
+    }
+    ceq = (T)c_scale * ceq;
+    const T wv[5] = {T(1) / T(3), T(1) / T(6), T(1) / T(6), T(1) / T(6), T(1) / T(6)};
+    T sp = T(0), sn = T(0);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const T v = wv[i] * ceq;
+        pops.p[i * nn + k] = v;
+        pops.n[i * nn + k] = v;
+        sp += v;
+        sn += v;
+    }
+    const T phi = phig[(long long)(y + 1) * P.nx + x];
+    snap[k] = phi;
+    snap[nn + k] = T(0);
+    snap[2 * nn + k] = T(0);
+    snap[3 * nn + k] = T(0);
+    snap[4 * nn + k] = psi;
+    snap[5 * nn + k] = Ex;
+    snap[6 * nn + k] = Ey;
+    snap[7 * nn + k] = sp;
+    snap[8 * nn + k] = sn;
+    snap[9 * nn + k] = sp - sn;
+}
+
+// ---- state transfer (checkpoint / test hook) ---------------------------------------
+// Packs rows [y0, y0 + rows) of the state into 35 doubles per node.
+template <typename T>
+__global__ void k_pack_state(const DevP<T> P, const Pops<T> pops, const T *__restrict__ g,
+                             const T *__restrict__ phiu, double *__restrict__ out, int y0, int rows)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long cnt = (long long)rows * P.nx;
+    if (i >= cnt) return;
+    const int y = y0 + (int)(i / P.nx);
+    const long long nn = P.nn, k = (long long)y0 * P.nx + i;
+    double *o = out + 35 * i;
+    o[0] = 0.0;
+    for (int q = 1; q < 9; ++q) o[q] = (double)pops.f[(q - 1) * nn + k];
+    for (int q = 0; q < 9; ++q) o[9 + q] = (double)pops.h[q * nn + k];
+    for (int q = 0; q < 5; ++q) o[18 + q] = (double)pops.p[q * nn + k];
+    for (int q = 0; q < 5; ++q) o[23 + q] = (double)pops.n[q * nn + k];
+    const double pl = (double)psi_lin(P, y);
+    o[28] = 0.0;
+    for (int q = 0; q < 4; ++q) o[29 + q] = (double)g[q * nn + k] + pl / 6.0;
+    o[33] = (double)phiu[k];
+    o[34] = (double)phiu[nn + k];
+}
+
+template <typename T>
+__global__ void k_unpack_state(const DevP<T> P, Pops<T> pops, T *__restrict__ g, T *__restrict__ phiu,
+                               const double *__restrict__ in, int y0, int rows)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long cnt = (long long)rows * P.nx;
+    if (i >= cnt) return;
+    const int y = y0 + (int)(i / P.nx);
+    const long long nn = P.nn, k = (long long)y0 * P.nx + i;
+    const double *o = in + 35 * i;
+    for (int q = 1; q < 9; ++q) pops.f[(q - 1) * nn + k] = (T)o[q];
+    for (int q = 0; q < 9; ++q) pops.h[q * nn + k] = (T)o[9 + q];
+    for (int q = 0; q < 5; ++q) pops.p[q * nn + k] = (T)o[18 + q];
+    for (int q = 0; q < 5; ++q) pops.n[q * nn + k] = (T)o[23 + q];
+    const double pl = (double)psi_lin(P, y);
+    for (int q = 0; q < 4; ++q) g[q * nn + k] = (T)(o[29 + q] - pl / 6.0);
+    phiu[k] = (T)o[33];
+    phiu[nn + k] = (T)o[34];
+}
+
+template <typename T>
+__global__ void k_to_double(const T *__restrict__ a, double *__restrict__ out, long long n)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)a[i];
+}
+
+}  // namespace ehdlb

@@ -1,0 +1,414 @@
+// ehdlb_solver.cuh -- host side of one lattice: device buffers, the initial
+// state, the kernel sequence of a time step, transfers.  Instantiated for
+// float and double in solver_fp32.cu / solver_fp64.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "ehdlb.h"
+#include "ehdlb_kernels.cuh"
+#include "ehdlb_solver_base.h"
+
+namespace ehdlb {
+
+#define EHDLB_CK(call)                                                              \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            err = std::string(#call) + ": " + cudaGetErrorString(e_);               \
+            return e_ == cudaErrorMemoryAllocation ? EHDLB_ENOMEM : EHDLB_ECUDA;    \
+        }                                                                           \
+    } while (0)
+
+template <typename T> class Solver : public SolverBase {
+  public:
+    static constexpr int BX = 64, BY = 4;
+
+    Solver(int nx, int ny, cudaStream_t s) : nx_(nx), ny_(ny), nn_((long long)nx * ny), stream_(s) {}
+
+    ~Solver() override
+    {
+        for (void *p : allocs_) cudaFree(p);
+        for (cudaEvent_t e : events_) cudaEventDestroy(e);
+        if (own_stream_) cudaStreamDestroy(stream_);
+    }
+
+    int allocate(std::string &err)
+    {
+        if (!stream_) {
+            EHDLB_CK(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
+            own_stream_ = true;
+        }
+        grid_ = dim3((nx_ + BX - 1) / BX, (ny_ + BY - 1) / BY);
+        nb_ = (long long)grid_.x * grid_.y;
+        const size_t plane = sizeof(T) * (size_t)nn_;
+        for (int b = 0; b < 2; ++b) {
+            T *base;
+            EHDLB_CK(alloc((void **)&base, plane * 27));
+            pops_[b].f = base;
+            pops_[b].h = base + 8 * nn_;
+            pops_[b].p = base + 17 * nn_;
+            pops_[b].n = base + 22 * nn_;
+            EHDLB_CK(alloc((void **)&g_[b], plane * 4));
+        }
+        EHDLB_CK(alloc((void **)&phig_, sizeof(T) * (size_t)(ny_ + 2) * nx_));
+        EHDLB_CK(alloc((void **)&q_, plane));
+        EHDLB_CK(alloc((void **)&phiu_, plane * 2));
+        EHDLB_CK(alloc((void **)&psi_prev_, plane));
+        EHDLB_CK(alloc((void **)&snap_, plane * EHDLB_NFIELDS));
+        EHDLB_CK(alloc((void **)&part_, sizeof(double) * 5 * (size_t)nb_));
+        EHDLB_CK(alloc((void **)&ctl_, sizeof(Control)));
+        EHDLB_CK(alloc((void **)&stage_, sizeof(double) * (size_t)nn_));
+        EHDLB_CK(cudaMemsetAsync(snap_, 0, plane * EHDLB_NFIELDS, stream_));
+        EHDLB_CK(cudaStreamSynchronize(stream_));
+        return EHDLB_OK;
+    }
+
+    int set_params(const ehdlb_params &p, std::string &err) override
+    {
+        P_ = p;
+        make_devp();
+        Control c{};
+        c.cur0 = 0;
+        c.tol = p.sweep_tol;
+        c.r_last = NAN;
+        c.r_step = NAN;
+        ctl_h_ = c;
+        EHDLB_CK(cudaMemcpyAsync(ctl_, &ctl_h_, sizeof(Control), cudaMemcpyHostToDevice, stream_));
+        const double Wi = p.W_init > 0.0 ? p.W_init : p.W;
+        k_init_state<T><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[0], g_[0], phiu_, p.xc, p.yc, p.R,
+                                                             Wi, p.init_shape, p.init_psi_zero);
+        EHDLB_CK(cudaGetLastError());
+        // initial potential solve with q = 0 (p = n = 0 at this point)
+        if (p.freeze_E) {
+            launch_prep(0, 0, 0, 0);
+        } else if (p.init_sweeps_fixed >= 0) {
+            launch_prep(0, p.init_sweeps_fixed, p.init_sweeps_fixed, p.init_sweeps_fixed);
+            for (int j = 1; j <= p.init_sweeps_fixed; ++j) launch_sweep(j, false, false, false);
+        } else {
+            launch_prep(0, -1, 0, p.init_sweeps_max);
+            const int chunk = 256;
+            for (int j0 = 1; j0 <= p.init_sweeps_max; j0 += chunk) {
+                const int j1 = std::min(p.init_sweeps_max, j0 + chunk - 1);
+                for (int j = j0; j <= j1; ++j) {
+                    launch_sweep(j, true, j >= 2, true);
+                    k_sweep_decide<<<1, 256, 0, stream_>>>(part_, nb_, ctl_, j);
+                }
+                EHDLB_CK(cudaGetLastError());
+                EHDLB_CK(cudaMemcpyAsync(&ctl_h_, ctl_, sizeof(Control), cudaMemcpyDeviceToHost, stream_));
+                EHDLB_CK(cudaStreamSynchronize(stream_));
+                if (ctl_h_.done) break;
+            }
+        }
+        EHDLB_CK(cudaGetLastError());
+        k_init_ions<T><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[0], g_[0], g_[1], ctl_, phig_, snap_,
+                                                            p.c_init_scale, p.c0);
+        EHDLB_CK(cudaGetLastError());
+        EHDLB_CK(cudaMemcpyAsync(&ctl_h_, ctl_, sizeof(Control), cudaMemcpyDeviceToHost, stream_));
+        EHDLB_CK(cudaStreamSynchronize(stream_));
+        init_sweeps_ = ctl_h_.K;
+        c = Control{};
+        c.cur0 = (ctl_h_.cur0 + ctl_h_.K) & 1;
+        c.tol = p.sweep_tol;
+        c.r_last = NAN;
+        c.r_step = NAN;
+        ctl_h_ = c;
+        EHDLB_CK(cudaMemcpyAsync(ctl_, &ctl_h_, sizeof(Control), cudaMemcpyHostToDevice, stream_));
+        EHDLB_CK(cudaStreamSynchronize(stream_));
+        tpar_ = 0;
+        t_ = 0;
+        return EHDLB_OK;
+    }
+
+    void set_schedule(const int *c, int n) override { sched_.assign(c, c + n); }
+    void set_timing(int on) override { timing_ = on != 0; }
+
+    int step(int nsteps, ehdlb_stats *st, std::string &err) override
+    {
+        const auto t0 = std::chrono::steady_clock::now();
+        if (nsteps > counts_cap_) {
+            int *nc;
+            EHDLB_CK(alloc((void **)&nc, sizeof(int) * (size_t)nsteps));
+            counts_ = nc;
+            counts_cap_ = nsteps;
+        }
+        // open the call: per-call counters
+        ctl_h_.tloc = 0;
+        ctl_h_.sweeps_total = 0;
+        ctl_h_.sweeps_max = 0;
+        ctl_h_.notconv = 0;
+        ctl_h_.unstable = 0;
+        EHDLB_CK(cudaMemcpyAsync(&ctl_->tloc, &ctl_h_.tloc, sizeof(long long), cudaMemcpyHostToDevice, stream_));
+        EHDLB_CK(cudaMemcpyAsync(&ctl_->sweeps_total, &ctl_h_.sweeps_total, sizeof(long long),
+                                 cudaMemcpyHostToDevice, stream_));
+        EHDLB_CK(cudaMemsetAsync(&ctl_->unstable, 0, sizeof(int), stream_));
+        EHDLB_CK(cudaMemsetAsync(&ctl_->notconv, 0, sizeof(int), stream_));
+        EHDLB_CK(cudaMemsetAsync(&ctl_->sweeps_max, 0, sizeof(int), stream_));
+        if (timing_ && (int)events_.size() < 4 * nsteps) {
+            while ((int)events_.size() < 4 * nsteps) {
+                cudaEvent_t e;
+                EHDLB_CK(cudaEventCreate(&e));
+                events_.push_back(e);
+            }
+        }
+        launches_ = 0;
+        for (int s = 0; s < nsteps; ++s) {
+            enqueue_step(s, s == nsteps - 1);
+            EHDLB_CK(cudaGetLastError());
+        }
+        EHDLB_CK(cudaMemcpyAsync(&ctl_h_, ctl_, sizeof(Control), cudaMemcpyDeviceToHost, stream_));
+        EHDLB_CK(cudaStreamSynchronize(stream_));
+        EHDLB_CK(cudaGetLastError());
+        last_nsteps = nsteps;
+        const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (st) {
+            st->steps = nsteps;
+            st->t = ctl_h_.t;
+            st->sweeps_total = ctl_h_.sweeps_total;
+            st->sweeps_max = ctl_h_.sweeps_max;
+            st->not_converged = ctl_h_.notconv;
+            st->last_residual = ctl_h_.r_step;
+            st->sum_phi = ctl_h_.sum_phi;
+            st->sum_q = ctl_h_.sum_q;
+            st->seconds = secs;
+            st->mlups = secs > 0 ? (double)nn_ * nsteps / secs / 1e6 : 0.0;
+            st->ms_prep = st->ms_sweeps = st->ms_main = 0.0;
+            if (timing_) {
+                for (int s = 0; s < nsteps; ++s) {
+                    float a = 0, b = 0, c = 0;
+                    cudaEventElapsedTime(&a, events_[4 * s], events_[4 * s + 1]);
+                    cudaEventElapsedTime(&b, events_[4 * s + 1], events_[4 * s + 2]);
+                    cudaEventElapsedTime(&c, events_[4 * s + 2], events_[4 * s + 3]);
+                    st->ms_prep += a;
+                    st->ms_sweeps += b;
+                    st->ms_main += c;
+                }
+            }
+            st->launches = launches_;
+        }
+        if (ctl_h_.unstable) {
+            err = "NaN or Inf in the fields";
+            return EHDLB_EUNSTABLE;
+        }
+        return ctl_h_.notconv > 0 ? EHDLB_WNOTCONV : EHDLB_OK;
+    }
+
+    int get_fields(unsigned mask, double *dst, std::string &err) override
+    {
+        size_t off = 0;
+        const int nthr = 256;
+        const unsigned nblk = (unsigned)((nn_ + nthr - 1) / nthr);
+        for (int f = 0; f < EHDLB_NFIELDS; ++f) {
+            if (!(mask & (1u << f))) continue;
+            k_to_double<T><<<nblk, nthr, 0, stream_>>>(snap_ + (size_t)f * nn_, stage_, nn_);
+            EHDLB_CK(cudaGetLastError());
+            EHDLB_CK(cudaMemcpyAsync(dst + off, stage_, sizeof(double) * (size_t)nn_, cudaMemcpyDeviceToHost,
+                                     stream_));
+            off += (size_t)nn_;
+        }
+        EHDLB_CK(cudaStreamSynchronize(stream_));
+        return EHDLB_OK;
+    }
+
+    int get_counts(int *dst, int n, std::string &err) override
+    {
+        if (n <= 0) return EHDLB_OK;
+        EHDLB_CK(cudaMemcpyAsync(dst, counts_, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, stream_));
+        EHDLB_CK(cudaStreamSynchronize(stream_));
+        return EHDLB_OK;
+    }
+
+    int get_state(double *dst, std::string &err) override { return transfer_state(dst, nullptr, err); }
+    int set_state(const double *src, std::string &err) override { return transfer_state(nullptr, src, err); }
+
+  private:
+    cudaError_t alloc(void **p, size_t bytes)
+    {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) allocs_.push_back(*p);
+        return e;
+    }
+
+    void make_devp()
+    {
+        const ehdlb_params &p = P_;
+        DevP<T> d{};
+        d.nx = nx_;
+        d.ny = ny_;
+        d.nn = nn_;
+        d.onsager_form = p.onsager_form;
+        d.ion_bc = p.ion_bc;
+        d.einstein_D = p.einstein_D;
+        d.ion_L_term = p.ion_L_term;
+        d.bgk = p.bgk;
+        d.freeze_E = p.freeze_E;
+        const double tau_g = 0.5 + 3.0 * p.vartheta;  // Eq. 47
+        d.tau_g = (T)tau_g;
+        d.s_g = (T)(1.0 / tau_g);
+        d.s_free_g = (T)(p.bgk ? 1.0 / tau_g : p.s_free);
+        d.src_norm = (T)(p.vartheta * (p.psi_src_literal ? 1.0 : 1.5));
+        d.Kq = (T)p.Kq;
+        d.er1 = (T)(p.eps_r - 1.0);
+        d.psi_a = (T)p.psi_anode;
+        d.psi_c = (T)p.psi_cathode;
+        d.G = (T)((p.psi_cathode - p.psi_anode) / ny_);
+        d.wG = (T)((p.psi_cathode - p.psi_anode) / ny_ / 6.0);
+        d.rho1 = (T)(p.rho_ratio - 1.0);
+        d.eta_v = (T)((p.tau_f - 0.5) / 3.0);
+        d.eta1 = (T)(p.eta_ratio - 1.0);
+        d.beta = (T)(12.0 * p.sigma / p.W);
+        d.kappa = (T)(1.5 * p.sigma * p.W);
+        d.W = (T)p.W;
+        d.tau_h = (T)(0.5 + 3.0 * p.M_phi);
+        d.mu_v = (T)p.mu_v;
+        d.mu1 = (T)(p.mu_r - 1.0);
+        d.m = (T)p.m;
+        d.D = (T)p.D;
+        d.k_d = (T)p.k_d;
+        d.k_r = (T)p.k_r;
+        d.cb = (T)p.onsager_cb;
+        d.s_free = (T)p.s_free;
+        d.Ex_frozen = (T)p.E_frozen_x;
+        d.Ey_frozen = (T)p.E_frozen_y;
+        dp_ = d;
+    }
+
+    void launch_prep(int par, int fixedK, int kmin, int kmax)
+    {
+        k_prep<T><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n, phig_,
+                                                       q_, ctl_, fixedK, kmin, kmax);
+        ++launches_;
+    }
+
+    void launch_sweep(int j, bool write_psi, bool resid, bool ctrl)
+    {
+        const dim3 b(BX, BY);
+#define EHDLB_SWEEP(W, R, C)                                                                            \
+    k_sweep<T, W, R, C><<<grid_, b, 0, stream_>>>(dp_, g_[0], g_[1], phig_, q_, psi_prev_, part_, ctl_, j)
+        if (ctrl) {
+            if (resid) EHDLB_SWEEP(true, true, true);
+            else EHDLB_SWEEP(true, false, true);
+        } else {
+            if (write_psi) EHDLB_SWEEP(true, false, false);
+            else EHDLB_SWEEP(false, false, false);
+        }
+#undef EHDLB_SWEEP
+        ++launches_;
+    }
+
+    // Kernel sequence of one time step; s is the step index within the call.
+    void enqueue_step(int s, bool snap)
+    {
+        const int par = tpar_;
+        const bool frozen = P_.freeze_E != 0;
+        int fixedK = -1, kmin = P_.sweeps_min, kmax = P_.sweeps_max;
+        if (frozen) fixedK = 0;
+        else if (t_ < (long long)sched_.size()) fixedK = sched_[(size_t)t_];
+        else if (P_.sweeps_min == P_.sweeps_max) fixedK = P_.sweeps_max;
+        if (fixedK >= 0) kmin = kmax = fixedK;
+        if (timing_) cudaEventRecord(events_[4 * s], stream_);
+        launch_prep(par, fixedK, kmin, kmax);
+        if (timing_) cudaEventRecord(events_[4 * s + 1], stream_);
+        if (fixedK >= 0) {
+            for (int j = 1; j <= fixedK; ++j) launch_sweep(j, j == fixedK, false, false);
+        } else {
+            for (int j = 1; j <= kmax; ++j) {
+                launch_sweep(j, true, j >= 2, true);
+                k_sweep_decide<<<1, 256, 0, stream_>>>(part_, nb_, ctl_, j);
+                ++launches_;
+            }
+        }
+        if (timing_) cudaEventRecord(events_[4 * s + 2], stream_);
+        const bool resid = !frozen && kmax >= 1;
+        const dim3 b(BX, BY);
+#define EHDLB_MAIN(S, F, R)                                                                              \
+    k_main<T, S, F, R><<<grid_, b, 0, stream_>>>(dp_, pops_[par], pops_[par ^ 1], g_[0], g_[1], ctl_,     \
+                                                 phig_, phiu_, psi_prev_, snap_, part_)
+        if (snap) {
+            if (frozen) EHDLB_MAIN(true, true, false);
+            else if (resid) EHDLB_MAIN(true, false, true);
+            else EHDLB_MAIN(true, false, false);
+        } else {
+            if (frozen) EHDLB_MAIN(false, true, false);
+            else if (resid) EHDLB_MAIN(false, false, true);
+            else EHDLB_MAIN(false, false, false);
+        }
+#undef EHDLB_MAIN
+        k_step_end<<<1, 256, 0, stream_>>>(part_, nb_, ctl_, counts_, resid ? 1 : 0);
+        launches_ += 2;
+        if (timing_) cudaEventRecord(events_[4 * s + 3], stream_);
+        tpar_ ^= 1;
+        ++t_;
+    }
+
+    int transfer_state(double *dst, const double *src, std::string &err)
+    {
+        EHDLB_CK(cudaMemcpyAsync(&ctl_h_, ctl_, sizeof(Control), cudaMemcpyDeviceToHost, stream_));
+        EHDLB_CK(cudaStreamSynchronize(stream_));
+        const int cur = ctl_h_.cur0;
+        const size_t per_row = (size_t)35 * nx_;
+        int rows = (int)std::max<size_t>(1, std::min<size_t>((size_t)ny_, ((size_t)nn_) / per_row));
+        double *stage = nullptr;
+        EHDLB_CK(cudaMalloc((void **)&stage, sizeof(double) * per_row * rows));
+        int status = EHDLB_OK;
+        for (int y0 = 0; y0 < ny_ && status == EHDLB_OK; y0 += rows) {
+            const int r = std::min(rows, ny_ - y0);
+            const long long cnt = (long long)r * nx_;
+            const unsigned nblk = (unsigned)((cnt + 255) / 256);
+            cudaError_t e = cudaSuccess;
+            if (dst) {
+                k_pack_state<T><<<nblk, 256, 0, stream_>>>(dp_, pops_[tpar_], g_[cur], phiu_, stage, y0, r);
+                e = cudaGetLastError();
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(dst + per_row * y0, stage, sizeof(double) * per_row * r,
+                                        cudaMemcpyDeviceToHost, stream_);
+            } else {
+                e = cudaMemcpyAsync(stage, src + per_row * y0, sizeof(double) * per_row * r,
+                                    cudaMemcpyHostToDevice, stream_);
+                if (e == cudaSuccess)
+                    k_unpack_state<T><<<nblk, 256, 0, stream_>>>(dp_, pops_[tpar_], g_[cur], phiu_, stage, y0, r);
+                if (e == cudaSuccess) e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+            if (e != cudaSuccess) {
+                err = std::string("state transfer: ") + cudaGetErrorString(e);
+                status = EHDLB_ECUDA;
+            }
+        }
+        cudaFree(stage);
+        return status;
+    }
+
+    int nx_, ny_;
+    long long nn_;
+    cudaStream_t stream_;
+    bool own_stream_ = false;
+    dim3 grid_;
+    long long nb_ = 0;
+    Pops<T> pops_[2]{};
+    T *g_[2]{};
+    T *phig_ = nullptr, *q_ = nullptr, *phiu_ = nullptr, *psi_prev_ = nullptr, *snap_ = nullptr;
+    double *part_ = nullptr, *stage_ = nullptr;
+    Control *ctl_ = nullptr;
+    Control ctl_h_{};
+    int *counts_ = nullptr;
+    int counts_cap_ = 0;
+    std::vector<void *> allocs_;
+    std::vector<cudaEvent_t> events_;
+    std::vector<int> sched_;
+    ehdlb_params P_{};
+    DevP<T> dp_{};
+    int tpar_ = 0;
+    long long t_ = 0;
+    int init_sweeps_ = 0;
+    bool timing_ = false;
+    long long launches_ = 0;
+};
+
+}  // namespace ehdlb

@@ -1,0 +1,260 @@
+"""Thin ctypes binding of libehdlb (include/ehdlb.h), same names as the C ABI.
+
+Only argument marshalling happens here: every step of the solver runs in the
+CUDA kernels of the library.  If the library cannot be loaded the import
+fails; there is no other implementation behind these functions.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FIELDS = ["phi", "ux", "uy", "p", "psi", "Ex", "Ey", "cp", "cm", "q"]
+FP64, FP32 = 0, 1
+OK, WNOTCONV, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ESTATE = 0, 1, -1, -2, -3, -4, -5
+STATUS_NAMES = {0: "OK", 1: "WNOTCONV", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA",
+                -4: "EUNSTABLE", -5: "ESTATE"}
+
+_PARAM_FIELDS = [
+    ("size", C.c_size_t),
+    ("tau_f", C.c_double), ("rho_ratio", C.c_double), ("eta_ratio", C.c_double),
+    ("sigma", C.c_double), ("W", C.c_double), ("W_init", C.c_double),
+    ("M_phi", C.c_double),
+    ("xc", C.c_double), ("yc", C.c_double), ("R", C.c_double),
+    ("init_shape", C.c_int),
+    ("D", C.c_double), ("mu_v", C.c_double), ("mu_r", C.c_double),
+    ("m", C.c_double), ("k_d", C.c_double), ("k_r", C.c_double),
+    ("onsager_cb", C.c_double),
+    ("onsager_form", C.c_int), ("ion_bc", C.c_int), ("einstein_D", C.c_int),
+    ("ion_L_term", C.c_int),
+    ("c_init_scale", C.c_double), ("c0", C.c_double),
+    ("eps_r", C.c_double), ("Kq", C.c_double), ("vartheta", C.c_double),
+    ("psi_src_literal", C.c_int),
+    ("psi_anode", C.c_double), ("psi_cathode", C.c_double),
+    ("sweeps_min", C.c_int), ("sweeps_max", C.c_int),
+    ("sweep_tol", C.c_double),
+    ("init_sweeps_max", C.c_int), ("init_sweeps_fixed", C.c_int),
+    ("init_psi_zero", C.c_int),
+    ("freeze_E", C.c_int), ("E_frozen_x", C.c_double), ("E_frozen_y", C.c_double),
+    ("s_free", C.c_double), ("bgk", C.c_int),
+]
+
+
+class ehdlb_params(C.Structure):
+    _fields_ = _PARAM_FIELDS
+
+
+class ehdlb_stats(C.Structure):
+    _fields_ = [
+        ("steps", C.c_longlong), ("t", C.c_longlong), ("sweeps_total", C.c_longlong),
+        ("sweeps_max", C.c_int), ("not_converged", C.c_int),
+        ("last_residual", C.c_double), ("sum_phi", C.c_double), ("sum_q", C.c_double),
+        ("seconds", C.c_double), ("mlups", C.c_double),
+        ("ms_prep", C.c_double), ("ms_sweeps", C.c_double), ("ms_main", C.c_double),
+        ("launches", C.c_longlong),
+    ]
+
+
+class EhdlbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libehdlb.so (building it in-tree with nvcc if it is out of date)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError(f"libehdlb.so missing at {path}")
+        L = C.CDLL(path)
+        vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+        L.ehdlb_version.restype = C.c_int
+        L.ehdlb_params_default.argtypes = [C.POINTER(ehdlb_params)]
+        L.ehdlb_params_from_physical.argtypes = [C.POINTER(ehdlb_params), C.c_int, C.c_int,
+                                                 C.c_double, C.c_double, C.c_double, C.c_double]
+        L.ehdlb_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, vp]
+        L.ehdlb_set_params.argtypes = [vp, C.POINTER(ehdlb_params)]
+        L.ehdlb_set_sweep_schedule.argtypes = [vp, ip, C.c_int]
+        L.ehdlb_step.argtypes = [vp, C.c_int, C.POINTER(ehdlb_stats)]
+        L.ehdlb_get_fields.argtypes = [vp, C.c_uint, dp, C.c_size_t]
+        L.ehdlb_get_sweep_counts.argtypes = [vp, ip, C.c_int]
+        L.ehdlb_state_len.argtypes = [vp]
+        L.ehdlb_state_len.restype = C.c_size_t
+        L.ehdlb_get_state.argtypes = [vp, dp, C.c_size_t]
+        L.ehdlb_set_state.argtypes = [vp, dp, C.c_size_t]
+        L.ehdlb_set_timing.argtypes = [vp, C.c_int]
+        L.ehdlb_destroy.argtypes = [vp]
+        L.ehdlb_destroy.restype = None
+        L.ehdlb_last_error.argtypes = [vp]
+        L.ehdlb_last_error.restype = C.c_char_p
+        if L.ehdlb_version() != 1:
+            raise ImportError("libehdlb ABI version mismatch")
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _check(ctx, status, what):
+    if status < 0:
+        msg = lib().ehdlb_last_error(ctx).decode() if ctx else ""
+        raise EhdlbError(status, f"{what}: {msg}")
+    return status
+
+
+# ---- the C functions, one to one ---------------------------------------------
+
+def ehdlb_version() -> int:
+    return lib().ehdlb_version()
+
+
+def ehdlb_params_default(overrides: dict | None = None) -> ehdlb_params:
+    p = ehdlb_params()
+    _check(None, lib().ehdlb_params_default(C.byref(p)), "ehdlb_params_default")
+    return _apply(p, overrides)
+
+
+def ehdlb_params_from_physical(nx, ny, d_mm, dpsi_kV, eps_r, mu_r,
+                               overrides: dict | None = None) -> ehdlb_params:
+    p = ehdlb_params()
+    _check(None, lib().ehdlb_params_from_physical(C.byref(p), nx, ny, d_mm, dpsi_kV, eps_r, mu_r),
+           "ehdlb_params_from_physical")
+    return _apply(p, overrides)
+
+
+def _apply(p, overrides):
+    if overrides:
+        names = {n for n, _ in _PARAM_FIELDS}
+        bad = set(overrides) - names
+        if bad:
+            raise KeyError(f"unknown parameters: {sorted(bad)}")
+        for k, v in overrides.items():
+            setattr(p, k, v)
+    return p
+
+
+def params_dict(p: ehdlb_params) -> dict:
+    return {n: getattr(p, n) for n, _ in _PARAM_FIELDS if n != "size"}
+
+
+def ehdlb_create(nx: int, ny: int, precision: int = FP32, cuda_stream: int | None = None):
+    h = C.c_void_p()
+    _check(None, lib().ehdlb_create(C.byref(h), nx, ny, precision,
+                                    C.c_void_p(cuda_stream) if cuda_stream else None),
+           "ehdlb_create")
+    return h
+
+
+def ehdlb_set_params(ctx, p: ehdlb_params):
+    return _check(ctx, lib().ehdlb_set_params(ctx, C.byref(p)), "ehdlb_set_params")
+
+
+def ehdlb_set_sweep_schedule(ctx, counts):
+    a = np.ascontiguousarray(np.asarray(counts, dtype=np.int32))
+    return _check(ctx, lib().ehdlb_set_sweep_schedule(
+        ctx, a.ctypes.data_as(C.POINTER(C.c_int)), int(a.size)), "ehdlb_set_sweep_schedule")
+
+
+def ehdlb_step(ctx, nsteps: int):
+    st = ehdlb_stats()
+    status = _check(ctx, lib().ehdlb_step(ctx, nsteps, C.byref(st)), "ehdlb_step")
+    return status, st
+
+
+def ehdlb_get_fields(ctx, mask: int, dst: np.ndarray):
+    assert dst.dtype == np.float64 and dst.flags.c_contiguous
+    return _check(ctx, lib().ehdlb_get_fields(ctx, mask, _dp(dst), dst.size), "ehdlb_get_fields")
+
+
+def ehdlb_get_sweep_counts(ctx, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.int32)
+    _check(ctx, lib().ehdlb_get_sweep_counts(ctx, out.ctypes.data_as(C.POINTER(C.c_int)), n),
+           "ehdlb_get_sweep_counts")
+    return out
+
+
+def ehdlb_state_len(ctx) -> int:
+    return lib().ehdlb_state_len(ctx)
+
+
+def ehdlb_get_state(ctx, dst: np.ndarray):
+    assert dst.dtype == np.float64 and dst.flags.c_contiguous
+    return _check(ctx, lib().ehdlb_get_state(ctx, _dp(dst), dst.size), "ehdlb_get_state")
+
+
+def ehdlb_set_state(ctx, src: np.ndarray):
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    return _check(ctx, lib().ehdlb_set_state(ctx, _dp(src), src.size), "ehdlb_set_state")
+
+
+def ehdlb_set_timing(ctx, on: bool):
+    return _check(ctx, lib().ehdlb_set_timing(ctx, 1 if on else 0), "ehdlb_set_timing")
+
+
+def ehdlb_destroy(ctx):
+    lib().ehdlb_destroy(ctx)
+
+
+def ehdlb_last_error(ctx) -> str:
+    return lib().ehdlb_last_error(ctx).decode()
+
+
+# ---- convenience wrapper -------------------------------------------------------
+
+class Lattice:
+    """One solver context: create + set_params, then step / fields / state."""
+
+    def __init__(self, nx, ny, params: dict | ehdlb_params | None = None, precision=FP32,
+                 cuda_stream=None, schedule=None):
+        self.nx, self.ny, self.precision = nx, ny, precision
+        self.ctx = ehdlb_create(nx, ny, precision, cuda_stream)
+        if schedule is not None:
+            ehdlb_set_sweep_schedule(self.ctx, schedule)
+        p = params if isinstance(params, ehdlb_params) else ehdlb_params_default(params)
+        self.params = p
+        ehdlb_set_params(self.ctx, p)
+
+    def step(self, nsteps: int):
+        status, st = ehdlb_step(self.ctx, nsteps)
+        return status, st
+
+    def fields(self, names=None) -> dict:
+        names = FIELDS if names is None else list(names)
+        idx = sorted(FIELDS.index(n) for n in names)
+        mask = sum(1 << i for i in idx)
+        out = np.zeros((len(idx), self.ny, self.nx))
+        ehdlb_get_fields(self.ctx, mask, out)
+        return {FIELDS[i]: out[j] for j, i in enumerate(idx)}
+
+    def sweep_counts(self, n):
+        return ehdlb_get_sweep_counts(self.ctx, n)
+
+    def state(self) -> np.ndarray:
+        out = np.zeros((self.ny, self.nx, 35))
+        ehdlb_get_state(self.ctx, out)
+        return out
+
+    def set_state(self, s):
+        ehdlb_set_state(self.ctx, np.asarray(s, dtype=np.float64).reshape(self.ny, self.nx, 35))
+
+    def close(self):
+        if self.ctx:
+            ehdlb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,211 @@
+"""CUDA path against the FP64 oracle, element by element (needs a GB300).
+
+Tolerances: FP64 path 1e-12 relative L-infinity, FP32 path 1e-5, per field
+(phi, |u|, psi, q and the other snapshot fields), where relative L-infinity
+is max|a - b| / max|b|.  Sweep counts decided by the residual are replayed
+from the oracle so that both sides take the same number of potential
+sweeps; a separate test checks the counts the GPU picks by itself.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_04920_gb300 import ehdlb, workloads
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-5
+
+
+def rel_linf(a, b):
+    scale = np.max(np.abs(b))
+    if scale == 0.0:
+        return float(np.max(np.abs(a)))
+    return float(np.max(np.abs(a - b)) / scale)
+
+
+def field_errors(got, ref):
+    err = {k: rel_linf(got[k], ref[k]) for k in ("phi", "psi", "q", "cp", "cm", "Ex", "Ey", "p")}
+    err["u"] = rel_linf(np.hypot(got["ux"], got["uy"]), np.hypot(ref["ux"], ref["uy"]))
+    return err
+
+
+def run_pair(nx, ny, prm, steps, precision=ehdlb.FP64, replay=True):
+    """Oracle and GPU from the same parameters; GPU replays the oracle's sweep counts."""
+    orc = oracle.Oracle(nx, ny, prm)
+    counts, _, _ = orc.step(steps) if steps else (np.zeros(0, np.int32), None, 0)
+    gprm = dict(prm)
+    if replay and not prm.get("freeze_E", 0):
+        gprm["init_sweeps_fixed"] = orc.init_sweeps
+    lat = ehdlb.Lattice(nx, ny, gprm, precision=precision,
+                        schedule=counts if replay else None)
+    if steps:
+        lat.step(steps)
+    got, ref = lat.fields(), orc.fields()
+    return got, ref, lat, orc, counts
+
+
+def assert_close(err, tol, keys=None):
+    keys = keys or list(err)
+    bad = {k: v for k, v in err.items() if k in keys and not v <= tol}
+    assert not bad, f"above {tol}: {bad}  (all: {err})"
+
+
+# ---- FP64: the plain 64x64 droplet case -----------------------------------------
+
+def test_fp64_droplet64_initial_state_matches():
+    got, ref, lat, orc, _ = run_pair(64, 64, workloads.droplet64(), 0)
+    assert_close(field_errors(got, ref), FP64_TOL)
+
+
+def test_fp64_droplet64_200_steps_matches():
+    got, ref, lat, orc, counts = run_pair(64, 64, workloads.droplet64(), 200)
+    assert_close(field_errors(got, ref), FP64_TOL)
+    assert np.array_equal(lat.sweep_counts(200), counts)
+
+
+@pytest.mark.slow
+def test_fp64_droplet64_full_2000_steps_matches():
+    got, ref, lat, orc, counts = run_pair(64, 64, workloads.droplet64(), 2000)
+    assert_close(field_errors(got, ref), FP64_TOL)
+
+
+def test_gpu_residual_picks_the_oracle_sweep_counts():
+    prm = workloads.droplet64()
+    orc = oracle.Oracle(64, 64, prm)
+    oc, _, _ = orc.step(60)
+    lat = ehdlb.Lattice(64, 64, prm, precision=ehdlb.FP64)   # stop rule on the device
+    lat.step(60)
+    gc = lat.sweep_counts(60)
+    assert np.max(np.abs(gc.astype(int) - oc.astype(int))) <= 1, (gc, oc)
+
+
+# ---- FP64: small and ragged lattices with every switch ------------------------------
+
+VARIANTS = {
+    "base": {},
+    "bgk": dict(bgk=1),
+    "ion_bc1": dict(ion_bc=1),
+    "ion_bc2": dict(ion_bc=2),
+    "onsager_linear": dict(onsager_form=1),
+    "no_reaction": dict(onsager_form=2, c0=0.7),
+    "mobility": dict(einstein_D=0, m=0.5, mu_r=2.0),
+    "no_L_term": dict(ion_L_term=0),
+    "density_viscosity": dict(rho_ratio=2.0, eta_ratio=3.0),
+    "literal_source": dict(psi_src_literal=1),
+    "psi_zero_start": dict(init_psi_zero=1),
+    "frozen_field": dict(freeze_E=1, E_frozen_x=0.01, E_frozen_y=0.03),
+    "free_rate": dict(s_free=1.3),
+    "slab": dict(init_shape=1, R=2.0),
+    "wide_interface": dict(W_init=6.0, eps_r=0.5, mu_r=5.0),
+}
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (16, 12), (13, 7)])
+@pytest.mark.parametrize("name", sorted(VARIANTS))
+def test_fp64_small_lattices_every_switch(shape, name):
+    nx, ny = shape
+    prm = workloads.droplet64()
+    prm.update(xc=(nx - 1) / 2, yc=(ny - 1) / 2, R=min(nx, ny) / 4, Kq=0.05,
+               psi_anode=0.7, psi_cathode=-0.2, sweeps_min=1, sweeps_max=6,
+               sweep_tol=1e-6, init_sweeps_max=300)
+    prm.update(VARIANTS[name])
+    got, ref, *_ = run_pair(nx, ny, prm, 25)
+    assert_close(field_errors(got, ref), FP64_TOL)
+
+
+# ---- FP32: the oracle-sized copy of the 2048^2 case -------------------------------
+
+def test_fp32_droplet256_matches_oracle():
+    n, steps = 256, 100
+    got, ref, *_ = run_pair(n, n, workloads.droplet(n), steps, precision=ehdlb.FP32)
+    err = field_errors(got, ref)
+    assert_close(err, FP32_TOL, keys=["phi", "u", "psi", "q"])
+
+
+def test_fp64_droplet256_matches_oracle():
+    n, steps = 256, 20
+    got, ref, *_ = run_pair(n, n, workloads.droplet(n), steps, precision=ehdlb.FP64)
+    assert_close(field_errors(got, ref), FP64_TOL)
+
+
+@pytest.mark.slow
+def test_fp32_droplet2048_full_size_matches_oracle():
+    # the launch configuration the benchmark times, two steps from t = 0
+    n, steps = 2048, 2
+    got, ref, *_ = run_pair(n, n, workloads.droplet(n), steps, precision=ehdlb.FP32)
+    err = field_errors(got, ref)
+    assert_close(err, FP32_TOL, keys=["phi", "u", "psi", "q"])
+
+
+# ---- invariants, determinism, checkpoints, errors --------------------------------------
+
+def test_sum_phi_conserved_on_the_gpu():
+    lat = ehdlb.Lattice(64, 64, workloads.droplet64(), precision=ehdlb.FP64)
+    _, s0 = lat.step(1)
+    _, s1 = lat.step(300)
+    assert abs(s1.sum_phi - s0.sum_phi) <= 1e-13 * s0.sum_phi
+    lat32 = ehdlb.Lattice(256, 256, workloads.droplet(256), precision=ehdlb.FP32)
+    _, a = lat32.step(1)
+    _, b = lat32.step(300)
+    assert abs(b.sum_phi - a.sum_phi) <= 1e-5 * a.sum_phi
+
+
+def test_runs_are_bitwise_repeatable_and_state_round_trips():
+    prm = workloads.droplet(128)
+    a = ehdlb.Lattice(128, 128, prm, precision=ehdlb.FP32)
+    a.step(10)
+    saved = a.state()
+    a.step(10)
+    fa = a.fields()
+    b = ehdlb.Lattice(128, 128, prm, precision=ehdlb.FP32)
+    b.step(20)
+    fb = b.fields()
+    c = ehdlb.Lattice(128, 128, prm, precision=ehdlb.FP32)
+    c.set_state(saved)
+    c.step(10)
+    fc = c.fields()
+    for k in ehdlb.FIELDS:
+        assert np.array_equal(fa[k], fb[k]), k
+        assert np.array_equal(fa[k], fc[k]), k
+
+
+def test_oracle_state_imported_steps_identically():
+    prm = workloads.droplet64()
+    prm.update(sweeps_min=10, sweeps_max=10)
+    orc = oracle.Oracle(64, 64, prm)
+    orc.step(30)
+    s = orc.state()
+    lat = ehdlb.Lattice(64, 64, dict(prm, init_sweeps_fixed=0), precision=ehdlb.FP64)
+    lat.set_state(s)
+    orc.step(15)
+    lat.step(15)
+    assert_close(field_errors(lat.fields(), orc.fields()), FP64_TOL)
+
+
+def test_error_codes():
+    L = ehdlb.lib()
+    h = ehdlb.ehdlb_create(16, 16, ehdlb.FP32)
+    st = ehdlb.ehdlb_stats()
+    assert L.ehdlb_step(h, 1, ehdlb.C.byref(st)) == ehdlb.ESTATE
+    bad = ehdlb.ehdlb_params_default(dict(tau_f=0.5))
+    assert L.ehdlb_set_params(h, ehdlb.C.byref(bad)) == ehdlb.EINVAL
+    assert "tau_f" in ehdlb.ehdlb_last_error(h)
+    bad = ehdlb.ehdlb_params_default(dict(sweeps_min=5, sweeps_max=2))
+    assert L.ehdlb_set_params(h, ehdlb.C.byref(bad)) == ehdlb.EINVAL
+    good = ehdlb.ehdlb_params_default(dict(xc=7.5, yc=7.5, R=4.0, sweeps_min=0, sweeps_max=1,
+                                           sweep_tol=0.0, init_sweeps_max=10))
+    assert L.ehdlb_set_params(h, ehdlb.C.byref(good)) == ehdlb.OK
+    assert L.ehdlb_step(h, 2, ehdlb.C.byref(st)) == ehdlb.WNOTCONV
+    assert st.not_converged == 2
+    out = np.zeros(16 * 16)
+    assert L.ehdlb_get_fields(h, 1 << 12, ehdlb._dp(out), out.size) == ehdlb.EINVAL
+    assert L.ehdlb_get_fields(h, 3, ehdlb._dp(out), out.size) == ehdlb.EINVAL   # too small
+    # a NaN injected into the host-side state is reported, not propagated silently
+    s = np.zeros(ehdlb.ehdlb_state_len(h))
+    ehdlb.ehdlb_get_state(h, s)
+    s[35 * 100 + 9] = np.nan
+    ehdlb.ehdlb_set_state(h, s)
+    assert L.ehdlb_step(h, 1, ehdlb.C.byref(st)) == ehdlb.EUNSTABLE
+    ehdlb.ehdlb_destroy(h)
