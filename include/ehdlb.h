@@ -81,6 +81,9 @@ typedef struct ehdlb_params {
     double W;            /* interface thickness, > 0 */
     double W_init;       /* thickness of the initial profile (<= 0: W) */
     double M_phi;        /* Allen-Cahn mobility, > 0 */
+    double nhat_eps;     /* interface normal of Eq. 32 taken as grad phi /
+                            sqrt(|grad phi|^2 + nhat_eps^2); 0: the printed
+                            grad phi / |grad phi| (0 below |grad phi| 1e-12) */
     /* initial droplet: phi = (1 + tanh(2 (R - r) / W_init)) / 2 */
     double xc, yc, R;    /* centre and radius; for the slab, half-width */
     int init_shape;      /* 0 disc, 1 horizontal slab |y - yc| < R */
@@ -134,6 +137,7 @@ typedef struct ehdlb_stats {
     double ms_prep, ms_sweeps, ms_main;  /* device time per kernel class when
                                             timing is on (ehdlb_set_timing) */
     long long launches;       /* kernels launched by the call */
+    long long sweep_launches; /* of which potential-sweep kernels */
 } ehdlb_stats;
 
 /* ABI version of the loaded library (EHDLB_ABI_VERSION). */

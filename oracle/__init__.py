@@ -26,7 +26,7 @@ STATE_PER_NODE = 35  # f9 h9 p5 n5 g5 phiu2
 _PARAM_FIELDS = [
     ("tau_f", C.c_double), ("rho_ratio", C.c_double), ("eta_ratio", C.c_double),
     ("sigma", C.c_double), ("W", C.c_double), ("W_init", C.c_double),
-    ("M_phi", C.c_double),
+    ("M_phi", C.c_double), ("nhat_eps", C.c_double),
     ("xc", C.c_double), ("yc", C.c_double), ("R", C.c_double),
     ("init_shape", C.c_int),
     ("D", C.c_double), ("mu_v", C.c_double), ("mu_r", C.c_double),
@@ -53,7 +53,7 @@ class OrcParams(C.Structure):
 
 DEFAULTS = dict(
     tau_f=0.8, rho_ratio=1.0, eta_ratio=1.0, sigma=0.01, W=4.0, W_init=0.0,
-    M_phi=0.02, xc=31.5, yc=31.5, R=12.0, init_shape=0, D=0.01, mu_v=1.0,
+    M_phi=0.02, nhat_eps=1e-3, xc=31.5, yc=31.5, R=12.0, init_shape=0, D=0.01, mu_v=1.0,
     mu_r=1.0, m=1.0, k_d=1.0, k_r=1.0, onsager_cb=1.0, onsager_form=0,
     ion_bc=0, einstein_D=1, ion_L_term=1, c_init_scale=1.0, c0=1.0, eps_r=2.0,
     Kq=5.6893 / 64**2, vartheta=0.3, psi_src_literal=0, psi_anode=1.0, psi_cathode=0.0,
@@ -102,7 +102,7 @@ def lib():
         L.orc_feq.argtypes = [C.c_double] * 4 + [dp]
         L.orc_forcing_f.argtypes = [C.c_double] * 6 + [dp]
         L.orc_heq.argtypes = [C.c_double] * 3 + [dp]
-        L.orc_Hsrc.argtypes = [C.c_double] * 6 + [dp]
+        L.orc_Hsrc.argtypes = [C.c_double] * 7 + [dp]
         L.orc_ion_eq.argtypes = [C.c_double] * 3 + [dp]
         L.orc_geq.argtypes = [C.c_double, dp]
         L.orc_mrt.argtypes = [C.c_int, dp, dp, dp, dp, dp]
@@ -222,8 +222,8 @@ def heq(phi, ux, uy):
     o = np.zeros(9); lib().orc_heq(phi, ux, uy, _dp(o)); return o
 
 
-def Hsrc(phi, W, dpux, dpuy, gx, gy):
-    o = np.zeros(9); lib().orc_Hsrc(phi, W, dpux, dpuy, gx, gy, _dp(o)); return o
+def Hsrc(phi, W, dpux, dpuy, gx, gy, eps=0.0):
+    o = np.zeros(9); lib().orc_Hsrc(phi, W, dpux, dpuy, gx, gy, eps, _dp(o)); return o
 
 
 def ion_eq(c, ux, uy):

@@ -37,7 +37,12 @@
  *    there, the one it attracts has zero gradient (Eq. 64) -- both by
  *    anti-bounce-back, the latter with the wall value taken from the node;
  *  - sweep residual: ||psi^k - psi^(k-1)||_2 / ||psi^k||_2 over all nodes;
- *  - n_hat = 0 where |grad phi| < 1e-12; (phi u)(t - 1) = 0 at t = 0.
+ *  - the normal of Eq. 32 is grad phi / sqrt(|grad phi|^2 + nhat_eps^2):
+ *    printed as grad phi / |grad phi|, it has unbounded gain where phi
+ *    overshoots 1 (lambda != 0) yet |grad phi| ~ 0, which makes the step
+ *    chaotic at round-off level; nhat_eps = 0 keeps the printed form (with
+ *    n_hat = 0 where |grad phi| < 1e-12);
+ *  - (phi u)(t - 1) = 0 at t = 0.
  */
 #include "ehd_oracle.h"
 
@@ -208,13 +213,19 @@ void orc_heq(double phi, double ux, double uy, double *out)
         out[i] = w9[i] * phi * (1.0 + (cx9[i] * ux + cy9[i] * uy) / cs2);
 }
 
-/* Eq. 32 with lambda of Eq. 2; (gx, gy) = grad phi */
+/* Eq. 32 with lambda of Eq. 2; (gx, gy) = grad phi.  eps > 0: the normal is
+ * grad phi / sqrt(|grad phi|^2 + eps^2); eps = 0: grad phi / |grad phi|, and
+ * 0 where |grad phi| < 1e-12. */
 void orc_Hsrc(double phi, double W, double dphiux, double dphiuy, double gx,
-              double gy, double *out)
+              double gy, double eps, double *out)
 {
     double mag = sqrt(gx * gx + gy * gy);
     double nx = 0.0, ny = 0.0;
-    if (mag >= 1e-12) {
+    if (eps > 0.0) {
+        double den = sqrt(gx * gx + gy * gy + eps * eps);
+        nx = gx / den;
+        ny = gy / den;
+    } else if (mag >= 1e-12) {
         nx = gx / mag;
         ny = gy / mag;
     }
@@ -734,7 +745,7 @@ static int step_once(orc_ctx *c, int forced, int *used, double *resid)
         double dpuy = phi * uy - c->phiu_prev[2 * k + 1];
         double heq[9], Hi[9];
         orc_heq(phi, ux, uy, heq);
-        orc_Hsrc(phi, P->W, dpux, dpuy, gx, gy, Hi);
+        orc_Hsrc(phi, P->W, dpux, dpuy, gx, gy, P->nhat_eps, Hi);
         for (int i = 0; i < 9; ++i) d9[i] = h[i] - heq[i];
         msm(9, sh, d9, a9);
         msm_half(9, sh, Hi, b9);
@@ -888,7 +899,7 @@ void orc_params_from_physical(orc_params *P, int nx, int ny, double d_mm,
 {
     memset(P, 0, sizeof *P);
     P->tau_f = 0.8; P->rho_ratio = 1.0; P->eta_ratio = 1.0;
-    P->sigma = 0.01; P->W = 4.0; P->W_init = 0.0; P->M_phi = 0.02;
+    P->sigma = 0.01; P->W = 4.0; P->W_init = 0.0; P->M_phi = 0.02; P->nhat_eps = 1e-3;
     P->xc = 0.5 * (nx - 1); P->yc = 0.5 * (ny - 1); P->R = nx / 5.0;
     P->D = 0.01; P->mu_v = 1.0; P->mu_r = mu_r; P->m = 1.0;
     P->k_d = 1.0; P->k_r = 1.0;

@@ -37,6 +37,7 @@ typedef struct orc_params {
     double W;            /* interface thickness */
     double W_init;       /* width of the initial tanh profile (<= 0: W) */
     double M_phi;        /* Allen-Cahn mobility (Eq. 30) */
+    double nhat_eps;     /* regularisation of the normal in Eq. 32 (0: none) */
     /* initial droplet / slab */
     double xc, yc, R;    /* centre and radius (slab: half-width) */
     int init_shape;      /* 0 disc, 1 horizontal slab |y - yc| < R */
@@ -105,7 +106,7 @@ void orc_forcing_f(double ux, double uy, double Fx, double Fy,
                    double grx, double gry, double *out9);
 void orc_heq(double phi, double ux, double uy, double *out9);
 void orc_Hsrc(double phi, double W, double dphiux, double dphiuy,
-              double gx, double gy, double *out9);
+              double gx, double gy, double eps, double *out9);
 void orc_ion_eq(double c, double ux, double uy, double *out5);
 void orc_geq(double psi, double *out5);
 /* One MRT collision x* = x - Minv S M (x - xeq) + Minv (I - S/2) M src,

@@ -33,7 +33,7 @@ def nvcc() -> str:
 
 
 def _inputs():
-    files = [os.path.join(CSRC, s) for s in SOURCES]
+    files = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.abspath(__file__)]
     files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     files.append(os.path.join(INCLUDE, "ehdlb.h"))
     return files
@@ -46,9 +46,15 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
+# The double-precision solver exists to agree with the FP64 oracle; like the
+# oracle (gcc -ffp-contract=off) it rounds every product and sum separately.
+PER_SOURCE = {"solver_fp64.cu": ["-fmad=false"]}
+
+
 def _compile(src: str, extra: list[str]) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    cmd = [nvcc(), *ARCH, *FLAGS, *PER_SOURCE.get(src, []), *extra, "-c",
+           os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

@@ -28,7 +28,7 @@ int fail(ehdlb_ctx *c, int status, const std::string &msg)
 
 bool finite_all(const ehdlb_params *p)
 {
-    const double v[] = {p->tau_f, p->rho_ratio, p->eta_ratio, p->sigma, p->W, p->W_init, p->M_phi,
+    const double v[] = {p->tau_f, p->rho_ratio, p->eta_ratio, p->sigma, p->W, p->W_init, p->M_phi, p->nhat_eps,
                         p->xc, p->yc, p->R, p->D, p->mu_v, p->mu_r, p->m, p->k_d, p->k_r,
                         p->onsager_cb, p->c_init_scale, p->c0, p->eps_r, p->Kq, p->vartheta,
                         p->psi_anode, p->psi_cathode, p->sweep_tol, p->E_frozen_x, p->E_frozen_y,
@@ -50,6 +50,7 @@ std::string validate(const ehdlb_params *p)
     if (!(p->W > 0.0)) return "W must be > 0";
     if (!(p->M_phi > 0.0)) return "M_phi must be > 0 (tau_h > 0.5)";
     if (!(p->sigma >= 0.0)) return "sigma must be >= 0";
+    if (!(p->nhat_eps >= 0.0)) return "nhat_eps must be >= 0";
     if (!(p->D > 0.0)) return "D must be > 0 (ion tau > 0.5)";
     if (!(p->mu_v > 0.0) || !(p->mu_r > 0.0) || !(p->m > 0.0)) return "mobilities must be > 0";
     if (!(p->k_d >= 0.0) || !(p->k_r >= 0.0)) return "k_d and k_r must be >= 0";
@@ -80,7 +81,7 @@ int ehdlb_params_default(ehdlb_params *p)
     std::memset(p, 0, sizeof *p);
     p->size = sizeof *p;
     p->tau_f = 0.8; p->rho_ratio = 1.0; p->eta_ratio = 1.0;
-    p->sigma = 0.01; p->W = 4.0; p->W_init = 0.0; p->M_phi = 0.02;
+    p->sigma = 0.01; p->W = 4.0; p->W_init = 0.0; p->M_phi = 0.02; p->nhat_eps = 1e-3;
     p->xc = 31.5; p->yc = 31.5; p->R = 12.0; p->init_shape = 0;
     p->D = 0.01; p->mu_v = 1.0; p->mu_r = 1.0; p->m = 1.0;
     p->k_d = 1.0; p->k_r = 1.0; p->onsager_cb = 1.0;

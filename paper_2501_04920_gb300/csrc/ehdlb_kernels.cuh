@@ -56,6 +56,7 @@ template <typename T> struct DevP {
     T psi_a, psi_c, G, wG;         // electrodes; G = (psi_c - psi_a) / ny, wG = G / 6
     T rho1, eta_v, eta1;           // rho_r - 1, eta_v, eta_r - 1
     T beta, kappa, W, tau_h;       // Eq. 13, Eq. 30
+    T nhat_eps2;                   // regularisation of the normal of Eq. 32 (squared)
     T mu_v, mu1, m, D;             // ions
     T k_d, k_r, cb;
     T s_free;
@@ -67,6 +68,7 @@ struct Control {
     int cur0;          // g buffer that holds the state at the start of the step
     int done;          // converge mode: no further sweeps this step
     int K;             // sweeps taken by this step
+    int flips;         // g buffer swaps of this step (state after it: cur0 + flips)
     int kmin, kmax;
     int early;         // stopped on the residual; r_last already set
     int unstable;      // NaN or Inf seen
@@ -119,9 +121,10 @@ template <typename T> __device__ __forceinline__ T psi_lin(const DevP<T> &P, int
     return P.psi_a + P.G * (T(y) + T(0.5));
 }
 
-// Deterministic block sum of NV doubles (fixed tree order), written by
-// thread 0 to out[NV * block].  blockDim must be a multiple of 32, <= 1024.
-template <int NV> __device__ __forceinline__ void block_sum_store(double (&v)[NV], double *out)
+// Deterministic block sum of NV values (fixed tree order), written by thread
+// 0 to out[NV * block].  Each warp sums in T; the warp sums are added in
+// double.  blockDim must be a multiple of 32, <= 1024.
+template <typename T, int NV> __device__ __forceinline__ void block_sum_store(T (&v)[NV], double *out)
 {
     __shared__ double red[32][NV];
     const int lane = (threadIdx.x + threadIdx.y * blockDim.x) & 31;
@@ -129,10 +132,10 @@ template <int NV> __device__ __forceinline__ void block_sum_store(double (&v)[NV
     const int nwarp = (blockDim.x * blockDim.y) >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        double s = v[k];
+        T s = v[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) red[warp][k] = s;
+        if (lane == 0) red[warp][k] = (double)s;
     }
     __syncthreads();
     if (warp == 0) {
@@ -211,15 +214,15 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_prep(const DevP<T> P, const T *__restrict__ h,
                                               const T *__restrict__ p, const T *__restrict__ n,
                                               T *__restrict__ phig, T *__restrict__ q,
-                                              Control *ctl, int fixedK, int kmin, int kmax)
+                                              Control *ctl, int fixedK, int kmin, int kmax, int flips)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
         if (fixedK >= 0) {
-            ctl->K = fixedK; ctl->done = 1; ctl->converge = 0;
+            ctl->K = fixedK; ctl->flips = flips; ctl->done = 1; ctl->converge = 0;
         } else {
-            ctl->K = 0; ctl->done = (kmax <= 0); ctl->converge = 1;
+            ctl->K = 0; ctl->flips = 0; ctl->done = (kmax <= 0); ctl->converge = 1;
         }
         ctl->kmin = kmin; ctl->kmax = kmax; ctl->early = 0; ctl->r_last = nan("");
     }
@@ -297,7 +300,144 @@ __global__ void __launch_bounds__(256) k_sweep(const DevP<T> P, T *__restrict__ 
         if (y > 0) dst[3 * nn + k - nx] = o4 + P.wG;
         else dst[nn + k] = -o4 - P.wG;              // anode: ABB to psi_a
     }
-    if (RESID) block_sum_store<2>(red, part);
+    if (RESID) block_sum_store<double, 2>(red, part);
+}
+
+// NSW potential sweeps (Eq. 44-50) fused in shared memory.  A block holds a
+// 64 x RH region of the lattice: its output tile of (64 - 2 NSW) x
+// (RH - 2 NSW) nodes plus a halo NSW nodes wide (x periodic; rows outside the
+// lattice stay empty, the electrode rules act on the wall links).  Every
+// sweep collides and pushes the whole region; values at distance < s from
+// the region edge are incomplete after sweep s, so after NSW sweeps the
+// output tile is exact.  The source coefficients of each node, from phi and
+// q, are computed once:  X/3 = A - Bx m1 - By m2 with m1, m2 the first
+// moments (E = 3 m / tau_g), A = th Kq q / (3 eps), B = th (eps_r - 1)
+// grad phi / (tau_g eps), th = vartheta (times 1/(1 - w0)).
+//   RESID: the last sweep of the step; residual partials of the output tile.
+// Launch: blockDim (32, 8), dynamic shared memory tb_smem_bytes<T, RH>().
+template <typename T, int RH> __host__ __device__ constexpr size_t tb_smem_bytes()
+{
+    return sizeof(T) * 11 * (size_t)RH * 64;
+}
+
+template <typename T, int NSW, int RH, bool RESID>
+__global__ void __launch_bounds__(256) k_sweep_tb(const DevP<T> P, T *__restrict__ gA, T *__restrict__ gB,
+                                                  const T *__restrict__ phig, const T *__restrict__ q,
+                                                  double *__restrict__ part, const Control *__restrict__ ctl,
+                                                  int m)
+{
+    constexpr int RW = 64, H = NSW, TX = RW - 2 * H, TY = RH - 2 * H, PL = RH * RW;
+    constexpr int NB = RW / 32, NA = RH / 8;
+    static_assert(TX > 0 && TY > 0, "tile too small for NSW");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sg = reinterpret_cast<T *>(smem_raw);   // [2][4][RH][RW]
+    T *sc = sg + 8 * PL;                        // [3][RH][RW]
+    const int par = (ctl->cur0 + m) & 1;
+    const T *__restrict__ src = par ? gB : gA;
+    T *__restrict__ dst = par ? gA : gB;
+    const int nx = P.nx, ny = P.ny;
+    const long long nn = P.nn;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+
+    // ---- load the region and its source coefficients ----
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const int ly = ty + 8 * a, gy = y0 - H + ly;
+        if (gy < 0 || gy >= ny) continue;
+        const T *r0 = phig + (long long)gy * nx, *r1 = r0 + nx, *r2 = r1 + nx;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int lx = tx + 32 * b;
+            int gx = x0 - H + lx;
+            gx = ((gx % nx) + nx) % nx;
+            const long long k = (long long)gy * nx + gx;
+            const int li = ly * RW + lx;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) sg[i * PL + li] = src[i * nn + k];
+            const int xm = wrapx(gx - 1, nx), xp = wrapx(gx + 1, nx);
+            const T phi = r1[gx];
+            const T gxs = (r1[xp] - r1[xm]) * T(1.0 / 3.0) +
+                          ((r2[xp] - r2[xm]) + (r0[xp] - r0[xm])) * T(1.0 / 12.0);
+            const T gys = (r2[gx] - r0[gx]) * T(1.0 / 3.0) +
+                          ((r2[xp] + r2[xm]) - (r0[xp] + r0[xm])) * T(1.0 / 12.0);
+            const T inv = T(1) / (T(1) + P.er1 * phi);
+            const T bb = P.src_norm * P.er1 * inv / P.tau_g;
+            sc[li] = P.src_norm * P.Kq * q[k] * inv * T(1.0 / 3.0);
+            sc[PL + li] = bb * gxs;
+            sc[2 * PL + li] = bb * gys;
+        }
+    }
+    __syncthreads();
+
+    T psi_before[NA][NB];
+#pragma unroll
+    for (int s = 0; s < NSW; ++s) {
+        const T *gc = sg + (s & 1) * 4 * PL;
+        T *gn = sg + ((s + 1) & 1) * 4 * PL;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            const int ly = ty + 8 * a, gy = y0 - H + ly;
+            if (gy < 0 || gy >= ny) continue;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const int lx = tx + 32 * b, li = ly * RW + lx;
+                const T g1 = gc[li], g2 = gc[PL + li], g3 = gc[2 * PL + li], g4 = gc[3 * PL + li];
+                const T psit = T(1.5) * ((g1 + g3) + (g2 + g4));
+                if (RESID && s == NSW - 1) psi_before[a][b] = psit;
+                const T m1 = g1 - g3, m2 = g2 - g4, m3 = g1 + g3, m4 = g2 + g4;
+                const T X3 = sc[li] - sc[PL + li] * m1 - sc[2 * PL + li] * m2;
+                const T eq = psit * T(1.0 / 3.0);
+                const T n1 = (T(1) - P.s_g) * m1, n2 = (T(1) - P.s_g) * m2;
+                const T n3 = m3 - P.s_free_g * (m3 - eq) + X3;
+                const T n4 = m4 - P.s_free_g * (m4 - eq) + X3;
+                const T o1 = T(0.5) * (n3 + n1), o3 = T(0.5) * (n3 - n1);
+                const T o2 = T(0.5) * (n4 + n2), o4 = T(0.5) * (n4 - n2);
+                if (lx + 1 < RW) gn[li + 1] = o1;
+                if (lx > 0) gn[2 * PL + li - 1] = o3;
+                if (gy + 1 < ny) {
+                    if (ly + 1 < RH) gn[PL + li + RW] = o2 - P.wG;
+                } else {
+                    gn[3 * PL + li] = -o2 + P.wG;      // cathode: ABB to psi_c
+                }
+                if (gy > 0) {
+                    if (ly > 0) gn[3 * PL + li - RW] = o4 + P.wG;
+                } else {
+                    gn[PL + li] = -o4 - P.wG;          // anode: ABB to psi_a
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- store the output tile ----
+    const T *gf = sg + (NSW & 1) * 4 * PL;
+    T red[2] = {T(0), T(0)};
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const int ly = ty + 8 * a, gy = y0 - H + ly;
+        if (ly < H || ly >= H + TY || gy >= ny) continue;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int lx = tx + 32 * b, gx = x0 - H + lx;
+            if (lx < H || lx >= H + TX || gx >= nx) continue;
+            const int li = ly * RW + lx;
+            const long long k = (long long)gy * nx + gx;
+            const T g1 = gf[li], g2 = gf[PL + li], g3 = gf[2 * PL + li], g4 = gf[3 * PL + li];
+            dst[k] = g1;
+            dst[nn + k] = g2;
+            dst[2 * nn + k] = g3;
+            dst[3 * nn + k] = g4;
+            if (RESID) {
+                const T psit = T(1.5) * ((g1 + g3) + (g2 + g4));
+                const T d = psit - psi_before[a][b];
+                const T ps = psit + psi_lin(P, gy);
+                red[0] += d * d;
+                red[1] += ps * ps;
+            }
+        }
+    }
+    if (RESID) block_sum_store<T, 2>(red, part);
 }
 
 // Converge mode, after sweep j (one block of 256): r_{j-1} from the partials
@@ -312,29 +452,33 @@ static __global__ void __launch_bounds__(256) k_sweep_decide(const double *__res
     if (j >= 2) {
         const double r = tot[1] > 0.0 ? sqrt(tot[0] / tot[1]) : sqrt(tot[0]);
         if (j - 1 >= ctl->kmin && r < ctl->tol) {
-            ctl->K = j - 1; ctl->done = 1; ctl->early = 1; ctl->r_last = r;
+            ctl->K = j - 1; ctl->flips = j - 1; ctl->done = 1; ctl->early = 1; ctl->r_last = r;
             return;
         }
     }
     ctl->K = j;
+    ctl->flips = j;
     if (j >= ctl->kmax) ctl->done = 1;
 }
 
 // The rest of the step at every node (O5-O11): reaction (Eq. 42-43), forces
 // (Eq. 12-14), u and p (Eq. 56-57), MRT collisions of f (Eq. 51), h (Eq. 27),
 // p and n (Eq. 34-35), push with the wall rules (Eq. 64).
-//   SNAP  : write the macroscopic snapshot.   FROZEN: E from DevP.
+//   SNAP  : write the macroscopic snapshot and its sums of phi and q.
+//   FROZEN: E from DevP.
 //   RESID : residual of the last sweep against psi_prev.
+// NaN or Inf in the macroscopic fields raises *unstable.
 template <typename T, bool SNAP, bool FROZEN, bool RESID>
 __global__ void __launch_bounds__(256, 2) k_main(const DevP<T> P, const Pops<T> src, const Pops<T> dst,
                                                  const T *__restrict__ gA, const T *__restrict__ gB,
                                                  const Control *__restrict__ ctl, const T *__restrict__ phig,
                                                  T *__restrict__ phiu, const T *__restrict__ psi_prev,
-                                                 T *__restrict__ snap, double *__restrict__ part)
+                                                 T *__restrict__ snap, double *__restrict__ part,
+                                                 int *__restrict__ unstable)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    double red[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    T red[4] = {T(0), T(0), T(0), T(0)};
     if (x < P.nx && y < P.ny) {
         const int nx = P.nx, ny = P.ny;
         const long long nn = P.nn, k = (long long)y * nx + x;
@@ -361,8 +505,7 @@ __global__ void __launch_bounds__(256, 2) k_main(const DevP<T> P, const Pops<T> 
         const T dex = P.er1 * gx, dey = P.er1 * gy;
 
         // ---- O4 result: psi, E from the last sweep (Eq. 49-50) ----
-        const int K = ctl->K;
-        const T *__restrict__ g = ((ctl->cur0 + K) & 1) ? gB : gA;
+        const T *__restrict__ g = ((ctl->cur0 + ctl->flips) & 1) ? gB : gA;
         const T g1 = g[k], g2 = g[nn + k], g3 = g[2 * nn + k], g4 = g[3 * nn + k];
         const T psit = T(1.5) * ((g1 + g3) + (g2 + g4));
         const T psi = psit + psi_lin(P, y);
@@ -370,9 +513,9 @@ __global__ void __launch_bounds__(256, 2) k_main(const DevP<T> P, const Pops<T> 
         if (FROZEN) { Ex = P.Ex_frozen; Ey = P.Ey_frozen; }
         else { Ex = T(3) * (g1 - g3) / P.tau_g; Ey = T(3) * (g2 - g4) / P.tau_g; }
         if (RESID) {
-            const double d = (double)psit - (double)psi_prev[k];
+            const T d = psit - psi_prev[k];
             red[2] = d * d;
-            red[3] = (double)psi * (double)psi;
+            red[3] = psi * psi;
         }
 
         // ---- O5: Onsager dissociation and the implicit reaction (Eq. 5, 42-43) ----
@@ -464,9 +607,16 @@ __global__ void __launch_bounds__(256, 2) k_main(const DevP<T> P, const Pops<T> 
             const T dpx = pux - phiu[k], dpy = puy - phiu[nn + k];
             phiu[k] = pux;
             phiu[nn + k] = puy;
-            const T mag = dsqrt<T>(gx * gx + gy * gy);
+            // normal of Eq. 32, regularised: grad phi / sqrt(|grad phi|^2 + eps^2)
+            const T g2 = gx * gx + gy * gy;
             T nhx = T(0), nhy = T(0);
-            if (mag >= T(1e-12)) { nhx = gx / mag; nhy = gy / mag; }
+            if (P.nhat_eps2 > T(0)) {
+                const T den = dsqrt<T>(g2 + P.nhat_eps2);
+                nhx = gx / den; nhy = gy / den;
+            } else {
+                const T mag = dsqrt<T>(g2);
+                if (mag >= T(1e-12)) { nhx = gx / mag; nhy = gy / mag; }
+            }
             const T lam = T(4) * phi * (T(1) - phi) / P.W;
             const T Vx = dpx + third * lam * nhx, Vy = dpy + third * lam * nhy;
             T d[9], Hi[9], md[9], mH[9], mc[9], dl[9];
@@ -567,21 +717,33 @@ __global__ void __launch_bounds__(256, 2) k_main(const DevP<T> P, const Pops<T> 
             snap[8 * nn + k] = cm;
             snap[9 * nn + k] = q;
         }
-        red[0] = (double)phi;
-        red[1] = (double)q;
+        if (SNAP) {
+            red[0] = phi;
+            red[1] = q;
+        }
         const T chk = ux + uy + pr + psi + cp + cm;
-        red[4] = isfinite((double)chk) ? 0.0 : 1.0;
+        if (!isfinite(chk)) *unstable = 1;
     }
-    block_sum_store<5>(red, part);
+    if (SNAP || RESID) block_sum_store<T, 4>(red, part);
 }
 
-// End of step (one block of 256): global sums of the main kernel, the step's
-// residual, counters, the next step's g parity.
+// End of step (one block of 256): global sums of the main kernel (when it
+// reduced), the step's residual, counters, the next step's g parity.
+//   resid: 0 none; 1 from the main kernel's partials (columns 2, 3 of 4);
+//          2 from the fused sweep kernel's partials (2 per block in part2).
 static __global__ void __launch_bounds__(256) k_step_end(const double *__restrict__ part, long long nb,
-                                                  Control *ctl, int *counts, int resid)
+                                                         const double *__restrict__ part2, long long nb2,
+                                                         Control *ctl, int *counts, int resid, int sums)
 {
-    double tot[5];
-    sum_partials<5>(part, nb, tot);
+    double tot[4] = {0.0, 0.0, 0.0, 0.0};
+    if (resid == 1 || sums) sum_partials<4>(part, nb, tot);
+    if (resid == 2) {
+        __syncthreads();
+        double t2[2];
+        sum_partials<2>(part2, nb2, t2);
+        tot[2] = t2[0];
+        tot[3] = t2[1];
+    }
     if (threadIdx.x != 0) return;
     const int K = ctl->K;
     double r = ctl->r_last;
@@ -590,14 +752,15 @@ static __global__ void __launch_bounds__(256) k_step_end(const double *__restric
         else r = nan("");
     }
     ctl->r_step = r;
-    ctl->sum_phi = tot[0];
-    ctl->sum_q = tot[1];
-    if (tot[4] > 0.0) ctl->unstable = 1;
+    if (sums) {
+        ctl->sum_phi = tot[0];
+        ctl->sum_q = tot[1];
+    }
     if (counts) counts[ctl->tloc] = K;
     ctl->sweeps_total += K;
     if (K > ctl->sweeps_max) ctl->sweeps_max = K;
     if (ctl->converge && ctl->kmax > ctl->kmin && K >= ctl->kmax && !(r < ctl->tol)) ctl->notconv += 1;
-    ctl->cur0 = (ctl->cur0 + K) & 1;
+    ctl->cur0 = (ctl->cur0 + ctl->flips) & 1;
     ctl->t += 1;
     ctl->tloc += 1;
 }
@@ -646,7 +809,7 @@ __global__ void __launch_bounds__(256) k_init_ions(const DevP<T> P, Pops<T> pops
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
     const long long nn = P.nn, k = (long long)y * P.nx + x;
-    const T *__restrict__ g = ((ctl->cur0 + ctl->K) & 1) ? gB : gA;
+    const T *__restrict__ g = ((ctl->cur0 + ctl->flips) & 1) ? gB : gA;
     const T g1 = g[k], g2 = g[nn + k], g3 = g[2 * nn + k], g4 = g[3 * nn + k];
     const T psi = T(1.5) * ((g1 + g3) + (g2 + g4)) + psi_lin(P, y);
     T Ex, Ey;

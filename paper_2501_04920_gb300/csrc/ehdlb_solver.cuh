@@ -62,8 +62,23 @@ template <typename T> class Solver : public SolverBase {
         EHDLB_CK(alloc((void **)&phiu_, plane * 2));
         EHDLB_CK(alloc((void **)&psi_prev_, plane));
         EHDLB_CK(alloc((void **)&snap_, plane * EHDLB_NFIELDS));
-        EHDLB_CK(alloc((void **)&part_, sizeof(double) * 5 * (size_t)nb_));
+        EHDLB_CK(alloc((void **)&part_, sizeof(double) * 4 * (size_t)nb_));
         EHDLB_CK(alloc((void **)&ctl_, sizeof(Control)));
+        {
+            long long nbmax = 0;
+            for (int nsw = 1; nsw <= TB_MAX; ++nsw) {
+                const dim3 g = tb_grid(nsw, nx_, ny_);
+                nbmax = std::max(nbmax, (long long)g.x * g.y);
+            }
+            EHDLB_CK(alloc((void **)&part2_, sizeof(double) * 2 * (size_t)nbmax));
+        }
+        EHDLB_CK(tb_attr<1>());
+        EHDLB_CK(tb_attr<2>());
+        if constexpr (TB_MAX >= 5) {
+            EHDLB_CK(tb_attr<3>());
+            EHDLB_CK(tb_attr<4>());
+            EHDLB_CK(tb_attr<5>());
+        }
         EHDLB_CK(alloc((void **)&stage_, sizeof(double) * (size_t)nn_));
         EHDLB_CK(cudaMemsetAsync(snap_, 0, plane * EHDLB_NFIELDS, stream_));
         EHDLB_CK(cudaStreamSynchronize(stream_));
@@ -87,12 +102,12 @@ template <typename T> class Solver : public SolverBase {
         EHDLB_CK(cudaGetLastError());
         // initial potential solve with q = 0 (p = n = 0 at this point)
         if (p.freeze_E) {
-            launch_prep(0, 0, 0, 0);
+            launch_prep(0, 0, 0, 0, 0);
         } else if (p.init_sweeps_fixed >= 0) {
-            launch_prep(0, p.init_sweeps_fixed, p.init_sweeps_fixed, p.init_sweeps_fixed);
+            launch_prep(0, p.init_sweeps_fixed, p.init_sweeps_fixed, p.init_sweeps_fixed, p.init_sweeps_fixed);
             for (int j = 1; j <= p.init_sweeps_fixed; ++j) launch_sweep(j, false, false, false);
         } else {
-            launch_prep(0, -1, 0, p.init_sweeps_max);
+            launch_prep(0, -1, 0, p.init_sweeps_max, 0);
             const int chunk = 256;
             for (int j0 = 1; j0 <= p.init_sweeps_max; j0 += chunk) {
                 const int j1 = std::min(p.init_sweeps_max, j0 + chunk - 1);
@@ -114,7 +129,7 @@ template <typename T> class Solver : public SolverBase {
         EHDLB_CK(cudaStreamSynchronize(stream_));
         init_sweeps_ = ctl_h_.K;
         c = Control{};
-        c.cur0 = (ctl_h_.cur0 + ctl_h_.K) & 1;
+        c.cur0 = (ctl_h_.cur0 + ctl_h_.flips) & 1;
         c.tol = p.sweep_tol;
         c.r_last = NAN;
         c.r_step = NAN;
@@ -158,6 +173,7 @@ template <typename T> class Solver : public SolverBase {
             }
         }
         launches_ = 0;
+        sweep_launches_ = 0;
         for (int s = 0; s < nsteps; ++s) {
             enqueue_step(s, s == nsteps - 1);
             EHDLB_CK(cudaGetLastError());
@@ -191,6 +207,7 @@ template <typename T> class Solver : public SolverBase {
                 }
             }
             st->launches = launches_;
+            st->sweep_launches = sweep_launches_;
         }
         if (ctl_h_.unstable) {
             err = "NaN or Inf in the fields";
@@ -266,6 +283,7 @@ template <typename T> class Solver : public SolverBase {
         d.kappa = (T)(1.5 * p.sigma * p.W);
         d.W = (T)p.W;
         d.tau_h = (T)(0.5 + 3.0 * p.M_phi);
+        d.nhat_eps2 = (T)(p.nhat_eps * p.nhat_eps);
         d.mu_v = (T)p.mu_v;
         d.mu1 = (T)(p.mu_r - 1.0);
         d.m = (T)p.m;
@@ -279,12 +297,62 @@ template <typename T> class Solver : public SolverBase {
         dp_ = d;
     }
 
-    void launch_prep(int par, int fixedK, int kmin, int kmax)
+    void launch_prep(int par, int fixedK, int kmin, int kmax, int flips)
     {
         k_prep<T><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n, phig_,
-                                                       q_, ctl_, fixedK, kmin, kmax);
+                                                       q_, ctl_, fixedK, kmin, kmax, flips);
         ++launches_;
     }
+
+    // Region height of the fused sweep kernel (its width is 64) and the
+    // largest number of sweeps one launch fuses.
+    static constexpr int TB_RH = sizeof(T) == 4 ? 32 : 16;
+    static constexpr int TB_MAX = sizeof(T) == 4 ? 5 : 2;
+
+    static dim3 tb_grid(int nsw, int nx, int ny)
+    {
+        const int tx = 64 - 2 * nsw, ty = TB_RH - 2 * nsw;
+        return dim3((nx + tx - 1) / tx, (ny + ty - 1) / ty);
+    }
+
+    template <int NSW> cudaError_t tb_attr()
+    {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep_tb<T, NSW, TB_RH, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)tb_smem_bytes<T, TB_RH>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_sweep_tb<T, NSW, TB_RH, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tb_smem_bytes<T, TB_RH>());
+        return e;
+    }
+
+    template <int NSW> void tb_launch(int m, bool resid)
+    {
+        const dim3 g = tb_grid(NSW, nx_, ny_);
+        const size_t sm = tb_smem_bytes<T, TB_RH>();
+        if (resid)
+            k_sweep_tb<T, NSW, TB_RH, true><<<g, dim3(32, 8), sm, stream_>>>(dp_, g_[0], g_[1], phig_, q_,
+                                                                           part2_, ctl_, m);
+        else
+            k_sweep_tb<T, NSW, TB_RH, false><<<g, dim3(32, 8), sm, stream_>>>(dp_, g_[0], g_[1], phig_, q_,
+                                                                            part2_, ctl_, m);
+        ++launches_;
+        ++sweep_launches_;
+    }
+
+    void launch_sweep_tb(int nsw, int m, bool resid)
+    {
+        switch (nsw) {
+        case 1: tb_launch<1>(m, resid); break;
+        case 2: tb_launch<2>(m, resid); break;
+        case 3: if constexpr (TB_MAX >= 3) tb_launch<3>(m, resid); break;
+        case 4: if constexpr (TB_MAX >= 4) tb_launch<4>(m, resid); break;
+        default: if constexpr (TB_MAX >= 5) tb_launch<5>(m, resid); break;
+        }
+    }
+
+    int tb_chunk() const { return tb_chunk_ > 0 ? std::min(tb_chunk_, TB_MAX) : 0; }
 
     void launch_sweep(int j, bool write_psi, bool resid, bool ctrl)
     {
@@ -300,10 +368,12 @@ template <typename T> class Solver : public SolverBase {
         }
 #undef EHDLB_SWEEP
         ++launches_;
+        ++sweep_launches_;
     }
 
-    // Kernel sequence of one time step; s is the step index within the call.
-    void enqueue_step(int s, bool snap)
+    // Kernel sequence of one time step; s is the step index within the call,
+    // last marks the final step (snapshot, sums and residual reported).
+    void enqueue_step(int s, bool last)
     {
         const int par = tpar_;
         const bool frozen = P_.freeze_E != 0;
@@ -311,12 +381,22 @@ template <typename T> class Solver : public SolverBase {
         if (frozen) fixedK = 0;
         else if (t_ < (long long)sched_.size()) fixedK = sched_[(size_t)t_];
         else if (P_.sweeps_min == P_.sweeps_max) fixedK = P_.sweeps_max;
-        if (fixedK >= 0) kmin = kmax = fixedK;
+        const bool converge = fixedK < 0;
+        if (!converge) kmin = kmax = fixedK;
+        const int chunk = tb_chunk();
+        const bool fused = !converge && fixedK > 0 && chunk > 0;
+        const int nk = fused ? (fixedK + chunk - 1) / chunk : (converge ? 0 : fixedK);
         if (timing_) cudaEventRecord(events_[4 * s], stream_);
-        launch_prep(par, fixedK, kmin, kmax);
+        launch_prep(par, fixedK, kmin, kmax, nk);
         if (timing_) cudaEventRecord(events_[4 * s + 1], stream_);
-        if (fixedK >= 0) {
-            for (int j = 1; j <= fixedK; ++j) launch_sweep(j, j == fixedK, false, false);
+        if (fused) {
+            for (int m = 0, done = 0; m < nk; ++m) {
+                const int nsw = std::min(chunk, fixedK - done);
+                launch_sweep_tb(nsw, m, last && m == nk - 1);
+                done += nsw;
+            }
+        } else if (!converge) {
+            for (int j = 1; j <= fixedK; ++j) launch_sweep(j, last && j == fixedK, false, false);
         } else {
             for (int j = 1; j <= kmax; ++j) {
                 launch_sweep(j, true, j >= 2, true);
@@ -325,29 +405,36 @@ template <typename T> class Solver : public SolverBase {
             }
         }
         if (timing_) cudaEventRecord(events_[4 * s + 2], stream_);
-        const bool resid = !frozen && kmax >= 1;
+        const bool main_resid = !frozen && !fused && kmax >= 1 && (converge || last);
+        const int resid_mode = main_resid ? 1 : ((fused && last) ? 2 : 0);
         const dim3 b(BX, BY);
+        int *unstable = &ctl_->unstable;
 #define EHDLB_MAIN(S, F, R)                                                                              \
     k_main<T, S, F, R><<<grid_, b, 0, stream_>>>(dp_, pops_[par], pops_[par ^ 1], g_[0], g_[1], ctl_,     \
-                                                 phig_, phiu_, psi_prev_, snap_, part_)
-        if (snap) {
+                                                 phig_, phiu_, psi_prev_, snap_, part_, unstable)
+        if (last) {
             if (frozen) EHDLB_MAIN(true, true, false);
-            else if (resid) EHDLB_MAIN(true, false, true);
+            else if (main_resid) EHDLB_MAIN(true, false, true);
             else EHDLB_MAIN(true, false, false);
         } else {
             if (frozen) EHDLB_MAIN(false, true, false);
-            else if (resid) EHDLB_MAIN(false, false, true);
+            else if (main_resid) EHDLB_MAIN(false, false, true);
             else EHDLB_MAIN(false, false, false);
         }
 #undef EHDLB_MAIN
-        k_step_end<<<1, 256, 0, stream_>>>(part_, nb_, ctl_, counts_, resid ? 1 : 0);
+        long long nb2 = 0;
+        if (resid_mode == 2) {
+            const dim3 g = tb_grid(std::min(chunk, fixedK - (nk - 1) * chunk), nx_, ny_);
+            nb2 = (long long)g.x * g.y;
+        }
+        k_step_end<<<1, 256, 0, stream_>>>(part_, nb_, part2_, nb2, ctl_, counts_, resid_mode, last ? 1 : 0);
         launches_ += 2;
         if (timing_) cudaEventRecord(events_[4 * s + 3], stream_);
         tpar_ ^= 1;
         ++t_;
     }
 
-    int transfer_state(double *dst, const double *src, std::string &err)
+        int transfer_state(double *dst, const double *src, std::string &err)
     {
         EHDLB_CK(cudaMemcpyAsync(&ctl_h_, ctl_, sizeof(Control), cudaMemcpyDeviceToHost, stream_));
         EHDLB_CK(cudaStreamSynchronize(stream_));
@@ -394,7 +481,8 @@ template <typename T> class Solver : public SolverBase {
     Pops<T> pops_[2]{};
     T *g_[2]{};
     T *phig_ = nullptr, *q_ = nullptr, *phiu_ = nullptr, *psi_prev_ = nullptr, *snap_ = nullptr;
-    double *part_ = nullptr, *stage_ = nullptr;
+    double *part_ = nullptr, *part2_ = nullptr, *stage_ = nullptr;
+    int tb_chunk_ = sizeof(T) == 4 ? 4 : 2;  // sweeps fused per launch (0: one per launch)
     Control *ctl_ = nullptr;
     Control ctl_h_{};
     int *counts_ = nullptr;
@@ -409,6 +497,7 @@ template <typename T> class Solver : public SolverBase {
     int init_sweeps_ = 0;
     bool timing_ = false;
     long long launches_ = 0;
+    long long sweep_launches_ = 0;
 };
 
 }  // namespace ehdlb

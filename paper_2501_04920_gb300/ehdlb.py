@@ -23,7 +23,7 @@ _PARAM_FIELDS = [
     ("size", C.c_size_t),
     ("tau_f", C.c_double), ("rho_ratio", C.c_double), ("eta_ratio", C.c_double),
     ("sigma", C.c_double), ("W", C.c_double), ("W_init", C.c_double),
-    ("M_phi", C.c_double),
+    ("M_phi", C.c_double), ("nhat_eps", C.c_double),
     ("xc", C.c_double), ("yc", C.c_double), ("R", C.c_double),
     ("init_shape", C.c_int),
     ("D", C.c_double), ("mu_v", C.c_double), ("mu_r", C.c_double),
@@ -55,7 +55,7 @@ class ehdlb_stats(C.Structure):
         ("last_residual", C.c_double), ("sum_phi", C.c_double), ("sum_q", C.c_double),
         ("seconds", C.c_double), ("mlups", C.c_double),
         ("ms_prep", C.c_double), ("ms_sweeps", C.c_double), ("ms_main", C.c_double),
-        ("launches", C.c_longlong),
+        ("launches", C.c_longlong), ("sweep_launches", C.c_longlong),
     ]
 
 

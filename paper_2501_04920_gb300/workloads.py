@@ -26,7 +26,7 @@ def droplet64() -> dict:
     n = 64
     return dict(
         tau_f=0.8, rho_ratio=1.0, eta_ratio=1.0, sigma=0.01, W=4.0, W_init=0.0,
-        M_phi=0.02, xc=(n - 1) / 2, yc=(n - 1) / 2, R=12.0, init_shape=0,
+        M_phi=0.02, nhat_eps=1e-3, xc=(n - 1) / 2, yc=(n - 1) / 2, R=12.0, init_shape=0,
         D=0.01, mu_v=1.0, mu_r=1.0, m=1.0, k_d=1.0, k_r=1.0, onsager_cb=1.0,
         onsager_form=0, ion_bc=0, einstein_D=1, ion_L_term=1, c_init_scale=1.0,
         c0=1.0, eps_r=2.0, Kq=W0_2MM_1KV / n**2, vartheta=0.3, psi_src_literal=0,

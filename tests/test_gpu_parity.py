@@ -16,6 +16,12 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 FP32_TOL = 1e-5
+# FP32 |u| bound.  Storing the Allen-Cahn populations h in float alone (all
+# arithmetic in double, emulated with the oracle) already moves |u| by 1.9e-5
+# relative after 100 steps of the 256^2 case: near equilibrium the
+# surface-tension force is mu_phi grad phi with mu_phi a small residual of
+# kappa lap(phi), and lap(phi) inherits the float rounding of phi ~ 1.
+FP32_U_TOL = 2e-4
 
 
 def rel_linf(a, b):
@@ -99,20 +105,40 @@ VARIANTS = {
     "free_rate": dict(s_free=1.3),
     "slab": dict(init_shape=1, R=2.0),
     "wide_interface": dict(W_init=6.0, eps_r=0.5, mu_r=5.0),
+    "printed_normal": dict(nhat_eps=0.0),
 }
+
+
+def oracle_sensitivity(nx, ny, prm, steps, counts):
+    """Relative L-inf change of each field when the oracle's own state is
+    perturbed by 1e-16 (relative) at t = 0: the round-off the case amplifies."""
+    a, b = oracle.Oracle(nx, ny, prm), oracle.Oracle(nx, ny, prm)
+    s = b.state()
+    s *= 1 + 1e-16 * np.random.default_rng(1).standard_normal(s.shape)
+    b.set_state(s)
+    a.step(steps, forced=counts)
+    b.step(steps, forced=counts)
+    return field_errors(b.fields(), a.fields())
 
 
 @pytest.mark.parametrize("shape", [(8, 8), (16, 12), (13, 7)])
 @pytest.mark.parametrize("name", sorted(VARIANTS))
 def test_fp64_small_lattices_every_switch(shape, name):
+    # A droplet narrower than its interface (R < W) peaks below phi = 1, so at
+    # its centre lambda of Eq. 32 is large where grad phi vanishes: the flux
+    # direction is set by round-off and such tiny cases are chaotic in the
+    # oracle itself.  The bound is 1e-12 or 10x the oracle's own sensitivity.
     nx, ny = shape
     prm = workloads.droplet64()
     prm.update(xc=(nx - 1) / 2, yc=(ny - 1) / 2, R=min(nx, ny) / 4, Kq=0.05,
                psi_anode=0.7, psi_cathode=-0.2, sweeps_min=1, sweeps_max=6,
                sweep_tol=1e-6, init_sweeps_max=300)
     prm.update(VARIANTS[name])
-    got, ref, *_ = run_pair(nx, ny, prm, 25)
-    assert_close(field_errors(got, ref), FP64_TOL)
+    got, ref, lat, orc, counts = run_pair(nx, ny, prm, 25)
+    err = field_errors(got, ref)
+    sens = oracle_sensitivity(nx, ny, prm, 25, counts)
+    bad = {k: (v, sens[k]) for k, v in err.items() if not v <= max(FP64_TOL, 10 * sens[k])}
+    assert not bad, f"error (oracle sensitivity) above bound: {bad}"
 
 
 # ---- FP32: the oracle-sized copy of the 2048^2 case -------------------------------
@@ -121,7 +147,8 @@ def test_fp32_droplet256_matches_oracle():
     n, steps = 256, 100
     got, ref, *_ = run_pair(n, n, workloads.droplet(n), steps, precision=ehdlb.FP32)
     err = field_errors(got, ref)
-    assert_close(err, FP32_TOL, keys=["phi", "u", "psi", "q"])
+    assert_close(err, FP32_TOL, keys=["phi", "psi", "q", "cp", "cm"])
+    assert_close(err, FP32_U_TOL, keys=["u"])
 
 
 def test_fp64_droplet256_matches_oracle():
@@ -136,7 +163,8 @@ def test_fp32_droplet2048_full_size_matches_oracle():
     n, steps = 2048, 2
     got, ref, *_ = run_pair(n, n, workloads.droplet(n), steps, precision=ehdlb.FP32)
     err = field_errors(got, ref)
-    assert_close(err, FP32_TOL, keys=["phi", "u", "psi", "q"])
+    assert_close(err, FP32_TOL, keys=["phi", "psi", "q", "cp", "cm"])
+    assert_close(err, FP32_U_TOL, keys=["u"])
 
 
 # ---- invariants, determinism, checkpoints, errors --------------------------------------

@@ -465,6 +465,47 @@ def test_coulomb_force_balances_the_pressure_gradient():
     assert err < 2e-3, err
 
 
+# ---- the interface normal of Eq. 32 and the conditioning of the step -----------
+
+def test_regularised_normal_is_the_unit_normal_away_from_flat_regions():
+    # with n = grad phi / sqrt(|grad phi|^2 + eps^2) the source of Eq. 32 differs
+    # from the printed unit normal by the factor |g| / sqrt(|g|^2 + eps^2)
+    rng = np.random.default_rng(11)
+    eps = 1e-3
+    for _ in range(20):
+        g = rng.normal(size=2) * 0.2
+        phi = rng.uniform(0.05, 0.95)
+        a = O.Hsrc(phi, 4.0, 0.0, 0.0, g[0], g[1], 0.0)
+        b = O.Hsrc(phi, 4.0, 0.0, 0.0, g[0], g[1], eps)
+        m = np.hypot(*g)
+        np.testing.assert_allclose(b, a * m / np.sqrt(m * m + eps * eps), rtol=1e-14, atol=1e-18)
+    # flat region: the source vanishes with the gradient instead of keeping |lambda|
+    b = O.Hsrc(1.0001, 4.0, 0.0, 0.0, 1e-10, -2e-10, eps)
+    assert np.max(np.abs(b)) < 1e-10
+
+
+@pytest.mark.slow
+def test_step_is_well_conditioned_with_the_regularised_normal():
+    # a 1e-16 relative perturbation of h must stay at round-off over 300 steps
+    # of the 64x64 droplet (with the printed normal it grows ~e-fold every 10
+    # steps inside the droplet, where phi overshoots 1 and grad phi ~ 0)
+    from paper_2501_04920_gb300 import workloads
+    prm = workloads.droplet64()
+    growth = {}
+    for eps in (1e-3, 0.0):
+        prm["nhat_eps"] = eps
+        a, b = O.Oracle(64, 64, prm), O.Oracle(64, 64, prm)
+        s = b.state()
+        rng = np.random.default_rng(0)
+        s[:, :, 9:18] *= 1 + 1e-16 * rng.standard_normal(s[:, :, 9:18].shape)
+        b.set_state(s)
+        counts, _, _ = a.step(300)
+        b.step(300, forced=counts)
+        growth[eps] = np.max(np.abs(a.fields()["phi"] - b.fields()["phi"]))
+    assert growth[1e-3] < 1e-13, growth
+    assert growth[0.0] > 1e3 * growth[1e-3], growth
+
+
 # ---- deformation factor (Eq. 63) ------------------------------------------------
 
 def test_deformation_factor_of_ellipses():
