@@ -204,6 +204,44 @@ int ehdlb_set_state(ehdlb_ctx *c, const double *src, size_t len);
 /* Record device time per kernel class in ehdlb_stats (1) or not (0). */
 int ehdlb_set_timing(ehdlb_ctx *c, int on);
 
+/* Largest lattice, in nodes nx * ny, that ehdlb_potential_noalloc accepts. */
+#define EHDLB_NOALLOC_MAX_NODES 65536
+
+/* Potential solve that allocates no device memory.  The paper has no
+ * counterpart; this entry point exists for callers that cannot call
+ * cudaMalloc: code inside an allocator or memory-pool callback, a process
+ * whose device memory is entirely held and budgeted by another runtime, or a
+ * latency-critical loop that must not risk the implicit device
+ * synchronisation of an allocation.
+ *
+ * Runs nsweeps pseudo-time sweeps of the potential equation (Eq. 44-50) in
+ * FP64 on an nx x ny lattice (nx ny <= EHDLB_NOALLOC_MAX_NODES, nx, ny >= 4),
+ * starting from the initial potential of ehdlb_set_params (linear between the
+ * electrodes, or zero if p->init_psi_zero), with the source from phi (eps,
+ * Eq. 61) and q (net charge), and writes psi (Eq. 49) and E (Eq. 50).  With
+ * q = 0 the result is the initial potential ehdlb_set_params computes with
+ * p->init_sweeps_fixed = nsweeps.  Only the potential fields of p are read.
+ *   phi, q     : caller-owned DEVICE arrays [ny][nx] of double (inputs)
+ *   psi, Ex, Ey: caller-owned DEVICE arrays [ny][nx] of double (outputs)
+ *   residual   : host pointer or NULL; receives ||psi^K - psi^(K-1)|| /
+ *                ||psi^K|| of the last sweep (NaN for nsweeps = 0); when it is
+ *                not NULL the call waits for the stream
+ *   cuda_stream: cudaStream_t to launch on, or NULL for the default stream
+ * Every intermediate lives in one file-scope device array of about 5.6 MB
+ * that each GPU loading this library reserves until the process exits; the
+ * call makes no allocation.  All calls share that array and it keeps the last
+ * call's contents (the call resets what must start at zero), so calls whose
+ * work overlaps on the GPU -- on different streams, or from different host
+ * threads -- race and must be serialised by the caller.  The first call on a
+ * device looks up the array's device address (with that device current); make
+ * that first call before any stream capture begins.
+ * Returns EHDLB_EINVAL for a lattice above the maximum, nx or ny < 4, NULL
+ * arrays, p->size != sizeof(ehdlb_params) or invalid potential parameters;
+ * EHDLB_ECUDA if a launch or copy fails. */
+int ehdlb_potential_noalloc(int nx, int ny, const ehdlb_params *p, const double *phi,
+                            const double *q, int nsweeps, double *psi, double *Ex,
+                            double *Ey, double *residual, void *cuda_stream);
+
 /* Free all device memory of the context (NULL is a no-op). */
 void ehdlb_destroy(ehdlb_ctx *c);
 

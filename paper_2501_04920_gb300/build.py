@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libehdlb.so")
 
-SOURCES = ["ehdlb_api.cu", "solver_fp32.cu", "solver_fp64.cu"]
+SOURCES = ["ehdlb_api.cu", "solver_fp32.cu", "solver_fp64.cu", "ehdlb_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          f"-I{INCLUDE}", f"-I{CSRC}"]
@@ -48,7 +48,7 @@ def up_to_date() -> bool:
 
 # The double-precision solver exists to agree with the FP64 oracle; like the
 # oracle (gcc -ffp-contract=off) it rounds every product and sum separately.
-PER_SOURCE = {"solver_fp64.cu": ["-fmad=false"]}
+PER_SOURCE = {"solver_fp64.cu": ["-fmad=false"], "ehdlb_noalloc.cu": ["-fmad=false"]}
 
 
 def _compile(src: str, extra: list[str]) -> str:

@@ -92,6 +92,8 @@ def lib():
         L.ehdlb_get_state.argtypes = [vp, dp, C.c_size_t]
         L.ehdlb_set_state.argtypes = [vp, dp, C.c_size_t]
         L.ehdlb_set_timing.argtypes = [vp, C.c_int]
+        L.ehdlb_potential_noalloc.argtypes = [C.c_int, C.c_int, C.POINTER(ehdlb_params), vp, vp,
+                                              C.c_int, vp, vp, vp, dp, vp]
         L.ehdlb_destroy.argtypes = [vp]
         L.ehdlb_destroy.restype = None
         L.ehdlb_last_error.argtypes = [vp]
@@ -200,6 +202,18 @@ def ehdlb_set_state(ctx, src: np.ndarray):
 
 def ehdlb_set_timing(ctx, on: bool):
     return _check(ctx, lib().ehdlb_set_timing(ctx, 1 if on else 0), "ehdlb_set_timing")
+
+
+def ehdlb_potential_noalloc(nx, ny, p: ehdlb_params, phi_dev: int, q_dev: int, nsweeps: int,
+                            psi_dev: int, ex_dev: int, ey_dev: int, cuda_stream: int | None = None):
+    """Potential solve that allocates nothing; arrays are device addresses.
+    Returns (status, residual of the last sweep)."""
+    r = C.c_double(float("nan"))
+    status = lib().ehdlb_potential_noalloc(
+        nx, ny, C.byref(p), C.c_void_p(phi_dev), C.c_void_p(q_dev), nsweeps,
+        C.c_void_p(psi_dev), C.c_void_p(ex_dev), C.c_void_p(ey_dev), C.byref(r),
+        C.c_void_p(cuda_stream) if cuda_stream else None)
+    return status, r.value
 
 
 def ehdlb_destroy(ctx):
