@@ -30,7 +30,11 @@ METRIC = "MLUPS over 5 LB fields, % HBM roofline; served cases/h vs plain, p99 l
 N = 2048
 SWEEPS = 20
 SAMPLE_N = 256          # oracle sample: a 256^2 copy of the case (R = 32)
-SWEEP_BYTES_PER_NODE = 40   # FP32: 4 populations read + 4 written, phi and q read
+# Algorithmic bytes per node and potential sweep in FP32 (10 s + 8 with s = 4:
+# 5 populations read and written, phi and q read), the per-sweep unit of the
+# byte model; one launch of the fused kernel processes sweeps_per_launch such
+# units per node while its DRAM traffic is that of a single sweep.
+SWEEP_BYTES_PER_NODE = 48
 
 
 def parse():
@@ -41,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=N, help="lattice side (default: the 2048^2 case)")
+    ap.add_argument("--sweeps-per-launch", type=int, default=-1,
+                    help="potential sweeps fused per kernel launch (default: the library's)")
     return ap.parse_args()
 
 
@@ -104,6 +110,23 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def measured_traffic(kernel: str, n: int):
+    """DRAM bytes per launch of kernel at n x n from profiles/traffic.json,
+    or None when the kernel source changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[kernel]
+        src = os.path.join(ROOT, "paper_2501_04920_gb300", "csrc", "ehdlb_kernels.cuh")
+        with open(src, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()[:16]
+    except (OSError, KeyError, ValueError):
+        return None
+    if rec.get("source_sha256_16") != digest:
+        return None
+    return rec["dram_bytes_per_node"] * n * n
 
 
 def measured_peaks():
@@ -177,6 +200,8 @@ def run_ours(args):
     n = args.n
     prm = workloads.droplet(n)
     lat = ehdlb.Lattice(n, n, prm, precision=ehdlb.FP32, cuda_stream=stream.cuda_stream)
+    if args.sweeps_per_launch >= 0:
+        ehdlb.ehdlb_set_tuning(lat.ctx, args.sweeps_per_launch)
     nn = n * n
 
     def barrier():
@@ -206,7 +231,8 @@ def run_ours(args):
     sweeps_per_launch = args.steps * SWEEPS / max(1, st.sweep_launches)
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
-    achieved = SWEEP_BYTES_PER_NODE * nn / (sweep_launch_ms / 1e3) / 1e9
+    achieved = SWEEP_BYTES_PER_NODE * sweeps_per_launch * nn / (sweep_launch_ms / 1e3) / 1e9
+    traffic = measured_traffic("k_sweep_tb", n)
     launches = int(st.launches)
     ehdlb.ehdlb_set_timing(lat.ctx, False)
 
@@ -250,8 +276,11 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": "k_sweep_tb (potential sweeps fused in shared memory)",
                      "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "peak_source": peak_kind,
-                     "traffic": None, "bytes_per_launch": SWEEP_BYTES_PER_NODE * nn,
-                     "sweeps_per_launch": sweeps_per_launch, "launch_ms": sweep_launch_ms},
+                     "traffic": traffic,
+                     "bytes_per_launch": SWEEP_BYTES_PER_NODE * sweeps_per_launch * nn,
+                     "sweeps_per_launch": sweeps_per_launch, "launch_ms": sweep_launch_ms,
+                     "dram_achieved": (round(traffic / (sweep_launch_ms / 1e3) / 1e9, 1)
+                                       if traffic else None)},
         "gpu_launches": launches,
         "kernel_ms": {"prep": st.ms_prep / args.steps, "sweeps": st.ms_sweeps / args.steps,
                       "main": st.ms_main / args.steps},

@@ -222,6 +222,15 @@ int ehdlb_set_timing(ehdlb_ctx *c, int on)
     return EHDLB_OK;
 }
 
+int ehdlb_set_tuning(ehdlb_ctx *c, int sweeps_per_launch)
+{
+    if (!c) return EHDLB_EINVAL;
+    if (sweeps_per_launch < 0 || sweeps_per_launch > 5)
+        return fail(c, EHDLB_EINVAL, "sweeps_per_launch must lie in 0..5");
+    c->solver->set_tuning(sweeps_per_launch);
+    return EHDLB_OK;
+}
+
 void ehdlb_destroy(ehdlb_ctx *c)
 {
     if (!c) return;

@@ -61,6 +61,11 @@ template <typename T> struct DevP {
     T k_d, k_r, cb;
     T s_free;
     T Ex_frozen, Ey_frozen;
+    // derived constants of the main kernel
+    T s_h, sfree_h;                // Allen-Cahn rates (Eq. 30) and the free rate
+    T s_f0;                        // 1/tau_f when rho and eta are uniform, else 0
+    T s_p0, s_n0;                  // ion rates (Eq. 37) when D is uniform, else 0
+    T inv_mu_v, three_over_tau_g, inv_W;
 };
 
 // Per-run control block in device memory (all kernels of a step read it).
@@ -303,35 +308,47 @@ __global__ void __launch_bounds__(256) k_sweep(const DevP<T> P, T *__restrict__ 
     if (RESID) block_sum_store<double, 2>(red, part);
 }
 
+// Asynchronous 4- or 8-byte global -> shared copy (no register staging).
+template <typename T> __device__ __forceinline__ void cp_async(T *smem, const T *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // NSW potential sweeps (Eq. 44-50) fused in shared memory.  A block holds a
 // 64 x RH region of the lattice: its output tile of (64 - 2 NSW) x
 // (RH - 2 NSW) nodes plus a halo NSW nodes wide (x periodic; rows outside the
 // lattice stay empty, the electrode rules act on the wall links).  Every
 // sweep collides and pushes the whole region; values at distance < s from
 // the region edge are incomplete after sweep s, so after NSW sweeps the
-// output tile is exact.  The source coefficients of each node, from phi and
-// q, are computed once:  X/3 = A - Bx m1 - By m2 with m1, m2 the first
-// moments (E = 3 m / tau_g), A = th Kq q / (3 eps), B = th (eps_r - 1)
-// grad phi / (tau_g eps), th = vartheta (times 1/(1 - w0)).
+// output tile is exact.  The shared planes carry a one-node pad on every
+// side that absorbs pushes leaving the region.  The source coefficients of
+// each node, from phi and q, stay in registers:  X/3 = A - Bx m1 - By m2
+// with m1, m2 the first moments (E = 3 m / tau_g), A = th Kq q / (3 eps),
+// B = th (eps_r - 1) grad phi / (tau_g eps), th = vartheta (times 1/(1 - w0)).
 //   RESID: the last sweep of the step; residual partials of the output tile.
-// Launch: blockDim (32, 8), dynamic shared memory tb_smem_bytes<T, RH>().
+// Launch: blockDim (32, 16), dynamic shared memory tb_smem_bytes<T, RH>().
 template <typename T, int RH> __host__ __device__ constexpr size_t tb_smem_bytes()
 {
-    return sizeof(T) * 11 * (size_t)RH * 64;
+    return sizeof(T) * 8 * (size_t)(RH + 2) * (64 + 2);
 }
 
 template <typename T, int NSW, int RH, bool RESID>
-__global__ void __launch_bounds__(256) k_sweep_tb(const DevP<T> P, T *__restrict__ gA, T *__restrict__ gB,
-                                                  const T *__restrict__ phig, const T *__restrict__ q,
-                                                  double *__restrict__ part, const Control *__restrict__ ctl,
-                                                  int m)
+__global__ void __launch_bounds__(512, 2) k_sweep_tb(const DevP<T> P, T *__restrict__ gA, T *__restrict__ gB,
+                                                     const T *__restrict__ phig, const T *__restrict__ q,
+                                                     double *__restrict__ part, const Control *__restrict__ ctl,
+                                                     int m)
 {
-    constexpr int RW = 64, H = NSW, TX = RW - 2 * H, TY = RH - 2 * H, PL = RH * RW;
-    constexpr int NB = RW / 32, NA = RH / 8;
-    static_assert(TX > 0 && TY > 0, "tile too small for NSW");
+    constexpr int RW = 64, H = NSW, TX = RW - 2 * H, TY = RH - 2 * H;
+    constexpr int PW = RW + 2, PH = RH + 2, PL = PW * PH;
+    constexpr int NB = RW / 32, NA = RH / 16;
+    static_assert(TX > 0 && TY > 0 && NA >= 1, "tile too small for NSW");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sg = reinterpret_cast<T *>(smem_raw);   // [2][4][RH][RW]
-    T *sc = sg + 8 * PL;                        // [3][RH][RW]
+    T *sg = reinterpret_cast<T *>(smem_raw);   // [2][4][PH][PW]
     const int par = (ctl->cur0 + m) & 1;
     const T *__restrict__ src = par ? gB : gA;
     T *__restrict__ dst = par ? gA : gB;
@@ -340,74 +357,138 @@ __global__ void __launch_bounds__(256) k_sweep_tb(const DevP<T> P, T *__restrict
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int tx = threadIdx.x, ty = threadIdx.y;
 
-    // ---- load the region and its source coefficients ----
+    // ---- load the region: g into buffer 0; phi (with a one-node ring) and
+    // q into buffer 1, which the first sweep overwrites; all copies async ----
+    {
+        T *sphi = sg + 4 * PL, *sq = sg + 5 * PL;
 #pragma unroll
-    for (int a = 0; a < NA; ++a) {
-        const int ly = ty + 8 * a, gy = y0 - H + ly;
-        if (gy < 0 || gy >= ny) continue;
-        const T *r0 = phig + (long long)gy * nx, *r1 = r0 + nx, *r2 = r1 + nx;
+        for (int a = 0; a < NA; ++a) {
+            const int ly = ty + 16 * a, gy = y0 - H + ly;
+            if (gy < 0 || gy >= ny) continue;
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const int lx = tx + 32 * b;
-            int gx = x0 - H + lx;
+            for (int b = 0; b < NB; ++b) {
+                const int lx = tx + 32 * b;
+                int gx = x0 - H + lx;
+                gx = ((gx % nx) + nx) % nx;
+                const long long k = (long long)gy * nx + gx;
+                const int li = (ly + 1) * PW + lx + 1;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) cp_async(sg + i * PL + li, src + i * nn + k);
+                cp_async(sq + li, q + k);
+            }
+        }
+        // phi rows gy = y0 - H - 1 .. y0 - H + RH, of which phig holds -1 .. ny
+        for (int e = tx + 32 * ty; e < PL; e += 512) {
+            const int py = e / PW, px = e - py * PW;
+            const int gy = y0 - H - 1 + py;
+            if (gy < -1 || gy > ny) continue;
+            int gx = x0 - H - 1 + px;
             gx = ((gx % nx) + nx) % nx;
-            const long long k = (long long)gy * nx + gx;
-            const int li = ly * RW + lx;
+            cp_async(sphi + e, phig + (long long)(gy + 1) * nx + gx);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    T cA[NA][NB], cBx[NA][NB], cBy[NA][NB];
+    {
+        const T *sphi = sg + 4 * PL, *sq = sg + 5 * PL;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) sg[i * PL + li] = src[i * nn + k];
-            const int xm = wrapx(gx - 1, nx), xp = wrapx(gx + 1, nx);
-            const T phi = r1[gx];
-            const T gxs = (r1[xp] - r1[xm]) * T(1.0 / 3.0) +
-                          ((r2[xp] - r2[xm]) + (r0[xp] - r0[xm])) * T(1.0 / 12.0);
-            const T gys = (r2[gx] - r0[gx]) * T(1.0 / 3.0) +
-                          ((r2[xp] + r2[xm]) - (r0[xp] + r0[xm])) * T(1.0 / 12.0);
-            const T inv = T(1) / (T(1) + P.er1 * phi);
-            const T bb = P.src_norm * P.er1 * inv / P.tau_g;
-            sc[li] = P.src_norm * P.Kq * q[k] * inv * T(1.0 / 3.0);
-            sc[PL + li] = bb * gxs;
-            sc[2 * PL + li] = bb * gys;
+        for (int a = 0; a < NA; ++a) {
+            const int ly = ty + 16 * a, gy = y0 - H + ly;
+            const bool vrow = gy >= 0 && gy < ny;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                cA[a][b] = cBx[a][b] = cBy[a][b] = T(0);
+                if (!vrow) continue;
+                const int li = (ly + 1) * PW + tx + 32 * b + 1;
+                const T *r1 = sphi + li, *r0 = r1 - PW, *r2 = r1 + PW;
+                const T phi = r1[0];
+                const T gxs = (r1[1] - r1[-1]) * T(1.0 / 3.0) +
+                              ((r2[1] - r2[-1]) + (r0[1] - r0[-1])) * T(1.0 / 12.0);
+                const T gys = (r2[0] - r0[0]) * T(1.0 / 3.0) +
+                              ((r2[1] + r2[-1]) - (r0[1] + r0[-1])) * T(1.0 / 12.0);
+                const T inv = T(1) / (T(1) + P.er1 * phi);
+                const T bb = P.src_norm * P.er1 * inv / P.tau_g;
+                cA[a][b] = P.src_norm * P.Kq * sq[li] * inv * T(1.0 / 3.0);
+                cBx[a][b] = bb * gxs;
+                cBy[a][b] = bb * gys;
+            }
         }
     }
     __syncthreads();
 
     T psi_before[NA][NB];
+    // half of the collision constants: o = 0.5 (n3 +- n1) etc.
+    const T k1 = T(0.5) * (T(1) - P.s_g);            // first moments
+    const T kf = T(0.5) * (T(1) - P.s_free_g);       // second moments
+    const T ke = T(0.25) * P.s_free_g;               // their equilibrium psi/3, psi = 1.5 (m3 + m4)
+    const T wG = P.wG;
+    const bool interior = y0 - H >= 0 && y0 - H + RH <= ny;
+    if (interior) {
+        // no wall and no empty row in the region: the same update everywhere
+        int li[NA][NB];
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+#pragma unroll
+            for (int b = 0; b < NB; ++b) li[a][b] = (ty + 16 * a + 1) * PW + tx + 32 * b + 1;
+#pragma unroll
+        for (int s = 0; s < NSW; ++s) {
+            const T *gc = sg + (s & 1) * 4 * PL;
+            T *gn = sg + ((s + 1) & 1) * 4 * PL;
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const int l = li[a][b];
+                    const T g1 = gc[l], g2 = gc[PL + l], g3 = gc[2 * PL + l], g4 = gc[3 * PL + l];
+                    const T m1 = g1 - g3, m2 = g2 - g4, m3 = g1 + g3, m4 = g2 + g4;
+                    if (RESID && s == NSW - 1) psi_before[a][b] = T(1.5) * (m3 + m4);
+                    const T X6 = T(0.5) * (cA[a][b] - cBx[a][b] * m1 - cBy[a][b] * m2);
+                    const T e = ke * (m3 + m4) + X6;                 // half of s psi/3 + X/3
+                    const T h3 = kf * m3 + e, h4 = kf * m4 + e;      // half of n3, n4
+                    const T h1 = k1 * m1, h2 = k1 * m2;              // half of n1, n2
+                    gn[l + 1] = h3 + h1;
+                    gn[2 * PL + l - 1] = h3 - h1;
+                    gn[PL + l + PW] = (h4 + h2) - wG;
+                    gn[3 * PL + l - PW] = (h4 - h2) + wG;
+                }
+            __syncthreads();
+        }
+    } else {
 #pragma unroll
     for (int s = 0; s < NSW; ++s) {
         const T *gc = sg + (s & 1) * 4 * PL;
         T *gn = sg + ((s + 1) & 1) * 4 * PL;
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
-            const int ly = ty + 8 * a, gy = y0 - H + ly;
+            const int ly = ty + 16 * a, gy = y0 - H + ly;
             if (gy < 0 || gy >= ny) continue;
+            const bool top = gy + 1 >= ny, bot = gy == 0;
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-                const int lx = tx + 32 * b, li = ly * RW + lx;
+                const int lx = tx + 32 * b, li = (ly + 1) * PW + lx + 1;
                 const T g1 = gc[li], g2 = gc[PL + li], g3 = gc[2 * PL + li], g4 = gc[3 * PL + li];
                 const T psit = T(1.5) * ((g1 + g3) + (g2 + g4));
                 if (RESID && s == NSW - 1) psi_before[a][b] = psit;
                 const T m1 = g1 - g3, m2 = g2 - g4, m3 = g1 + g3, m4 = g2 + g4;
-                const T X3 = sc[li] - sc[PL + li] * m1 - sc[2 * PL + li] * m2;
+                const T X3 = cA[a][b] - cBx[a][b] * m1 - cBy[a][b] * m2;
                 const T eq = psit * T(1.0 / 3.0);
                 const T n1 = (T(1) - P.s_g) * m1, n2 = (T(1) - P.s_g) * m2;
                 const T n3 = m3 - P.s_free_g * (m3 - eq) + X3;
                 const T n4 = m4 - P.s_free_g * (m4 - eq) + X3;
                 const T o1 = T(0.5) * (n3 + n1), o3 = T(0.5) * (n3 - n1);
                 const T o2 = T(0.5) * (n4 + n2), o4 = T(0.5) * (n4 - n2);
-                if (lx + 1 < RW) gn[li + 1] = o1;
-                if (lx > 0) gn[2 * PL + li - 1] = o3;
-                if (gy + 1 < ny) {
-                    if (ly + 1 < RH) gn[PL + li + RW] = o2 - P.wG;
-                } else {
-                    gn[3 * PL + li] = -o2 + P.wG;      // cathode: ABB to psi_c
-                }
-                if (gy > 0) {
-                    if (ly > 0) gn[3 * PL + li - RW] = o4 + P.wG;
-                } else {
-                    gn[PL + li] = -o4 - P.wG;          // anode: ABB to psi_a
-                }
+                gn[li + 1] = o1;
+                gn[2 * PL + li - 1] = o3;
+                if (!top) gn[PL + li + PW] = o2 - P.wG;
+                else gn[3 * PL + li] = -o2 + P.wG;          // cathode: ABB to psi_c
+                if (!bot) gn[3 * PL + li - PW] = o4 + P.wG;
+                else gn[PL + li] = -o4 - P.wG;              // anode: ABB to psi_a
             }
         }
         __syncthreads();
+    }
+
     }
 
     // ---- store the output tile ----
@@ -415,13 +496,13 @@ __global__ void __launch_bounds__(256) k_sweep_tb(const DevP<T> P, T *__restrict
     T red[2] = {T(0), T(0)};
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
-        const int ly = ty + 8 * a, gy = y0 - H + ly;
+        const int ly = ty + 16 * a, gy = y0 - H + ly;
         if (ly < H || ly >= H + TY || gy >= ny) continue;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const int lx = tx + 32 * b, gx = x0 - H + lx;
             if (lx < H || lx >= H + TX || gx >= nx) continue;
-            const int li = ly * RW + lx;
+            const int li = (ly + 1) * PW + lx + 1;
             const long long k = (long long)gy * nx + gx;
             const T g1 = gf[li], g2 = gf[PL + li], g3 = gf[2 * PL + li], g4 = gf[3 * PL + li];
             dst[k] = g1;
@@ -461,29 +542,67 @@ static __global__ void __launch_bounds__(256) k_sweep_decide(const double *__res
     if (j >= ctl->kmax) ctl->done = 1;
 }
 
+// Number of values k_main stages per node: f1..f8, h0..h8, p0..p4, n0..n4,
+// g1..g4, (phi u)(t-1) x, y, psi of the previous sweep.
+constexpr int MAIN_STAGE = 8 + 9 + 5 + 5 + 4 + 2 + 1;
+template <typename T> __host__ __device__ constexpr size_t main_smem_bytes()
+{
+    return sizeof(T) * MAIN_STAGE * 256;
+}
+
 // The rest of the step at every node (O5-O11): reaction (Eq. 42-43), forces
 // (Eq. 12-14), u and p (Eq. 56-57), MRT collisions of f (Eq. 51), h (Eq. 27),
-// p and n (Eq. 34-35), push with the wall rules (Eq. 64).
+// p and n (Eq. 34-35), push with the wall rules (Eq. 64).  The node's inputs
+// are copied to shared memory asynchronously first, so that all of them are
+// in flight at once.  The equilibria and sources of f and h enter directly as
+// their moments in the basis of Eq. 28:
+//   M f_eq = (0, rho u, p + rho ux^2, p + rho uy^2, rho ux uy, rho ux/3,
+//             rho uy/3, p/3 + rho u^2/3)          (rows 1..8, Eq. 52-53)
+//   M F    = (F, ux gx + uy gy/3, uy gy + ux gx/3, (ux gy + uy gx)/3, Fx/3,
+//             Fy/3, u.g/3),  g = grad rho           (Eq. 54)
+//   M h_eq = (phi, phi u, phi/3, phi/3, 0, phi ux/3, phi uy/3, phi/9) (Eq. 31)
+//   M H    = (0, V, 0, 0, 0, Vx/3, Vy/3, 0), V = d(phi u)/dt + cs^2 lambda n (Eq. 32)
 //   SNAP  : write the macroscopic snapshot and its sums of phi and q.
 //   FROZEN: E from DevP.
 //   RESID : residual of the last sweep against psi_prev.
 // NaN or Inf in the macroscopic fields raises *unstable.
+// Launch: blockDim (64, 4), dynamic shared memory main_smem_bytes<T>().
 template <typename T, bool SNAP, bool FROZEN, bool RESID>
-__global__ void __launch_bounds__(256, 2) k_main(const DevP<T> P, const Pops<T> src, const Pops<T> dst,
+__global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<T> src, const Pops<T> dst,
                                                  const T *__restrict__ gA, const T *__restrict__ gB,
                                                  const Control *__restrict__ ctl, const T *__restrict__ phig,
                                                  T *__restrict__ phiu, const T *__restrict__ psi_prev,
                                                  T *__restrict__ snap, double *__restrict__ part,
                                                  int *__restrict__ unstable)
 {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *st = reinterpret_cast<T *>(smem_raw);
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool inside = x < P.nx && y < P.ny;
+    const long long nn = P.nn, k = (long long)y * P.nx + x;
     T red[4] = {T(0), T(0), T(0), T(0)};
-    if (x < P.nx && y < P.ny) {
+    if (inside) {
+        const T *__restrict__ g = ((ctl->cur0 + ctl->flips) & 1) ? gB : gA;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) cp_async(st + i * 256 + tid, src.f + i * nn + k);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) cp_async(st + (8 + i) * 256 + tid, src.h + i * nn + k);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            cp_async(st + (17 + i) * 256 + tid, src.p + i * nn + k);
+            cp_async(st + (22 + i) * 256 + tid, src.n + i * nn + k);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) cp_async(st + (27 + i) * 256 + tid, g + i * nn + k);
+        cp_async(st + 31 * 256 + tid, phiu + k);
+        cp_async(st + 32 * 256 + tid, phiu + nn + k);
+        if (RESID) cp_async(st + 33 * 256 + tid, psi_prev + k);
+    }
+    if (inside) {
         const int nx = P.nx, ny = P.ny;
-        const long long nn = P.nn, k = (long long)y * nx + x;
         const T third = T(1.0 / 3.0);
-
         // ---- O1-O2: phi, properties (Eq. 61), stencils (Eq. 59) ----
         const int xm = wrapx(x - 1, nx), xp = wrapx(x + 1, nx);
         const T *r0 = phig + (long long)y * nx, *r1 = r0 + nx, *r2 = r1 + nx;
@@ -495,25 +614,23 @@ __global__ void __launch_bounds__(256, 2) k_main(const DevP<T> P, const Pops<T> 
         const T lap = T(2.0 / 3.0) * ((pE + pN + pW + pS) - T(4) * phi) +
                       T(1.0 / 6.0) * ((pNE + pNW + pSW + pSE) - T(4) * phi);
         const T rho = T(1) + P.rho1 * phi;
-        const T eta = P.eta_v * (T(1) + P.eta1 * phi);
-        const T tau_f = T(0.5) + T(3) * eta / rho;
+        const T inv_rho = T(1) / rho;
         const T mup = P.mu_v * (T(1) + P.mu1 * phi);
         const T mum = P.m * mup;
-        const T Dp = P.einstein_D ? P.D * mup / P.mu_v : P.D;
-        const T Dm = P.einstein_D ? P.D * mum / P.mu_v : P.D;
         const T grx = P.rho1 * gx, gry = P.rho1 * gy;
         const T dex = P.er1 * gx, dey = P.er1 * gy;
+        cp_async_wait_all();
 
         // ---- O4 result: psi, E from the last sweep (Eq. 49-50) ----
-        const T *__restrict__ g = ((ctl->cur0 + ctl->flips) & 1) ? gB : gA;
-        const T g1 = g[k], g2 = g[nn + k], g3 = g[2 * nn + k], g4 = g[3 * nn + k];
+        const T g1 = st[27 * 256 + tid], g2 = st[28 * 256 + tid], g3 = st[29 * 256 + tid],
+                g4 = st[30 * 256 + tid];
         const T psit = T(1.5) * ((g1 + g3) + (g2 + g4));
         const T psi = psit + psi_lin(P, y);
         T Ex, Ey;
         if (FROZEN) { Ex = P.Ex_frozen; Ey = P.Ey_frozen; }
-        else { Ex = T(3) * (g1 - g3) / P.tau_g; Ey = T(3) * (g2 - g4) / P.tau_g; }
+        else { Ex = P.three_over_tau_g * (g1 - g3); Ey = P.three_over_tau_g * (g2 - g4); }
         if (RESID) {
-            const T d = psit - psi_prev[k];
+            const T d = psit - st[33 * 256 + tid];
             red[2] = d * d;
             red[3] = psi * psi;
         }
@@ -521,7 +638,7 @@ __global__ void __launch_bounds__(256, 2) k_main(const DevP<T> P, const Pops<T> 
         // ---- O5: Onsager dissociation and the implicit reaction (Eq. 5, 42-43) ----
         T pv[5], nv[5];
 #pragma unroll
-        for (int i = 0; i < 5; ++i) { pv[i] = src.p[i * nn + k]; nv[i] = src.n[i * nn + k]; }
+        for (int i = 0; i < 5; ++i) { pv[i] = st[(17 + i) * 256 + tid]; nv[i] = st[(22 + i) * 256 + tid]; }
         const T sp = (((pv[0] + pv[1]) + pv[2]) + pv[3]) + pv[4];
         const T sn = (((nv[0] + nv[1]) + nv[2]) + nv[3]) + nv[4];
         const T q = sp - sn;
@@ -547,46 +664,51 @@ __global__ void __launch_bounds__(256, 2) k_main(const DevP<T> P, const Pops<T> 
         const T Fx = mu_phi * gx + P.Kq * q * Ex - T(0.5) * E2 * dex;
         const T Fy = mu_phi * gy + P.Kq * q * Ey - T(0.5) * E2 * dey;
 
-        // ---- O7: u and p (Eq. 56-57) ----
+        // ---- O7: u and p (Eq. 56-57), moments of f ----
         T fv[9];
         fv[0] = T(0);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) fv[i] = src.f[(i - 1) * nn + k];
-        const T jx = ((fv[1] - fv[3]) + (fv[5] - fv[6])) + (fv[8] - fv[7]);
-        const T jy = ((fv[2] - fv[4]) + (fv[5] + fv[6])) - (fv[7] + fv[8]);
-        const T ux = (jx + T(0.5) * Fx) / rho;
-        const T uy = (jy + T(0.5) * Fy) / rho;
+        for (int i = 1; i < 9; ++i) fv[i] = st[(i - 1) * 256 + tid];
+        T mf[9];
+        moments9<T>(fv, mf);     // mf[0] is not used (f0 is not stored)
+        const T ux = (mf[1] + T(0.5) * Fx) * inv_rho;
+        const T uy = (mf[2] + T(0.5) * Fy) * inv_rho;
         const T uu = ux * ux + uy * uy;
-        T sne0 = T(0);
-#pragma unroll
-        for (int i = 1; i < 9; ++i) sne0 += fv[i];
+        const T sne0 = mf[3] + mf[4] - mf[8];           // sum of f1..f8
         const T ugr = ux * grx + uy * gry;
         const T pr = T(0.6) * (sne0 + T(0.5) * ugr - rho * T(2.0 / 3.0) * uu);
 
-        // ---- O8: f collision (Eq. 51-55) ----
+        // ---- O8: f collision (Eq. 51-55) in moment space ----
         {
-            T d[9], Fi[9], md[9], mF[9], mc[9], dl[9];
-            d[0] = T(0); Fi[0] = T(0);
-#pragma unroll
-            for (int i = 1; i < 9; ++i) {
-                const T cu = T(cx9(i)) * ux + T(cy9(i)) * uy;
-                const T cF = T(cx9(i)) * Fx + T(cy9(i)) * Fy;
-                const T cg = T(cx9(i)) * grx + T(cy9(i)) * gry;
-                const T feq = w9<T>(i) * (T(3) * pr + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
-                d[i] = fv[i] - feq;
-                Fi[i] = w9<T>(i) * T(3) * (cF + cu * cg);   // Eq. 54 (its u.grad rho terms cancel)
-            }
-            moments9<T>(d, md);
-            moments9<T>(Fi, mF);
-            const T sv = T(1) / tau_f;
+            const T sv = P.s_f0 > T(0) ? P.s_f0 : T(1) / (T(0.5) + T(3) * P.eta_v * (T(1) + P.eta1 * phi) * inv_rho);
             const T sfree = P.bgk ? sv : P.s_free;
+            const T ru = rho * ux, rv = rho * uy;
+            T d[9], mF[9];
+            d[0] = T(0);
+            d[1] = mf[1] - ru;
+            d[2] = mf[2] - rv;
+            d[3] = mf[3] - (pr + ru * ux);
+            d[4] = mf[4] - (pr + rv * uy);
+            d[5] = mf[5] - ru * uy;
+            d[6] = mf[6] - ru * third;
+            d[7] = mf[7] - rv * third;
+            d[8] = mf[8] - (pr + rho * uu) * third;
+            mF[0] = T(0);
+            mF[1] = Fx;
+            mF[2] = Fy;
+            mF[3] = ux * grx + uy * gry * third;
+            mF[4] = uy * gry + ux * grx * third;
+            mF[5] = (ux * gry + uy * grx) * third;
+            mF[6] = Fx * third;
+            mF[7] = Fy * third;
+            mF[8] = ugr * third;
+            T mc[9], dl[9];
 #pragma unroll
             for (int kk = 0; kk < 9; ++kk) {
                 const T s = (kk >= 1 && kk <= 5) ? sv : sfree;
-                mc[kk] = s * md[kk] - (T(1) - T(0.5) * s) * mF[kk];
+                mc[kk] = s * d[kk] - (T(1) - T(0.5) * s) * mF[kk];
             }
             inverse9<T>(mc, dl);
-            // push with half-way bounce-back (f0 not stored)
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
                 const T v = fv[i] - dl[i];
@@ -598,44 +720,51 @@ __global__ void __launch_bounds__(256, 2) k_main(const DevP<T> P, const Pops<T> 
             }
         }
 
-        // ---- O9: h collision (Eq. 27-33, Eq. 58) ----
+        // ---- O9: h collision (Eq. 27-33, Eq. 58) in moment space ----
         {
             T hv[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) hv[i] = src.h[i * nn + k];
+            for (int i = 0; i < 9; ++i) hv[i] = st[(8 + i) * 256 + tid];
             const T pux = phi * ux, puy = phi * uy;
-            const T dpx = pux - phiu[k], dpy = puy - phiu[nn + k];
+            const T dpx = pux - st[31 * 256 + tid], dpy = puy - st[32 * 256 + tid];
             phiu[k] = pux;
             phiu[nn + k] = puy;
             // normal of Eq. 32, regularised: grad phi / sqrt(|grad phi|^2 + eps^2)
-            const T g2 = gx * gx + gy * gy;
+            const T g2s = gx * gx + gy * gy;
             T nhx = T(0), nhy = T(0);
             if (P.nhat_eps2 > T(0)) {
-                const T den = dsqrt<T>(g2 + P.nhat_eps2);
-                nhx = gx / den; nhy = gy / den;
+                const T inv = T(1) / dsqrt<T>(g2s + P.nhat_eps2);
+                nhx = gx * inv; nhy = gy * inv;
             } else {
-                const T mag = dsqrt<T>(g2);
+                const T mag = dsqrt<T>(g2s);
                 if (mag >= T(1e-12)) { nhx = gx / mag; nhy = gy / mag; }
             }
-            const T lam = T(4) * phi * (T(1) - phi) / P.W;
+            const T lam = T(4) * phi * (T(1) - phi) * P.inv_W;
             const T Vx = dpx + third * lam * nhx, Vy = dpy + third * lam * nhy;
-            T d[9], Hi[9], md[9], mH[9], mc[9], dl[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const T cu = T(cx9(i)) * ux + T(cy9(i)) * uy;
-                const T cV = T(cx9(i)) * Vx + T(cy9(i)) * Vy;
-                d[i] = hv[i] - w9<T>(i) * phi * (T(1) + T(3) * cu);
-                Hi[i] = w9<T>(i) * T(3) * cV;
-            }
-            moments9<T>(d, md);
-            moments9<T>(Hi, mH);
-            const T sv = T(1) / P.tau_h;
-            const T sfree = P.bgk ? sv : P.s_free;
-#pragma unroll
-            for (int kk = 0; kk < 9; ++kk) {
-                const T s = (kk == 1 || kk == 2) ? sv : sfree;
-                mc[kk] = s * md[kk] - (T(1) - T(0.5) * s) * mH[kk];
-            }
+            T mh[9];
+            moments9<T>(hv, mh);
+            T d[9];
+            d[0] = mh[0] - phi;
+            d[1] = mh[1] - pux;
+            d[2] = mh[2] - puy;
+            d[3] = mh[3] - phi * third;
+            d[4] = mh[4] - phi * third;
+            d[5] = mh[5];
+            d[6] = mh[6] - pux * third;
+            d[7] = mh[7] - puy * third;
+            d[8] = mh[8] - phi * T(1.0 / 9.0);
+            const T sv = P.s_h, sfree = P.sfree_h;
+            const T hv_ = T(1) - T(0.5) * sv;
+            T mc[9], dl[9];
+            mc[0] = sfree * d[0];
+            mc[1] = sv * d[1] - hv_ * Vx;
+            mc[2] = sv * d[2] - hv_ * Vy;
+            mc[3] = sfree * d[3];
+            mc[4] = sfree * d[4];
+            mc[5] = sfree * d[5];
+            mc[6] = sfree * d[6] - (T(1) - T(0.5) * sfree) * Vx * third;
+            mc[7] = sfree * d[7] - (T(1) - T(0.5) * sfree) * Vy * third;
+            mc[8] = sfree * d[8];
             inverse9<T>(mc, dl);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
@@ -650,8 +779,13 @@ __global__ void __launch_bounds__(256, 2) k_main(const DevP<T> P, const Pops<T> 
 
         // ---- O10-O11: ions (Eq. 34-40) on D2Q5, push with Eq. 64 ----
         {
-            const T sv_p = T(1) / (T(0.5) + T(3) * Dp);
-            const T sv_n = T(1) / (T(0.5) + T(3) * Dm);
+            T sv_p = P.s_p0, sv_n = P.s_n0;
+            if (!(sv_p > T(0))) {
+                const T Dp = P.einstein_D ? P.D * mup * P.inv_mu_v : P.D;
+                const T Dm = P.einstein_D ? P.D * mum * P.inv_mu_v : P.D;
+                sv_p = T(1) / (T(0.5) + T(3) * Dp);
+                sv_n = T(1) / (T(0.5) + T(3) * Dm);
+            }
             const T fp = P.bgk ? sv_p : P.s_free, fn = P.bgk ? sv_n : P.s_free;
             const T Lx = P.ion_L_term ? Fx : T(0), Ly = P.ion_L_term ? Fy : T(0);
             // cations: moments of (p - p_eq) + G and of R_i + L_i
@@ -716,8 +850,6 @@ __global__ void __launch_bounds__(256, 2) k_main(const DevP<T> P, const Pops<T> 
             snap[7 * nn + k] = cp;
             snap[8 * nn + k] = cm;
             snap[9 * nn + k] = q;
-        }
-        if (SNAP) {
             red[0] = phi;
             red[1] = q;
         }

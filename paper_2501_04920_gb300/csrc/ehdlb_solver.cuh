@@ -72,6 +72,12 @@ template <typename T> class Solver : public SolverBase {
             }
             EHDLB_CK(alloc((void **)&part2_, sizeof(double) * 2 * (size_t)nbmax));
         }
+        EHDLB_CK((main_attr<true, true, false>()));
+        EHDLB_CK((main_attr<true, false, true>()));
+        EHDLB_CK((main_attr<true, false, false>()));
+        EHDLB_CK((main_attr<false, true, false>()));
+        EHDLB_CK((main_attr<false, false, true>()));
+        EHDLB_CK((main_attr<false, false, false>()));
         EHDLB_CK(tb_attr<1>());
         EHDLB_CK(tb_attr<2>());
         if constexpr (TB_MAX >= 5) {
@@ -143,6 +149,7 @@ template <typename T> class Solver : public SolverBase {
 
     void set_schedule(const int *c, int n) override { sched_.assign(c, c + n); }
     void set_timing(int on) override { timing_ = on != 0; }
+    void set_tuning(int sweeps_per_launch) override { tb_chunk_ = sweeps_per_launch; }
 
     int step(int nsteps, ehdlb_stats *st, std::string &err) override
     {
@@ -284,6 +291,15 @@ template <typename T> class Solver : public SolverBase {
         d.W = (T)p.W;
         d.tau_h = (T)(0.5 + 3.0 * p.M_phi);
         d.nhat_eps2 = (T)(p.nhat_eps * p.nhat_eps);
+        d.s_h = (T)(1.0 / (0.5 + 3.0 * p.M_phi));
+        d.sfree_h = (T)(p.bgk ? 1.0 / (0.5 + 3.0 * p.M_phi) : p.s_free);
+        d.s_f0 = (T)((p.rho_ratio == 1.0 && p.eta_ratio == 1.0) ? 1.0 / p.tau_f : 0.0);
+        const bool uniform_D = !p.einstein_D || p.mu_r == 1.0;
+        d.s_p0 = (T)(uniform_D ? 1.0 / (0.5 + 3.0 * (p.einstein_D ? p.D : p.D)) : 0.0);
+        d.s_n0 = (T)(uniform_D ? 1.0 / (0.5 + 3.0 * (p.einstein_D ? p.D * p.m : p.D)) : 0.0);
+        d.inv_mu_v = (T)(1.0 / p.mu_v);
+        d.three_over_tau_g = (T)(3.0 / (0.5 + 3.0 * p.vartheta));
+        d.inv_W = (T)(1.0 / p.W);
         d.mu_v = (T)p.mu_v;
         d.mu1 = (T)(p.mu_r - 1.0);
         d.m = (T)p.m;
@@ -315,6 +331,12 @@ template <typename T> class Solver : public SolverBase {
         return dim3((nx + tx - 1) / tx, (ny + ty - 1) / ty);
     }
 
+    template <bool S, bool F, bool R> cudaError_t main_attr()
+    {
+        return cudaFuncSetAttribute(k_main<T, S, F, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)main_smem_bytes<T>());
+    }
+
     template <int NSW> cudaError_t tb_attr()
     {
         cudaError_t e = cudaFuncSetAttribute(k_sweep_tb<T, NSW, TB_RH, false>,
@@ -332,10 +354,10 @@ template <typename T> class Solver : public SolverBase {
         const dim3 g = tb_grid(NSW, nx_, ny_);
         const size_t sm = tb_smem_bytes<T, TB_RH>();
         if (resid)
-            k_sweep_tb<T, NSW, TB_RH, true><<<g, dim3(32, 8), sm, stream_>>>(dp_, g_[0], g_[1], phig_, q_,
+            k_sweep_tb<T, NSW, TB_RH, true><<<g, dim3(32, 16), sm, stream_>>>(dp_, g_[0], g_[1], phig_, q_,
                                                                            part2_, ctl_, m);
         else
-            k_sweep_tb<T, NSW, TB_RH, false><<<g, dim3(32, 8), sm, stream_>>>(dp_, g_[0], g_[1], phig_, q_,
+            k_sweep_tb<T, NSW, TB_RH, false><<<g, dim3(32, 16), sm, stream_>>>(dp_, g_[0], g_[1], phig_, q_,
                                                                             part2_, ctl_, m);
         ++launches_;
         ++sweep_launches_;
@@ -410,8 +432,8 @@ template <typename T> class Solver : public SolverBase {
         const dim3 b(BX, BY);
         int *unstable = &ctl_->unstable;
 #define EHDLB_MAIN(S, F, R)                                                                              \
-    k_main<T, S, F, R><<<grid_, b, 0, stream_>>>(dp_, pops_[par], pops_[par ^ 1], g_[0], g_[1], ctl_,     \
-                                                 phig_, phiu_, psi_prev_, snap_, part_, unstable)
+    k_main<T, S, F, R><<<grid_, b, main_smem_bytes<T>(), stream_>>>(dp_, pops_[par], pops_[par ^ 1], g_[0], \
+                                                 g_[1], ctl_, phig_, phiu_, psi_prev_, snap_, part_, unstable)
         if (last) {
             if (frozen) EHDLB_MAIN(true, true, false);
             else if (main_resid) EHDLB_MAIN(true, false, true);
@@ -482,7 +504,7 @@ template <typename T> class Solver : public SolverBase {
     T *g_[2]{};
     T *phig_ = nullptr, *q_ = nullptr, *phiu_ = nullptr, *psi_prev_ = nullptr, *snap_ = nullptr;
     double *part_ = nullptr, *part2_ = nullptr, *stage_ = nullptr;
-    int tb_chunk_ = sizeof(T) == 4 ? 4 : 2;  // sweeps fused per launch (0: one per launch)
+    int tb_chunk_ = sizeof(T) == 4 ? 5 : 2;  // sweeps fused per launch (0: one per launch)
     Control *ctl_ = nullptr;
     Control ctl_h_{};
     int *counts_ = nullptr;
