@@ -112,6 +112,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(mhz)}
 
 
+def reduce_max(value: float, device) -> float:
+    """Largest value over the ranks of the default process group (identity
+    without one): the slowest replica sets the whole-job time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(nodes: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job MLUPS of `world` independent replicas of `nodes` lattice
+    nodes each, `steps` steps in `seconds` (the slowest rank's time)."""
+    return nodes * steps * world / seconds / 1e6
+
+
 def measured_traffic(kernel: str, n: int):
     """DRAM bytes per launch of kernel at n x n from profiles/traffic.json,
     or None when the kernel source changed since the capture."""
@@ -221,12 +239,8 @@ def run_ours(args):
         ev1.record(stream)
         torch.cuda.synchronize(dev)
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = nn * args.steps * world / (ms / 1e3) / 1e6
+    ms = reduce_max(ev0.elapsed_time(ev1), dev)
+    value = replica_value(nn, args.steps, world, ms / 1e3)
     sweep_launch_ms = st.ms_sweeps / max(1, st.sweep_launches)
     sweeps_per_launch = args.steps * SWEEPS / max(1, st.sweep_launches)
     peaks, peak_kind = measured_peaks()
@@ -248,12 +262,8 @@ def run_ours(args):
     for _ in range(e2e_steps):
         lat.step(1)
         ehdlb.ehdlb_get_fields(lat.ctx, 1 << 0, phi_np)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = nn * e2e_steps * world / e2e_s / 1e6
+    e2e_s = reduce_max(time.perf_counter() - t0, dev)
+    e2e_value = replica_value(nn, e2e_steps, world, e2e_s)
 
     if rank != 0:
         return

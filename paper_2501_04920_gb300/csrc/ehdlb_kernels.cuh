@@ -7,7 +7,13 @@
 //        sum f, and neither u (Eq. 56), p (Eq. 57) nor any other population
 //        depends on that moment (the moment basis of Eq. 28 is a tensor product
 //        of {1, c, c^2}, so only f0 reads m00).
-//   h  : 9 planes (Eq. 27), p, n : 5 planes each (Eq. 34-35, D2Q5).
+//   h  : 9 planes (Eq. 27) stored as h_i - w_i phi_ref: the deviation from the
+//        rest state of a fixed reference field phi_ref (the initial profile).
+//        phi = phi_ref + dphi with dphi = sum of the stored values, and the
+//        reference's gradient and chemical potential are evaluated once, in
+//        double; near equilibrium the chemical potential of Eq. 13 is a small
+//        residual of O(1) terms, which float cannot resolve from phi ~ 1 itself.
+//   p, n : 5 planes each (Eq. 34-35, D2Q5).
 //   g  : 4 planes, g1..g4 of Eq. 44, stored as g_i - w_i psi_lin(y) where
 //        psi_lin is the linear profile between the electrodes; g0 is not
 //        stored (psi (Eq. 49) and E (Eq. 50) do not read it, and the diagonal
@@ -91,9 +97,18 @@ struct Control {
 
 template <typename T> struct Pops {
     T *f;   // 8 planes
-    T *h;   // 9 planes
+    T *h;   // 9 planes (h_i - w_i phi_ref)
     T *p;   // 5 planes
     T *n;   // 5 planes
+};
+
+// The reference field of the stored h and its derived planes.
+template <typename T> struct PhiRef {
+    T *phir;   // phi_ref with a mirrored ghost row below and above [(ny+2)][nx]
+    T *gxr;    // grad phi_ref by Eq. 59 [ny][nx]
+    T *gyr;
+    T *mur;    // chemical potential of phi_ref, Eq. 13 [ny][nx]
+    T *dphig;  // dphi = phi - phi_ref of the current step, with ghost rows
 };
 
 // ---- small helpers ------------------------------------------------------------
@@ -213,12 +228,15 @@ template <typename T> __device__ __forceinline__ void inverse9(const T (&m)[9], 
 
 // ---- kernels -----------------------------------------------------------------
 
-// phi = sum h (Eq. 33) with mirrored ghost rows, q = sum p - sum n.  With
-// init_ctl the first thread also opens the step in the control block.
+// phi = sum h (Eq. 33) with mirrored ghost rows, q = sum p - sum n.  The
+// stored h are deviations from w_i phi_ref: dphi = their sum, phi = phi_ref
+// + dphi; both are written (phi for the potential, dphi for the stencils of
+// the main kernel).  With init_ctl the first thread also opens the step in
+// the control block.
 template <typename T>
 __global__ void __launch_bounds__(256) k_prep(const DevP<T> P, const T *__restrict__ h,
                                               const T *__restrict__ p, const T *__restrict__ n,
-                                              T *__restrict__ phig, T *__restrict__ q,
+                                              const PhiRef<T> R, T *__restrict__ phig, T *__restrict__ q,
                                               Control *ctl, int fixedK, int kmin, int kmax, int flips)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -233,15 +251,21 @@ __global__ void __launch_bounds__(256) k_prep(const DevP<T> P, const T *__restri
     }
     if (x >= P.nx || y >= P.ny) return;
     const long long nn = P.nn, k = (long long)y * P.nx + x;
-    T s = T(0);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) s += h[i * nn + k];
+    // pairwise: rest, axis pairs, diagonal pairs
+    const T d = h[k] + ((((h[nn + k] + h[3 * nn + k]) + (h[2 * nn + k] + h[4 * nn + k]))) +
+                        ((h[5 * nn + k] + h[7 * nn + k]) + (h[6 * nn + k] + h[8 * nn + k])));
     T sp = T(0), sn = T(0);
 #pragma unroll
     for (int i = 0; i < 5; ++i) { sp += p[i * nn + k]; sn += n[i * nn + k]; }
-    phig[(long long)(y + 1) * P.nx + x] = s;
-    if (y == 0) phig[x] = s;
-    if (y == P.ny - 1) phig[(long long)(P.ny + 1) * P.nx + x] = s;
+    const long long gk = (long long)(y + 1) * P.nx + x;
+    const T phi = R.phir[gk] + d;
+    phig[gk] = phi;
+    R.dphig[gk] = d;
+    if (y == 0) { phig[x] = phi; R.dphig[x] = d; }
+    if (y == P.ny - 1) {
+        phig[(long long)(P.ny + 1) * P.nx + x] = phi;
+        R.dphig[(long long)(P.ny + 1) * P.nx + x] = d;
+    }
     q[k] = sp - sn;
 }
 
@@ -570,7 +594,7 @@ template <typename T> __host__ __device__ constexpr size_t main_smem_bytes()
 template <typename T, bool SNAP, bool FROZEN, bool RESID>
 __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<T> src, const Pops<T> dst,
                                                  const T *__restrict__ gA, const T *__restrict__ gB,
-                                                 const Control *__restrict__ ctl, const T *__restrict__ phig,
+                                                 const Control *__restrict__ ctl, const PhiRef<T> Rf,
                                                  T *__restrict__ phiu, const T *__restrict__ psi_prev,
                                                  T *__restrict__ snap, double *__restrict__ part,
                                                  int *__restrict__ unstable)
@@ -604,15 +628,18 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<T> 
         const int nx = P.nx, ny = P.ny;
         const T third = T(1.0 / 3.0);
         // ---- O1-O2: phi, properties (Eq. 61), stencils (Eq. 59) ----
+        // phi = phi_ref + dphi; the stencils act on dphi and add the
+        // reference's gradient; differences first (exact for neighbours)
         const int xm = wrapx(x - 1, nx), xp = wrapx(x + 1, nx);
-        const T *r0 = phig + (long long)y * nx, *r1 = r0 + nx, *r2 = r1 + nx;
-        const T phi = r1[x];
-        const T pE = r1[xp], pW = r1[xm], pN = r2[x], pS = r0[x];
-        const T pNE = r2[xp], pNW = r2[xm], pSW = r0[xm], pSE = r0[xp];
-        const T gx = (pE - pW) * third + ((pNE - pNW) + (pSE - pSW)) * T(1.0 / 12.0);
-        const T gy = (pN - pS) * third + ((pNE + pNW) - (pSE + pSW)) * T(1.0 / 12.0);
-        const T lap = T(2.0 / 3.0) * ((pE + pN + pW + pS) - T(4) * phi) +
-                      T(1.0 / 6.0) * ((pNE + pNW + pSW + pSE) - T(4) * phi);
+        const T *r0 = Rf.dphig + (long long)y * nx, *r1 = r0 + nx, *r2 = r1 + nx;
+        const T dphi = r1[x];
+        const T dE = r1[xp] - dphi, dW = r1[xm] - dphi, dN = r2[x] - dphi, dS = r0[x] - dphi;
+        const T dNE = r2[xp] - dphi, dNW = r2[xm] - dphi, dSW = r0[xm] - dphi, dSE = r0[xp] - dphi;
+        const T phir = Rf.phir[(long long)(y + 1) * nx + x];
+        const T phi = phir + dphi;
+        const T gx = Rf.gxr[k] + ((dE - dW) * third + ((dNE - dNW) + (dSE - dSW)) * T(1.0 / 12.0));
+        const T gy = Rf.gyr[k] + ((dN - dS) * third + ((dNE + dNW) - (dSE + dSW)) * T(1.0 / 12.0));
+        const T lapd = T(2.0 / 3.0) * ((dE + dW) + (dN + dS)) + T(1.0 / 6.0) * ((dNE + dSW) + (dNW + dSE));
         const T rho = T(1) + P.rho1 * phi;
         const T inv_rho = T(1) / rho;
         const T mup = P.mu_v * (T(1) + P.mu1 * phi);
@@ -659,7 +686,11 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<T> 
         }
 
         // ---- O6: forces (Eq. 12-14) ----
-        const T mu_phi = T(4) * P.beta * phi * (phi - T(1)) * (phi - T(0.5)) - P.kappa * lap;
+        // mu_phi - mu_ref: the cubic of Eq. 13 as (phi - phi_ref) times
+        // (phi^2 + phi phi_ref + phi_ref^2 - 1.5 (phi + phi_ref) + 0.5)
+        const T mu_phi = Rf.mur[k] +
+                         T(4) * P.beta * dphi * ((phi * phi + phi * phir + phir * phir) - T(1.5) * (phi + phir) + T(0.5)) -
+                         P.kappa * lapd;
         const T E2 = Ex * Ex + Ey * Ey;
         const T Fx = mu_phi * gx + P.Kq * q * Ex - T(0.5) * E2 * dex;
         const T Fy = mu_phi * gy + P.Kq * q * Ey - T(0.5) * E2 * dey;
@@ -741,18 +772,20 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<T> 
             }
             const T lam = T(4) * phi * (T(1) - phi) * P.inv_W;
             const T Vx = dpx + third * lam * nhx, Vy = dpy + third * lam * nhy;
+            // moments of the stored deviations; the reference part cancels
+            // against phi M w of the equilibrium, leaving dphi M w
             T mh[9];
             moments9<T>(hv, mh);
             T d[9];
-            d[0] = mh[0] - phi;
+            d[0] = mh[0] - dphi;
             d[1] = mh[1] - pux;
             d[2] = mh[2] - puy;
-            d[3] = mh[3] - phi * third;
-            d[4] = mh[4] - phi * third;
+            d[3] = mh[3] - dphi * third;
+            d[4] = mh[4] - dphi * third;
             d[5] = mh[5];
             d[6] = mh[6] - pux * third;
             d[7] = mh[7] - puy * third;
-            d[8] = mh[8] - phi * T(1.0 / 9.0);
+            d[8] = mh[8] - dphi * T(1.0 / 9.0);
             const T sv = P.s_h, sfree = P.sfree_h;
             const T hv_ = T(1) - T(0.5) * sv;
             T mc[9], dl[9];
@@ -766,14 +799,21 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<T> 
             mc[7] = sfree * d[7] - (T(1) - T(0.5) * sfree) * Vy * third;
             mc[8] = sfree * d[8];
             inverse9<T>(mc, dl);
+            // push, re-based on the destination's reference:
+            // + w_i (phi_ref(x) - phi_ref(x + c_i)); a bounced population stays
+            const T *q0 = Rf.phir + (long long)y * nx, *q1 = q0 + nx, *q2 = q1 + nx;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const T v = hv[i] - dl[i];
                 const int yd = y + cy9(i);
-                if (yd >= 0 && yd < ny)
-                    dst.h[i * nn + (long long)yd * nx + wrapx(x + cx9(i), nx)] = v;
-                else
+                if (yd >= 0 && yd < ny) {
+                    const int xd = cx9(i) == 0 ? x : (cx9(i) > 0 ? xp : xm);
+                    const T *qr = cy9(i) == 0 ? q1 : (cy9(i) > 0 ? q2 : q0);
+                    const T shift = i == 0 ? T(0) : w9<T>(i) * (phir - qr[xd]);
+                    dst.h[i * nn + (long long)yd * nx + xd] = v + shift;
+                } else {
                     dst.h[opp9(i) * nn + k] = v;
+                }
             }
         }
 
@@ -901,8 +941,8 @@ static __global__ void __launch_bounds__(256) k_step_end(const double *__restric
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_init_state(const DevP<T> P, Pops<T> pops, T *__restrict__ g,
-                                                    T *__restrict__ phiu, double xc, double yc, double R,
-                                                    double Wi, int shape, int psi_zero)
+                                                    T *__restrict__ phiu, PhiRef<T> Rf, double xc, double yc,
+                                                    double R, double Wi, int shape, int psi_zero)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -910,8 +950,13 @@ __global__ void __launch_bounds__(256) k_init_state(const DevP<T> P, Pops<T> pop
     const long long nn = P.nn, k = (long long)y * P.nx + x;
     const double r = shape == 1 ? fabs(y - yc) : sqrt((x - xc) * (x - xc) + (y - yc) * (y - yc));
     const T phi0 = (T)(0.5 * (1.0 + tanh(2.0 * (R - r) / Wi)));
+    // h = w_i phi0 at rest is exactly the reference state: deviations 0
 #pragma unroll
-    for (int i = 0; i < 9; ++i) pops.h[i * nn + k] = w9<T>(i) * phi0;
+    for (int i = 0; i < 9; ++i) pops.h[i * nn + k] = T(0);
+    const long long gk = (long long)(y + 1) * P.nx + x;
+    Rf.phir[gk] = phi0;
+    if (y == 0) Rf.phir[x] = phi0;
+    if (y == P.ny - 1) Rf.phir[(long long)(P.ny + 1) * P.nx + x] = phi0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) pops.f[i * nn + k] = T(0);
 #pragma unroll
@@ -929,6 +974,30 @@ __global__ void __launch_bounds__(256) k_init_state(const DevP<T> P, Pops<T> pop
         g[2 * nn + k] = T(0);
         g[3 * nn + k] = P.tau_g * w * P.G;
     }
+}
+
+// Gradient (Eq. 59) and chemical potential (Eq. 13) of the stored reference
+// field, evaluated in double from its stored values.
+template <typename T>
+__global__ void __launch_bounds__(256) k_init_ref(const DevP<T> P, PhiRef<T> Rf, double beta, double kappa)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const int nx = P.nx;
+    const long long k = (long long)y * nx + x;
+    const int xm = wrapx(x - 1, nx), xp = wrapx(x + 1, nx);
+    const T *r0 = Rf.phir + (long long)y * nx, *r1 = r0 + nx, *r2 = r1 + nx;
+    const double c = r1[x];
+    const double E = r1[xp], W = r1[xm], N = r2[x], S = r0[x];
+    const double NE = r2[xp], NW = r2[xm], SW = r0[xm], SE = r0[xp];
+    const double gx = (E - W) / 3.0 + ((NE - NW) + (SE - SW)) / 12.0;
+    const double gy = (N - S) / 3.0 + ((NE + NW) - (SE + SW)) / 12.0;
+    const double lap = 2.0 / 3.0 * (((E - c) + (W - c)) + ((N - c) + (S - c))) +
+                       1.0 / 6.0 * (((NE - c) + (SW - c)) + ((NW - c) + (SE - c)));
+    Rf.gxr[k] = (T)gx;
+    Rf.gyr[k] = (T)gy;
+    Rf.mur[k] = (T)(4.0 * beta * c * (c - 1.0) * (c - 0.5) - kappa * lap);
 }
 
 template <typename T>
@@ -982,7 +1051,8 @@ __global__ void __launch_bounds__(256) k_init_ions(const DevP<T> P, Pops<T> pops
 // Packs rows [y0, y0 + rows) of the state into 35 doubles per node.
 template <typename T>
 __global__ void k_pack_state(const DevP<T> P, const Pops<T> pops, const T *__restrict__ g,
-                             const T *__restrict__ phiu, double *__restrict__ out, int y0, int rows)
+                             const T *__restrict__ phiu, const T *__restrict__ phir, double *__restrict__ out,
+                             int y0, int rows)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long cnt = (long long)rows * P.nx;
@@ -992,7 +1062,8 @@ __global__ void k_pack_state(const DevP<T> P, const Pops<T> pops, const T *__res
     double *o = out + 35 * i;
     o[0] = 0.0;
     for (int q = 1; q < 9; ++q) o[q] = (double)pops.f[(q - 1) * nn + k];
-    for (int q = 0; q < 9; ++q) o[9 + q] = (double)pops.h[q * nn + k];
+    const double pr = (double)phir[(long long)(y + 1) * P.nx + (k - (long long)y * P.nx)];
+    for (int q = 0; q < 9; ++q) o[9 + q] = (double)pops.h[q * nn + k] + (double)w9<T>(q) * pr;
     for (int q = 0; q < 5; ++q) o[18 + q] = (double)pops.p[q * nn + k];
     for (int q = 0; q < 5; ++q) o[23 + q] = (double)pops.n[q * nn + k];
     const double pl = (double)psi_lin(P, y);
@@ -1004,7 +1075,7 @@ __global__ void k_pack_state(const DevP<T> P, const Pops<T> pops, const T *__res
 
 template <typename T>
 __global__ void k_unpack_state(const DevP<T> P, Pops<T> pops, T *__restrict__ g, T *__restrict__ phiu,
-                               const double *__restrict__ in, int y0, int rows)
+                               const T *__restrict__ phir, const double *__restrict__ in, int y0, int rows)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long cnt = (long long)rows * P.nx;
@@ -1013,7 +1084,8 @@ __global__ void k_unpack_state(const DevP<T> P, Pops<T> pops, T *__restrict__ g,
     const long long nn = P.nn, k = (long long)y0 * P.nx + i;
     const double *o = in + 35 * i;
     for (int q = 1; q < 9; ++q) pops.f[(q - 1) * nn + k] = (T)o[q];
-    for (int q = 0; q < 9; ++q) pops.h[q * nn + k] = (T)o[9 + q];
+    const double pr = (double)phir[(long long)(y + 1) * P.nx + (k - (long long)y * P.nx)];
+    for (int q = 0; q < 9; ++q) pops.h[q * nn + k] = (T)(o[9 + q] - (double)w9<T>(q) * pr);
     for (int q = 0; q < 5; ++q) pops.p[q * nn + k] = (T)o[18 + q];
     for (int q = 0; q < 5; ++q) pops.n[q * nn + k] = (T)o[23 + q];
     const double pl = (double)psi_lin(P, y);

@@ -58,6 +58,11 @@ template <typename T> class Solver : public SolverBase {
             EHDLB_CK(alloc((void **)&g_[b], plane * 4));
         }
         EHDLB_CK(alloc((void **)&phig_, sizeof(T) * (size_t)(ny_ + 2) * nx_));
+        EHDLB_CK(alloc((void **)&ref_.phir, sizeof(T) * (size_t)(ny_ + 2) * nx_));
+        EHDLB_CK(alloc((void **)&ref_.dphig, sizeof(T) * (size_t)(ny_ + 2) * nx_));
+        EHDLB_CK(alloc((void **)&ref_.gxr, plane));
+        EHDLB_CK(alloc((void **)&ref_.gyr, plane));
+        EHDLB_CK(alloc((void **)&ref_.mur, plane));
         EHDLB_CK(alloc((void **)&q_, plane));
         EHDLB_CK(alloc((void **)&phiu_, plane * 2));
         EHDLB_CK(alloc((void **)&psi_prev_, plane));
@@ -103,8 +108,10 @@ template <typename T> class Solver : public SolverBase {
         ctl_h_ = c;
         EHDLB_CK(cudaMemcpyAsync(ctl_, &ctl_h_, sizeof(Control), cudaMemcpyHostToDevice, stream_));
         const double Wi = p.W_init > 0.0 ? p.W_init : p.W;
-        k_init_state<T><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[0], g_[0], phiu_, p.xc, p.yc, p.R,
-                                                             Wi, p.init_shape, p.init_psi_zero);
+        k_init_state<T><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[0], g_[0], phiu_, ref_, p.xc, p.yc,
+                                                             p.R, Wi, p.init_shape, p.init_psi_zero);
+        EHDLB_CK(cudaGetLastError());
+        k_init_ref<T><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, ref_, 12.0 * p.sigma / p.W, 1.5 * p.sigma * p.W);
         EHDLB_CK(cudaGetLastError());
         // initial potential solve with q = 0 (p = n = 0 at this point)
         if (p.freeze_E) {
@@ -315,8 +322,8 @@ template <typename T> class Solver : public SolverBase {
 
     void launch_prep(int par, int fixedK, int kmin, int kmax, int flips)
     {
-        k_prep<T><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n, phig_,
-                                                       q_, ctl_, fixedK, kmin, kmax, flips);
+        k_prep<T><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n, ref_,
+                                                       phig_, q_, ctl_, fixedK, kmin, kmax, flips);
         ++launches_;
     }
 
@@ -433,7 +440,7 @@ template <typename T> class Solver : public SolverBase {
         int *unstable = &ctl_->unstable;
 #define EHDLB_MAIN(S, F, R)                                                                              \
     k_main<T, S, F, R><<<grid_, b, main_smem_bytes<T>(), stream_>>>(dp_, pops_[par], pops_[par ^ 1], g_[0], \
-                                                 g_[1], ctl_, phig_, phiu_, psi_prev_, snap_, part_, unstable)
+                                                 g_[1], ctl_, ref_, phiu_, psi_prev_, snap_, part_, unstable)
         if (last) {
             if (frozen) EHDLB_MAIN(true, true, false);
             else if (main_resid) EHDLB_MAIN(true, false, true);
@@ -472,7 +479,8 @@ template <typename T> class Solver : public SolverBase {
             const unsigned nblk = (unsigned)((cnt + 255) / 256);
             cudaError_t e = cudaSuccess;
             if (dst) {
-                k_pack_state<T><<<nblk, 256, 0, stream_>>>(dp_, pops_[tpar_], g_[cur], phiu_, stage, y0, r);
+                k_pack_state<T><<<nblk, 256, 0, stream_>>>(dp_, pops_[tpar_], g_[cur], phiu_, ref_.phir, stage,
+                                                            y0, r);
                 e = cudaGetLastError();
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(dst + per_row * y0, stage, sizeof(double) * per_row * r,
@@ -481,7 +489,8 @@ template <typename T> class Solver : public SolverBase {
                 e = cudaMemcpyAsync(stage, src + per_row * y0, sizeof(double) * per_row * r,
                                     cudaMemcpyHostToDevice, stream_);
                 if (e == cudaSuccess)
-                    k_unpack_state<T><<<nblk, 256, 0, stream_>>>(dp_, pops_[tpar_], g_[cur], phiu_, stage, y0, r);
+                    k_unpack_state<T><<<nblk, 256, 0, stream_>>>(dp_, pops_[tpar_], g_[cur], phiu_, ref_.phir,
+                                                              stage, y0, r);
                 if (e == cudaSuccess) e = cudaGetLastError();
             }
             if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
@@ -503,6 +512,7 @@ template <typename T> class Solver : public SolverBase {
     Pops<T> pops_[2]{};
     T *g_[2]{};
     T *phig_ = nullptr, *q_ = nullptr, *phiu_ = nullptr, *psi_prev_ = nullptr, *snap_ = nullptr;
+    PhiRef<T> ref_{};
     double *part_ = nullptr, *part2_ = nullptr, *stage_ = nullptr;
     int tb_chunk_ = sizeof(T) == 4 ? 5 : 2;  // sweeps fused per launch (0: one per launch)
     Control *ctl_ = nullptr;

@@ -16,12 +16,14 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 FP32_TOL = 1e-5
-# FP32 |u| bound.  Storing the Allen-Cahn populations h in float alone (all
-# arithmetic in double, emulated with the oracle) already moves |u| by 1.9e-5
-# relative after 100 steps of the 256^2 case: near equilibrium the
-# surface-tension force is mu_phi grad phi with mu_phi a small residual of
-# kappa lap(phi), and lap(phi) inherits the float rounding of phi ~ 1.
-FP32_U_TOL = 2e-4
+# FP32 |u| bound.  Near equilibrium the surface-tension force is mu_phi
+# grad phi with mu_phi a small residual of kappa lap(phi) and a cubic of phi
+# ~ 1; the library stores h relative to a reference profile so that float
+# carries only the small deviation (the storage alone, emulated with the
+# oracle, then moves |u| by 9.4e-7 after 100 steps of the 256^2 case).  The
+# float arithmetic of the remaining terms leaves 1.2e-5 after 100 steps and
+# 8.2e-6 after 300 of that case; phi, psi and q stay below 1e-6.
+FP32_U_TOL = 3e-5
 
 
 def rel_linf(a, b):
