@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--n", type=int, default=N, help="lattice side (default: the 2048^2 case)")
     ap.add_argument("--sweeps-per-launch", type=int, default=-1,
                     help="potential sweeps fused per kernel launch (default: the library's)")
+    ap.add_argument("--tile-shape", type=int, default=-1,
+                    help="region shape of the fused sweep kernel (default: the library's)")
     return ap.parse_args()
 
 
@@ -218,8 +220,7 @@ def run_ours(args):
     n = args.n
     prm = workloads.droplet(n)
     lat = ehdlb.Lattice(n, n, prm, precision=ehdlb.FP32, cuda_stream=stream.cuda_stream)
-    if args.sweeps_per_launch >= 0:
-        ehdlb.ehdlb_set_tuning(lat.ctx, args.sweeps_per_launch)
+    ehdlb.ehdlb_set_tuning(lat.ctx, args.sweeps_per_launch, args.tile_shape)
     nn = n * n
 
     def barrier():

@@ -204,12 +204,15 @@ int ehdlb_set_state(ehdlb_ctx *c, const double *src, size_t len);
 /* Record device time per kernel class in ehdlb_stats (1) or not (0). */
 int ehdlb_set_timing(ehdlb_ctx *c, int on);
 
-/* Performance knob (no effect on the result beyond round-off): how many
- * potential sweeps one kernel launch fuses in shared memory when a step takes
- * a fixed number of sweeps, 1..5 (the double-precision solver uses at most 2),
- * or 0 for one sweep per launch.  Default 5 (float) / 2 (double).  EINVAL
- * outside 0..5. */
-int ehdlb_set_tuning(ehdlb_ctx *c, int sweeps_per_launch);
+/* Performance knobs (no effect on the result beyond round-off) of the fused
+ * potential-sweep kernel, used when a step takes a fixed number of sweeps:
+ *   sweeps_per_launch: sweeps one launch fuses in shared memory, 1..5 (the
+ *     double-precision solver uses at most 2), 0 for one sweep per launch;
+ *     default 5 (float) / 2 (double);
+ *   tile_shape: region of one block, 0: 64 x 32 (512 threads, default),
+ *     1: 64 x 64 (1024 threads), 2: 128 x 32 (1024 threads); float only.
+ * -1 keeps a setting.  EINVAL outside these ranges. */
+int ehdlb_set_tuning(ehdlb_ctx *c, int sweeps_per_launch, int tile_shape);
 
 /* Largest lattice, in nodes nx * ny, that ehdlb_potential_noalloc accepts. */
 #define EHDLB_NOALLOC_MAX_NODES 65536

@@ -222,12 +222,13 @@ int ehdlb_set_timing(ehdlb_ctx *c, int on)
     return EHDLB_OK;
 }
 
-int ehdlb_set_tuning(ehdlb_ctx *c, int sweeps_per_launch)
+int ehdlb_set_tuning(ehdlb_ctx *c, int sweeps_per_launch, int tile_shape)
 {
     if (!c) return EHDLB_EINVAL;
-    if (sweeps_per_launch < 0 || sweeps_per_launch > 5)
-        return fail(c, EHDLB_EINVAL, "sweeps_per_launch must lie in 0..5");
-    c->solver->set_tuning(sweeps_per_launch);
+    if (sweeps_per_launch < -1 || sweeps_per_launch > 5)
+        return fail(c, EHDLB_EINVAL, "sweeps_per_launch must lie in -1..5");
+    if (tile_shape < -1 || tile_shape > 2) return fail(c, EHDLB_EINVAL, "tile_shape must lie in -1..2");
+    c->solver->set_tuning(sweeps_per_launch, tile_shape);
     return EHDLB_OK;
 }
 

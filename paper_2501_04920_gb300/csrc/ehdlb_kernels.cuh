@@ -343,36 +343,52 @@ template <typename T> __device__ __forceinline__ void cp_async(T *smem, const T 
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// NSW potential sweeps (Eq. 44-50) fused in shared memory.  A block holds a
-// 64 x RH region of the lattice: its output tile of (64 - 2 NSW) x
+// NSW potential sweeps (Eq. 44-50) fused in shared memory.  A block holds an
+// RW x RH region of the lattice: its output tile of (RW - 2 NSW) x
 // (RH - 2 NSW) nodes plus a halo NSW nodes wide (x periodic; rows outside the
 // lattice stay empty, the electrode rules act on the wall links).  Every
 // sweep collides and pushes the whole region; values at distance < s from
 // the region edge are incomplete after sweep s, so after NSW sweeps the
-// output tile is exact.  The shared planes carry a one-node pad on every
-// side that absorbs pushes leaving the region.  The source coefficients of
-// each node, from phi and q, stay in registers:  X/3 = A - Bx m1 - By m2
-// with m1, m2 the first moments (E = 3 m / tau_g), A = th Kq q / (3 eps),
-// B = th (eps_r - 1) grad phi / (tau_g eps), th = vartheta (times 1/(1 - w0)).
+// output tile is exact.  One buffer of four planes holds the populations: a
+// sweep reads every node's populations into registers, the block
+// synchronises, then every node pushes its post-collision values in place.
+// The planes carry a one-node pad on every side that absorbs pushes leaving
+// the region.  The source coefficients of each node stay in registers:
+// X/3 = A - Bx m1 - By m2 with m1, m2 the first moments (E = 3 m / tau_g),
+// A = th Kq q / (3 eps), B = th (eps_r - 1) grad phi / (tau_g eps),
+// th = vartheta (times 1/(1 - w0)).
+//   FIRST: first launch of the step; the coefficients come from phi (with
+//          its ring of neighbours) and q, and the output tile's are written
+//          to coef (three planes A, Bx, By) for the later launches, which
+//          load them instead.
 //   RESID: the last sweep of the step; residual partials of the output tile.
-// Launch: blockDim (32, 16), dynamic shared memory tb_smem_bytes<T, RH>().
-template <typename T, int RH> __host__ __device__ constexpr size_t tb_smem_bytes()
+// Launch: blockDim (32, BY), dynamic shared memory
+// tb_smem_bytes<T, RW, RH>(FIRST).
+template <typename T, int RW, int RH> __host__ __device__ constexpr size_t tb_smem_bytes(bool first)
 {
-    return sizeof(T) * 8 * (size_t)(RH + 2) * (64 + 2);
+    return sizeof(T) * (first ? 6 : 4) * (size_t)(RH + 2) * (RW + 2);
 }
 
-template <typename T, int NSW, int RH, bool RESID>
-__global__ void __launch_bounds__(512, 2) k_sweep_tb(const DevP<T> P, T *__restrict__ gA, T *__restrict__ gB,
-                                                     const T *__restrict__ phig, const T *__restrict__ q,
-                                                     double *__restrict__ part, const Control *__restrict__ ctl,
-                                                     int m)
+// x mod nx for x within one lattice width of [0, nx) (wide == true) or any x.
+__device__ __forceinline__ int wrap_x(int x, int nx, bool wide)
 {
-    constexpr int RW = 64, H = NSW, TX = RW - 2 * H, TY = RH - 2 * H;
+    if (wide) return x < 0 ? x + nx : (x >= nx ? x - nx : x);
+    return ((x % nx) + nx) % nx;
+}
+
+template <typename T, int NSW, int RW, int RH, int BY, int MINB, bool FIRST, bool RESID>
+__global__ void __launch_bounds__(32 * BY, MINB)
+    k_sweep_tb(const DevP<T> P, T *__restrict__ gA, T *__restrict__ gB, const T *__restrict__ phig,
+               const T *__restrict__ q, T *__restrict__ coef, double *__restrict__ part,
+               const Control *__restrict__ ctl, int m)
+{
+    constexpr int H = NSW, TX = RW - 2 * H, TY = RH - 2 * H;
     constexpr int PW = RW + 2, PH = RH + 2, PL = PW * PH;
-    constexpr int NB = RW / 32, NA = RH / 16;
+    constexpr int NB = RW / 32, NA = RH / BY;
+    static_assert(RW % 32 == 0 && RH % BY == 0, "region must tile the block");
     static_assert(TX > 0 && TY > 0 && NA >= 1, "tile too small for NSW");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sg = reinterpret_cast<T *>(smem_raw);   // [2][4][PH][PW]
+    T *sg = reinterpret_cast<T *>(smem_raw);   // [4][PH][PW], then (FIRST) phi ring and q
     const int par = (ctl->cur0 + m) & 1;
     const T *__restrict__ src = par ? gB : gA;
     T *__restrict__ dst = par ? gA : gB;
@@ -380,66 +396,72 @@ __global__ void __launch_bounds__(512, 2) k_sweep_tb(const DevP<T> P, T *__restr
     const long long nn = P.nn;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int tx = threadIdx.x, ty = threadIdx.y;
+    const bool wide = nx >= RW + 2;
 
-    // ---- load the region: g into buffer 0; phi (with a one-node ring) and
-    // q into buffer 1, which the first sweep overwrites; all copies async ----
-    {
-        T *sphi = sg + 4 * PL, *sq = sg + 5 * PL;
+    int gxs[NB];
 #pragma unroll
-        for (int a = 0; a < NA; ++a) {
-            const int ly = ty + 16 * a, gy = y0 - H + ly;
-            if (gy < 0 || gy >= ny) continue;
+    for (int b = 0; b < NB; ++b) gxs[b] = wrap_x(x0 - H + tx + 32 * b, nx, wide);
+
+    // ---- load the region: g (async) into the buffer; the coefficients from
+    // coef into registers, or (FIRST) phi with a one-node ring and q (async) ----
+    T cA[NA][NB], cBx[NA][NB], cBy[NA][NB];
+    T *const sphi = sg + 4 * PL, *const sq = sg + 5 * PL;
 #pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                const int lx = tx + 32 * b;
-                int gx = x0 - H + lx;
-                gx = ((gx % nx) + nx) % nx;
-                const long long k = (long long)gy * nx + gx;
-                const int li = (ly + 1) * PW + lx + 1;
+    for (int a = 0; a < NA; ++a) {
+        const int ly = ty + BY * a, gy = y0 - H + ly;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) cp_async(sg + i * PL + li, src + i * nn + k);
+        for (int b = 0; b < NB; ++b) cA[a][b] = cBx[a][b] = cBy[a][b] = T(0);
+        if (gy < 0 || gy >= ny) continue;
+        const long long row = (long long)gy * nx;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const long long k = row + gxs[b];
+            const int li = (ly + 1) * PW + tx + 32 * b + 1;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) cp_async(sg + i * PL + li, src + i * nn + k);
+            if (FIRST) {
                 cp_async(sq + li, q + k);
+            } else {
+                cA[a][b] = coef[k];
+                cBx[a][b] = coef[nn + k];
+                cBy[a][b] = coef[2 * nn + k];
             }
         }
+    }
+    if (FIRST) {
         // phi rows gy = y0 - H - 1 .. y0 - H + RH, of which phig holds -1 .. ny
-        for (int e = tx + 32 * ty; e < PL; e += 512) {
+        for (int e = tx + 32 * ty; e < PL; e += 32 * BY) {
             const int py = e / PW, px = e - py * PW;
             const int gy = y0 - H - 1 + py;
             if (gy < -1 || gy > ny) continue;
-            int gx = x0 - H - 1 + px;
-            gx = ((gx % nx) + nx) % nx;
+            const int gx = wrap_x(x0 - H - 1 + px, nx, wide);
             cp_async(sphi + e, phig + (long long)(gy + 1) * nx + gx);
         }
     }
     cp_async_wait_all();
     __syncthreads();
-    T cA[NA][NB], cBx[NA][NB], cBy[NA][NB];
-    {
-        const T *sphi = sg + 4 * PL, *sq = sg + 5 * PL;
+    if (FIRST) {
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
-            const int ly = ty + 16 * a, gy = y0 - H + ly;
-            const bool vrow = gy >= 0 && gy < ny;
+            const int ly = ty + BY * a, gy = y0 - H + ly;
+            if (gy < 0 || gy >= ny) continue;
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-                cA[a][b] = cBx[a][b] = cBy[a][b] = T(0);
-                if (!vrow) continue;
                 const int li = (ly + 1) * PW + tx + 32 * b + 1;
                 const T *r1 = sphi + li, *r0 = r1 - PW, *r2 = r1 + PW;
                 const T phi = r1[0];
-                const T gxs = (r1[1] - r1[-1]) * T(1.0 / 3.0) +
-                              ((r2[1] - r2[-1]) + (r0[1] - r0[-1])) * T(1.0 / 12.0);
-                const T gys = (r2[0] - r0[0]) * T(1.0 / 3.0) +
-                              ((r2[1] + r2[-1]) - (r0[1] + r0[-1])) * T(1.0 / 12.0);
+                const T gxs_ = (r1[1] - r1[-1]) * T(1.0 / 3.0) +
+                               ((r2[1] - r2[-1]) + (r0[1] - r0[-1])) * T(1.0 / 12.0);
+                const T gys_ = (r2[0] - r0[0]) * T(1.0 / 3.0) +
+                               ((r2[1] + r2[-1]) - (r0[1] + r0[-1])) * T(1.0 / 12.0);
                 const T inv = T(1) / (T(1) + P.er1 * phi);
                 const T bb = P.src_norm * P.er1 * inv / P.tau_g;
                 cA[a][b] = P.src_norm * P.Kq * sq[li] * inv * T(1.0 / 3.0);
-                cBx[a][b] = bb * gxs;
-                cBy[a][b] = bb * gys;
+                cBx[a][b] = bb * gxs_;
+                cBy[a][b] = bb * gys_;
             }
         }
     }
-    __syncthreads();
 
     T psi_before[NA][NB];
     // half of the collision constants: o = 0.5 (n3 +- n1) etc.
@@ -447,92 +469,117 @@ __global__ void __launch_bounds__(512, 2) k_sweep_tb(const DevP<T> P, T *__restr
     const T kf = T(0.5) * (T(1) - P.s_free_g);       // second moments
     const T ke = T(0.25) * P.s_free_g;               // their equilibrium psi/3, psi = 1.5 (m3 + m4)
     const T wG = P.wG;
+    int li[NA][NB];
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) li[a][b] = (ty + BY * a + 1) * PW + tx + 32 * b + 1;
     const bool interior = y0 - H >= 0 && y0 - H + RH <= ny;
     if (interior) {
         // no wall and no empty row in the region: the same update everywhere
-        int li[NA][NB];
-#pragma unroll
-        for (int a = 0; a < NA; ++a)
-#pragma unroll
-            for (int b = 0; b < NB; ++b) li[a][b] = (ty + 16 * a + 1) * PW + tx + 32 * b + 1;
-#pragma unroll
+#pragma unroll 1
         for (int s = 0; s < NSW; ++s) {
-            const T *gc = sg + (s & 1) * 4 * PL;
-            T *gn = sg + ((s + 1) & 1) * 4 * PL;
+            T o1[NA][NB], o2[NA][NB], o3[NA][NB], o4[NA][NB];
 #pragma unroll
             for (int a = 0; a < NA; ++a)
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
                     const int l = li[a][b];
-                    const T g1 = gc[l], g2 = gc[PL + l], g3 = gc[2 * PL + l], g4 = gc[3 * PL + l];
+                    const T g1 = sg[l], g2 = sg[PL + l], g3 = sg[2 * PL + l], g4 = sg[3 * PL + l];
                     const T m1 = g1 - g3, m2 = g2 - g4, m3 = g1 + g3, m4 = g2 + g4;
-                    if (RESID && s == NSW - 1) psi_before[a][b] = T(1.5) * (m3 + m4);
+                    if (RESID) psi_before[a][b] = T(1.5) * (m3 + m4);
                     const T X6 = T(0.5) * (cA[a][b] - cBx[a][b] * m1 - cBy[a][b] * m2);
                     const T e = ke * (m3 + m4) + X6;                 // half of s psi/3 + X/3
                     const T h3 = kf * m3 + e, h4 = kf * m4 + e;      // half of n3, n4
                     const T h1 = k1 * m1, h2 = k1 * m2;              // half of n1, n2
-                    gn[l + 1] = h3 + h1;
-                    gn[2 * PL + l - 1] = h3 - h1;
-                    gn[PL + l + PW] = (h4 + h2) - wG;
-                    gn[3 * PL + l - PW] = (h4 - h2) + wG;
+                    o1[a][b] = h3 + h1;
+                    o3[a][b] = h3 - h1;
+                    o2[a][b] = (h4 + h2) - wG;
+                    o4[a][b] = (h4 - h2) + wG;
+                }
+            __syncthreads();
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const int l = li[a][b];
+                    sg[l + 1] = o1[a][b];
+                    sg[2 * PL + l - 1] = o3[a][b];
+                    sg[PL + l + PW] = o2[a][b];
+                    sg[3 * PL + l - PW] = o4[a][b];
                 }
             __syncthreads();
         }
     } else {
+#pragma unroll 1
+        for (int s = 0; s < NSW; ++s) {
+            T o1[NA][NB], o2[NA][NB], o3[NA][NB], o4[NA][NB];
 #pragma unroll
-    for (int s = 0; s < NSW; ++s) {
-        const T *gc = sg + (s & 1) * 4 * PL;
-        T *gn = sg + ((s + 1) & 1) * 4 * PL;
+            for (int a = 0; a < NA; ++a) {
+                const int gy = y0 - H + ty + BY * a;
+                if (gy < 0 || gy >= ny) continue;
 #pragma unroll
-        for (int a = 0; a < NA; ++a) {
-            const int ly = ty + 16 * a, gy = y0 - H + ly;
-            if (gy < 0 || gy >= ny) continue;
-            const bool top = gy + 1 >= ny, bot = gy == 0;
-#pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                const int lx = tx + 32 * b, li = (ly + 1) * PW + lx + 1;
-                const T g1 = gc[li], g2 = gc[PL + li], g3 = gc[2 * PL + li], g4 = gc[3 * PL + li];
-                const T psit = T(1.5) * ((g1 + g3) + (g2 + g4));
-                if (RESID && s == NSW - 1) psi_before[a][b] = psit;
-                const T m1 = g1 - g3, m2 = g2 - g4, m3 = g1 + g3, m4 = g2 + g4;
-                const T X3 = cA[a][b] - cBx[a][b] * m1 - cBy[a][b] * m2;
-                const T eq = psit * T(1.0 / 3.0);
-                const T n1 = (T(1) - P.s_g) * m1, n2 = (T(1) - P.s_g) * m2;
-                const T n3 = m3 - P.s_free_g * (m3 - eq) + X3;
-                const T n4 = m4 - P.s_free_g * (m4 - eq) + X3;
-                const T o1 = T(0.5) * (n3 + n1), o3 = T(0.5) * (n3 - n1);
-                const T o2 = T(0.5) * (n4 + n2), o4 = T(0.5) * (n4 - n2);
-                gn[li + 1] = o1;
-                gn[2 * PL + li - 1] = o3;
-                if (!top) gn[PL + li + PW] = o2 - P.wG;
-                else gn[3 * PL + li] = -o2 + P.wG;          // cathode: ABB to psi_c
-                if (!bot) gn[3 * PL + li - PW] = o4 + P.wG;
-                else gn[PL + li] = -o4 - P.wG;              // anode: ABB to psi_a
+                for (int b = 0; b < NB; ++b) {
+                    const int l = li[a][b];
+                    const T g1 = sg[l], g2 = sg[PL + l], g3 = sg[2 * PL + l], g4 = sg[3 * PL + l];
+                    const T psit = T(1.5) * ((g1 + g3) + (g2 + g4));
+                    if (RESID) psi_before[a][b] = psit;
+                    const T m1 = g1 - g3, m2 = g2 - g4, m3 = g1 + g3, m4 = g2 + g4;
+                    const T X3 = cA[a][b] - cBx[a][b] * m1 - cBy[a][b] * m2;
+                    const T eq = psit * T(1.0 / 3.0);
+                    const T n1 = (T(1) - P.s_g) * m1, n2 = (T(1) - P.s_g) * m2;
+                    const T n3 = m3 - P.s_free_g * (m3 - eq) + X3;
+                    const T n4 = m4 - P.s_free_g * (m4 - eq) + X3;
+                    o1[a][b] = T(0.5) * (n3 + n1);
+                    o3[a][b] = T(0.5) * (n3 - n1);
+                    o2[a][b] = T(0.5) * (n4 + n2);
+                    o4[a][b] = T(0.5) * (n4 - n2);
+                }
             }
+            __syncthreads();
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                const int gy = y0 - H + ty + BY * a;
+                if (gy < 0 || gy >= ny) continue;
+                const bool top = gy + 1 >= ny, bot = gy == 0;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const int l = li[a][b];
+                    sg[l + 1] = o1[a][b];
+                    sg[2 * PL + l - 1] = o3[a][b];
+                    if (!top) sg[PL + l + PW] = o2[a][b] - P.wG;
+                    else sg[3 * PL + l] = -o2[a][b] + P.wG;       // cathode: ABB to psi_c
+                    if (!bot) sg[3 * PL + l - PW] = o4[a][b] + P.wG;
+                    else sg[PL + l] = -o4[a][b] - P.wG;           // anode: ABB to psi_a
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 
-    }
-
-    // ---- store the output tile ----
-    const T *gf = sg + (NSW & 1) * 4 * PL;
+    // ---- store the output tile (and, FIRST, its coefficients) ----
     T red[2] = {T(0), T(0)};
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
-        const int ly = ty + 16 * a, gy = y0 - H + ly;
+        const int ly = ty + BY * a, gy = y0 - H + ly;
         if (ly < H || ly >= H + TY || gy >= ny) continue;
+        const long long row = (long long)gy * nx;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const int lx = tx + 32 * b, gx = x0 - H + lx;
             if (lx < H || lx >= H + TX || gx >= nx) continue;
-            const int li = (ly + 1) * PW + lx + 1;
-            const long long k = (long long)gy * nx + gx;
-            const T g1 = gf[li], g2 = gf[PL + li], g3 = gf[2 * PL + li], g4 = gf[3 * PL + li];
+            const int l = li[a][b];
+            const long long k = row + gx;
+            const T g1 = sg[l], g2 = sg[PL + l], g3 = sg[2 * PL + l], g4 = sg[3 * PL + l];
             dst[k] = g1;
             dst[nn + k] = g2;
             dst[2 * nn + k] = g3;
             dst[3 * nn + k] = g4;
+            if (FIRST) {
+                coef[k] = cA[a][b];
+                coef[nn + k] = cBx[a][b];
+                coef[2 * nn + k] = cBy[a][b];
+            }
             if (RESID) {
                 const T psit = T(1.5) * ((g1 + g3) + (g2 + g4));
                 const T d = psit - psi_before[a][b];

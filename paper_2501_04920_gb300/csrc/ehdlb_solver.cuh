@@ -64,6 +64,7 @@ template <typename T> class Solver : public SolverBase {
         EHDLB_CK(alloc((void **)&ref_.gyr, plane));
         EHDLB_CK(alloc((void **)&ref_.mur, plane));
         EHDLB_CK(alloc((void **)&q_, plane));
+        EHDLB_CK(alloc((void **)&coef_, plane * 3));
         EHDLB_CK(alloc((void **)&phiu_, plane * 2));
         EHDLB_CK(alloc((void **)&psi_prev_, plane));
         EHDLB_CK(alloc((void **)&snap_, plane * EHDLB_NFIELDS));
@@ -71,10 +72,11 @@ template <typename T> class Solver : public SolverBase {
         EHDLB_CK(alloc((void **)&ctl_, sizeof(Control)));
         {
             long long nbmax = 0;
-            for (int nsw = 1; nsw <= TB_MAX; ++nsw) {
-                const dim3 g = tb_grid(nsw, nx_, ny_);
-                nbmax = std::max(nbmax, (long long)g.x * g.y);
-            }
+            for (int nsw = 1; nsw <= TB_MAX; ++nsw)
+                for (int sh = 0; sh < TB_NSHAPES; ++sh) {
+                    const dim3 g = tb_grid(nsw, sh, nx_, ny_);
+                    nbmax = std::max(nbmax, (long long)g.x * g.y);
+                }
             EHDLB_CK(alloc((void **)&part2_, sizeof(double) * 2 * (size_t)nbmax));
         }
         EHDLB_CK((main_attr<true, true, false>()));
@@ -156,7 +158,11 @@ template <typename T> class Solver : public SolverBase {
 
     void set_schedule(const int *c, int n) override { sched_.assign(c, c + n); }
     void set_timing(int on) override { timing_ = on != 0; }
-    void set_tuning(int sweeps_per_launch) override { tb_chunk_ = sweeps_per_launch; }
+    void set_tuning(int sweeps_per_launch, int shape) override
+    {
+        if (sweeps_per_launch >= 0) tb_chunk_ = sweeps_per_launch;
+        if (shape >= 0) tb_shape_ = shape < TB_NSHAPES ? shape : 0;
+    }
 
     int step(int nsteps, ehdlb_stats *st, std::string &err) override
     {
@@ -327,14 +333,22 @@ template <typename T> class Solver : public SolverBase {
         ++launches_;
     }
 
-    // Region height of the fused sweep kernel (its width is 64) and the
-    // largest number of sweeps one launch fuses.
-    static constexpr int TB_RH = sizeof(T) == 4 ? 32 : 16;
+    // Fused sweep kernel: region shapes (width, height, threads per column,
+    // blocks per SM the registers are sized for) and the largest number of
+    // sweeps one launch fuses.
+    struct TbShape { int rw, rh, by, minb; };
+    static constexpr int TB_NSHAPES = sizeof(T) == 4 ? 3 : 1;
+    static constexpr TbShape tb_shape(int i)
+    {
+        return sizeof(T) == 4 ? (i == 1 ? TbShape{64, 32, 8, 4} : (i == 2 ? TbShape{96, 32, 16, 2} : TbShape{64, 32, 16, 3}))
+                              : TbShape{64, 16, 16, 2};
+    }
     static constexpr int TB_MAX = sizeof(T) == 4 ? 5 : 2;
 
-    static dim3 tb_grid(int nsw, int nx, int ny)
+    static dim3 tb_grid(int nsw, int shape, int nx, int ny)
     {
-        const int tx = 64 - 2 * nsw, ty = TB_RH - 2 * nsw;
+        const TbShape sh = tb_shape(shape);
+        const int tx = sh.rw - 2 * nsw, ty = sh.rh - 2 * nsw;
         return dim3((nx + tx - 1) / tx, (ny + ty - 1) / ty);
     }
 
@@ -344,28 +358,65 @@ template <typename T> class Solver : public SolverBase {
                                     (int)main_smem_bytes<T>());
     }
 
+    template <int NSW, int SH, bool FIRST, bool RESID> cudaError_t tb_attr2()
+    {
+        constexpr TbShape sh = tb_shape(SH);
+        return cudaFuncSetAttribute(k_sweep_tb<T, NSW, sh.rw, sh.rh, sh.by, sh.minb, FIRST, RESID>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)tb_smem_bytes<T, sh.rw, sh.rh>(FIRST));
+    }
+
+    template <int NSW, int SH> cudaError_t tb_attr1()
+    {
+        cudaError_t e = tb_attr2<NSW, SH, false, false>();
+        if (e == cudaSuccess) e = tb_attr2<NSW, SH, false, true>();
+        if (e == cudaSuccess) e = tb_attr2<NSW, SH, true, false>();
+        if (e == cudaSuccess) e = tb_attr2<NSW, SH, true, true>();
+        return e;
+    }
+
     template <int NSW> cudaError_t tb_attr()
     {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep_tb<T, NSW, TB_RH, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)tb_smem_bytes<T, TB_RH>());
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_sweep_tb<T, NSW, TB_RH, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)tb_smem_bytes<T, TB_RH>());
+        cudaError_t e = tb_attr1<NSW, 0>();
+        if constexpr (TB_NSHAPES > 1) {
+            if (e == cudaSuccess) e = tb_attr1<NSW, 1>();
+            if (e == cudaSuccess) e = tb_attr1<NSW, 2>();
+        }
         return e;
+    }
+
+    template <int NSW, int SH, bool FIRST, bool RESID> void tb_launch2()
+    {
+        constexpr TbShape sh = tb_shape(SH);
+        constexpr int TXo = sh.rw - 2 * NSW, TYo = sh.rh - 2 * NSW;
+        const dim3 g((nx_ + TXo - 1) / TXo, (ny_ + TYo - 1) / TYo);
+        k_sweep_tb<T, NSW, sh.rw, sh.rh, sh.by, sh.minb, FIRST, RESID>
+            <<<g, dim3(32, sh.by), tb_smem_bytes<T, sh.rw, sh.rh>(FIRST), stream_>>>(
+                dp_, g_[0], g_[1], phig_, q_, coef_, part2_, ctl_, tb_m_);
+    }
+
+    template <int NSW, int SH> void tb_launch1(bool first, bool resid)
+    {
+        if (first) {
+            if (resid) tb_launch2<NSW, SH, true, true>();
+            else tb_launch2<NSW, SH, true, false>();
+        } else {
+            if (resid) tb_launch2<NSW, SH, false, true>();
+            else tb_launch2<NSW, SH, false, false>();
+        }
     }
 
     template <int NSW> void tb_launch(int m, bool resid)
     {
-        const dim3 g = tb_grid(NSW, nx_, ny_);
-        const size_t sm = tb_smem_bytes<T, TB_RH>();
-        if (resid)
-            k_sweep_tb<T, NSW, TB_RH, true><<<g, dim3(32, 16), sm, stream_>>>(dp_, g_[0], g_[1], phig_, q_,
-                                                                           part2_, ctl_, m);
-        else
-            k_sweep_tb<T, NSW, TB_RH, false><<<g, dim3(32, 16), sm, stream_>>>(dp_, g_[0], g_[1], phig_, q_,
-                                                                            part2_, ctl_, m);
+        tb_m_ = m;
+        const bool first = m == 0;
+        if constexpr (TB_NSHAPES > 1) {
+            if (tb_shape_ == 1) tb_launch1<NSW, 1>(first, resid);
+            else if (tb_shape_ == 2) tb_launch1<NSW, 2>(first, resid);
+            else tb_launch1<NSW, 0>(first, resid);
+        } else {
+            tb_launch1<NSW, 0>(first, resid);
+        }
         ++launches_;
         ++sweep_launches_;
     }
@@ -453,7 +504,7 @@ template <typename T> class Solver : public SolverBase {
 #undef EHDLB_MAIN
         long long nb2 = 0;
         if (resid_mode == 2) {
-            const dim3 g = tb_grid(std::min(chunk, fixedK - (nk - 1) * chunk), nx_, ny_);
+            const dim3 g = tb_grid(std::min(chunk, fixedK - (nk - 1) * chunk), tb_shape_, nx_, ny_);
             nb2 = (long long)g.x * g.y;
         }
         k_step_end<<<1, 256, 0, stream_>>>(part_, nb_, part2_, nb2, ctl_, counts_, resid_mode, last ? 1 : 0);
@@ -515,6 +566,9 @@ template <typename T> class Solver : public SolverBase {
     PhiRef<T> ref_{};
     double *part_ = nullptr, *part2_ = nullptr, *stage_ = nullptr;
     int tb_chunk_ = sizeof(T) == 4 ? 5 : 2;  // sweeps fused per launch (0: one per launch)
+    int tb_shape_ = 0;                        // region shape of the fused sweep kernel
+    int tb_m_ = 0;                            // launch index within the step
+    T *coef_ = nullptr;                       // source coefficients A, Bx, By of the step
     Control *ctl_ = nullptr;
     Control ctl_h_{};
     int *counts_ = nullptr;

@@ -22,7 +22,7 @@ class SolverBase {
     virtual int set_state(const double *src, std::string &err) = 0;
     virtual void set_schedule(const int *c, int n) = 0;
     virtual void set_timing(int on) = 0;
-    virtual void set_tuning(int sweeps_per_launch) = 0;
+    virtual void set_tuning(int sweeps_per_launch, int shape) = 0;
     int last_nsteps = 0;
 };
 

@@ -170,6 +170,28 @@ def test_fp64_droplet256_matches_oracle():
     assert_close(field_errors(got, ref), FP64_TOL)
 
 
+def test_fp32_every_sweep_tuning_matches_oracle():
+    # sweeps fused per launch (0: one per launch) x region shapes of the fused
+    # kernel, on a lattice that no tile divides
+    nx, ny, steps = 130, 97, 12
+    prm = workloads.droplet(128)
+    prm.update(xc=(nx - 1) / 2, yc=(ny - 1) / 2, R=24.0, Kq=5.6893 / (nx * ny))
+    orc = oracle.Oracle(nx, ny, prm)
+    orc.step(steps)
+    ref = orc.fields()
+    for shape in range(3):
+        for spl in (0, 1, 2, 3, 4, 5):
+            lat = ehdlb.Lattice(nx, ny, prm, precision=ehdlb.FP32)
+            ehdlb.ehdlb_set_tuning(lat.ctx, spl, shape)
+            lat.step(steps)
+            err = field_errors(lat.fields(), ref)
+            try:
+                assert_close(err, FP32_TOL, keys=["phi", "psi", "q", "cp", "cm"])
+                assert_close(err, FP32_U_TOL, keys=["u"])
+            except AssertionError as e:
+                raise AssertionError(f"shape {shape}, {spl} sweeps per launch: {e}") from None
+
+
 @pytest.mark.slow
 def test_fp32_droplet2048_full_size_matches_oracle():
     # the launch configuration the benchmark times, two steps from t = 0
@@ -238,6 +260,9 @@ def test_error_codes():
     good = ehdlb.ehdlb_params_default(dict(xc=7.5, yc=7.5, R=4.0, sweeps_min=0, sweeps_max=1,
                                            sweep_tol=0.0, init_sweeps_max=10))
     assert L.ehdlb_set_params(h, ehdlb.C.byref(good)) == ehdlb.OK
+    assert L.ehdlb_set_tuning(h, 6, 0) == ehdlb.EINVAL
+    assert L.ehdlb_set_tuning(h, 2, 3) == ehdlb.EINVAL
+    assert L.ehdlb_set_tuning(h, -1, -1) == ehdlb.OK
     assert L.ehdlb_step(h, 2, ehdlb.C.byref(st)) == ehdlb.WNOTCONV
     assert st.not_converged == 2
     out = np.zeros(16 * 16)
