@@ -30,11 +30,17 @@ METRIC = "MLUPS over 5 LB fields, % HBM roofline; served cases/h vs plain, p99 l
 N = 2048
 SWEEPS = 20
 SAMPLE_N = 256          # oracle sample: a 256^2 copy of the case (R = 32)
-# Algorithmic bytes per node and potential sweep in FP32 (10 s + 8 with s = 4:
-# 5 populations read and written, phi and q read), the per-sweep unit of the
-# byte model; one launch of the fused kernel processes sweeps_per_launch such
-# units per node while its DRAM traffic is that of a single sweep.
-SWEEP_BYTES_PER_NODE = 48
+# Algorithmic bytes per node and potential sweep, 10 s + 8 with s bytes per
+# stored population (5 populations read and written, phi and q read): 48 in
+# FP32, 28 with FP16 storage.  This is the per-sweep unit of the byte model;
+# one launch of the fused kernel processes sweeps_per_launch such units per
+# node while its DRAM traffic is that of a single sweep.
+def sweep_bytes_per_node(storage_bytes: int) -> int:
+    return 10 * storage_bytes + 8
+
+
+PRECISIONS = {"fp32": ("FP32", 4, "f32"), "fp16s": ("FP16 storage, FP32 arithmetic", 2, "f32"),
+              "fp64": ("FP64", 8, "f64")}
 
 
 def parse():
@@ -49,6 +55,10 @@ def parse():
                     help="potential sweeps fused per kernel launch (default: the library's)")
     ap.add_argument("--tile-shape", type=int, default=-1,
                     help="region shape of the fused sweep kernel (default: the library's)")
+    ap.add_argument("--main-staging", type=int, default=-1,
+                    help="step kernel staging, 0 per node, 1 16-byte segments (default: the library's)")
+    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS),
+                    help="fp32 (the headline form), fp16s (FP16 storage) or fp64")
     return ap.parse_args()
 
 
@@ -219,8 +229,10 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     n = args.n
     prm = workloads.droplet(n)
-    lat = ehdlb.Lattice(n, n, prm, precision=ehdlb.FP32, cuda_stream=stream.cuda_stream)
-    ehdlb.ehdlb_set_tuning(lat.ctx, args.sweeps_per_launch, args.tile_shape)
+    label, sbytes, dtype = PRECISIONS[args.precision]
+    prec = {"fp32": ehdlb.FP32, "fp16s": ehdlb.FP16S, "fp64": ehdlb.FP64}[args.precision]
+    lat = ehdlb.Lattice(n, n, prm, precision=prec, cuda_stream=stream.cuda_stream)
+    ehdlb.ehdlb_set_tuning(lat.ctx, args.sweeps_per_launch, args.tile_shape, args.main_staging)
     nn = n * n
 
     def barrier():
@@ -246,8 +258,9 @@ def run_ours(args):
     sweeps_per_launch = args.steps * SWEEPS / max(1, st.sweep_launches)
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
-    achieved = SWEEP_BYTES_PER_NODE * sweeps_per_launch * nn / (sweep_launch_ms / 1e3) / 1e9
-    traffic = measured_traffic("k_sweep_tb", n)
+    unit_bytes = sweep_bytes_per_node(sbytes)
+    achieved = unit_bytes * sweeps_per_launch * nn / (sweep_launch_ms / 1e3) / 1e9
+    traffic = measured_traffic("k_sweep_tb" if args.precision == "fp32" else f"k_sweep_tb_{args.precision}", n)
     launches = int(st.launches)
     ehdlb.ehdlb_set_timing(lat.ctx, False)
 
@@ -277,18 +290,18 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
         "data": "synthetic",
-        "config": {"workload": f"droplet {n}x{n} FP32, 20 potential sweeps per step "
+        "config": {"workload": f"droplet {n}x{n} {label}, 20 potential sweeps per step "
                                f"(R = {n // 8}, eps_r = 4, mu_r = 2, dpsi = 2)",
-                   "nx": n, "ny": n, "sweeps_per_step": SWEEPS,
+                   "nx": n, "ny": n, "sweeps_per_step": SWEEPS, "storage_bytes": sbytes,
                    "l2": "inputs larger than L2 (state ~1.35 GB), no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "kernel": "k_sweep_tb (potential sweeps fused in shared memory)",
                      "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "peak_source": peak_kind,
                      "traffic": traffic,
-                     "bytes_per_launch": SWEEP_BYTES_PER_NODE * sweeps_per_launch * nn,
+                     "bytes_per_launch": unit_bytes * sweeps_per_launch * nn,
                      "sweeps_per_launch": sweeps_per_launch, "launch_ms": sweep_launch_ms,
                      "dram_achieved": (round(traffic / (sweep_launch_ms / 1e3) / 1e9, 1)
                                        if traffic else None)},

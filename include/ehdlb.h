@@ -48,8 +48,14 @@ typedef enum ehdlb_status {
 
 typedef enum ehdlb_precision {
     EHDLB_FP64 = 0,       /* populations and arithmetic in double */
-    EHDLB_FP32 = 1        /* populations and arithmetic in float; residual and
+    EHDLB_FP32 = 1,       /* populations and arithmetic in float; residual and
                              global sums in double */
+    EHDLB_FP16S = 2       /* populations stored in FP16 as scaled deviations
+                             from rest states (h from w_i phi_ref, g from
+                             w_i psi_lin, p and n from w_i c_ref), arithmetic
+                             in float, residual and sums in double; the storage
+                             form that halves the memory traffic of the state
+                             (a design choice with no counterpart in the paper) */
 } ehdlb_precision;
 
 /* Snapshot fields (bit i of a field mask selects field i). */
@@ -204,15 +210,19 @@ int ehdlb_set_state(ehdlb_ctx *c, const double *src, size_t len);
 /* Record device time per kernel class in ehdlb_stats (1) or not (0). */
 int ehdlb_set_timing(ehdlb_ctx *c, int on);
 
-/* Performance knobs (no effect on the result beyond round-off) of the fused
- * potential-sweep kernel, used when a step takes a fixed number of sweeps:
- *   sweeps_per_launch: sweeps one launch fuses in shared memory, 1..5 (the
- *     double-precision solver uses at most 2), 0 for one sweep per launch;
- *     default 5 (float) / 2 (double);
- *   tile_shape: region of one block, 0: 64 x 32 (512 threads, default),
- *     1: 64 x 64 (1024 threads), 2: 128 x 32 (1024 threads); float only.
+/* Performance knobs; none changes the result beyond round-off.
+ *   sweeps_per_launch: potential sweeps the fused sweep kernel computes in
+ *     shared memory per launch when a step takes a fixed number of sweeps,
+ *     1..5 (the double-precision solver uses at most 2), 0 for one sweep per
+ *     launch; default 5 (float) / 2 (double);
+ *   tile_shape: region of one block of the fused sweep kernel, 0: 64 x 32
+ *     (512 threads, default), 1: 64 x 32 (256 threads); float only;
+ *   main_staging: how the step kernel copies its block's populations to
+ *     shared memory, 0: one asynchronous copy per node and plane, 1: 16-byte
+ *     copies of row segments (default; used only when nx times the element
+ *     size is a multiple of 16 bytes, else 0).
  * -1 keeps a setting.  EINVAL outside these ranges. */
-int ehdlb_set_tuning(ehdlb_ctx *c, int sweeps_per_launch, int tile_shape);
+int ehdlb_set_tuning(ehdlb_ctx *c, int sweeps_per_launch, int tile_shape, int main_staging);
 
 /* Largest lattice, in nodes nx * ny, that ehdlb_potential_noalloc accepts. */
 #define EHDLB_NOALLOC_MAX_NODES 65536

@@ -127,7 +127,7 @@ int ehdlb_create(ehdlb_ctx **out, int nx, int ny, int precision, void *cuda_stre
     *out = nullptr;
     if (nx < 4 || ny < 4) return EHDLB_EINVAL;
     if ((long long)nx * ny > (1LL << 31)) return EHDLB_EINVAL;
-    if (precision != EHDLB_FP64 && precision != EHDLB_FP32) return EHDLB_EINVAL;
+    if (precision != EHDLB_FP64 && precision != EHDLB_FP32 && precision != EHDLB_FP16S) return EHDLB_EINVAL;
     ehdlb_ctx *c = new (std::nothrow) ehdlb_ctx;
     if (!c) return EHDLB_ENOMEM;
     c->nx = nx;
@@ -136,8 +136,9 @@ int ehdlb_create(ehdlb_ctx **out, int nx, int ny, int precision, void *cuda_stre
     int status = EHDLB_OK;
     std::string err;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    c->solver = precision == EHDLB_FP64 ? ehdlb::make_solver_fp64(nx, ny, s, &status, err)
-                                        : ehdlb::make_solver_fp32(nx, ny, s, &status, err);
+    c->solver = precision == EHDLB_FP64   ? ehdlb::make_solver_fp64(nx, ny, s, &status, err)
+                : precision == EHDLB_FP16S ? ehdlb::make_solver_fp16s(nx, ny, s, &status, err)
+                                           : ehdlb::make_solver_fp32(nx, ny, s, &status, err);
     if (!c->solver) {
         delete c;
         return status != EHDLB_OK ? status : EHDLB_ENOMEM;
@@ -222,13 +223,14 @@ int ehdlb_set_timing(ehdlb_ctx *c, int on)
     return EHDLB_OK;
 }
 
-int ehdlb_set_tuning(ehdlb_ctx *c, int sweeps_per_launch, int tile_shape)
+int ehdlb_set_tuning(ehdlb_ctx *c, int sweeps_per_launch, int tile_shape, int main_staging)
 {
     if (!c) return EHDLB_EINVAL;
     if (sweeps_per_launch < -1 || sweeps_per_launch > 5)
         return fail(c, EHDLB_EINVAL, "sweeps_per_launch must lie in -1..5");
-    if (tile_shape < -1 || tile_shape > 2) return fail(c, EHDLB_EINVAL, "tile_shape must lie in -1..2");
-    c->solver->set_tuning(sweeps_per_launch, tile_shape);
+    if (tile_shape < -1 || tile_shape > 1) return fail(c, EHDLB_EINVAL, "tile_shape must lie in -1..1");
+    if (main_staging < -1 || main_staging > 1) return fail(c, EHDLB_EINVAL, "main_staging must lie in -1..1");
+    c->solver->set_tuning(sweeps_per_launch, tile_shape, main_staging);
     return EHDLB_OK;
 }
 

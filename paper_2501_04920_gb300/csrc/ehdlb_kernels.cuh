@@ -24,11 +24,21 @@
 //   kernel reads its node's own populations and pushes post-collision values
 //   to the neighbours (x periodic, walls half-way below row 0 and above row
 //   ny - 1).
+// Storage type S of the populations f, h, p, n and of (phi u)(t-1) is T
+// itself or, with T = float, __half: each value is then stored as its
+// deviation from a rest state (h as above, p and n as w_i c_ref) times a
+// power-of-two scale per field that keeps it in the normal range of FP16;
+// the arithmetic stays in T.  g and every other plane are T: the potential
+// is relaxed by a few sweeps per step, and rounding g to FP16 at every
+// sweep would feed its slowest modes faster than the sweeps damp them.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 namespace ehdlb {
 
@@ -72,6 +82,10 @@ template <typename T> struct DevP {
     T s_f0;                        // 1/tau_f when rho and eta are uniform, else 0
     T s_p0, s_n0;                  // ion rates (Eq. 37) when D is uniform, else 0
     T inv_mu_v, three_over_tau_g, inv_W;
+    // storage scales (value x sc is stored, stored x isc is the value) and
+    // the rest concentration of the stored p, n; 1, 1 and 0 unless S != T
+    T sc_f, isc_f, sc_h, isc_h, sc_c, isc_c, sc_g, isc_g, sc_u, isc_u;  // sc_g: g stored as S
+    T cref;
 };
 
 // Per-run control block in device memory (all kernels of a step read it).
@@ -95,12 +109,85 @@ struct Control {
     double sum_phi, sum_q;
 };
 
-template <typename T> struct Pops {
-    T *f;   // 8 planes
-    T *h;   // 9 planes (h_i - w_i phi_ref)
-    T *p;   // 5 planes
-    T *n;   // 5 planes
+// One allocation of 27 planes: f at +0, h at +8 nn, p at +17 nn, n at +22 nn.
+template <typename S> struct Pops {
+    S *f;   // 8 planes
+    S *h;   // 9 planes (h_i - w_i phi_ref)
+    S *p;   // 5 planes
+    S *n;   // 5 planes
 };
+
+// ---- storage conversion --------------------------------------------------------
+
+template <typename S, typename T> constexpr bool kSame = std::is_same<S, T>::value;
+
+// Stored value -> T (times the field's isc when S != T).
+template <typename S, typename T> __device__ __forceinline__ T lds(const S *p, T isc)
+{
+    if constexpr (kSame<S, T>) return *p;
+    else return __half2float(*p) * isc;
+}
+// T -> stored value (times the field's sc when S != T, rounded to nearest).
+template <typename S, typename T> __device__ __forceinline__ void sts(S *p, T v, T sc)
+{
+    if constexpr (kSame<S, T>) *p = v;
+    else *p = __float2half_rn(v * sc);
+}
+// Stochastic rounding of the FP16 stores of f, h, p and n.  Rounding to
+// nearest makes the error of a quasi-steady population the same at every
+// step, so it accumulates linearly over the run; rounding up with
+// probability equal to the discarded fraction makes it a zero-mean random
+// walk.  The random bits come from a counter-based generator: the 32-bit
+// finaliser of MurmurHash3 (Appleby) over (node, step, stream), advanced per
+// store by the linear congruential step of Numerical Recipes (1664525,
+// 1013904223), whose high bits are used.
+__device__ __forceinline__ uint32_t mix32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x85ebca6bu;
+    x ^= x >> 13;
+    x *= 0xc2b2ae35u;
+    x ^= x >> 16;
+    return x;
+}
+
+struct SRng {
+    uint32_t s;
+    __device__ __forceinline__ SRng(long long node, long long step, uint32_t stream)
+        : s(mix32((uint32_t)node * 0x9e3779b1u ^ mix32((uint32_t)step * 0x632be5abu + stream)))
+    {
+    }
+    __device__ __forceinline__ uint32_t next()
+    {
+        s = s * 1664525u + 1013904223u;
+        return s;
+    }
+};
+
+// float -> FP16, rounded up in magnitude with probability equal to the
+// discarded fraction (r: 32 random bits): 13 random bits are added below the
+// 10 mantissa bits that FP16 keeps and the rest is cut off.  Below the normal
+// range of FP16 (2^-14) the final conversion rounds the partly randomised
+// value to nearest; the storage scales keep typical values above that range.
+__device__ __forceinline__ __half f2h_sr(float v, uint32_t r)
+{
+    const uint32_t b = (__float_as_uint(v) + (r >> 19)) & ~0x1fffu;
+    return __float2half_rn(__uint_as_float(b));
+}
+
+// T -> stored value as sts, stochastically rounded when S != T.
+template <typename S, typename T> __device__ __forceinline__ void sts_sr(S *p, T v, T sc, SRng &rng)
+{
+    if constexpr (kSame<S, T>) *p = v;
+    else *p = f2h_sr(v * sc, rng.next());
+}
+
+// Raw stored value -> T without scaling (for sums scaled once).
+template <typename S, typename T> __device__ __forceinline__ T raw(S v)
+{
+    if constexpr (kSame<S, T>) return v;
+    else return __half2float(v);
+}
 
 // The reference field of the stored h and its derived planes.
 template <typename T> struct PhiRef {
@@ -226,6 +313,23 @@ template <typename T> __device__ __forceinline__ void inverse9(const T (&m)[9], 
     v[4] = c0 - c2; v[8] = h * (c1 + c2); v[7] = h * (c2 - c1);
 }
 
+// Asynchronous 4- or 8-byte global -> shared copy (no register staging).
+template <typename T> __device__ __forceinline__ void cp_async(T *smem, const T *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+// Asynchronous 16-byte global -> shared copy; both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // ---- kernels -----------------------------------------------------------------
 
 // phi = sum h (Eq. 33) with mirrored ghost rows, q = sum p - sum n.  The
@@ -233,9 +337,9 @@ template <typename T> __device__ __forceinline__ void inverse9(const T (&m)[9], 
 // + dphi; both are written (phi for the potential, dphi for the stencils of
 // the main kernel).  With init_ctl the first thread also opens the step in
 // the control block.
-template <typename T>
-__global__ void __launch_bounds__(256) k_prep(const DevP<T> P, const T *__restrict__ h,
-                                              const T *__restrict__ p, const T *__restrict__ n,
+template <typename T, typename S>
+__global__ void __launch_bounds__(256) k_prep(const DevP<T> P, const S *__restrict__ h,
+                                              const S *__restrict__ p, const S *__restrict__ n,
                                               const PhiRef<T> R, T *__restrict__ phig, T *__restrict__ q,
                                               Control *ctl, int fixedK, int kmin, int kmax, int flips)
 {
@@ -251,12 +355,19 @@ __global__ void __launch_bounds__(256) k_prep(const DevP<T> P, const T *__restri
     }
     if (x >= P.nx || y >= P.ny) return;
     const long long nn = P.nn, k = (long long)y * P.nx + x;
+    S hv[9], pv[5], nv[5];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) hv[i] = h[i * nn + k];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) { pv[i] = p[i * nn + k]; nv[i] = n[i * nn + k]; }
     // pairwise: rest, axis pairs, diagonal pairs
-    const T d = h[k] + ((((h[nn + k] + h[3 * nn + k]) + (h[2 * nn + k] + h[4 * nn + k]))) +
-                        ((h[5 * nn + k] + h[7 * nn + k]) + (h[6 * nn + k] + h[8 * nn + k])));
+    T d = raw<S, T>(hv[0]) + ((((raw<S, T>(hv[1]) + raw<S, T>(hv[3])) + (raw<S, T>(hv[2]) + raw<S, T>(hv[4])))) +
+                              ((raw<S, T>(hv[5]) + raw<S, T>(hv[7])) + (raw<S, T>(hv[6]) + raw<S, T>(hv[8]))));
     T sp = T(0), sn = T(0);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) { sp += p[i * nn + k]; sn += n[i * nn + k]; }
+    for (int i = 0; i < 5; ++i) { sp += raw<S, T>(pv[i]); sn += raw<S, T>(nv[i]); }
+    T qv = sp - sn;   // the rest concentrations of stored p and n cancel
+    if constexpr (!kSame<S, T>) { d *= P.isc_h; qv *= P.isc_c; }
     const long long gk = (long long)(y + 1) * P.nx + x;
     const T phi = R.phir[gk] + d;
     phig[gk] = phi;
@@ -266,7 +377,7 @@ __global__ void __launch_bounds__(256) k_prep(const DevP<T> P, const T *__restri
         phig[(long long)(P.ny + 1) * P.nx + x] = phi;
         R.dphig[(long long)(P.ny + 1) * P.nx + x] = d;
     }
-    q[k] = sp - sn;
+    q[k] = qv;
 }
 
 // One pseudo-time sweep of the potential (Eq. 44-50) at every node: E and
@@ -276,24 +387,25 @@ __global__ void __launch_bounds__(256) k_prep(const DevP<T> P, const T *__restri
 //   WRITE_PSI: store psi (shifted) for the residual of the next sweep/main.
 //   RESID    : partial sums of (psi - psi_prev)^2 and psi^2 (FP64).
 //   CTRL     : converge mode; skip if the step is done, parity from K.
-template <typename T, bool WRITE_PSI, bool RESID, bool CTRL>
-__global__ void __launch_bounds__(256) k_sweep(const DevP<T> P, T *__restrict__ gA,
-                                               T *__restrict__ gB, const T *__restrict__ phig,
+template <typename T, typename S, bool WRITE_PSI, bool RESID, bool CTRL>
+__global__ void __launch_bounds__(256) k_sweep(const DevP<T> P, S *__restrict__ gA,
+                                               S *__restrict__ gB, const T *__restrict__ phig,
                                                const T *__restrict__ q, T *__restrict__ psi_prev,
                                                double *__restrict__ part, const Control *__restrict__ ctl,
                                                int j)
 {
     if (CTRL && ctl->done) return;
     const int par = (ctl->cur0 + j - 1) & 1;
-    const T *__restrict__ src = par ? gB : gA;
-    T *__restrict__ dst = par ? gA : gB;
+    const S *__restrict__ src = par ? gB : gA;
+    S *__restrict__ dst = par ? gA : gB;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     double red[2] = {0.0, 0.0};
     if (x < P.nx && y < P.ny) {
         const int nx = P.nx;
         const long long nn = P.nn, k = (long long)y * nx + x;
-        const T g1 = src[k], g2 = src[nn + k], g3 = src[2 * nn + k], g4 = src[3 * nn + k];
+        const T g1 = lds(src + k, P.isc_g), g2 = lds(src + nn + k, P.isc_g), g3 = lds(src + 2 * nn + k, P.isc_g),
+                g4 = lds(src + 3 * nn + k, P.isc_g);
         const T psit = T(1.5) * ((g1 + g3) + (g2 + g4));      // Eq. 49, minus psi_lin
         if (RESID) {
             const double d = (double)psit - (double)psi_prev[k];
@@ -322,26 +434,16 @@ __global__ void __launch_bounds__(256) k_sweep(const DevP<T> P, T *__restrict__ 
         const T n4 = m4 - P.s_free_g * (m4 - eq) + X3;
         const T o1 = T(0.5) * (n3 + n1), o3 = T(0.5) * (n3 - n1);
         const T o2 = T(0.5) * (n4 + n2), o4 = T(0.5) * (n4 - n2);
-        dst[(long long)y * nx + xp] = o1;
-        dst[2 * nn + (long long)y * nx + xm] = o3;
-        if (y + 1 < P.ny) dst[nn + k + nx] = o2 - P.wG;
-        else dst[3 * nn + k] = -o2 + P.wG;          // cathode: ABB to psi_c
-        if (y > 0) dst[3 * nn + k - nx] = o4 + P.wG;
-        else dst[nn + k] = -o4 - P.wG;              // anode: ABB to psi_a
+        sts(dst + (long long)y * nx + xp, o1, P.sc_g);
+        sts(dst + 2 * nn + (long long)y * nx + xm, o3, P.sc_g);
+        if (y + 1 < P.ny) sts(dst + nn + k + nx, o2 - P.wG, P.sc_g);
+        else sts(dst + 3 * nn + k, -o2 + P.wG, P.sc_g);          // cathode: ABB to psi_c
+        if (y > 0) sts(dst + 3 * nn + k - nx, o4 + P.wG, P.sc_g);
+        else sts(dst + nn + k, -o4 - P.wG, P.sc_g);              // anode: ABB to psi_a
     }
     if (RESID) block_sum_store<double, 2>(red, part);
 }
 
-// Asynchronous 4- or 8-byte global -> shared copy (no register staging).
-template <typename T> __device__ __forceinline__ void cp_async(T *smem, const T *gmem)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    if (sizeof(T) == 4)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // NSW potential sweeps (Eq. 44-50) fused in shared memory.  A block holds an
 // RW x RH region of the lattice: its output tile of (RW - 2 NSW) x
@@ -376,9 +478,9 @@ __device__ __forceinline__ int wrap_x(int x, int nx, bool wide)
     return ((x % nx) + nx) % nx;
 }
 
-template <typename T, int NSW, int RW, int RH, int BY, int MINB, bool FIRST, bool RESID>
+template <typename T, typename S, int NSW, int RW, int RH, int BY, int MINB, bool FIRST, bool RESID>
 __global__ void __launch_bounds__(32 * BY, MINB)
-    k_sweep_tb(const DevP<T> P, T *__restrict__ gA, T *__restrict__ gB, const T *__restrict__ phig,
+    k_sweep_tb(const DevP<T> P, S *__restrict__ gA, S *__restrict__ gB, const T *__restrict__ phig,
                const T *__restrict__ q, T *__restrict__ coef, double *__restrict__ part,
                const Control *__restrict__ ctl, int m)
 {
@@ -390,8 +492,8 @@ __global__ void __launch_bounds__(32 * BY, MINB)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sg = reinterpret_cast<T *>(smem_raw);   // [4][PH][PW], then (FIRST) phi ring and q
     const int par = (ctl->cur0 + m) & 1;
-    const T *__restrict__ src = par ? gB : gA;
-    T *__restrict__ dst = par ? gA : gB;
+    const S *__restrict__ src = par ? gB : gA;
+    S *__restrict__ dst = par ? gA : gB;
     const int nx = P.nx, ny = P.ny;
     const long long nn = P.nn;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -417,8 +519,13 @@ __global__ void __launch_bounds__(32 * BY, MINB)
         for (int b = 0; b < NB; ++b) {
             const long long k = row + gxs[b];
             const int li = (ly + 1) * PW + tx + 32 * b + 1;
+            if constexpr (kSame<S, T>) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) cp_async(sg + i * PL + li, src + i * nn + k);
+                for (int i = 0; i < 4; ++i) cp_async(sg + i * PL + li, src + i * nn + k);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) sg[i * PL + li] = lds(src + i * nn + k, P.isc_g);
+            }
             if (FIRST) {
                 cp_async(sq + li, q + k);
             } else {
@@ -571,10 +678,10 @@ __global__ void __launch_bounds__(32 * BY, MINB)
             const int l = li[a][b];
             const long long k = row + gx;
             const T g1 = sg[l], g2 = sg[PL + l], g3 = sg[2 * PL + l], g4 = sg[3 * PL + l];
-            dst[k] = g1;
-            dst[nn + k] = g2;
-            dst[2 * nn + k] = g3;
-            dst[3 * nn + k] = g4;
+            sts(dst + k, g1, P.sc_g);
+            sts(dst + nn + k, g2, P.sc_g);
+            sts(dst + 2 * nn + k, g3, P.sc_g);
+            sts(dst + 3 * nn + k, g4, P.sc_g);
             if (FIRST) {
                 coef[k] = cA[a][b];
                 coef[nn + k] = cBx[a][b];
@@ -613,20 +720,48 @@ static __global__ void __launch_bounds__(256) k_sweep_decide(const double *__res
     if (j >= ctl->kmax) ctl->done = 1;
 }
 
-// Number of values k_main stages per node: f1..f8, h0..h8, p0..p4, n0..n4,
-// g1..g4, (phi u)(t-1) x, y, psi of the previous sweep.
-constexpr int MAIN_STAGE = 8 + 9 + 5 + 5 + 4 + 2 + 1;
-template <typename T> __host__ __device__ constexpr size_t main_smem_bytes()
+// Planes k_main stages per node: f1..f8, h0..h8, p0..p4, n0..n4 (one
+// allocation of 27 planes) and (phi u)(t-1) x, y of type S, then g1..g4 of
+// type T.
+constexpr int MAIN_SPLANES = 27 + 2, MAIN_TPLANES = 4;
+template <typename T, typename S> __host__ __device__ constexpr size_t main_smem_bytes()
 {
-    return sizeof(T) * MAIN_STAGE * 256;
+    return (sizeof(S) * MAIN_SPLANES + sizeof(T) * MAIN_TPLANES) * 256;
+}
+
+// Copy NPL planes of the block's 64 x 4 nodes (x0, y0) to st[plane][256]
+// asynchronously; plane(i) gives the base of plane i.  VEC: 16-byte copies
+// of row segments shared by all threads (needs nx * sizeof(E) to be a
+// multiple of 16); else one copy per node.
+template <typename E, int NPL, bool VEC, typename PlaneF>
+__device__ __forceinline__ void stage_planes(E *st, PlaneF plane, int nx, int ny, int x0, int y0, int tid,
+                                             bool inside, long long k)
+{
+    if constexpr (VEC) {
+        constexpr int NE = 16 / (int)sizeof(E), CH = 64 / NE, NCH = NPL * 4 * CH;
+        for (int c = tid; c < NCH; c += 256) {
+            const int pl = c / (4 * CH), r = c - pl * (4 * CH);
+            const int row = r / CH, ch = r - row * CH;
+            const int y = y0 + row, x = x0 + ch * NE;
+            if (y >= ny || x >= nx) continue;
+            cp_async16(st + pl * 256 + row * 64 + ch * NE, plane(pl) + (long long)y * nx + x);
+        }
+    } else {
+        if (!inside) return;
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            if constexpr (sizeof(E) >= 4) cp_async(st + i * 256 + tid, plane(i) + k);
+            else st[i * 256 + tid] = plane(i)[k];
+        }
+    }
 }
 
 // The rest of the step at every node (O5-O11): reaction (Eq. 42-43), forces
 // (Eq. 12-14), u and p (Eq. 56-57), MRT collisions of f (Eq. 51), h (Eq. 27),
-// p and n (Eq. 34-35), push with the wall rules (Eq. 64).  The node's inputs
-// are copied to shared memory asynchronously first, so that all of them are
-// in flight at once.  The equilibria and sources of f and h enter directly as
-// their moments in the basis of Eq. 28:
+// p and n (Eq. 34-35), push with the wall rules (Eq. 64).  The block's
+// populations are copied to shared memory asynchronously first, so that all
+// of them are in flight at once.  The equilibria and sources of f and h
+// enter directly as their moments in the basis of Eq. 28:
 //   M f_eq = (0, rho u, p + rho ux^2, p + rho uy^2, rho ux uy, rho ux/3,
 //             rho uy/3, p/3 + rho u^2/3)          (rows 1..8, Eq. 52-53)
 //   M F    = (F, ux gx + uy gy/3, uy gy + ux gx/3, (ux gy + uy gx)/3, Fx/3,
@@ -636,75 +771,75 @@ template <typename T> __host__ __device__ constexpr size_t main_smem_bytes()
 //   SNAP  : write the macroscopic snapshot and its sums of phi and q.
 //   FROZEN: E from DevP.
 //   RESID : residual of the last sweep against psi_prev.
+//   VEC   : 16-byte staging (stage_planes).
 // NaN or Inf in the macroscopic fields raises *unstable.
-// Launch: blockDim (64, 4), dynamic shared memory main_smem_bytes<T>().
-template <typename T, bool SNAP, bool FROZEN, bool RESID>
-__global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<T> src, const Pops<T> dst,
+// Launch: blockDim (64, 4), dynamic shared memory main_smem_bytes<T, S>().
+template <typename T, typename S, bool SNAP, bool FROZEN, bool RESID, bool VEC>
+__global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<S> src, const Pops<S> dst,
                                                  const T *__restrict__ gA, const T *__restrict__ gB,
                                                  const Control *__restrict__ ctl, const PhiRef<T> Rf,
-                                                 T *__restrict__ phiu, const T *__restrict__ psi_prev,
+                                                 S *__restrict__ phiu, const T *__restrict__ psi_prev,
                                                  T *__restrict__ snap, double *__restrict__ part,
                                                  int *__restrict__ unstable)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *st = reinterpret_cast<T *>(smem_raw);
+    S *st = reinterpret_cast<S *>(smem_raw);
+    T *stg = reinterpret_cast<T *>(smem_raw + sizeof(S) * MAIN_SPLANES * 256);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const bool inside = x < P.nx && y < P.ny;
     const long long nn = P.nn, k = (long long)y * P.nx + x;
     T red[4] = {T(0), T(0), T(0), T(0)};
-    if (inside) {
+    {
         const T *__restrict__ g = ((ctl->cur0 + ctl->flips) & 1) ? gB : gA;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) cp_async(st + i * 256 + tid, src.f + i * nn + k);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) cp_async(st + (8 + i) * 256 + tid, src.h + i * nn + k);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            cp_async(st + (17 + i) * 256 + tid, src.p + i * nn + k);
-            cp_async(st + (22 + i) * 256 + tid, src.n + i * nn + k);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) cp_async(st + (27 + i) * 256 + tid, g + i * nn + k);
-        cp_async(st + 31 * 256 + tid, phiu + k);
-        cp_async(st + 32 * 256 + tid, phiu + nn + k);
-        if (RESID) cp_async(st + 33 * 256 + tid, psi_prev + k);
+        const S *pops = src.f, *pu = phiu;
+        const int x0 = blockIdx.x * blockDim.x, y0 = blockIdx.y * blockDim.y;
+        stage_planes<S, MAIN_SPLANES, VEC>(
+            st, [=](int i) { return i < 27 ? pops + i * nn : pu + (i - 27) * nn; }, P.nx, P.ny, x0, y0, tid, inside, k);
+        stage_planes<T, MAIN_TPLANES, VEC>(stg, [=](int i) { return g + i * nn; }, P.nx, P.ny, x0, y0, tid, inside, k);
     }
+    const T pprev = (RESID && inside) ? psi_prev[k] : T(0);
+    const int nx = P.nx, ny = P.ny;
+    const T third = T(1.0 / 3.0);
+    // ---- O1-O2: phi, properties (Eq. 61), stencils (Eq. 59) ----
+    // phi = phi_ref + dphi; the stencils act on dphi and add the
+    // reference's gradient; differences first (exact for neighbours)
+    int xm = 0, xp = 0;
+    T dphi = T(0), phir = T(0), phi = T(0), gx = T(0), gy = T(0), lapd = T(0);
     if (inside) {
-        const int nx = P.nx, ny = P.ny;
-        const T third = T(1.0 / 3.0);
-        // ---- O1-O2: phi, properties (Eq. 61), stencils (Eq. 59) ----
-        // phi = phi_ref + dphi; the stencils act on dphi and add the
-        // reference's gradient; differences first (exact for neighbours)
-        const int xm = wrapx(x - 1, nx), xp = wrapx(x + 1, nx);
+        xm = wrapx(x - 1, nx);
+        xp = wrapx(x + 1, nx);
         const T *r0 = Rf.dphig + (long long)y * nx, *r1 = r0 + nx, *r2 = r1 + nx;
-        const T dphi = r1[x];
+        dphi = r1[x];
         const T dE = r1[xp] - dphi, dW = r1[xm] - dphi, dN = r2[x] - dphi, dS = r0[x] - dphi;
         const T dNE = r2[xp] - dphi, dNW = r2[xm] - dphi, dSW = r0[xm] - dphi, dSE = r0[xp] - dphi;
-        const T phir = Rf.phir[(long long)(y + 1) * nx + x];
-        const T phi = phir + dphi;
-        const T gx = Rf.gxr[k] + ((dE - dW) * third + ((dNE - dNW) + (dSE - dSW)) * T(1.0 / 12.0));
-        const T gy = Rf.gyr[k] + ((dN - dS) * third + ((dNE + dNW) - (dSE + dSW)) * T(1.0 / 12.0));
-        const T lapd = T(2.0 / 3.0) * ((dE + dW) + (dN + dS)) + T(1.0 / 6.0) * ((dNE + dSW) + (dNW + dSE));
+        phir = Rf.phir[(long long)(y + 1) * nx + x];
+        phi = phir + dphi;
+        gx = Rf.gxr[k] + ((dE - dW) * third + ((dNE - dNW) + (dSE - dSW)) * T(1.0 / 12.0));
+        gy = Rf.gyr[k] + ((dN - dS) * third + ((dNE + dNW) - (dSE + dSW)) * T(1.0 / 12.0));
+        lapd = T(2.0 / 3.0) * ((dE + dW) + (dN + dS)) + T(1.0 / 6.0) * ((dNE + dSW) + (dNW + dSE));
+    }
+    cp_async_wait_all();
+    if constexpr (VEC) __syncthreads();
+    if (inside) {
+        SRng rng(k, kSame<S, T> ? 0 : ctl->t, 0x1b873593u);
         const T rho = T(1) + P.rho1 * phi;
         const T inv_rho = T(1) / rho;
         const T mup = P.mu_v * (T(1) + P.mu1 * phi);
         const T mum = P.m * mup;
         const T grx = P.rho1 * gx, gry = P.rho1 * gy;
         const T dex = P.er1 * gx, dey = P.er1 * gy;
-        cp_async_wait_all();
 
         // ---- O4 result: psi, E from the last sweep (Eq. 49-50) ----
-        const T g1 = st[27 * 256 + tid], g2 = st[28 * 256 + tid], g3 = st[29 * 256 + tid],
-                g4 = st[30 * 256 + tid];
+        const T g1 = stg[tid], g2 = stg[256 + tid], g3 = stg[2 * 256 + tid], g4 = stg[3 * 256 + tid];
         const T psit = T(1.5) * ((g1 + g3) + (g2 + g4));
         const T psi = psit + psi_lin(P, y);
         T Ex, Ey;
         if (FROZEN) { Ex = P.Ex_frozen; Ey = P.Ey_frozen; }
         else { Ex = P.three_over_tau_g * (g1 - g3); Ey = P.three_over_tau_g * (g2 - g4); }
         if (RESID) {
-            const T d = psit - st[33 * 256 + tid];
+            const T d = psit - pprev;
             red[2] = d * d;
             red[3] = psi * psi;
         }
@@ -712,7 +847,15 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<T> 
         // ---- O5: Onsager dissociation and the implicit reaction (Eq. 5, 42-43) ----
         T pv[5], nv[5];
 #pragma unroll
-        for (int i = 0; i < 5; ++i) { pv[i] = st[(17 + i) * 256 + tid]; nv[i] = st[(22 + i) * 256 + tid]; }
+        for (int i = 0; i < 5; ++i) {
+            pv[i] = lds(st + (17 + i) * 256 + tid, P.isc_c);
+            nv[i] = lds(st + (22 + i) * 256 + tid, P.isc_c);
+            if constexpr (!kSame<S, T>) {
+                const T wc = (i == 0 ? T(1.0 / 3.0) : T(1.0 / 6.0)) * P.cref;
+                pv[i] += wc;
+                nv[i] += wc;
+            }
+        }
         const T sp = (((pv[0] + pv[1]) + pv[2]) + pv[3]) + pv[4];
         const T sn = (((nv[0] + nv[1]) + nv[2]) + nv[3]) + nv[4];
         const T q = sp - sn;
@@ -746,7 +889,7 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<T> 
         T fv[9];
         fv[0] = T(0);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) fv[i] = st[(i - 1) * 256 + tid];
+        for (int i = 1; i < 9; ++i) fv[i] = lds(st + (i - 1) * 256 + tid, P.isc_f);
         T mf[9];
         moments9<T>(fv, mf);     // mf[0] is not used (f0 is not stored)
         const T ux = (mf[1] + T(0.5) * Fx) * inv_rho;
@@ -792,9 +935,9 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<T> 
                 const T v = fv[i] - dl[i];
                 const int yd = y + cy9(i);
                 if (yd >= 0 && yd < ny)
-                    dst.f[(i - 1) * nn + (long long)yd * nx + wrapx(x + cx9(i), nx)] = v;
+                    sts_sr(dst.f + (i - 1) * nn + (long long)yd * nx + wrapx(x + cx9(i), nx), v, P.sc_f, rng);
                 else
-                    dst.f[(opp9(i) - 1) * nn + k] = v;
+                    sts_sr(dst.f + (opp9(i) - 1) * nn + k, v, P.sc_f, rng);
             }
         }
 
@@ -802,11 +945,11 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<T> 
         {
             T hv[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) hv[i] = st[(8 + i) * 256 + tid];
+            for (int i = 0; i < 9; ++i) hv[i] = lds(st + (8 + i) * 256 + tid, P.isc_h);
             const T pux = phi * ux, puy = phi * uy;
-            const T dpx = pux - st[31 * 256 + tid], dpy = puy - st[32 * 256 + tid];
-            phiu[k] = pux;
-            phiu[nn + k] = puy;
+            const T dpx = pux - lds(st + 27 * 256 + tid, P.isc_u), dpy = puy - lds(st + 28 * 256 + tid, P.isc_u);
+            sts(phiu + k, pux, P.sc_u);
+            sts(phiu + nn + k, puy, P.sc_u);
             // normal of Eq. 32, regularised: grad phi / sqrt(|grad phi|^2 + eps^2)
             const T g2s = gx * gx + gy * gy;
             T nhx = T(0), nhy = T(0);
@@ -857,9 +1000,9 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<T> 
                     const int xd = cx9(i) == 0 ? x : (cx9(i) > 0 ? xp : xm);
                     const T *qr = cy9(i) == 0 ? q1 : (cy9(i) > 0 ? q2 : q0);
                     const T shift = i == 0 ? T(0) : w9<T>(i) * (phir - qr[xd]);
-                    dst.h[i * nn + (long long)yd * nx + xd] = v + shift;
+                    sts_sr(dst.h + i * nn + (long long)yd * nx + xd, v + shift, P.sc_h, rng);
                 } else {
-                    dst.h[opp9(i) * nn + k] = v;
+                    sts_sr(dst.h + opp9(i) * nn + k, v, P.sc_h, rng);
                 }
             }
         }
@@ -900,29 +1043,52 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<T> 
             no[2] = nv[2] - T(0.5) * (mc4 + mc2);
             no[4] = nv[4] - T(0.5) * (mc4 - mc2);
 
-            const long long row = (long long)y * nx;
-            dst.p[k] = po[0];
-            dst.n[k] = no[0];
-            dst.p[nn + row + xp] = po[1];
-            dst.n[nn + row + xp] = no[1];
-            dst.p[3 * nn + row + xm] = po[3];
-            dst.n[3 * nn + row + xm] = no[3];
             const T w = T(1) / T(6);
+            T bp2, bn2, bp4, bn4;     // pushed or bounced values of directions 2 and 4
             if (y + 1 < ny) {
-                dst.p[2 * nn + k + nx] = po[2];
-                dst.n[2 * nn + k + nx] = no[2];
+                bp2 = po[2];
+                bn2 = no[2];
             } else {  // cathode: attracts cations (zero gradient), repels anions
                 const T cwp = P.ion_bc == 0 ? cp : T(0);
-                dst.p[4 * nn + k] = P.ion_bc == 2 ? po[2] : -po[2] + T(2) * w * cwp;
-                dst.n[4 * nn + k] = P.ion_bc == 2 ? no[2] : -no[2];
+                bp2 = P.ion_bc == 2 ? po[2] : -po[2] + T(2) * w * cwp;
+                bn2 = P.ion_bc == 2 ? no[2] : -no[2];
             }
             if (y > 0) {
-                dst.p[4 * nn + k - nx] = po[4];
-                dst.n[4 * nn + k - nx] = no[4];
+                bp4 = po[4];
+                bn4 = no[4];
             } else {  // anode: repels cations, attracts anions
                 const T cwm = P.ion_bc == 0 ? cm : T(0);
-                dst.p[2 * nn + k] = P.ion_bc == 2 ? po[4] : -po[4];
-                dst.n[2 * nn + k] = P.ion_bc == 2 ? no[4] : -no[4] + T(2) * w * cwm;
+                bp4 = P.ion_bc == 2 ? po[4] : -po[4];
+                bn4 = P.ion_bc == 2 ? no[4] : -no[4] + T(2) * w * cwm;
+            }
+            if constexpr (!kSame<S, T>) {   // stored relative to w_i c_ref
+                const T c0 = P.cref * T(1.0 / 3.0), c1 = P.cref * w;
+                po[0] -= c0; no[0] -= c0;
+                po[1] -= c1; no[1] -= c1;
+                po[3] -= c1; no[3] -= c1;
+                bp2 -= c1; bn2 -= c1;
+                bp4 -= c1; bn4 -= c1;
+            }
+            const long long row = (long long)y * nx;
+            sts_sr(dst.p + k, po[0], P.sc_c, rng);
+            sts_sr(dst.n + k, no[0], P.sc_c, rng);
+            sts_sr(dst.p + nn + row + xp, po[1], P.sc_c, rng);
+            sts_sr(dst.n + nn + row + xp, no[1], P.sc_c, rng);
+            sts_sr(dst.p + 3 * nn + row + xm, po[3], P.sc_c, rng);
+            sts_sr(dst.n + 3 * nn + row + xm, no[3], P.sc_c, rng);
+            if (y + 1 < ny) {
+                sts_sr(dst.p + 2 * nn + k + nx, bp2, P.sc_c, rng);
+                sts_sr(dst.n + 2 * nn + k + nx, bn2, P.sc_c, rng);
+            } else {
+                sts_sr(dst.p + 4 * nn + k, bp2, P.sc_c, rng);
+                sts_sr(dst.n + 4 * nn + k, bn2, P.sc_c, rng);
+            }
+            if (y > 0) {
+                sts_sr(dst.p + 4 * nn + k - nx, bp4, P.sc_c, rng);
+                sts_sr(dst.n + 4 * nn + k - nx, bn4, P.sc_c, rng);
+            } else {
+                sts_sr(dst.p + 2 * nn + k, bp4, P.sc_c, rng);
+                sts_sr(dst.n + 2 * nn + k, bn4, P.sc_c, rng);
             }
         }
 
@@ -986,9 +1152,9 @@ static __global__ void __launch_bounds__(256) k_step_end(const double *__restric
 
 // ---- initial state (Sec. 6 set-up) ------------------------------------------------
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_init_state(const DevP<T> P, Pops<T> pops, T *__restrict__ g,
-                                                    T *__restrict__ phiu, PhiRef<T> Rf, double xc, double yc,
+template <typename T, typename S>
+__global__ void __launch_bounds__(256) k_init_state(const DevP<T> P, Pops<S> pops, T *__restrict__ g,
+                                                    S *__restrict__ phiu, PhiRef<T> Rf, double xc, double yc,
                                                     double R, double Wi, int shape, int psi_zero)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -999,17 +1165,18 @@ __global__ void __launch_bounds__(256) k_init_state(const DevP<T> P, Pops<T> pop
     const T phi0 = (T)(0.5 * (1.0 + tanh(2.0 * (R - r) / Wi)));
     // h = w_i phi0 at rest is exactly the reference state: deviations 0
 #pragma unroll
-    for (int i = 0; i < 9; ++i) pops.h[i * nn + k] = T(0);
+    for (int i = 0; i < 9; ++i) sts(pops.h + i * nn + k, T(0), P.sc_h);
     const long long gk = (long long)(y + 1) * P.nx + x;
     Rf.phir[gk] = phi0;
     if (y == 0) Rf.phir[x] = phi0;
     if (y == P.ny - 1) Rf.phir[(long long)(P.ny + 1) * P.nx + x] = phi0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) pops.f[i * nn + k] = T(0);
+    for (int i = 0; i < 8; ++i) sts(pops.f + i * nn + k, T(0), P.sc_f);
+    // p, n are set by k_init_ions
 #pragma unroll
-    for (int i = 0; i < 5; ++i) { pops.p[i * nn + k] = T(0); pops.n[i * nn + k] = T(0); }
-    phiu[k] = T(0);
-    phiu[nn + k] = T(0);
+    for (int i = 0; i < 5; ++i) { sts(pops.p + i * nn + k, T(0), P.sc_c); sts(pops.n + i * nn + k, T(0), P.sc_c); }
+    sts(phiu + k, T(0), P.sc_u);
+    sts(phiu + nn + k, T(0), P.sc_u);
     const T w = T(1) / T(6);
     if (psi_zero) {
         const T v = -w * psi_lin(P, y);
@@ -1047,8 +1214,8 @@ __global__ void __launch_bounds__(256) k_init_ref(const DevP<T> P, PhiRef<T> Rf,
     Rf.mur[k] = (T)(4.0 * beta * c * (c - 1.0) * (c - 0.5) - kappa * lap);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_init_ions(const DevP<T> P, Pops<T> pops, const T *__restrict__ gA,
+template <typename T, typename S>
+__global__ void __launch_bounds__(256) k_init_ions(const DevP<T> P, Pops<S> pops, const T *__restrict__ gA,
                                                    const T *__restrict__ gB, const Control *__restrict__ ctl,
                                                    const T *__restrict__ phig, T *__restrict__ snap,
                                                    double c_scale, double c0)
@@ -1076,8 +1243,9 @@ __global__ void __launch_bounds__(256) k_init_ions(const DevP<T> P, Pops<T> pops
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         const T v = wv[i] * ceq;
-        pops.p[i * nn + k] = v;
-        pops.n[i * nn + k] = v;
+        const T vs = kSame<S, T> ? v : v - wv[i] * P.cref;
+        sts(pops.p + i * nn + k, vs, P.sc_c);
+        sts(pops.n + i * nn + k, vs, P.sc_c);
         sp += v;
         sn += v;
     }
@@ -1096,9 +1264,9 @@ __global__ void __launch_bounds__(256) k_init_ions(const DevP<T> P, Pops<T> pops
 
 // ---- state transfer (checkpoint / test hook) ---------------------------------------
 // Packs rows [y0, y0 + rows) of the state into 35 doubles per node.
-template <typename T>
-__global__ void k_pack_state(const DevP<T> P, const Pops<T> pops, const T *__restrict__ g,
-                             const T *__restrict__ phiu, const T *__restrict__ phir, double *__restrict__ out,
+template <typename T, typename S>
+__global__ void k_pack_state(const DevP<T> P, const Pops<S> pops, const T *__restrict__ g,
+                             const S *__restrict__ phiu, const T *__restrict__ phir, double *__restrict__ out,
                              int y0, int rows)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1108,20 +1276,24 @@ __global__ void k_pack_state(const DevP<T> P, const Pops<T> pops, const T *__res
     const long long nn = P.nn, k = (long long)y0 * P.nx + i;
     double *o = out + 35 * i;
     o[0] = 0.0;
-    for (int q = 1; q < 9; ++q) o[q] = (double)pops.f[(q - 1) * nn + k];
+    for (int q = 1; q < 9; ++q) o[q] = (double)lds(pops.f + (q - 1) * nn + k, P.isc_f);
     const double pr = (double)phir[(long long)(y + 1) * P.nx + (k - (long long)y * P.nx)];
-    for (int q = 0; q < 9; ++q) o[9 + q] = (double)pops.h[q * nn + k] + (double)w9<T>(q) * pr;
-    for (int q = 0; q < 5; ++q) o[18 + q] = (double)pops.p[q * nn + k];
-    for (int q = 0; q < 5; ++q) o[23 + q] = (double)pops.n[q * nn + k];
+    for (int q = 0; q < 9; ++q) o[9 + q] = (double)lds(pops.h + q * nn + k, P.isc_h) + (double)w9<T>(q) * pr;
+    const double cr = (double)P.cref;
+    for (int q = 0; q < 5; ++q) {
+        const double wc = (q == 0 ? 1.0 / 3.0 : 1.0 / 6.0) * cr;
+        o[18 + q] = (double)lds(pops.p + q * nn + k, P.isc_c) + wc;
+        o[23 + q] = (double)lds(pops.n + q * nn + k, P.isc_c) + wc;
+    }
     const double pl = (double)psi_lin(P, y);
     o[28] = 0.0;
     for (int q = 0; q < 4; ++q) o[29 + q] = (double)g[q * nn + k] + pl / 6.0;
-    o[33] = (double)phiu[k];
-    o[34] = (double)phiu[nn + k];
+    o[33] = (double)lds(phiu + k, P.isc_u);
+    o[34] = (double)lds(phiu + nn + k, P.isc_u);
 }
 
-template <typename T>
-__global__ void k_unpack_state(const DevP<T> P, Pops<T> pops, T *__restrict__ g, T *__restrict__ phiu,
+template <typename T, typename S>
+__global__ void k_unpack_state(const DevP<T> P, Pops<S> pops, T *__restrict__ g, S *__restrict__ phiu,
                                const T *__restrict__ phir, const double *__restrict__ in, int y0, int rows)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1130,15 +1302,19 @@ __global__ void k_unpack_state(const DevP<T> P, Pops<T> pops, T *__restrict__ g,
     const int y = y0 + (int)(i / P.nx);
     const long long nn = P.nn, k = (long long)y0 * P.nx + i;
     const double *o = in + 35 * i;
-    for (int q = 1; q < 9; ++q) pops.f[(q - 1) * nn + k] = (T)o[q];
+    for (int q = 1; q < 9; ++q) sts(pops.f + (q - 1) * nn + k, (T)o[q], P.sc_f);
     const double pr = (double)phir[(long long)(y + 1) * P.nx + (k - (long long)y * P.nx)];
-    for (int q = 0; q < 9; ++q) pops.h[q * nn + k] = (T)(o[9 + q] - (double)w9<T>(q) * pr);
-    for (int q = 0; q < 5; ++q) pops.p[q * nn + k] = (T)o[18 + q];
-    for (int q = 0; q < 5; ++q) pops.n[q * nn + k] = (T)o[23 + q];
+    for (int q = 0; q < 9; ++q) sts(pops.h + q * nn + k, (T)(o[9 + q] - (double)w9<T>(q) * pr), P.sc_h);
+    const double cr = (double)P.cref;
+    for (int q = 0; q < 5; ++q) {
+        const double wc = (q == 0 ? 1.0 / 3.0 : 1.0 / 6.0) * cr;
+        sts(pops.p + q * nn + k, (T)(o[18 + q] - wc), P.sc_c);
+        sts(pops.n + q * nn + k, (T)(o[23 + q] - wc), P.sc_c);
+    }
     const double pl = (double)psi_lin(P, y);
     for (int q = 0; q < 4; ++q) g[q * nn + k] = (T)(o[29 + q] - pl / 6.0);
-    phiu[k] = (T)o[33];
-    phiu[nn + k] = (T)o[34];
+    sts(phiu + k, (T)o[33], P.sc_u);
+    sts(phiu + nn + k, (T)o[34], P.sc_u);
 }
 
 template <typename T>

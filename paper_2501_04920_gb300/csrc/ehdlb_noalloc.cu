@@ -183,10 +183,10 @@ extern "C" int ehdlb_potential_noalloc(int nx, int ny, const ehdlb_params *p, co
     k_noalloc_init_g<<<grid, blk, 0, s>>>(d, gbuf[0], p->init_psi_zero);
     for (int j = 1; j <= nsweeps; ++j) {
         if (j == nsweeps)
-            ehdlb::k_sweep<double, true, false, false>
+            ehdlb::k_sweep<double, double, true, false, false>
                 <<<grid, blk, 0, s>>>(d, gbuf[0], gbuf[1], phig, q, psi_prev, part, ctl, j);
         else
-            ehdlb::k_sweep<double, false, false, false>
+            ehdlb::k_sweep<double, double, false, false, false>
                 <<<grid, blk, 0, s>>>(d, gbuf[0], gbuf[1], phig, q, psi_prev, part, ctl, j);
     }
     k_noalloc_finish<<<grid, blk, 0, s>>>(d, gbuf[nsweeps & 1], psi_prev, nsweeps >= 1 ? 1 : 0, psi, Ex, Ey,

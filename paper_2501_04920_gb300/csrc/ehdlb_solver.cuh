@@ -1,6 +1,8 @@
 // ehdlb_solver.cuh -- host side of one lattice: device buffers, the initial
-// state, the kernel sequence of a time step, transfers.  Instantiated for
-// float and double in solver_fp32.cu / solver_fp64.cu.
+// state, the kernel sequence of a time step, transfers.  Instantiated with
+// arithmetic type T and population storage type S: (float, float) in
+// solver_fp32.cu, (double, double) in solver_fp64.cu and (float, __half) in
+// solver_fp16s.cu.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,7 +28,7 @@ namespace ehdlb {
         }                                                                           \
     } while (0)
 
-template <typename T> class Solver : public SolverBase {
+template <typename T, typename S = T> class Solver : public SolverBase {
   public:
     static constexpr int BX = 64, BY = 4;
 
@@ -47,16 +49,18 @@ template <typename T> class Solver : public SolverBase {
         }
         grid_ = dim3((nx_ + BX - 1) / BX, (ny_ + BY - 1) / BY);
         nb_ = (long long)grid_.x * grid_.y;
-        const size_t plane = sizeof(T) * (size_t)nn_;
+        const size_t plane = sizeof(T) * (size_t)nn_, splane = sizeof(S) * (size_t)nn_;
         for (int b = 0; b < 2; ++b) {
-            T *base;
-            EHDLB_CK(alloc((void **)&base, plane * 27));
+            S *base;
+            EHDLB_CK(alloc((void **)&base, splane * 27));
             pops_[b].f = base;
             pops_[b].h = base + 8 * nn_;
             pops_[b].p = base + 17 * nn_;
             pops_[b].n = base + 22 * nn_;
             EHDLB_CK(alloc((void **)&g_[b], plane * 4));
         }
+        // 16-byte staging of the main kernel: every row starts on a 16-byte boundary
+        vec_ok_ = ((size_t)nx_ * sizeof(S)) % 16 == 0 && ((size_t)nx_ * sizeof(T)) % 16 == 0;
         EHDLB_CK(alloc((void **)&phig_, sizeof(T) * (size_t)(ny_ + 2) * nx_));
         EHDLB_CK(alloc((void **)&ref_.phir, sizeof(T) * (size_t)(ny_ + 2) * nx_));
         EHDLB_CK(alloc((void **)&ref_.dphig, sizeof(T) * (size_t)(ny_ + 2) * nx_));
@@ -65,7 +69,7 @@ template <typename T> class Solver : public SolverBase {
         EHDLB_CK(alloc((void **)&ref_.mur, plane));
         EHDLB_CK(alloc((void **)&q_, plane));
         EHDLB_CK(alloc((void **)&coef_, plane * 3));
-        EHDLB_CK(alloc((void **)&phiu_, plane * 2));
+        EHDLB_CK(alloc((void **)&phiu_, splane * 2));
         EHDLB_CK(alloc((void **)&psi_prev_, plane));
         EHDLB_CK(alloc((void **)&snap_, plane * EHDLB_NFIELDS));
         EHDLB_CK(alloc((void **)&part_, sizeof(double) * 4 * (size_t)nb_));
@@ -110,7 +114,7 @@ template <typename T> class Solver : public SolverBase {
         ctl_h_ = c;
         EHDLB_CK(cudaMemcpyAsync(ctl_, &ctl_h_, sizeof(Control), cudaMemcpyHostToDevice, stream_));
         const double Wi = p.W_init > 0.0 ? p.W_init : p.W;
-        k_init_state<T><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[0], g_[0], phiu_, ref_, p.xc, p.yc,
+        k_init_state<T, S><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[0], g_[0], phiu_, ref_, p.xc, p.yc,
                                                              p.R, Wi, p.init_shape, p.init_psi_zero);
         EHDLB_CK(cudaGetLastError());
         k_init_ref<T><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, ref_, 12.0 * p.sigma / p.W, 1.5 * p.sigma * p.W);
@@ -137,7 +141,7 @@ template <typename T> class Solver : public SolverBase {
             }
         }
         EHDLB_CK(cudaGetLastError());
-        k_init_ions<T><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[0], g_[0], g_[1], ctl_, phig_, snap_,
+        k_init_ions<T, S><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[0], g_[0], g_[1], ctl_, phig_, snap_,
                                                             p.c_init_scale, p.c0);
         EHDLB_CK(cudaGetLastError());
         EHDLB_CK(cudaMemcpyAsync(&ctl_h_, ctl_, sizeof(Control), cudaMemcpyDeviceToHost, stream_));
@@ -158,10 +162,11 @@ template <typename T> class Solver : public SolverBase {
 
     void set_schedule(const int *c, int n) override { sched_.assign(c, c + n); }
     void set_timing(int on) override { timing_ = on != 0; }
-    void set_tuning(int sweeps_per_launch, int shape) override
+    void set_tuning(int sweeps_per_launch, int shape, int vec_staging) override
     {
         if (sweeps_per_launch >= 0) tb_chunk_ = sweeps_per_launch;
         if (shape >= 0) tb_shape_ = shape < TB_NSHAPES ? shape : 0;
+        if (vec_staging >= 0) vec_ = vec_staging != 0;
     }
 
     int step(int nsteps, ehdlb_stats *st, std::string &err) override
@@ -323,12 +328,29 @@ template <typename T> class Solver : public SolverBase {
         d.s_free = (T)p.s_free;
         d.Ex_frozen = (T)p.E_frozen_x;
         d.Ey_frozen = (T)p.E_frozen_y;
+        // FP16 storage: power-of-two scales that lift the fields' typical
+        // deviations (f ~ 1e-4, h ~ 1e-2, p and n ~ 0.1, phi u ~ 1e-4) to
+        // 1..100 and keep deviations down to ~1e-7 above the subnormal range,
+        // with room to 16 (f, phi u) or 255 (h, p, n) below the FP16 maximum;
+        // the rest concentration is that of the initial state in a uniform
+        // field (Eq. 43 with F = 1); g stays in T
+        const bool half = !kSame<S, T>;
+        const double sf = half ? 4096.0 : 1.0, sh = half ? 256.0 : 1.0, sc = half ? 256.0 : 1.0, sg = 1.0,
+                     su = half ? 4096.0 : 1.0;
+        d.sc_f = (T)sf; d.isc_f = (T)(1.0 / sf);
+        d.sc_h = (T)sh; d.isc_h = (T)(1.0 / sh);
+        d.sc_c = (T)sc; d.isc_c = (T)(1.0 / sc);
+        d.sc_g = (T)sg; d.isc_g = (T)(1.0 / sg);
+        d.sc_u = (T)su; d.isc_u = (T)(1.0 / su);
+        double cref = 0.0;
+        if (half) cref = p.c_init_scale * ((p.k_r > 0.0 && p.onsager_form != 2) ? std::sqrt(p.k_d / p.k_r) : p.c0);
+        d.cref = (T)cref;
         dp_ = d;
     }
 
     void launch_prep(int par, int fixedK, int kmin, int kmax, int flips)
     {
-        k_prep<T><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n, ref_,
+        k_prep<T, S><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n, ref_,
                                                        phig_, q_, ctl_, fixedK, kmin, kmax, flips);
         ++launches_;
     }
@@ -337,11 +359,10 @@ template <typename T> class Solver : public SolverBase {
     // blocks per SM the registers are sized for) and the largest number of
     // sweeps one launch fuses.
     struct TbShape { int rw, rh, by, minb; };
-    static constexpr int TB_NSHAPES = sizeof(T) == 4 ? 3 : 1;
+    static constexpr int TB_NSHAPES = sizeof(T) == 4 ? 2 : 1;
     static constexpr TbShape tb_shape(int i)
     {
-        return sizeof(T) == 4 ? (i == 1 ? TbShape{64, 32, 8, 4} : (i == 2 ? TbShape{96, 32, 16, 2} : TbShape{64, 32, 16, 3}))
-                              : TbShape{64, 16, 16, 2};
+        return sizeof(T) == 4 ? (i == 1 ? TbShape{64, 32, 8, 4} : TbShape{64, 32, 16, 3}) : TbShape{64, 16, 16, 2};
     }
     static constexpr int TB_MAX = sizeof(T) == 4 ? 5 : 2;
 
@@ -352,16 +373,20 @@ template <typename T> class Solver : public SolverBase {
         return dim3((nx + tx - 1) / tx, (ny + ty - 1) / ty);
     }
 
-    template <bool S, bool F, bool R> cudaError_t main_attr()
+    template <bool SN, bool F, bool R> cudaError_t main_attr()
     {
-        return cudaFuncSetAttribute(k_main<T, S, F, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)main_smem_bytes<T>());
+        cudaError_t e = cudaFuncSetAttribute(k_main<T, S, SN, F, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)main_smem_bytes<T, S>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_main<T, S, SN, F, R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)main_smem_bytes<T, S>());
+        return e;
     }
 
     template <int NSW, int SH, bool FIRST, bool RESID> cudaError_t tb_attr2()
     {
         constexpr TbShape sh = tb_shape(SH);
-        return cudaFuncSetAttribute(k_sweep_tb<T, NSW, sh.rw, sh.rh, sh.by, sh.minb, FIRST, RESID>,
+        return cudaFuncSetAttribute(k_sweep_tb<T, T, NSW, sh.rw, sh.rh, sh.by, sh.minb, FIRST, RESID>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)tb_smem_bytes<T, sh.rw, sh.rh>(FIRST));
     }
@@ -380,7 +405,6 @@ template <typename T> class Solver : public SolverBase {
         cudaError_t e = tb_attr1<NSW, 0>();
         if constexpr (TB_NSHAPES > 1) {
             if (e == cudaSuccess) e = tb_attr1<NSW, 1>();
-            if (e == cudaSuccess) e = tb_attr1<NSW, 2>();
         }
         return e;
     }
@@ -390,7 +414,7 @@ template <typename T> class Solver : public SolverBase {
         constexpr TbShape sh = tb_shape(SH);
         constexpr int TXo = sh.rw - 2 * NSW, TYo = sh.rh - 2 * NSW;
         const dim3 g((nx_ + TXo - 1) / TXo, (ny_ + TYo - 1) / TYo);
-        k_sweep_tb<T, NSW, sh.rw, sh.rh, sh.by, sh.minb, FIRST, RESID>
+        k_sweep_tb<T, T, NSW, sh.rw, sh.rh, sh.by, sh.minb, FIRST, RESID>
             <<<g, dim3(32, sh.by), tb_smem_bytes<T, sh.rw, sh.rh>(FIRST), stream_>>>(
                 dp_, g_[0], g_[1], phig_, q_, coef_, part2_, ctl_, tb_m_);
     }
@@ -412,7 +436,6 @@ template <typename T> class Solver : public SolverBase {
         const bool first = m == 0;
         if constexpr (TB_NSHAPES > 1) {
             if (tb_shape_ == 1) tb_launch1<NSW, 1>(first, resid);
-            else if (tb_shape_ == 2) tb_launch1<NSW, 2>(first, resid);
             else tb_launch1<NSW, 0>(first, resid);
         } else {
             tb_launch1<NSW, 0>(first, resid);
@@ -438,7 +461,7 @@ template <typename T> class Solver : public SolverBase {
     {
         const dim3 b(BX, BY);
 #define EHDLB_SWEEP(W, R, C)                                                                            \
-    k_sweep<T, W, R, C><<<grid_, b, 0, stream_>>>(dp_, g_[0], g_[1], phig_, q_, psi_prev_, part_, ctl_, j)
+    k_sweep<T, T, W, R, C><<<grid_, b, 0, stream_>>>(dp_, g_[0], g_[1], phig_, q_, psi_prev_, part_, ctl_, j)
         if (ctrl) {
             if (resid) EHDLB_SWEEP(true, true, true);
             else EHDLB_SWEEP(true, false, true);
@@ -489,9 +512,17 @@ template <typename T> class Solver : public SolverBase {
         const int resid_mode = main_resid ? 1 : ((fused && last) ? 2 : 0);
         const dim3 b(BX, BY);
         int *unstable = &ctl_->unstable;
-#define EHDLB_MAIN(S, F, R)                                                                              \
-    k_main<T, S, F, R><<<grid_, b, main_smem_bytes<T>(), stream_>>>(dp_, pops_[par], pops_[par ^ 1], g_[0], \
-                                                 g_[1], ctl_, ref_, phiu_, psi_prev_, snap_, part_, unstable)
+#define EHDLB_MAIN(SN, F, R)                                                                             \
+    do {                                                                                                 \
+        if (vec_ok_ && vec_)                                                                             \
+            k_main<T, S, SN, F, R, true><<<grid_, b, main_smem_bytes<T, S>(), stream_>>>(                   \
+                dp_, pops_[par], pops_[par ^ 1], g_[0], g_[1], ctl_, ref_, phiu_, psi_prev_, snap_, part_, \
+                unstable);                                                                               \
+        else                                                                                             \
+            k_main<T, S, SN, F, R, false><<<grid_, b, main_smem_bytes<T, S>(), stream_>>>(                  \
+                dp_, pops_[par], pops_[par ^ 1], g_[0], g_[1], ctl_, ref_, phiu_, psi_prev_, snap_, part_, \
+                unstable);                                                                               \
+    } while (0)
         if (last) {
             if (frozen) EHDLB_MAIN(true, true, false);
             else if (main_resid) EHDLB_MAIN(true, false, true);
@@ -530,7 +561,7 @@ template <typename T> class Solver : public SolverBase {
             const unsigned nblk = (unsigned)((cnt + 255) / 256);
             cudaError_t e = cudaSuccess;
             if (dst) {
-                k_pack_state<T><<<nblk, 256, 0, stream_>>>(dp_, pops_[tpar_], g_[cur], phiu_, ref_.phir, stage,
+                k_pack_state<T, S><<<nblk, 256, 0, stream_>>>(dp_, pops_[tpar_], g_[cur], phiu_, ref_.phir, stage,
                                                             y0, r);
                 e = cudaGetLastError();
                 if (e == cudaSuccess)
@@ -540,7 +571,7 @@ template <typename T> class Solver : public SolverBase {
                 e = cudaMemcpyAsync(stage, src + per_row * y0, sizeof(double) * per_row * r,
                                     cudaMemcpyHostToDevice, stream_);
                 if (e == cudaSuccess)
-                    k_unpack_state<T><<<nblk, 256, 0, stream_>>>(dp_, pops_[tpar_], g_[cur], phiu_, ref_.phir,
+                    k_unpack_state<T, S><<<nblk, 256, 0, stream_>>>(dp_, pops_[tpar_], g_[cur], phiu_, ref_.phir,
                                                               stage, y0, r);
                 if (e == cudaSuccess) e = cudaGetLastError();
             }
@@ -560,9 +591,12 @@ template <typename T> class Solver : public SolverBase {
     bool own_stream_ = false;
     dim3 grid_;
     long long nb_ = 0;
-    Pops<T> pops_[2]{};
+    Pops<S> pops_[2]{};
     T *g_[2]{};
-    T *phig_ = nullptr, *q_ = nullptr, *phiu_ = nullptr, *psi_prev_ = nullptr, *snap_ = nullptr;
+    S *phiu_ = nullptr;
+    bool vec_ok_ = false;                     // 16-byte staging possible
+    bool vec_ = true;                         // and chosen (tuning)
+    T *phig_ = nullptr, *q_ = nullptr, *psi_prev_ = nullptr, *snap_ = nullptr;
     PhiRef<T> ref_{};
     double *part_ = nullptr, *part2_ = nullptr, *stage_ = nullptr;
     int tb_chunk_ = sizeof(T) == 4 ? 5 : 2;  // sweeps fused per launch (0: one per launch)

@@ -1,6 +1,6 @@
 // ehdlb_solver_base.h -- interface between the C-ABI layer and the
 // precision-specific CUDA solvers (float: solver_fp32.cu, double:
-// solver_fp64.cu).
+// solver_fp64.cu, float with FP16 storage: solver_fp16s.cu).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -22,11 +22,12 @@ class SolverBase {
     virtual int set_state(const double *src, std::string &err) = 0;
     virtual void set_schedule(const int *c, int n) = 0;
     virtual void set_timing(int on) = 0;
-    virtual void set_tuning(int sweeps_per_launch, int shape) = 0;
+    virtual void set_tuning(int sweeps_per_launch, int shape, int vec_staging) = 0;
     int last_nsteps = 0;
 };
 
 SolverBase *make_solver_fp32(int nx, int ny, cudaStream_t s, int *status, std::string &err);
 SolverBase *make_solver_fp64(int nx, int ny, cudaStream_t s, int *status, std::string &err);
+SolverBase *make_solver_fp16s(int nx, int ny, cudaStream_t s, int *status, std::string &err);
 
 }  // namespace ehdlb

@@ -14,7 +14,7 @@ import numpy as np
 from . import build as _build
 
 FIELDS = ["phi", "ux", "uy", "p", "psi", "Ex", "Ey", "cp", "cm", "q"]
-FP64, FP32 = 0, 1
+FP64, FP32, FP16S = 0, 1, 2
 OK, WNOTCONV, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ESTATE = 0, 1, -1, -2, -3, -4, -5
 STATUS_NAMES = {0: "OK", 1: "WNOTCONV", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA",
                 -4: "EUNSTABLE", -5: "ESTATE"}
@@ -92,7 +92,7 @@ def lib():
         L.ehdlb_get_state.argtypes = [vp, dp, C.c_size_t]
         L.ehdlb_set_state.argtypes = [vp, dp, C.c_size_t]
         L.ehdlb_set_timing.argtypes = [vp, C.c_int]
-        L.ehdlb_set_tuning.argtypes = [vp, C.c_int, C.c_int]
+        L.ehdlb_set_tuning.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.ehdlb_potential_noalloc.argtypes = [C.c_int, C.c_int, C.POINTER(ehdlb_params), vp, vp,
                                               C.c_int, vp, vp, vp, dp, vp]
         L.ehdlb_destroy.argtypes = [vp]
@@ -217,8 +217,9 @@ def ehdlb_potential_noalloc(nx, ny, p: ehdlb_params, phi_dev: int, q_dev: int, n
     return status, r.value
 
 
-def ehdlb_set_tuning(ctx, sweeps_per_launch: int = -1, tile_shape: int = -1):
-    return _check(ctx, lib().ehdlb_set_tuning(ctx, sweeps_per_launch, tile_shape), "ehdlb_set_tuning")
+def ehdlb_set_tuning(ctx, sweeps_per_launch: int = -1, tile_shape: int = -1, main_staging: int = -1):
+    return _check(ctx, lib().ehdlb_set_tuning(ctx, sweeps_per_launch, tile_shape, main_staging),
+                  "ehdlb_set_tuning")
 
 
 def ehdlb_destroy(ctx):

@@ -1,0 +1,132 @@
+"""FP16 storage form against the FP64 oracle (needs a GB300).
+
+The FP16S context stores every population as an FP16 deviation from a rest
+state (h from w_i phi_ref, g from w_i psi_lin, p and n from w_i c_ref) and
+computes in float.  Its error against FP64 is set by the storage rounding,
+so the bound of each field is derived from the same rounding emulated on the
+oracle: after every oracle step the state is replaced by its deviations
+rounded to FP16 (round to nearest) plus the rest states.  The GPU error must
+stay within a small factor of that emulated error (plus the float floor of
+the FP32 path), and the droplet deformation D (Eq. 63) within 1e-3 of FP64.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_04920_gb300 import ehdlb, workloads
+
+pytestmark = pytest.mark.gpu
+
+W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+W5 = np.array([1 / 3] + [1 / 6] * 4)
+KEYS = ("phi", "psi", "q", "cp", "cm")
+FLOAT_FLOOR = 3e-5       # FP32 path bound on these fields (|u|: same)
+FACTOR = 4.0             # GPU error against the emulated storage error
+D_TOL = 1e-3
+
+
+def rel_linf(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def errors(got, ref):
+    e = {k: rel_linf(got[k], ref[k]) for k in KEYS}
+    e["u"] = rel_linf(np.hypot(got["ux"], got["uy"]), np.hypot(ref["ux"], ref["uy"]))
+    return e
+
+
+def rest_state(orc, prm, nx, ny):
+    """Rest states the FP16 form stores deviations from, per state entry."""
+    f0 = orc.fields()
+    phi_ref = f0["phi"]
+    cref = prm["c_init_scale"] * np.sqrt(prm["k_d"] / prm["k_r"])
+    y = np.arange(ny)
+    psi_lin = prm["psi_anode"] + (prm["psi_cathode"] - prm["psi_anode"]) * (y + 0.5) / ny
+    shift = np.zeros((ny, nx, 35))
+    shift[:, :, 9:18] = phi_ref[:, :, None] * W9
+    shift[:, :, 18:23] = cref * W5
+    shift[:, :, 23:28] = cref * W5
+    shift[:, :, 29:33] = psi_lin[:, None, None] / 6.0
+    return shift
+
+
+def emulated_fp16(nx, ny, prm, steps):
+    """Oracle run whose state is rounded to FP16 deviations after each step."""
+    orc = oracle.Oracle(nx, ny, prm)
+    shift = rest_state(orc, prm, nx, ny)
+    keep = np.zeros(35, bool)
+    keep[[0, 28]] = True   # f0 and g0 are not stored
+    for _ in range(steps):
+        orc.step(1)
+        s = orc.state()
+        r = (s - shift).astype(np.float16).astype(np.float64) + shift
+        r[:, :, keep] = s[:, :, keep]
+        orc.set_state(r)
+    return orc.fields()
+
+
+def check_case(nx, ny, prm, steps):
+    ref = oracle.Oracle(nx, ny, prm)
+    ref.step(steps)
+    fr = ref.fields()
+    emu = errors(emulated_fp16(nx, ny, prm, steps), fr)
+    lat = ehdlb.Lattice(nx, ny, prm, precision=ehdlb.FP16S)
+    lat.step(steps)
+    got = lat.fields()
+    err = errors(got, fr)
+    bad = {k: (err[k], emu[k]) for k in err if not err[k] <= FACTOR * emu[k] + FLOAT_FLOOR}
+    assert not bad, f"GPU error (emulated FP16 storage error) above bound: {bad}"
+    dD = abs(oracle.deformation(got["phi"]) - oracle.deformation(fr["phi"]))
+    assert dD <= D_TOL, dD
+    return err, emu, dD
+
+
+def test_fp16s_droplet256_within_storage_bound():
+    # 16-byte staging path (nx a multiple of 8)
+    n = 256
+    check_case(n, n, workloads.droplet(n), 200)
+
+
+def test_fp16s_ragged_lattice_within_storage_bound():
+    # per-node staging path (nx not a multiple of 8) and partial tiles
+    nx, ny = 130, 97
+    prm = workloads.droplet(128)
+    prm.update(xc=(nx - 1) / 2, yc=(ny - 1) / 2, R=24.0, Kq=5.6893 / (nx * ny))
+    check_case(nx, ny, prm, 100)
+
+
+def test_fp16s_state_round_trip_and_repeatability():
+    # the stochastic rounding is a function of (node, step, store), so runs
+    # repeat bit for bit; a state written out and read back is the same
+    # state, and stepping it from another step count draws other rounding
+    prm = workloads.droplet(128)
+    a = ehdlb.Lattice(128, 128, prm, precision=ehdlb.FP16S)
+    a.step(10)
+    saved = a.state()
+    a.step(10)
+    fa = a.fields()
+    b = ehdlb.Lattice(128, 128, prm, precision=ehdlb.FP16S)
+    b.step(20)
+    fb = b.fields()
+    for k in ehdlb.FIELDS:
+        assert np.array_equal(fa[k], fb[k]), k
+    c = ehdlb.Lattice(128, 128, prm, precision=ehdlb.FP16S)
+    c.set_state(saved)
+    assert np.array_equal(c.state(), saved)
+    c.step(10)
+    fc = c.fields()
+    for k in ("phi", "psi", "cp", "cm"):
+        assert rel(fc[k], fa[k]) <= 1e-3, k
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def test_fp16s_sum_phi_drift_is_bounded():
+    # the storage rounding of h is not mass conserving; its drift over 300
+    # steps of the 256^2 case stays far below the interface's own mass
+    lat = ehdlb.Lattice(256, 256, workloads.droplet(256), precision=ehdlb.FP16S)
+    _, a = lat.step(1)
+    _, b = lat.step(300)
+    assert abs(b.sum_phi - a.sum_phi) <= 1e-4 * a.sum_phi

@@ -172,17 +172,17 @@ def test_fp64_droplet256_matches_oracle():
 
 def test_fp32_every_sweep_tuning_matches_oracle():
     # sweeps fused per launch (0: one per launch) x region shapes of the fused
-    # kernel, on a lattice that no tile divides
-    nx, ny, steps = 130, 97, 12
+    # kernel x staging of the step kernel, on a lattice that no tile divides
+    nx, ny, steps = 136, 97, 12
     prm = workloads.droplet(128)
     prm.update(xc=(nx - 1) / 2, yc=(ny - 1) / 2, R=24.0, Kq=5.6893 / (nx * ny))
     orc = oracle.Oracle(nx, ny, prm)
     orc.step(steps)
     ref = orc.fields()
-    for shape in range(3):
+    for shape in range(2):
         for spl in (0, 1, 2, 3, 4, 5):
             lat = ehdlb.Lattice(nx, ny, prm, precision=ehdlb.FP32)
-            ehdlb.ehdlb_set_tuning(lat.ctx, spl, shape)
+            ehdlb.ehdlb_set_tuning(lat.ctx, spl, shape, spl % 2)
             lat.step(steps)
             err = field_errors(lat.fields(), ref)
             try:
@@ -260,9 +260,10 @@ def test_error_codes():
     good = ehdlb.ehdlb_params_default(dict(xc=7.5, yc=7.5, R=4.0, sweeps_min=0, sweeps_max=1,
                                            sweep_tol=0.0, init_sweeps_max=10))
     assert L.ehdlb_set_params(h, ehdlb.C.byref(good)) == ehdlb.OK
-    assert L.ehdlb_set_tuning(h, 6, 0) == ehdlb.EINVAL
-    assert L.ehdlb_set_tuning(h, 2, 3) == ehdlb.EINVAL
-    assert L.ehdlb_set_tuning(h, -1, -1) == ehdlb.OK
+    assert L.ehdlb_set_tuning(h, 6, 0, 0) == ehdlb.EINVAL
+    assert L.ehdlb_set_tuning(h, 2, 2, 0) == ehdlb.EINVAL
+    assert L.ehdlb_set_tuning(h, 2, 0, 2) == ehdlb.EINVAL
+    assert L.ehdlb_set_tuning(h, -1, -1, -1) == ehdlb.OK
     assert L.ehdlb_step(h, 2, ehdlb.C.byref(st)) == ehdlb.WNOTCONV
     assert st.not_converged == 2
     out = np.zeros(16 * 16)
