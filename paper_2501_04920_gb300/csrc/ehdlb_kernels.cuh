@@ -810,20 +810,33 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<S> 
     if (inside) {
         xm = wrapx(x - 1, nx);
         xp = wrapx(x + 1, nx);
-        const T *r0 = Rf.dphig + (long long)y * nx, *r1 = r0 + nx, *r2 = r1 + nx;
-        dphi = r1[x];
-        const T dE = r1[xp] - dphi, dW = r1[xm] - dphi, dN = r2[x] - dphi, dS = r0[x] - dphi;
+        const int ki = y * nx + x;   // in-plane index (nx ny < 2^31)
+        const T *r1 = Rf.dphig + nx + ki, *r0 = r1 - nx, *r2 = r1 + nx;
+        xm -= x;   // column offsets from here on
+        xp -= x;
+        dphi = r1[0];
+        const T dE = r1[xp] - dphi, dW = r1[xm] - dphi, dN = r2[0] - dphi, dS = r0[0] - dphi;
         const T dNE = r2[xp] - dphi, dNW = r2[xm] - dphi, dSW = r0[xm] - dphi, dSE = r0[xp] - dphi;
-        phir = Rf.phir[(long long)(y + 1) * nx + x];
+        phir = Rf.phir[nx + ki];
         phi = phir + dphi;
-        gx = Rf.gxr[k] + ((dE - dW) * third + ((dNE - dNW) + (dSE - dSW)) * T(1.0 / 12.0));
-        gy = Rf.gyr[k] + ((dN - dS) * third + ((dNE + dNW) - (dSE + dSW)) * T(1.0 / 12.0));
+        gx = Rf.gxr[ki] + ((dE - dW) * third + ((dNE - dNW) + (dSE - dSW)) * T(1.0 / 12.0));
+        gy = Rf.gyr[ki] + ((dN - dS) * third + ((dNE + dNW) - (dSE + dSW)) * T(1.0 / 12.0));
         lapd = T(2.0 / 3.0) * ((dE + dW) + (dN + dS)) + T(1.0 / 6.0) * ((dNE + dSW) + (dNW + dSE));
     }
     cp_async_wait_all();
     if constexpr (VEC) __syncthreads();
     if (inside) {
         SRng rng(k, kSame<S, T> ? 0 : ctl->t, 0x1b873593u);
+        // in-plane offsets of the push targets: rows below / at / above, the
+        // columns left / at / right; a link through a wall bounces back to
+        // the node itself
+        const bool top = y + 1 >= ny, bot = y == 0;
+        const int rowC = y * nx + x, rowN = top ? rowC : rowC + nx, rowS = bot ? rowC : rowC - nx;
+        auto dest = [&](int cx, int cy) -> int {
+            const int col = cx < 0 ? xm : (cx > 0 ? xp : 0);
+            return cy > 0 ? rowN + col : (cy < 0 ? rowS + col : rowC + col);
+        };
+        auto bounced = [&](int cy) -> bool { return cy > 0 ? top : (cy < 0 ? bot : false); };
         const T rho = T(1) + P.rho1 * phi;
         const T inv_rho = T(1) / rho;
         const T mup = P.mu_v * (T(1) + P.mu1 * phi);
@@ -878,7 +891,7 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<S> 
         // ---- O6: forces (Eq. 12-14) ----
         // mu_phi - mu_ref: the cubic of Eq. 13 as (phi - phi_ref) times
         // (phi^2 + phi phi_ref + phi_ref^2 - 1.5 (phi + phi_ref) + 0.5)
-        const T mu_phi = Rf.mur[k] +
+        const T mu_phi = Rf.mur[rowC] +
                          T(4) * P.beta * dphi * ((phi * phi + phi * phir + phir * phir) - T(1.5) * (phi + phir) + T(0.5)) -
                          P.kappa * lapd;
         const T E2 = Ex * Ex + Ey * Ey;
@@ -933,11 +946,8 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<S> 
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
                 const T v = fv[i] - dl[i];
-                const int yd = y + cy9(i);
-                if (yd >= 0 && yd < ny)
-                    sts_sr(dst.f + (i - 1) * nn + (long long)yd * nx + wrapx(x + cx9(i), nx), v, P.sc_f, rng);
-                else
-                    sts_sr(dst.f + (opp9(i) - 1) * nn + k, v, P.sc_f, rng);
+                if (bounced(cy9(i))) sts_sr(dst.f + (opp9(i) - 1) * nn + rowC, v, P.sc_f, rng);
+                else sts_sr(dst.f + (i - 1) * nn + dest(cx9(i), cy9(i)), v, P.sc_f, rng);
             }
         }
 
@@ -991,18 +1001,16 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<S> 
             inverse9<T>(mc, dl);
             // push, re-based on the destination's reference:
             // + w_i (phi_ref(x) - phi_ref(x + c_i)); a bounced population stays
-            const T *q0 = Rf.phir + (long long)y * nx, *q1 = q0 + nx, *q2 = q1 + nx;
+            const T *qr = Rf.phir + nx;   // phi_ref without its ghost row
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const T v = hv[i] - dl[i];
-                const int yd = y + cy9(i);
-                if (yd >= 0 && yd < ny) {
-                    const int xd = cx9(i) == 0 ? x : (cx9(i) > 0 ? xp : xm);
-                    const T *qr = cy9(i) == 0 ? q1 : (cy9(i) > 0 ? q2 : q0);
-                    const T shift = i == 0 ? T(0) : w9<T>(i) * (phir - qr[xd]);
-                    sts_sr(dst.h + i * nn + (long long)yd * nx + xd, v + shift, P.sc_h, rng);
+                if (bounced(cy9(i))) {
+                    sts_sr(dst.h + opp9(i) * nn + rowC, v, P.sc_h, rng);
                 } else {
-                    sts_sr(dst.h + opp9(i) * nn + k, v, P.sc_h, rng);
+                    const int o = dest(cx9(i), cy9(i));
+                    const T shift = i == 0 ? T(0) : w9<T>(i) * (phir - qr[o]);
+                    sts_sr(dst.h + i * nn + o, v + shift, P.sc_h, rng);
                 }
             }
         }
@@ -1069,27 +1077,19 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<S> 
                 bp2 -= c1; bn2 -= c1;
                 bp4 -= c1; bn4 -= c1;
             }
-            const long long row = (long long)y * nx;
-            sts_sr(dst.p + k, po[0], P.sc_c, rng);
-            sts_sr(dst.n + k, no[0], P.sc_c, rng);
-            sts_sr(dst.p + nn + row + xp, po[1], P.sc_c, rng);
-            sts_sr(dst.n + nn + row + xp, no[1], P.sc_c, rng);
-            sts_sr(dst.p + 3 * nn + row + xm, po[3], P.sc_c, rng);
-            sts_sr(dst.n + 3 * nn + row + xm, no[3], P.sc_c, rng);
-            if (y + 1 < ny) {
-                sts_sr(dst.p + 2 * nn + k + nx, bp2, P.sc_c, rng);
-                sts_sr(dst.n + 2 * nn + k + nx, bn2, P.sc_c, rng);
-            } else {
-                sts_sr(dst.p + 4 * nn + k, bp2, P.sc_c, rng);
-                sts_sr(dst.n + 4 * nn + k, bn2, P.sc_c, rng);
-            }
-            if (y > 0) {
-                sts_sr(dst.p + 4 * nn + k - nx, bp4, P.sc_c, rng);
-                sts_sr(dst.n + 4 * nn + k - nx, bn4, P.sc_c, rng);
-            } else {
-                sts_sr(dst.p + 2 * nn + k, bp4, P.sc_c, rng);
-                sts_sr(dst.n + 2 * nn + k, bn4, P.sc_c, rng);
-            }
+            sts_sr(dst.p + rowC, po[0], P.sc_c, rng);
+            sts_sr(dst.n + rowC, no[0], P.sc_c, rng);
+            sts_sr(dst.p + nn + rowC + xp, po[1], P.sc_c, rng);
+            sts_sr(dst.n + nn + rowC + xp, no[1], P.sc_c, rng);
+            sts_sr(dst.p + 3 * nn + rowC + xm, po[3], P.sc_c, rng);
+            sts_sr(dst.n + 3 * nn + rowC + xm, no[3], P.sc_c, rng);
+            // direction 2 lands in plane 2 of the row above or, bounced, in plane 4 here
+            const long long o2 = top ? 4 * nn + rowC : 2 * nn + rowN;
+            const long long o4 = bot ? 2 * nn + rowC : 4 * nn + rowS;
+            sts_sr(dst.p + o2, bp2, P.sc_c, rng);
+            sts_sr(dst.n + o2, bn2, P.sc_c, rng);
+            sts_sr(dst.p + o4, bp4, P.sc_c, rng);
+            sts_sr(dst.n + o4, bn4, P.sc_c, rng);
         }
 
         if (SNAP) {
