@@ -215,8 +215,11 @@ int ehdlb_set_timing(ehdlb_ctx *c, int on);
  *     shared memory per launch when a step takes a fixed number of sweeps,
  *     1..5 (the double-precision solver uses at most 2), 0 for one sweep per
  *     launch; default 5 (float) / 2 (double);
- *   tile_shape: region of one block of the fused sweep kernel, 0: 64 x 32
- *     (512 threads, default), 1: 64 x 32 (256 threads); float only;
+ *   tile_shape: blocks of the fused sweep kernel, 0: 64 x 32 region per
+ *     block (512 threads, default), 1: 64 x 32 (256 threads), 2: clusters of
+ *     2 x 4 blocks of 64 x 32 that exchange populations through distributed
+ *     shared memory every sweep; 1 and 2 float only (the double solver keeps
+ *     0);
  *   main_staging: how the step kernel copies its block's populations to
  *     shared memory, 0: one asynchronous copy per node and plane, 1: 16-byte
  *     copies of row segments (default; used only when nx times the element

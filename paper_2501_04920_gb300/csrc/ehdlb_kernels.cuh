@@ -699,6 +699,262 @@ __global__ void __launch_bounds__(32 * BY, MINB)
     if (RESID) block_sum_store<T, 2>(red, part);
 }
 
+// ---- thread-block clusters -------------------------------------------------------
+
+__device__ __forceinline__ unsigned cluster_ctaid_x()
+{
+    unsigned v;
+    asm volatile("mov.u32 %0, %%cluster_ctaid.x;" : "=r"(v));
+    return v;
+}
+__device__ __forceinline__ unsigned cluster_ctaid_y()
+{
+    unsigned v;
+    asm volatile("mov.u32 %0, %%cluster_ctaid.y;" : "=r"(v));
+    return v;
+}
+__device__ __forceinline__ unsigned cluster_ctarank()
+{
+    unsigned v;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(v));
+    return v;
+}
+// All threads of all CTAs of the cluster; shared-memory writes before it
+// (local or remote) are visible to every CTA after it.
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Shared-memory address of the same offset in CTA `rank` of the cluster.
+__device__ __forceinline__ unsigned map_shared(unsigned local, unsigned rank)
+{
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster(unsigned addr, float v)
+{
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster(unsigned addr, double v)
+{
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+
+// NSW potential sweeps (Eq. 44-50) by a cluster of CX x CY CTAs that
+// together hold a (CX 64) x (CY 32) region of the lattice, each CTA a 64 x 32
+// part of it.  Populations that cross from one CTA's part into another's are
+// written straight into the neighbour's shared memory, and the cluster
+// synchronises once per sweep, so only the cluster region needs a halo: NSW
+// nodes at its outer edge, after which its output tile of
+// (CX 64 - 2 NSW) x (CY 32 - 2 NSW) nodes is exact.  Two buffers of four
+// planes: sweep s reads buffer s mod 2 and writes the other one, so that the
+// barrier after sweep s also orders every read of the buffer that sweep s + 1
+// writes.  The other rules (empty rows outside the lattice, electrode links,
+// periodic x, coefficients in registers, FIRST and RESID) are those of
+// k_sweep_tb.
+// Launch: grid (CX ceil(nx / TX), CY ceil(ny / TY)) with TX = CX 64 - 2 NSW,
+// TY = CY 32 - 2 NSW, blockDim (32, BY), cluster (CX, CY), dynamic shared
+// memory tb_cl_smem_bytes<T>().
+template <typename T> __host__ __device__ constexpr size_t tb_cl_smem_bytes()
+{
+    return sizeof(T) * 8 * (size_t)(32 + 2) * (64 + 2);
+}
+
+template <typename T, int NSW, int CX, int CY, int BY, bool FIRST, bool RESID>
+__global__ void __cluster_dims__(CX, CY, 1) __launch_bounds__(32 * BY, 3)
+    k_sweep_cl(const DevP<T> P, T *__restrict__ gA, T *__restrict__ gB, const T *__restrict__ phig,
+               const T *__restrict__ q, T *__restrict__ coef, double *__restrict__ part,
+               const Control *__restrict__ ctl, int m)
+{
+    constexpr int RW = 64, RH = 32, H = NSW;
+    constexpr int CW = CX * RW, CH = CY * RH, TX = CW - 2 * H, TY = CH - 2 * H;
+    constexpr int PW = RW + 2, PH = RH + 2, PL = PW * PH;
+    constexpr int NB = RW / 32, NA = RH / BY;
+    static_assert(RH % BY == 0 && TX > 0 && TY > 0, "cluster too small for NSW");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sg = reinterpret_cast<T *>(smem_raw);   // [2][4][PH][PW]
+    const int par = (ctl->cur0 + m) & 1;
+    const T *__restrict__ src = par ? gB : gA;
+    T *__restrict__ dst = par ? gA : gB;
+    const int nx = P.nx, ny = P.ny;
+    const long long nn = P.nn;
+    const int cx = (int)cluster_ctaid_x(), cy = (int)cluster_ctaid_y();
+    const unsigned rank = cluster_ctarank();
+    const int X0 = (blockIdx.x / CX) * TX - H, Y0 = (blockIdx.y / CY) * TY - H;   // cluster region origin
+    const int x0 = X0 + cx * RW, y0 = Y0 + cy * RH;                               // this CTA's part
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const bool wide = nx >= CW + 2;
+    // neighbours in the cluster (rank x-fastest); a missing one maps to itself
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(sg);
+    const bool has_r = cx < CX - 1, has_l = cx > 0, has_u = cy < CY - 1, has_d = cy > 0;
+    const unsigned base_r = map_shared(sbase, has_r ? rank + 1 : rank);
+    const unsigned base_l = map_shared(sbase, has_l ? rank - 1 : rank);
+    const unsigned base_u = map_shared(sbase, has_u ? rank + CX : rank);
+    const unsigned base_d = map_shared(sbase, has_d ? rank - CX : rank);
+
+    int gxs[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) gxs[b] = wrap_x(x0 + tx + 32 * b, nx, wide);
+
+    // ---- load this CTA's part: g into buffer 0, coefficients or (FIRST)
+    // phi with its ring and q into planes 0 and 1 of buffer 1 ----
+    T cA[NA][NB], cBx[NA][NB], cBy[NA][NB];
+    T *const sphi = sg + 4 * PL, *const sq = sg + 5 * PL;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const int ly = ty + BY * a, gy = y0 + ly;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) cA[a][b] = cBx[a][b] = cBy[a][b] = T(0);
+        if (gy < 0 || gy >= ny) continue;
+        const long long row = (long long)gy * nx;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const long long k = row + gxs[b];
+            const int li = (ly + 1) * PW + tx + 32 * b + 1;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) cp_async(sg + i * PL + li, src + i * nn + k);
+            if (FIRST) {
+                cp_async(sq + li, q + k);
+            } else {
+                cA[a][b] = coef[k];
+                cBx[a][b] = coef[nn + k];
+                cBy[a][b] = coef[2 * nn + k];
+            }
+        }
+    }
+    if (FIRST) {
+        for (int e = tx + 32 * ty; e < PL; e += 32 * BY) {
+            const int py = e / PW, px = e - py * PW;
+            const int gy = y0 - 1 + py;
+            if (gy < -1 || gy > ny) continue;
+            const int gx = wrap_x(x0 - 1 + px, nx, wide);
+            cp_async(sphi + e, phig + (long long)(gy + 1) * nx + gx);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (FIRST) {
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            const int ly = ty + BY * a, gy = y0 + ly;
+            if (gy < 0 || gy >= ny) continue;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const int li = (ly + 1) * PW + tx + 32 * b + 1;
+                const T *r1 = sphi + li, *r0 = r1 - PW, *r2 = r1 + PW;
+                const T phi = r1[0];
+                const T gxs_ = (r1[1] - r1[-1]) * T(1.0 / 3.0) +
+                               ((r2[1] - r2[-1]) + (r0[1] - r0[-1])) * T(1.0 / 12.0);
+                const T gys_ = (r2[0] - r0[0]) * T(1.0 / 3.0) +
+                               ((r2[1] + r2[-1]) - (r0[1] + r0[-1])) * T(1.0 / 12.0);
+                const T inv = T(1) / (T(1) + P.er1 * phi);
+                const T bb = P.src_norm * P.er1 * inv / P.tau_g;
+                cA[a][b] = P.src_norm * P.Kq * sq[li] * inv * T(1.0 / 3.0);
+                cBx[a][b] = bb * gxs_;
+                cBy[a][b] = bb * gys_;
+            }
+        }
+    }
+    // every CTA has loaded (and read its staging) before any sweep writes into it
+    cluster_sync();
+
+    T psi_before[NA][NB];
+    const T k1 = T(0.5) * (T(1) - P.s_g);
+    const T kf = T(0.5) * (T(1) - P.s_free_g);
+    const T ke = T(0.25) * P.s_free_g;
+    const T wG = P.wG;
+    const bool interior = y0 >= 0 && y0 + RH <= ny;
+    int li[NA][NB];
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) li[a][b] = (ty + BY * a + 1) * PW + tx + 32 * b + 1;
+    // pad cells that hold populations leaving this CTA's part, and where they
+    // land in the neighbour: column RW of g1 -> column 0 of the right one,
+    // column -1 of g3 -> column RW - 1 of the left one, row RH of g2 -> row 0
+    // of the upper one, row -1 of g4 -> row RH - 1 of the lower one
+    const int tid = tx + 32 * ty;
+#pragma unroll 1
+    for (int s = 0; s < NSW; ++s) {
+        const T *gc = sg + (s & 1) * 4 * PL;
+        T *gn = sg + ((s + 1) & 1) * 4 * PL;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            const int gy = y0 + ty + BY * a;
+            if (!interior && (gy < 0 || gy >= ny)) continue;
+            const bool top = !interior && gy + 1 >= ny, bot = !interior && gy == 0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const int l = li[a][b];
+                const T g1 = gc[l], g2 = gc[PL + l], g3 = gc[2 * PL + l], g4 = gc[3 * PL + l];
+                const T m1 = g1 - g3, m2 = g2 - g4, m3 = g1 + g3, m4 = g2 + g4;
+                if (RESID) psi_before[a][b] = T(1.5) * (m3 + m4);
+                const T X6 = T(0.5) * (cA[a][b] - cBx[a][b] * m1 - cBy[a][b] * m2);
+                const T e = ke * (m3 + m4) + X6;
+                const T h3 = kf * m3 + e, h4 = kf * m4 + e;
+                const T h1 = k1 * m1, h2 = k1 * m2;
+                const T p2 = h4 + h2, p4 = h4 - h2;
+                gn[l + 1] = h3 + h1;
+                gn[2 * PL + l - 1] = h3 - h1;
+                if (top) gn[3 * PL + l] = -p2 + wG;     // cathode: ABB to psi_c
+                else gn[PL + l + PW] = p2 - wG;
+                if (bot) gn[PL + l] = -p4 - wG;         // anode: ABB to psi_a
+                else gn[3 * PL + l - PW] = p4 + wG;
+            }
+        }
+        __syncthreads();
+        // hand the pad cells to the neighbours (their copies of these cells
+        // are not written by their own pushes)
+        const unsigned nb_off = (unsigned)(((s + 1) & 1) * 4 * PL * (int)sizeof(T));
+        if (tid < RW) {
+            const int c = tid + 1;
+            if (has_u) st_cluster(base_u + nb_off + (unsigned)((PL + PW + c) * (int)sizeof(T)), gn[PL + (RH + 1) * PW + c]);
+            if (has_d) st_cluster(base_d + nb_off + (unsigned)((3 * PL + RH * PW + c) * (int)sizeof(T)), gn[3 * PL + c]);
+        } else if (tid < RW + RH) {
+            const int r = tid - RW + 1;
+            if (has_r) st_cluster(base_r + nb_off + (unsigned)((r * PW + 1) * (int)sizeof(T)), gn[r * PW + RW + 1]);
+            if (has_l) st_cluster(base_l + nb_off + (unsigned)((2 * PL + r * PW + RW) * (int)sizeof(T)), gn[2 * PL + r * PW]);
+        }
+        cluster_sync();
+    }
+
+    // ---- store the output tile (and, FIRST, its coefficients) ----
+    const T *gf = sg + (NSW & 1) * 4 * PL;
+    T red[2] = {T(0), T(0)};
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const int ly = ty + BY * a, gy = y0 + ly, Y = cy * RH + ly;
+        if (Y < H || Y >= CH - H || gy >= ny) continue;
+        const long long row = (long long)gy * nx;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int lx = tx + 32 * b, gx = x0 + lx, X = cx * RW + lx;
+            if (X < H || X >= CW - H || gx >= nx) continue;
+            const int l = (ly + 1) * PW + lx + 1;
+            const long long k = row + gx;
+            const T g1 = gf[l], g2 = gf[PL + l], g3 = gf[2 * PL + l], g4 = gf[3 * PL + l];
+            dst[k] = g1;
+            dst[nn + k] = g2;
+            dst[2 * nn + k] = g3;
+            dst[3 * nn + k] = g4;
+            if (FIRST) {
+                coef[k] = cA[a][b];
+                coef[nn + k] = cBx[a][b];
+                coef[2 * nn + k] = cBy[a][b];
+            }
+            if (RESID) {
+                const T psit = T(1.5) * ((g1 + g3) + (g2 + g4));
+                const T d = psit - psi_before[a][b];
+                const T ps = psit + psi_lin(P, gy);
+                red[0] += d * d;
+                red[1] += ps * ps;
+            }
+        }
+    }
+    if (RESID) block_sum_store<T, 2>(red, part);
+}
+
 // Converge mode, after sweep j (one block of 256): r_{j-1} from the partials
 // of sweep j, then the stop rule k >= kmin and (r_k < tol or k = kmax).
 static __global__ void __launch_bounds__(256) k_sweep_decide(const double *__restrict__ part, long long nb,

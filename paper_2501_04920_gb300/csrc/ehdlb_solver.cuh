@@ -359,7 +359,9 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     // blocks per SM the registers are sized for) and the largest number of
     // sweeps one launch fuses.
     struct TbShape { int rw, rh, by, minb; };
-    static constexpr int TB_NSHAPES = sizeof(T) == 4 ? 2 : 1;
+    // float: shape 2 is the cluster kernel (k_sweep_cl), 2 x 4 CTAs of 64 x 32
+    static constexpr int TB_NSHAPES = sizeof(T) == 4 ? 3 : 1;
+    static constexpr int CL_X = 2, CL_Y = 4, CL_BY = 16;
     static constexpr TbShape tb_shape(int i)
     {
         return sizeof(T) == 4 ? (i == 1 ? TbShape{64, 32, 8, 4} : TbShape{64, 32, 16, 3}) : TbShape{64, 16, 16, 2};
@@ -368,6 +370,10 @@ template <typename T, typename S = T> class Solver : public SolverBase {
 
     static dim3 tb_grid(int nsw, int shape, int nx, int ny)
     {
+        if (sizeof(T) == 4 && shape == 2) {
+            const int tx = CL_X * 64 - 2 * nsw, ty = CL_Y * 32 - 2 * nsw;
+            return dim3(CL_X * ((nx + tx - 1) / tx), CL_Y * ((ny + ty - 1) / ty));
+        }
         const TbShape sh = tb_shape(shape);
         const int tx = sh.rw - 2 * nsw, ty = sh.rh - 2 * nsw;
         return dim3((nx + tx - 1) / tx, (ny + ty - 1) / ty);
@@ -400,13 +406,31 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         return e;
     }
 
+    template <int NSW, bool FIRST, bool RESID> cudaError_t cl_attr2()
+    {
+        return cudaFuncSetAttribute(k_sweep_cl<T, NSW, CL_X, CL_Y, CL_BY, FIRST, RESID>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb_cl_smem_bytes<T>());
+    }
+
     template <int NSW> cudaError_t tb_attr()
     {
         cudaError_t e = tb_attr1<NSW, 0>();
         if constexpr (TB_NSHAPES > 1) {
             if (e == cudaSuccess) e = tb_attr1<NSW, 1>();
+            if (e == cudaSuccess) e = cl_attr2<NSW, false, false>();
+            if (e == cudaSuccess) e = cl_attr2<NSW, false, true>();
+            if (e == cudaSuccess) e = cl_attr2<NSW, true, false>();
+            if (e == cudaSuccess) e = cl_attr2<NSW, true, true>();
         }
         return e;
+    }
+
+    template <int NSW, bool FIRST, bool RESID> void cl_launch2()
+    {
+        const dim3 g = tb_grid(NSW, 2, nx_, ny_);
+        k_sweep_cl<T, NSW, CL_X, CL_Y, CL_BY, FIRST, RESID>
+            <<<g, dim3(32, CL_BY), tb_cl_smem_bytes<T>(), stream_>>>(dp_, g_[0], g_[1], phig_, q_, coef_, part2_,
+                                                                     ctl_, tb_m_);
     }
 
     template <int NSW, int SH, bool FIRST, bool RESID> void tb_launch2()
@@ -435,8 +459,19 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         tb_m_ = m;
         const bool first = m == 0;
         if constexpr (TB_NSHAPES > 1) {
-            if (tb_shape_ == 1) tb_launch1<NSW, 1>(first, resid);
-            else tb_launch1<NSW, 0>(first, resid);
+            if (tb_shape_ == 2) {
+                if (first) {
+                    if (resid) cl_launch2<NSW, true, true>();
+                    else cl_launch2<NSW, true, false>();
+                } else {
+                    if (resid) cl_launch2<NSW, false, true>();
+                    else cl_launch2<NSW, false, false>();
+                }
+            } else if (tb_shape_ == 1) {
+                tb_launch1<NSW, 1>(first, resid);
+            } else {
+                tb_launch1<NSW, 0>(first, resid);
+            }
         } else {
             tb_launch1<NSW, 0>(first, resid);
         }
