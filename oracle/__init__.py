@@ -44,6 +44,7 @@ _PARAM_FIELDS = [
     ("init_psi_zero", C.c_int),
     ("freeze_E", C.c_int), ("E_frozen_x", C.c_double), ("E_frozen_y", C.c_double),
     ("s_free", C.c_double), ("bgk", C.c_int),
+    ("side_walls", C.c_int),
 ]
 
 
@@ -59,7 +60,7 @@ DEFAULTS = dict(
     Kq=5.6893 / 64**2, vartheta=0.3, psi_src_literal=0, psi_anode=1.0, psi_cathode=0.0,
     sweeps_min=1, sweeps_max=200, sweep_tol=1e-8, init_sweeps_max=100000,
     init_sweeps_fixed=-1, init_psi_zero=0, freeze_E=0, E_frozen_x=0.0,
-    E_frozen_y=0.0, s_free=1.0, bgk=0,
+    E_frozen_y=0.0, s_free=1.0, bgk=0, side_walls=0,
 )
 
 
@@ -110,6 +111,7 @@ def lib():
         L.orc_onsager.restype = C.c_double
         L.orc_reaction.argtypes = [C.c_double] * 5 + [dp, dp, dp]
         L.orc_stencil.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp]
+        L.orc_stencil_walls.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, dp]
         L.orc_params_from_physical.argtypes = [C.POINTER(OrcParams), C.c_int,
                                                C.c_int] + [C.c_double] * 4
         L.orc_deformation.argtypes = [C.c_int, C.c_int, dp]
@@ -254,11 +256,14 @@ def reaction(sum_p, sum_n, k_d, k_r, F):
     return cp.value, cm.value, R.value
 
 
-def stencil(chi: np.ndarray):
+def stencil(chi: np.ndarray, side_walls: int = 0):
     chi = np.ascontiguousarray(chi, dtype=np.float64)
     ny, nx = chi.shape
     gx = np.zeros_like(chi); gy = np.zeros_like(chi); lap = np.zeros_like(chi)
-    lib().orc_stencil(nx, ny, _dp(chi), _dp(gx), _dp(gy), _dp(lap))
+    if side_walls:
+        lib().orc_stencil_walls(nx, ny, 1, _dp(chi), _dp(gx), _dp(gy), _dp(lap))
+    else:
+        lib().orc_stencil(nx, ny, _dp(chi), _dp(gx), _dp(gy), _dp(lap))
     return gx, gy, lap
 
 

@@ -314,6 +314,12 @@ static int wrapx(const orc_ctx *c, int x)
 void orc_stencil(int nx, int ny, const double *chi, double *gx, double *gy,
                  double *lap)
 {
+    orc_stencil_walls(nx, ny, 0, chi, gx, gy, lap);
+}
+
+void orc_stencil_walls(int nx, int ny, int side_walls, const double *chi, double *gx,
+                       double *gy, double *lap)
+{
 #pragma omp parallel for
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
@@ -321,6 +327,11 @@ void orc_stencil(int nx, int ny, const double *chi, double *gx, double *gy,
             double sx = 0.0, sy = 0.0, sl = 0.0;
             for (int i = 1; i < 9; ++i) {
                 int xn = ((x + cx9[i]) % nx + nx) % nx;
+                if (side_walls) {            /* mirror ghost column */
+                    xn = x + cx9[i];
+                    if (xn < 0) xn = 0;
+                    if (xn >= nx) xn = nx - 1;
+                }
                 int yn = y + cy9[i];
                 if (yn < 0) yn = 0;          /* mirror ghost row: zero normal */
                 if (yn >= ny) yn = ny - 1;   /* gradient at the half-way wall  */
@@ -399,13 +410,14 @@ void orc_destroy(orc_ctx *c)
 /* Pull-stream a D2Q9 field; a link that crosses a wall bounces back. */
 static void stream9_bounce(const orc_ctx *c, const double *post, double *out)
 {
+    const int walls = c->P.side_walls;
 #pragma omp parallel for
     for (int y = 0; y < c->ny; ++y)
         for (int x = 0; x < c->nx; ++x) {
             long k = idx(c, x, y);
             for (int i = 0; i < 9; ++i) {
-                int sy = y - cy9[i];
-                if (sy < 0 || sy >= c->ny)
+                int sy = y - cy9[i], sx = x - cx9[i];
+                if (sy < 0 || sy >= c->ny || (walls && (sx < 0 || sx >= c->nx)))
                     out[k * 9 + i] = post[k * 9 + opp9[i]];
                 else
                     out[k * 9 + i] = post[idx(c, wrapx(c, x - cx9[i]), sy) * 9 + i];
@@ -415,18 +427,22 @@ static void stream9_bounce(const orc_ctx *c, const double *post, double *out)
 
 /* Pull-stream a D2Q5 field.  A link crossing the bottom (top) wall takes
  * anti-bounce-back  out_i = -post_opp(i) + 2 w_i v_wall  when mode = 0, or
- * plain bounce-back out_i = post_opp(i) when mode = 1. */
+ * plain bounce-back out_i = post_opp(i) when mode = 1.  A link crossing a
+ * side wall bounces back (zero normal gradient, Eq. 64). */
 static void stream5(const orc_ctx *c, const double *post, double *out,
                     int mode_bot, const double *vbot, int mode_top,
                     const double *vtop)
 {
+    const int walls = c->P.side_walls;
 #pragma omp parallel for
     for (int y = 0; y < c->ny; ++y)
         for (int x = 0; x < c->nx; ++x) {
             long k = idx(c, x, y);
             for (int i = 0; i < 5; ++i) {
-                int sy = y - cy5[i];
-                if (sy < 0 || sy >= c->ny) {
+                int sy = y - cy5[i], sx = x - cx5[i];
+                if (walls && (sx < 0 || sx >= c->nx)) {
+                    out[k * 5 + i] = post[k * 5 + opp5[i]];
+                } else if (sy < 0 || sy >= c->ny) {
                     int bottom = sy < 0;
                     int mode = bottom ? mode_bot : mode_top;
                     double v = bottom ? vbot[x] : vtop[x];
@@ -544,7 +560,7 @@ static void macro_phi_q(orc_ctx *c)
         }
         c->q[k] = sp - sn;
     }
-    orc_stencil(c->nx, c->ny, c->phi, c->gpx, c->gpy, c->lap);
+    orc_stencil_walls(c->nx, c->ny, c->P.side_walls, c->phi, c->gpx, c->gpy, c->lap);
 }
 
 static double n_eq_of(const orc_params *P, double Emag)

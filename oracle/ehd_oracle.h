@@ -71,6 +71,12 @@ typedef struct orc_params {
     /* collision */
     double s_free;       /* the free relaxation rates (1.0 in Sec. 6) */
     int bgk;             /* 1: every rate equals the hydrodynamic one */
+    /* geometry */
+    int side_walls;      /* 0: periodic x; 1: solid walls half-way left of
+                            x = 0 and right of x = nx - 1 with the "other
+                            boundaries" rules of Eq. 64: u = 0, zero normal
+                            gradient of c+-, psi and phi (bounce-back of f, h,
+                            p, n and g; mirrored ghost columns in Eq. 59) */
 } orc_params;
 
 /* Snapshot fields, row-major [field][ny][nx]. */
@@ -119,6 +125,10 @@ void orc_reaction(double sum_p, double sum_n, double k_d, double k_r, double F,
 /* Isotropic gradient and Laplacian (Eq. 59), mirrored ghost rows, x periodic. */
 void orc_stencil(int nx, int ny, const double *chi, double *gx, double *gy,
                  double *lap);
+/* The same with side walls (side_walls = 1): ghost columns mirror the
+ * first and last column, as the ghost rows do. */
+void orc_stencil_walls(int nx, int ny, int side_walls, const double *chi, double *gx,
+                       double *gy, double *lap);
 /* Physical -> lattice mapping of Sec. 3 (see the definition for the steps). */
 void orc_params_from_physical(orc_params *P, int nx, int ny, double d_mm,
                               double dpsi_kV, double eps_r, double mu_r);

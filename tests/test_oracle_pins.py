@@ -515,3 +515,70 @@ def test_deformation_factor_of_ellipses():
         r = np.sqrt(((x - 47.5) / b) ** 2 + ((y - 47.5) / a) ** 2)
         phi = 0.5 * (1 + np.tanh(2 * (1 - r) * min(a, b) / 4.0))
         assert abs(O.deformation(phi) - (a - b) / (a + b)) < 2e-3
+
+
+# ---- side walls (Eq. 64, "the other boundaries") ------------------------------------
+
+def test_side_wall_stencil_mirrors_the_ghost_columns():
+    # Eq. 59 with ghost columns equal to the first / last column: exact at a
+    # wall for a quadratic that is even about that wall (x = -1/2, nx - 1/2)
+    nx, ny = 12, 6
+    x = np.arange(nx)[None, :] * np.ones((ny, 1))
+    for chi, col, d1, d2 in (((x + 0.5) ** 2, 0, 1.0, 2.0),
+                             ((x - nx + 0.5) ** 2, nx - 1, -1.0, 2.0)):
+        gx, gy, lap = O.stencil(chi, side_walls=1)
+        np.testing.assert_allclose(gx[:, col], d1, atol=1e-12)
+        np.testing.assert_allclose(lap[:, col], d2, atol=1e-12)
+        np.testing.assert_allclose(gy, 0.0, atol=1e-12)
+    # the periodic stencil sees the other side of the lattice instead
+    gx, _, _ = O.stencil((x + 0.5) ** 2, side_walls=0)
+    assert abs(gx[0, 0] - 1.0) > 1.0
+
+
+def test_side_walls_potential_equals_the_mirrored_periodic_lattice():
+    # D2Q5 bounce-back at a side wall is a mirror for the potential: a
+    # droplet centred on the right wall of an nx-wide walled lattice has the
+    # initial potential of the 2 nx-wide periodic lattice whose droplet sits
+    # at the same place (it is even about x = -1/2 and x = nx - 1/2)
+    nx, ny = 12, 16
+    base = dict(QUIET, freeze_E=0, psi_anode=1.0, psi_cathode=0.0, eps_r=4.0,
+                R=5.0, yc=(ny - 1) / 2, xc=nx - 0.5, init_sweeps_fixed=400)
+    walled = O.Oracle(nx, ny, dict(base, side_walls=1)).fields()
+    periodic = O.Oracle(2 * nx, ny, dict(base, side_walls=0)).fields()
+    for k in ("psi", "Ex", "Ey", "phi"):
+        np.testing.assert_allclose(walled[k], periodic[k][:, :nx], rtol=0, atol=1e-13, err_msg=k)
+    # and it is not the periodic nx-wide answer
+    per_nx = O.Oracle(nx, ny, dict(base, side_walls=0)).fields()
+    assert np.max(np.abs(per_nx["Ex"] - walled["Ex"])) > 1e-4
+
+
+def test_side_walls_and_electrode_walls_act_alike_on_the_fluid():
+    # with no field and no ions, f and h see four bounce-back walls: a
+    # droplet on the diagonal of a square box evolves symmetric under x <-> y
+    n = 24
+    o = O.Oracle(n, n, dict(QUIET, side_walls=1, xc=8.3, yc=8.3, R=5.0, sigma=0.02))
+    o.step(60)
+    f = o.fields()
+    scale = np.max(np.hypot(f["ux"], f["uy"]))
+    assert scale > 1e-6                         # the droplet does move
+    np.testing.assert_allclose(f["phi"], f["phi"].T, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(f["ux"], f["uy"].T, rtol=0, atol=1e-13 * max(1.0, scale))
+    np.testing.assert_allclose(f["p"], f["p"].T, rtol=0, atol=1e-13)
+
+
+def test_side_walls_keep_a_centred_case_mirror_symmetric_and_conserve_phi():
+    nx, ny = 20, 24
+    prm = dict(side_walls=1, xc=(nx - 1) / 2, yc=9.0, R=5.0, Kq=5.6893 / ny**2,
+               eps_r=3.0, mu_r=2.0, sweeps_min=40, sweeps_max=40, init_sweeps_fixed=300)
+    o = O.Oracle(nx, ny, prm)
+    s0 = o.sum_phi()
+    o.step(80)
+    f = o.fields()
+    assert abs(o.sum_phi() - s0) <= 1e-13 * s0
+    for k, sign in (("phi", 1), ("psi", 1), ("q", 1), ("cp", 1), ("uy", 1), ("Ey", 1),
+                    ("ux", -1), ("Ex", -1)):
+        a = f[k]
+        np.testing.assert_allclose(a, sign * a[:, ::-1], rtol=0,
+                                   atol=1e-12 * max(1e-12, np.max(np.abs(a))), err_msg=k)
+    # no flux through the side walls: the wall columns do not leak ions
+    assert np.max(np.abs(f["ux"])) > 0
