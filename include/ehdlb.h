@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define EHDLB_ABI_VERSION 1
+#define EHDLB_ABI_VERSION 2
 
 typedef struct ehdlb_ctx ehdlb_ctx;
 
@@ -127,6 +127,13 @@ typedef struct ehdlb_params {
     /* collision */
     double s_free;       /* the free MRT rates, in (0, 2); 1.0 in Sec. 6 */
     int bgk;             /* 1: all rates equal the hydrodynamic one */
+    /* geometry */
+    int side_walls;      /* 0: periodic x (default); 1: solid walls half-way
+                            left of x = 0 and right of x = nx - 1 with the
+                            "other boundaries" rules of Eq. 64 (u = 0, zero
+                            normal gradient of c+-, psi and phi): bounce-back
+                            of f, h, p, n and g, mirrored ghost columns in
+                            Eq. 59.  Potential sweeps then run one per launch. */
 } ehdlb_params;
 
 /* Counters of one ehdlb_step() call. */

@@ -66,6 +66,7 @@ std::string validate(const ehdlb_params *p)
     if (p->init_sweeps_fixed > 100000000) return "init_sweeps_fixed out of range";
     if (!(p->s_free > 0.0 && p->s_free < 2.0)) return "s_free must lie in (0, 2)";
     if (!(p->c_init_scale >= 0.0) || !(p->c0 >= 0.0)) return "initial concentrations must be >= 0";
+    if (p->side_walls != 0 && p->side_walls != 1) return "side_walls must be 0 or 1";
     return "";
 }
 
@@ -93,6 +94,7 @@ int ehdlb_params_default(ehdlb_params *p)
     p->init_sweeps_max = 100000; p->init_sweeps_fixed = -1; p->init_psi_zero = 0;
     p->freeze_E = 0; p->E_frozen_x = 0.0; p->E_frozen_y = 0.0;
     p->s_free = 1.0; p->bgk = 0;
+    p->side_walls = 0;
     return EHDLB_OK;
 }
 

@@ -66,6 +66,7 @@ template <typename T> struct DevP {
     int nx, ny;
     long long nn;
     int onsager_form, ion_bc, einstein_D, ion_L_term, bgk, freeze_E;
+    int side_walls;                // 1: walls left of x = 0 and right of x = nx - 1 (Eq. 64)
     T tau_g, s_g, s_free_g;        // potential rates
     T src_norm;                    // vartheta (Eq. 44) times 1 or 1/(1 - w0)
     T Kq, er1;                     // Kq, eps_r - 1
@@ -221,6 +222,16 @@ template <typename T> __device__ __forceinline__ T onsager(T b, int form)
 __device__ __forceinline__ int wrapx(int x, int nx)
 {
     return x < 0 ? x + nx : (x >= nx ? x - nx : x);
+}
+
+// Column of the x neighbour at x + dx (|dx| = 1) for the stencils of
+// Eq. 59: periodic, or with side walls the mirrored ghost column (the node
+// itself).
+__device__ __forceinline__ int nbx(int x, int dx, int nx, int walls)
+{
+    const int v = x + dx;
+    if (walls) return v < 0 ? 0 : (v >= nx ? nx - 1 : v);
+    return v < 0 ? v + nx : (v >= nx ? v - nx : v);
 }
 
 template <typename T> __device__ __forceinline__ T psi_lin(const DevP<T> &P, int y)
@@ -415,7 +426,7 @@ __global__ void __launch_bounds__(256) k_sweep(const DevP<T> P, S *__restrict__ 
         }
         if (WRITE_PSI) psi_prev[k] = psit;
         // grad phi by Eq. 59 (only grad eps enters the potential)
-        const int xm = wrapx(x - 1, nx), xp = wrapx(x + 1, nx);
+        const int xm = nbx(x, -1, nx, P.side_walls), xp = nbx(x, 1, nx, P.side_walls);
         const T *r0 = phig + (long long)y * nx, *r1 = r0 + nx, *r2 = r1 + nx;
         const T phi = r1[x];
         const T gx = (r1[xp] - r1[xm]) * T(1.0 / 3.0) +
@@ -434,8 +445,11 @@ __global__ void __launch_bounds__(256) k_sweep(const DevP<T> P, S *__restrict__ 
         const T n4 = m4 - P.s_free_g * (m4 - eq) + X3;
         const T o1 = T(0.5) * (n3 + n1), o3 = T(0.5) * (n3 - n1);
         const T o2 = T(0.5) * (n4 + n2), o4 = T(0.5) * (n4 - n2);
-        sts(dst + (long long)y * nx + xp, o1, P.sc_g);
-        sts(dst + 2 * nn + (long long)y * nx + xm, o3, P.sc_g);
+        // side walls: bounce-back (zero normal gradient of psi, Eq. 64)
+        if (P.side_walls && x == nx - 1) sts(dst + 2 * nn + k, o1, P.sc_g);
+        else sts(dst + (long long)y * nx + wrapx(x + 1, nx), o1, P.sc_g);
+        if (P.side_walls && x == 0) sts(dst + k, o3, P.sc_g);
+        else sts(dst + 2 * nn + (long long)y * nx + wrapx(x - 1, nx), o3, P.sc_g);
         if (y + 1 < P.ny) sts(dst + nn + k + nx, o2 - P.wG, P.sc_g);
         else sts(dst + 3 * nn + k, -o2 + P.wG, P.sc_g);          // cathode: ABB to psi_c
         if (y > 0) sts(dst + 3 * nn + k - nx, o4 + P.wG, P.sc_g);
@@ -1064,8 +1078,8 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<S> 
     int xm = 0, xp = 0;
     T dphi = T(0), phir = T(0), phi = T(0), gx = T(0), gy = T(0), lapd = T(0);
     if (inside) {
-        xm = wrapx(x - 1, nx);
-        xp = wrapx(x + 1, nx);
+        xm = nbx(x, -1, nx, P.side_walls);
+        xp = nbx(x, 1, nx, P.side_walls);
         const int ki = y * nx + x;   // in-plane index (nx ny < 2^31)
         const T *r1 = Rf.dphig + nx + ki, *r0 = r1 - nx, *r2 = r1 + nx;
         xm -= x;   // column offsets from here on
@@ -1087,12 +1101,15 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<S> 
         // columns left / at / right; a link through a wall bounces back to
         // the node itself
         const bool top = y + 1 >= ny, bot = y == 0;
+        const bool lwall = P.side_walls && x == 0, rwall = P.side_walls && x == nx - 1;
         const int rowC = y * nx + x, rowN = top ? rowC : rowC + nx, rowS = bot ? rowC : rowC - nx;
         auto dest = [&](int cx, int cy) -> int {
             const int col = cx < 0 ? xm : (cx > 0 ? xp : 0);
             return cy > 0 ? rowN + col : (cy < 0 ? rowS + col : rowC + col);
         };
-        auto bounced = [&](int cy) -> bool { return cy > 0 ? top : (cy < 0 ? bot : false); };
+        auto bounced = [&](int cx, int cy) -> bool {
+            return (cy > 0 && top) || (cy < 0 && bot) || (cx > 0 && rwall) || (cx < 0 && lwall);
+        };
         const T rho = T(1) + P.rho1 * phi;
         const T inv_rho = T(1) / rho;
         const T mup = P.mu_v * (T(1) + P.mu1 * phi);
@@ -1202,7 +1219,7 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<S> 
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
                 const T v = fv[i] - dl[i];
-                if (bounced(cy9(i))) sts_sr(dst.f + (opp9(i) - 1) * nn + rowC, v, P.sc_f, rng);
+                if (bounced(cx9(i), cy9(i))) sts_sr(dst.f + (opp9(i) - 1) * nn + rowC, v, P.sc_f, rng);
                 else sts_sr(dst.f + (i - 1) * nn + dest(cx9(i), cy9(i)), v, P.sc_f, rng);
             }
         }
@@ -1261,7 +1278,7 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<S> 
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const T v = hv[i] - dl[i];
-                if (bounced(cy9(i))) {
+                if (bounced(cx9(i), cy9(i))) {
                     sts_sr(dst.h + opp9(i) * nn + rowC, v, P.sc_h, rng);
                 } else {
                     const int o = dest(cx9(i), cy9(i));
@@ -1335,10 +1352,13 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<S> 
             }
             sts_sr(dst.p + rowC, po[0], P.sc_c, rng);
             sts_sr(dst.n + rowC, no[0], P.sc_c, rng);
-            sts_sr(dst.p + nn + rowC + xp, po[1], P.sc_c, rng);
-            sts_sr(dst.n + nn + rowC + xp, no[1], P.sc_c, rng);
-            sts_sr(dst.p + 3 * nn + rowC + xm, po[3], P.sc_c, rng);
-            sts_sr(dst.n + 3 * nn + rowC + xm, no[3], P.sc_c, rng);
+            // directions 1 and 3 bounce back at the side walls (zero gradient)
+            const long long o1 = rwall ? 3 * nn + rowC : nn + rowC + xp;
+            const long long o3 = lwall ? nn + rowC : 3 * nn + rowC + xm;
+            sts_sr(dst.p + o1, po[1], P.sc_c, rng);
+            sts_sr(dst.n + o1, no[1], P.sc_c, rng);
+            sts_sr(dst.p + o3, po[3], P.sc_c, rng);
+            sts_sr(dst.n + o3, no[3], P.sc_c, rng);
             // direction 2 lands in plane 2 of the row above or, bounced, in plane 4 here
             const long long o2 = top ? 4 * nn + rowC : 2 * nn + rowN;
             const long long o4 = bot ? 2 * nn + rowC : 4 * nn + rowS;
@@ -1456,7 +1476,7 @@ __global__ void __launch_bounds__(256) k_init_ref(const DevP<T> P, PhiRef<T> Rf,
     if (x >= P.nx || y >= P.ny) return;
     const int nx = P.nx;
     const long long k = (long long)y * nx + x;
-    const int xm = wrapx(x - 1, nx), xp = wrapx(x + 1, nx);
+    const int xm = nbx(x, -1, nx, P.side_walls), xp = nbx(x, 1, nx, P.side_walls);
     const T *r0 = Rf.phir + (long long)y * nx, *r1 = r0 + nx, *r2 = r1 + nx;
     const double c = r1[x];
     const double E = r1[xp], W = r1[xm], N = r2[x], S = r0[x];

@@ -164,6 +164,7 @@ extern "C" int ehdlb_potential_noalloc(int nx, int ny, const ehdlb_params *p, co
     d.ny = ny;
     d.nn = nn;
     d.bgk = p->bgk;
+    d.side_walls = p->side_walls;
     const double tau_g = 0.5 + 3.0 * p->vartheta;
     d.tau_g = tau_g;
     d.s_g = 1.0 / tau_g;

@@ -290,6 +290,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         d.ion_L_term = p.ion_L_term;
         d.bgk = p.bgk;
         d.freeze_E = p.freeze_E;
+        d.side_walls = p.side_walls;
         const double tau_g = 0.5 + 3.0 * p.vartheta;  // Eq. 47
         d.tau_g = (T)tau_g;
         d.s_g = (T)(1.0 / tau_g);
@@ -522,7 +523,9 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         const bool converge = fixedK < 0;
         if (!converge) kmin = kmax = fixedK;
         const int chunk = tb_chunk();
-        const bool fused = !converge && fixedK > 0 && chunk > 0;
+        // the fused sweep kernels implement the periodic x of the benchmark
+        // cases; with side walls every sweep is its own launch
+        const bool fused = !converge && fixedK > 0 && chunk > 0 && !P_.side_walls;
         const int nk = fused ? (fixedK + chunk - 1) / chunk : (converge ? 0 : fixedK);
         if (timing_) cudaEventRecord(events_[4 * s], stream_);
         launch_prep(par, fixedK, kmin, kmax, nk);

@@ -41,6 +41,7 @@ _PARAM_FIELDS = [
     ("init_psi_zero", C.c_int),
     ("freeze_E", C.c_int), ("E_frozen_x", C.c_double), ("E_frozen_y", C.c_double),
     ("s_free", C.c_double), ("bgk", C.c_int),
+    ("side_walls", C.c_int),
 ]
 
 
@@ -99,7 +100,7 @@ def lib():
         L.ehdlb_destroy.restype = None
         L.ehdlb_last_error.argtypes = [vp]
         L.ehdlb_last_error.restype = C.c_char_p
-        if L.ehdlb_version() != 1:
+        if L.ehdlb_version() != 2:
             raise ImportError("libehdlb ABI version mismatch")
         _lib = L
     return _lib

@@ -81,4 +81,4 @@ def test_null_and_bad_arguments_are_rejected_without_a_device():
     assert L.ehdlb_create(C.byref(h), 64, 64, 7, None) == ehdlb.EINVAL
     assert not h.value
     L.ehdlb_destroy(None)
-    assert ehdlb.ehdlb_version() == 1
+    assert ehdlb.ehdlb_version() == 2

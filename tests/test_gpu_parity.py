@@ -118,6 +118,8 @@ VARIANTS = {
     "slab": dict(init_shape=1, R=2.5),
     "wide_interface": dict(W_init=6.0, eps_r=0.5, mu_r=5.0),
     "printed_normal": dict(nhat_eps=0.0),
+    "side_walls": dict(side_walls=1),
+    "side_walls_bgk_ionbc1": dict(side_walls=1, bgk=1, ion_bc=1),
 }
 
 
@@ -159,6 +161,16 @@ def test_fp64_small_lattices_every_switch(shape, name):
 def test_fp32_droplet256_matches_oracle():
     n, steps = 256, 100
     got, ref, *_ = run_pair(n, n, workloads.droplet(n), steps, precision=ehdlb.FP32)
+    err = field_errors(got, ref)
+    assert_close(err, FP32_TOL, keys=["phi", "psi", "q", "cp", "cm"])
+    assert_close(err, FP32_U_TOL, keys=["u"])
+
+
+def test_fp32_side_walls_match_oracle():
+    # the enclosure of Sec. 6: side walls (Eq. 64) instead of periodic x
+    n, steps = 128, 100
+    prm = dict(workloads.droplet(n), side_walls=1, xc=40.0)
+    got, ref, *_ = run_pair(n, n, prm, steps, precision=ehdlb.FP32)
     err = field_errors(got, ref)
     assert_close(err, FP32_TOL, keys=["phi", "psi", "q", "cp", "cm"])
     assert_close(err, FP32_U_TOL, keys=["u"])
