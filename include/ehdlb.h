@@ -43,7 +43,8 @@ typedef enum ehdlb_status {
     EHDLB_ENOMEM = -2,    /* device or host allocation failed */
     EHDLB_ECUDA = -3,     /* a CUDA call failed */
     EHDLB_EUNSTABLE = -4, /* NaN or Inf in the fields */
-    EHDLB_ESTATE = -5     /* call out of order (e.g. step before set_params) */
+    EHDLB_ESTATE = -5,    /* call out of order (e.g. step before set_params) */
+    EHDLB_EFULL = -6      /* a batch's device-memory budget has no room for the case */
 } ehdlb_status;
 
 typedef enum ehdlb_precision {
@@ -152,6 +153,19 @@ typedef struct ehdlb_stats {
     long long launches;       /* kernels launched by the call */
     long long sweep_launches; /* of which potential-sweep kernels */
 } ehdlb_stats;
+
+/* Counters of one ehdlb_batch_step() call. */
+typedef struct ehdlb_batch_stats {
+    long long steps;          /* batch steps (every case advances by this many) */
+    int cases;                /* cases stepped */
+    int unstable_cases;       /* cases with NaN or Inf in their fields */
+    double seconds;           /* wall time of the call */
+    double device_ms;         /* device time of the call (CUDA events) */
+    double mlups;             /* sum over cases of nx ny, times steps, / device time / 1e6 */
+    long long launches;       /* kernels (graph nodes included) launched by the call */
+    int sweeps_per_launch;    /* fused potential sweeps per launch used */
+    int tile_shape;           /* block shape of the fused sweep kernel used (0, 1) */
+} ehdlb_batch_stats;
 
 /* ABI version of the loaded library (EHDLB_ABI_VERSION). */
 int ehdlb_version(void);
@@ -272,11 +286,89 @@ int ehdlb_potential_noalloc(int nx, int ny, const ehdlb_params *p, const double 
                             const double *q, int nsweeps, double *psi, double *Ex,
                             double *Ey, double *residual, void *cuda_stream);
 
+/* Deformation factor D = (L - H) / (L + H) of Eq. 63 from the phi field of the
+ * last snapshot (the last step of the last ehdlb_step call): L is the extent
+ * of phi >= 1/2 along the field (y) on the line through the phi-weighted
+ * centroid, H the same across it (x); the line is sampled by bilinear
+ * interpolation of the nodes and each end is the crossing of 1/2 interpolated
+ * linearly between unit-spaced samples.  Computed on the device (one block).
+ * EHDLB_EINVAL on NULL, EHDLB_ESTATE before set_params. */
+int ehdlb_deformation(ehdlb_ctx *c, double *D);
+
 /* Free all device memory of the context (NULL is a no-op). */
 void ehdlb_destroy(ehdlb_ctx *c);
 
 /* Text of the last error on c (empty if none); valid until the next call. */
 const char *ehdlb_last_error(const ehdlb_ctx *c);
+
+/* ---- batches: many lattices stepped together -------------------------------------
+ * A batch owns one device arena of budget_bytes from which every case's
+ * buffers are carved (first fit); ehdlb_batch_add admits a case only if its
+ * footprint (ehdlb_batch_footprint) fits.  ehdlb_batch_step advances every
+ * case by nsteps time steps with one launch per kernel kind and step: the
+ * persistent kernels walk a device work-list of (case, tile) items and run
+ * the per-block code of the single-lattice kernels, so a case's fields are
+ * bit for bit those of the same case stepped alone with the same sweeps per
+ * launch and tile shape.  The steps of a call but the last replay a captured
+ * CUDA graph of one batch step.  All cases take the batch's fixed number of
+ * potential sweeps per step (params.sweeps_min = sweeps_max = sweeps); batch
+ * cases need nx a multiple of 8, periodic x (side_walls = 0), freeze_E = 0 and
+ * init_sweeps_fixed >= 0.  precision: EHDLB_FP32 or EHDLB_FP16S.  One host
+ * thread at a time per batch.  (A design of this build; the paper steps one
+ * lattice.) */
+typedef struct ehdlb_batch ehdlb_batch;
+
+/* Create a batch; cuda_stream: cudaStream_t or NULL (the batch makes one).
+ * EHDLB_EINVAL for a bad precision, sweeps < 1 or budget 0; EHDLB_ENOMEM if
+ * the arena cannot be allocated. */
+int ehdlb_batch_create(ehdlb_batch **out, int precision, size_t budget_bytes, int sweeps,
+                       void *cuda_stream);
+
+/* Device bytes one case of nx x ny nodes takes in a batch of that precision. */
+int ehdlb_batch_footprint(int precision, int nx, int ny, size_t *bytes);
+
+/* Add a case (set up as by ehdlb_set_params, state at t = 0); *id identifies
+ * it.  EHDLB_EFULL if the arena has no room; EHDLB_EINVAL for parameters a
+ * batch does not take (see above) or that ehdlb_set_params rejects. */
+int ehdlb_batch_add(ehdlb_batch *b, int nx, int ny, const ehdlb_params *p, int *id);
+
+/* Remove a case and return its memory to the arena. */
+int ehdlb_batch_remove(ehdlb_batch *b, int id);
+
+/* Advance every case by nsteps steps; the last step writes each case's
+ * snapshot.  st may be NULL.  EHDLB_EUNSTABLE if a case's fields hold NaN or
+ * Inf, EHDLB_ESTATE for an empty batch. */
+int ehdlb_batch_step(ehdlb_batch *b, int nsteps, ehdlb_batch_stats *st);
+
+/* Snapshot fields of case id, as ehdlb_get_fields (dst: host, FP64,
+ * [field][ny][nx] for the fields of mask in order). */
+int ehdlb_batch_get_fields(ehdlb_batch *b, int id, unsigned mask, double *dst, size_t dst_len);
+
+/* State of case id as ehdlb_get_state (35 doubles per node). */
+int ehdlb_batch_get_state(ehdlb_batch *b, int id, double *dst, size_t len);
+
+/* D of Eq. 63 (as ehdlb_deformation) of n cases from their last snapshots,
+ * all computed on the device in one launch. */
+int ehdlb_batch_deformation(ehdlb_batch *b, int n, const int *ids, double *D);
+
+/* Sweeps fused per launch (1..5; default 5), tile shape of the fused sweep
+ * kernel (0: 512 threads, default; 1: 256 threads) and whether steps replay
+ * a captured graph (default 1); -1 keeps a setting. */
+int ehdlb_batch_set_tuning(ehdlb_batch *b, int sweeps_per_launch, int tile_shape, int use_graphs);
+
+/* Autotuner: time `steps` batch steps of the current cases for every sweeps
+ * per launch in 3..5 and both tile shapes, keep the fastest and report it.
+ * The timed steps are real steps: the cases advance by 6 (steps + 1). */
+int ehdlb_batch_autotune(ehdlb_batch *b, int steps, int *sweeps_per_launch, int *tile_shape,
+                         double *ms_per_step);
+
+/* Number of cases, arena bytes in use and arena capacity (any may be NULL). */
+int ehdlb_batch_info(const ehdlb_batch *b, int *cases, size_t *bytes_in_use, size_t *capacity);
+
+const char *ehdlb_batch_last_error(const ehdlb_batch *b);
+
+/* Free the batch and all its device memory (NULL is a no-op). */
+void ehdlb_batch_destroy(ehdlb_batch *b);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libehdlb.so")
 
-SOURCES = ["ehdlb_api.cu", "solver_fp32.cu", "solver_fp64.cu", "solver_fp16s.cu", "ehdlb_noalloc.cu"]
+SOURCES = ["ehdlb_api.cu", "solver_fp32.cu", "solver_fp64.cu", "solver_fp16s.cu", "batch_fp32.cu",
+           "ehdlb_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          f"-I{INCLUDE}", f"-I{CSRC}"]

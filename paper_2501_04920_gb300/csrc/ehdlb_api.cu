@@ -18,6 +18,12 @@ struct ehdlb_ctx {
     std::string err;
 };
 
+struct ehdlb_batch {
+    ehdlb::BatchBase *batch = nullptr;
+    int precision = 0;
+    std::string err;
+};
+
 namespace {
 
 int fail(ehdlb_ctx *c, int status, const std::string &msg)
@@ -244,5 +250,133 @@ void ehdlb_destroy(ehdlb_ctx *c)
 }
 
 const char *ehdlb_last_error(const ehdlb_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int ehdlb_deformation(ehdlb_ctx *c, double *D)
+{
+    if (!c || !D) return EHDLB_EINVAL;
+    if (!c->has_params) return fail(c, EHDLB_ESTATE, "ehdlb_set_params first");
+    return c->solver->deformation(D, c->err);
+}
+
+// ---- batches ----------------------------------------------------------------
+
+static int bfail(ehdlb_batch *b, int status, const std::string &msg)
+{
+    if (b) b->err = msg;
+    return status;
+}
+
+int ehdlb_batch_create(ehdlb_batch **out, int precision, size_t budget_bytes, int sweeps, void *cuda_stream)
+{
+    if (!out) return EHDLB_EINVAL;
+    *out = nullptr;
+    if (precision != EHDLB_FP32 && precision != EHDLB_FP16S) return EHDLB_EINVAL;
+    if (sweeps < 1 || sweeps > 1000000 || budget_bytes == 0) return EHDLB_EINVAL;
+    ehdlb_batch *b = new (std::nothrow) ehdlb_batch;
+    if (!b) return EHDLB_ENOMEM;
+    b->precision = precision;
+    int status = EHDLB_OK;
+    std::string err;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    b->batch = precision == EHDLB_FP16S ? ehdlb::make_batch_fp16s(budget_bytes, sweeps, s, &status, err)
+                                        : ehdlb::make_batch_fp32(budget_bytes, sweeps, s, &status, err);
+    if (!b->batch) {
+        delete b;
+        return status != EHDLB_OK ? status : EHDLB_ENOMEM;
+    }
+    *out = b;
+    return EHDLB_OK;
+}
+
+int ehdlb_batch_footprint(int precision, int nx, int ny, size_t *bytes)
+{
+    if (!bytes || nx < 4 || ny < 4) return EHDLB_EINVAL;
+    if (precision == EHDLB_FP32) *bytes = ehdlb::footprint_fp32(nx, ny);
+    else if (precision == EHDLB_FP16S) *bytes = ehdlb::footprint_fp16s(nx, ny);
+    else return EHDLB_EINVAL;
+    return EHDLB_OK;
+}
+
+int ehdlb_batch_add(ehdlb_batch *b, int nx, int ny, const ehdlb_params *p, int *id)
+{
+    if (!b || !p || !id) return EHDLB_EINVAL;
+    if (nx < 4 || ny < 4 || (long long)nx * ny + 4LL * nx >= (1LL << 31)) return bfail(b, EHDLB_EINVAL, "bad lattice size");
+    const std::string why = validate(p);
+    if (!why.empty()) return bfail(b, EHDLB_EINVAL, why);
+    return b->batch->add(nx, ny, *p, id, b->err);
+}
+
+int ehdlb_batch_remove(ehdlb_batch *b, int id)
+{
+    if (!b) return EHDLB_EINVAL;
+    return b->batch->remove(id, b->err);
+}
+
+int ehdlb_batch_step(ehdlb_batch *b, int nsteps, ehdlb_batch_stats *st)
+{
+    if (!b || nsteps < 0) return EHDLB_EINVAL;
+    if (nsteps == 0) return EHDLB_OK;
+    return b->batch->step(nsteps, st, b->err);
+}
+
+int ehdlb_batch_get_fields(ehdlb_batch *b, int id, unsigned mask, double *dst, size_t dst_len)
+{
+    if (!b || !dst) return EHDLB_EINVAL;
+    int nx = 0, ny = 0;
+    if (b->batch->case_size(id, &nx, &ny) != EHDLB_OK) return bfail(b, EHDLB_EINVAL, "no such case");
+    if (mask == 0 || (mask >> EHDLB_NFIELDS) != 0) return bfail(b, EHDLB_EINVAL, "bad field mask");
+    int nf = 0;
+    for (int f = 0; f < EHDLB_NFIELDS; ++f) nf += (mask >> f) & 1;
+    if (dst_len < (size_t)nf * nx * ny) return bfail(b, EHDLB_EINVAL, "dst too small");
+    return b->batch->get_fields(id, mask, dst, b->err);
+}
+
+int ehdlb_batch_get_state(ehdlb_batch *b, int id, double *dst, size_t len)
+{
+    if (!b || !dst) return EHDLB_EINVAL;
+    int nx = 0, ny = 0;
+    if (b->batch->case_size(id, &nx, &ny) != EHDLB_OK) return bfail(b, EHDLB_EINVAL, "no such case");
+    if (len < (size_t)35 * nx * ny) return bfail(b, EHDLB_EINVAL, "dst too small");
+    return b->batch->get_state(id, dst, b->err);
+}
+
+int ehdlb_batch_deformation(ehdlb_batch *b, int n, const int *ids, double *D)
+{
+    if (!b || n < 0 || (n > 0 && (!ids || !D))) return EHDLB_EINVAL;
+    if (n == 0) return EHDLB_OK;
+    return b->batch->deformation(n, ids, D, b->err);
+}
+
+int ehdlb_batch_set_tuning(ehdlb_batch *b, int sweeps_per_launch, int tile_shape, int use_graphs)
+{
+    if (!b) return EHDLB_EINVAL;
+    if (sweeps_per_launch < -1 || sweeps_per_launch == 0 || sweeps_per_launch > 5)
+        return bfail(b, EHDLB_EINVAL, "sweeps_per_launch must lie in 1..5 (or -1)");
+    if (tile_shape < -1 || tile_shape > 1) return bfail(b, EHDLB_EINVAL, "tile_shape must lie in -1..1");
+    if (use_graphs < -1 || use_graphs > 1) return bfail(b, EHDLB_EINVAL, "use_graphs must lie in -1..1");
+    return b->batch->set_tuning(sweeps_per_launch, tile_shape, use_graphs);
+}
+
+int ehdlb_batch_autotune(ehdlb_batch *b, int steps, int *sweeps_per_launch, int *tile_shape, double *ms_per_step)
+{
+    if (!b || steps < 1) return EHDLB_EINVAL;
+    return b->batch->autotune(steps, sweeps_per_launch, tile_shape, ms_per_step, b->err);
+}
+
+int ehdlb_batch_info(const ehdlb_batch *b, int *cases, size_t *bytes_in_use, size_t *capacity)
+{
+    if (!b) return EHDLB_EINVAL;
+    b->batch->info(cases, bytes_in_use, capacity);
+    return EHDLB_OK;
+}
+
+const char *ehdlb_batch_last_error(const ehdlb_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+void ehdlb_batch_destroy(ehdlb_batch *b)
+{
+    if (!b) return;
+    delete b->batch;
+    delete b;
+}
 
 }  // extern "C"

@@ -108,6 +108,8 @@ struct Control {
     double r_last;
     double r_step;     // residual of the last finished step
     double sum_phi, sum_q;
+    int tpar;          // f, h, p, n buffer that holds the state (flipped by k_step_end;
+                       // read by the batched kernels, the single-lattice host tracks its own)
 };
 
 // One allocation of 27 planes: f at +0, h at +8 nn, p at +17 nn, n at +22 nn.
@@ -240,9 +242,9 @@ template <typename T> __device__ __forceinline__ T psi_lin(const DevP<T> &P, int
 }
 
 // Deterministic block sum of NV values (fixed tree order), written by thread
-// 0 to out[NV * block].  Each warp sums in T; the warp sums are added in
+// 0 to out[NV * slot].  Each warp sums in T; the warp sums are added in
 // double.  blockDim must be a multiple of 32, <= 1024.
-template <typename T, int NV> __device__ __forceinline__ void block_sum_store(T (&v)[NV], double *out)
+template <typename T, int NV> __device__ __forceinline__ void block_sum_store_at(T (&v)[NV], double *out, long long slot)
 {
     __shared__ double red[32][NV];
     const int lane = (threadIdx.x + threadIdx.y * blockDim.x) & 31;
@@ -262,9 +264,15 @@ template <typename T, int NV> __device__ __forceinline__ void block_sum_store(T 
             double s = lane < nwarp ? red[lane][k] : 0.0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-            if (lane == 0) out[(size_t)NV * (blockIdx.x + (size_t)blockIdx.y * gridDim.x) + k] = s;
+            if (lane == 0) out[(size_t)NV * (size_t)slot + k] = s;
         }
     }
+}
+
+// The same into the slot of this block of the grid.
+template <typename T, int NV> __device__ __forceinline__ void block_sum_store(T (&v)[NV], double *out)
+{
+    block_sum_store_at<T, NV>(v, out, blockIdx.x + (long long)blockIdx.y * gridDim.x);
 }
 
 // Sum NV-wide partials of nb blocks in a fixed order (one block of 256).
@@ -348,15 +356,16 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // + dphi; both are written (phi for the potential, dphi for the stencils of
 // the main kernel).  With init_ctl the first thread also opens the step in
 // the control block.
+// Body of k_prep for the block at (bx, by) of the lattice's grid.
 template <typename T, typename S>
-__global__ void __launch_bounds__(256) k_prep(const DevP<T> P, const S *__restrict__ h,
-                                              const S *__restrict__ p, const S *__restrict__ n,
-                                              const PhiRef<T> R, T *__restrict__ phig, T *__restrict__ q,
-                                              Control *ctl, int fixedK, int kmin, int kmax, int flips)
+__device__ __forceinline__ void prep_body(const DevP<T> &P, const S *__restrict__ h, const S *__restrict__ p,
+                                          const S *__restrict__ n, const PhiRef<T> &R, T *__restrict__ phig,
+                                          T *__restrict__ q, Control *ctl, int fixedK, int kmin, int kmax,
+                                          int flips, int bx, int by)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+    const int x = bx * blockDim.x + threadIdx.x;
+    const int y = by * blockDim.y + threadIdx.y;
+    if (bx == 0 && by == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
         if (fixedK >= 0) {
             ctl->K = fixedK; ctl->flips = flips; ctl->done = 1; ctl->converge = 0;
         } else {
@@ -389,6 +398,16 @@ __global__ void __launch_bounds__(256) k_prep(const DevP<T> P, const S *__restri
         R.dphig[(long long)(P.ny + 1) * P.nx + x] = d;
     }
     q[k] = qv;
+}
+
+// Launch: blockDim (64, 4) over the lattice.
+template <typename T, typename S>
+__global__ void __launch_bounds__(256) k_prep(const DevP<T> P, const S *__restrict__ h,
+                                              const S *__restrict__ p, const S *__restrict__ n,
+                                              const PhiRef<T> R, T *__restrict__ phig, T *__restrict__ q,
+                                              Control *ctl, int fixedK, int kmin, int kmax, int flips)
+{
+    prep_body<T, S>(P, h, p, n, R, phig, q, ctl, fixedK, kmin, kmax, flips, blockIdx.x, blockIdx.y);
 }
 
 // One pseudo-time sweep of the potential (Eq. 44-50) at every node: E and
@@ -492,11 +511,13 @@ __device__ __forceinline__ int wrap_x(int x, int nx, bool wide)
     return ((x % nx) + nx) % nx;
 }
 
-template <typename T, typename S, int NSW, int RW, int RH, int BY, int MINB, bool FIRST, bool RESID>
-__global__ void __launch_bounds__(32 * BY, MINB)
-    k_sweep_tb(const DevP<T> P, S *__restrict__ gA, S *__restrict__ gB, const T *__restrict__ phig,
-               const T *__restrict__ q, T *__restrict__ coef, double *__restrict__ part,
-               const Control *__restrict__ ctl, int m)
+// Body of k_sweep_tb for the block at (bx, by) of the lattice's tile grid;
+// slot: its residual partials.
+template <typename T, typename S, int NSW, int RW, int RH, int BY, bool FIRST, bool RESID>
+__device__ __forceinline__ void tb_body(const DevP<T> &P, S *__restrict__ gA, S *__restrict__ gB,
+                                        const T *__restrict__ phig, const T *__restrict__ q, T *__restrict__ coef,
+                                        double *__restrict__ part, const Control *__restrict__ ctl, int m, int bx,
+                                        int by, long long slot)
 {
     constexpr int H = NSW, TX = RW - 2 * H, TY = RH - 2 * H;
     constexpr int PW = RW + 2, PH = RH + 2, PL = PW * PH;
@@ -510,7 +531,7 @@ __global__ void __launch_bounds__(32 * BY, MINB)
     S *__restrict__ dst = par ? gA : gB;
     const int nx = P.nx, ny = P.ny;
     const long long nn = P.nn;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx * TX, y0 = by * TY;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const bool wide = nx >= RW + 2;
 
@@ -710,7 +731,17 @@ __global__ void __launch_bounds__(32 * BY, MINB)
             }
         }
     }
-    if (RESID) block_sum_store<T, 2>(red, part);
+    if (RESID) block_sum_store_at<T, 2>(red, part, slot);
+}
+
+template <typename T, typename S, int NSW, int RW, int RH, int BY, int MINB, bool FIRST, bool RESID>
+__global__ void __launch_bounds__(32 * BY, MINB)
+    k_sweep_tb(const DevP<T> P, S *__restrict__ gA, S *__restrict__ gB, const T *__restrict__ phig,
+               const T *__restrict__ q, T *__restrict__ coef, double *__restrict__ part,
+               const Control *__restrict__ ctl, int m)
+{
+    tb_body<T, S, NSW, RW, RH, BY, FIRST, RESID>(P, gA, gB, phig, q, coef, part, ctl, m, blockIdx.x, blockIdx.y,
+                                                 blockIdx.x + (long long)blockIdx.y * gridDim.x);
 }
 
 // ---- thread-block clusters -------------------------------------------------------
@@ -1044,27 +1075,29 @@ __device__ __forceinline__ void stage_planes(E *st, PlaneF plane, int nx, int ny
 //   VEC   : 16-byte staging (stage_planes).
 // NaN or Inf in the macroscopic fields raises *unstable.
 // Launch: blockDim (64, 4), dynamic shared memory main_smem_bytes<T, S>().
+// Body of k_main for the block at (bx, by) of the lattice's grid; slot: its
+// partials.
 template <typename T, typename S, bool SNAP, bool FROZEN, bool RESID, bool VEC>
-__global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<S> src, const Pops<S> dst,
-                                                 const T *__restrict__ gA, const T *__restrict__ gB,
-                                                 const Control *__restrict__ ctl, const PhiRef<T> Rf,
-                                                 S *__restrict__ phiu, const T *__restrict__ psi_prev,
-                                                 T *__restrict__ snap, double *__restrict__ part,
-                                                 int *__restrict__ unstable)
+__device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, const Pops<S> &dst,
+                                          const T *__restrict__ gA, const T *__restrict__ gB,
+                                          const Control *__restrict__ ctl, const PhiRef<T> &Rf,
+                                          S *__restrict__ phiu, const T *__restrict__ psi_prev, T *__restrict__ snap,
+                                          double *__restrict__ part, int *__restrict__ unstable, int bx, int by,
+                                          long long slot)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S *st = reinterpret_cast<S *>(smem_raw);
     T *stg = reinterpret_cast<T *>(smem_raw + sizeof(S) * MAIN_SPLANES * 256);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int x = bx * blockDim.x + threadIdx.x;
+    const int y = by * blockDim.y + threadIdx.y;
     const bool inside = x < P.nx && y < P.ny;
     const long long nn = P.nn, k = (long long)y * P.nx + x;
     T red[4] = {T(0), T(0), T(0), T(0)};
     {
         const T *__restrict__ g = ((ctl->cur0 + ctl->flips) & 1) ? gB : gA;
         const S *pops = src.f, *pu = phiu;
-        const int x0 = blockIdx.x * blockDim.x, y0 = blockIdx.y * blockDim.y;
+        const int x0 = bx * blockDim.x, y0 = by * blockDim.y;
         stage_planes<S, MAIN_SPLANES, VEC>(
             st, [=](int i) { return i < 27 ? pops + i * nn : pu + (i - 27) * nn; }, P.nx, P.ny, x0, y0, tid, inside, k);
         stage_planes<T, MAIN_TPLANES, VEC>(stg, [=](int i) { return g + i * nn; }, P.nx, P.ny, x0, y0, tid, inside, k);
@@ -1385,16 +1418,28 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<S> 
         const T chk = ux + uy + pr + psi + cp + cm;
         if (!isfinite(chk)) *unstable = 1;
     }
-    if (SNAP || RESID) block_sum_store<T, 4>(red, part);
+    if (SNAP || RESID) block_sum_store_at<T, 4>(red, part, slot);
+}
+
+template <typename T, typename S, bool SNAP, bool FROZEN, bool RESID, bool VEC>
+__global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<S> src, const Pops<S> dst,
+                                                 const T *__restrict__ gA, const T *__restrict__ gB,
+                                                 const Control *__restrict__ ctl, const PhiRef<T> Rf,
+                                                 S *__restrict__ phiu, const T *__restrict__ psi_prev,
+                                                 T *__restrict__ snap, double *__restrict__ part,
+                                                 int *__restrict__ unstable)
+{
+    main_body<T, S, SNAP, FROZEN, RESID, VEC>(P, src, dst, gA, gB, ctl, Rf, phiu, psi_prev, snap, part, unstable,
+                                              blockIdx.x, blockIdx.y, blockIdx.x + (long long)blockIdx.y * gridDim.x);
 }
 
 // End of step (one block of 256): global sums of the main kernel (when it
 // reduced), the step's residual, counters, the next step's g parity.
 //   resid: 0 none; 1 from the main kernel's partials (columns 2, 3 of 4);
 //          2 from the fused sweep kernel's partials (2 per block in part2).
-static __global__ void __launch_bounds__(256) k_step_end(const double *__restrict__ part, long long nb,
-                                                         const double *__restrict__ part2, long long nb2,
-                                                         Control *ctl, int *counts, int resid, int sums)
+__device__ __forceinline__ void step_end_body(const double *__restrict__ part, long long nb,
+                                              const double *__restrict__ part2, long long nb2, Control *ctl,
+                                              int *counts, int resid, int sums)
 {
     double tot[4] = {0.0, 0.0, 0.0, 0.0};
     if (resid == 1 || sums) sum_partials<4>(part, nb, tot);
@@ -1405,25 +1450,34 @@ static __global__ void __launch_bounds__(256) k_step_end(const double *__restric
         tot[2] = t2[0];
         tot[3] = t2[1];
     }
-    if (threadIdx.x != 0) return;
-    const int K = ctl->K;
-    double r = ctl->r_last;
-    if (!ctl->early) {
-        if (resid && K >= 1) r = tot[3] > 0.0 ? sqrt(tot[2] / tot[3]) : sqrt(tot[2]);
-        else r = nan("");
+    if (threadIdx.x == 0) {
+        const int K = ctl->K;
+        double r = ctl->r_last;
+        if (!ctl->early) {
+            if (resid && K >= 1) r = tot[3] > 0.0 ? sqrt(tot[2] / tot[3]) : sqrt(tot[2]);
+            else r = nan("");
+        }
+        ctl->r_step = r;
+        if (sums) {
+            ctl->sum_phi = tot[0];
+            ctl->sum_q = tot[1];
+        }
+        if (counts) counts[ctl->tloc] = K;
+        ctl->sweeps_total += K;
+        if (K > ctl->sweeps_max) ctl->sweeps_max = K;
+        if (ctl->converge && ctl->kmax > ctl->kmin && K >= ctl->kmax && !(r < ctl->tol)) ctl->notconv += 1;
+        ctl->cur0 = (ctl->cur0 + ctl->flips) & 1;
+        ctl->t += 1;
+        ctl->tloc += 1;
+        ctl->tpar ^= 1;
     }
-    ctl->r_step = r;
-    if (sums) {
-        ctl->sum_phi = tot[0];
-        ctl->sum_q = tot[1];
-    }
-    if (counts) counts[ctl->tloc] = K;
-    ctl->sweeps_total += K;
-    if (K > ctl->sweeps_max) ctl->sweeps_max = K;
-    if (ctl->converge && ctl->kmax > ctl->kmin && K >= ctl->kmax && !(r < ctl->tol)) ctl->notconv += 1;
-    ctl->cur0 = (ctl->cur0 + ctl->flips) & 1;
-    ctl->t += 1;
-    ctl->tloc += 1;
+}
+
+static __global__ void __launch_bounds__(256) k_step_end(const double *__restrict__ part, long long nb,
+                                                         const double *__restrict__ part2, long long nb2,
+                                                         Control *ctl, int *counts, int resid, int sums)
+{
+    step_end_body(part, nb, part2, nb2, ctl, counts, resid, sums);
 }
 
 // ---- initial state (Sec. 6 set-up) ------------------------------------------------
@@ -1598,6 +1652,92 @@ __global__ void k_to_double(const T *__restrict__ a, double *__restrict__ out, l
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) out[i] = (double)a[i];
+}
+
+// ---- deformation factor (Eq. 63) ------------------------------------------------
+
+// Deformation factor D = (L - H) / (L + H) (Eq. 63) of the phi field (the
+// first plane of a snapshot), one block of 256 per lattice: L is the extent
+// of phi >= 1/2 along the field (y) through the phi-weighted centroid, H
+// the same across it (x); the line is sampled by bilinear interpolation of
+// the nodes (x periodic, rows clamped at the walls) and each end is the
+// crossing of 1/2 interpolated linearly between consecutive samples.
+template <typename T>
+__device__ __forceinline__ double phi_sample(const T *phi, int nx, int ny, double x, double y)
+{
+    int x0 = (int)floor(x), y0 = (int)floor(y);
+    const double fx = x - x0, fy = y - y0;
+    int x1 = x0 + 1, y1 = y0 + 1;
+    x0 = ((x0 % nx) + nx) % nx;
+    x1 = ((x1 % nx) + nx) % nx;
+    y0 = min(max(y0, 0), ny - 1);
+    y1 = min(max(y1, 0), ny - 1);
+    const double a = (double)phi[(long long)y0 * nx + x0] * (1.0 - fx) + (double)phi[(long long)y0 * nx + x1] * fx;
+    const double b = (double)phi[(long long)y1 * nx + x0] * (1.0 - fx) + (double)phi[(long long)y1 * nx + x1] * fx;
+    return a * (1.0 - fy) + b * fy;
+}
+
+template <typename T>
+__device__ __forceinline__ double phi_extent(const T *phi, int nx, int ny, double xc, double yc, bool along_y)
+{
+    const int lim = along_y ? ny : nx;
+    double e[2];
+    for (int dir = 0; dir < 2; ++dir) {
+        const double sgn = dir ? 1.0 : -1.0;
+        double pt = 0.0, pv = phi_sample(phi, nx, ny, xc, yc), end = sgn * lim;
+        for (int s = 1; s < lim; ++s) {
+            const double tt = sgn * s;
+            const double v = along_y ? phi_sample(phi, nx, ny, xc, yc + tt) : phi_sample(phi, nx, ny, xc + tt, yc);
+            if (pv >= 0.5 && v < 0.5) {
+                end = pt + (tt - pt) * (pv - 0.5) / (pv - v);
+                break;
+            }
+            pt = tt;
+            pv = v;
+        }
+        e[dir] = end;
+    }
+    return e[1] - e[0];
+}
+
+template <typename T>
+__device__ __forceinline__ void deformation_body(const T *__restrict__ phi, int nx, int ny, double *out)
+{
+    __shared__ double red[256][3];
+    double a[3] = {0.0, 0.0, 0.0};
+    const long long nn = (long long)nx * ny;
+    for (long long k = threadIdx.x; k < nn; k += blockDim.x) {
+        const double v = (double)phi[k];
+        a[0] += v;
+        a[1] += v * (double)(k % nx);
+        a[2] += v * (double)(k / nx);
+    }
+    for (int i = 0; i < 3; ++i) red[threadIdx.x][i] = a[i];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int i = 0; i < 3; ++i) red[threadIdx.x][i] += red[threadIdx.x + s][i];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double sphi = red[0][0];
+        if (!(sphi > 0.0)) {
+            *out = 0.0;
+        } else {
+            const double xc = red[0][1] / sphi, yc = red[0][2] / sphi;
+            const double L = phi_extent(phi, nx, ny, xc, yc, true);
+            const double H = phi_extent(phi, nx, ny, xc, yc, false);
+            *out = (L - H) / (L + H);
+        }
+    }
+    __syncthreads();
+}
+
+// One lattice (launch: 1 block of 256).
+template <typename T>
+__global__ void __launch_bounds__(256) k_deformation(const T *__restrict__ phi, int nx, int ny, double *out)
+{
+    deformation_body(phi, nx, ny, out);
 }
 
 }  // namespace ehdlb

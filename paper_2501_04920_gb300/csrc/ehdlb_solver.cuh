@@ -32,11 +32,17 @@ template <typename T, typename S = T> class Solver : public SolverBase {
   public:
     static constexpr int BX = 64, BY = 4;
 
-    Solver(int nx, int ny, cudaStream_t s) : nx_(nx), ny_(ny), nn_((long long)nx * ny), stream_(s) {}
+    Solver(int nx, int ny, cudaStream_t s, DevArena *arena = nullptr)
+        : nx_(nx), ny_(ny), nn_((long long)nx * ny), stream_(s), arena_(arena)
+    {
+    }
 
     ~Solver() override
     {
-        for (void *p : allocs_) cudaFree(p);
+        for (void *p : allocs_) {
+            if (arena_) arena_->release(p);
+            else cudaFree(p);
+        }
         for (cudaEvent_t e : events_) cudaEventDestroy(e);
         if (own_stream_) cudaStreamDestroy(stream_);
     }
@@ -267,15 +273,75 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     }
 
     int get_state(double *dst, std::string &err) override { return transfer_state(dst, nullptr, err); }
+
+    // D of Eq. 63 from the phi of the last snapshot
+    int deformation(double *out, std::string &err) override
+    {
+        k_deformation<T><<<1, 256, 0, stream_>>>(snap_, nx_, ny_, stage_);
+        EHDLB_CK(cudaGetLastError());
+        EHDLB_CK(cudaMemcpyAsync(out, stage_, sizeof(double), cudaMemcpyDeviceToHost, stream_));
+        EHDLB_CK(cudaStreamSynchronize(stream_));
+        return EHDLB_OK;
+    }
     int set_state(const double *src, std::string &err) override { return transfer_state(nullptr, src, err); }
 
   private:
     cudaError_t alloc(void **p, size_t bytes)
     {
-        cudaError_t e = cudaMalloc(p, bytes);
+        cudaError_t e = arena_ ? arena_->alloc(p, bytes) : cudaMalloc(p, bytes);
         if (e == cudaSuccess) allocs_.push_back(*p);
         return e;
     }
+
+  public:
+    // Device bytes of one lattice of nx x ny nodes (what allocate() takes,
+    // rounded up to 256-byte blocks; the per-call counters excluded).
+    static size_t footprint(int nx, int ny)
+    {
+        const size_t nn = (size_t)nx * ny, t = sizeof(T), s = sizeof(S);
+        const size_t gx = (size_t)(nx + BX - 1) / BX, gy = (size_t)(ny + BY - 1) / BY;
+        size_t nbmax = 0;
+        for (int nsw = 1; nsw <= TB_MAX; ++nsw)
+            for (int sh = 0; sh < TB_NSHAPES; ++sh) {
+                const dim3 g = tb_grid(nsw, sh, nx, ny);
+                nbmax = std::max(nbmax, (size_t)g.x * g.y);
+            }
+        const size_t planes_row = (size_t)(ny + 2) * nx;
+        // one entry per allocation of allocate(), in its order
+        const size_t b[] = {27 * nn * s, 4 * nn * t, 27 * nn * s, 4 * nn * t,
+                            planes_row * t, planes_row * t, planes_row * t,
+                            nn * t, nn * t, nn * t, nn * t, 3 * nn * t, 2 * nn * s, nn * t,
+                            EHDLB_NFIELDS * nn * t, 4 * gx * gy * 8, sizeof(Control), 2 * nbmax * 8, nn * 8};
+        size_t tot = 0;
+        for (size_t v : b) tot += (v + 255) / 256 * 256;
+        return tot;
+    }
+
+    // Pointers and constants of this lattice for the batched kernels.
+    void describe(DevP<T> &P, Pops<S> (&pops)[2], T *(&g)[2], S *&phiu, T *&phig, T *&q, T *&coef,
+                  T *&psi_prev, T *&snap, PhiRef<T> &ref, double *&part, double *&part2, Control *&ctl) const
+    {
+        P = dp_;
+        pops[0] = pops_[0];
+        pops[1] = pops_[1];
+        g[0] = g_[0];
+        g[1] = g_[1];
+        phiu = phiu_;
+        phig = phig_;
+        q = q_;
+        coef = coef_;
+        psi_prev = psi_prev_;
+        snap = snap_;
+        ref = ref_;
+        part = part_;
+        part2 = part2_;
+        ctl = ctl_;
+    }
+    int nx() const { return nx_; }
+    int ny() const { return ny_; }
+    const ehdlb_params &params() const { return P_; }
+
+  private:
 
     void make_devp()
     {
@@ -599,7 +665,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             const unsigned nblk = (unsigned)((cnt + 255) / 256);
             cudaError_t e = cudaSuccess;
             if (dst) {
-                k_pack_state<T, S><<<nblk, 256, 0, stream_>>>(dp_, pops_[tpar_], g_[cur], phiu_, ref_.phir, stage,
+                k_pack_state<T, S><<<nblk, 256, 0, stream_>>>(dp_, pops_[ctl_h_.tpar & 1], g_[cur], phiu_, ref_.phir, stage,
                                                             y0, r);
                 e = cudaGetLastError();
                 if (e == cudaSuccess)
@@ -609,7 +675,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
                 e = cudaMemcpyAsync(stage, src + per_row * y0, sizeof(double) * per_row * r,
                                     cudaMemcpyHostToDevice, stream_);
                 if (e == cudaSuccess)
-                    k_unpack_state<T, S><<<nblk, 256, 0, stream_>>>(dp_, pops_[tpar_], g_[cur], phiu_, ref_.phir,
+                    k_unpack_state<T, S><<<nblk, 256, 0, stream_>>>(dp_, pops_[ctl_h_.tpar & 1], g_[cur], phiu_, ref_.phir,
                                                               stage, y0, r);
                 if (e == cudaSuccess) e = cudaGetLastError();
             }
@@ -626,6 +692,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     int nx_, ny_;
     long long nn_;
     cudaStream_t stream_;
+    DevArena *arena_ = nullptr;
     bool own_stream_ = false;
     dim3 grid_;
     long long nb_ = 0;

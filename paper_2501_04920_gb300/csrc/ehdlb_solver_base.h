@@ -11,6 +11,15 @@
 
 namespace ehdlb {
 
+// Device memory source of a solver: cudaMalloc by default, or an arena of
+// the batch engine.
+class DevArena {
+  public:
+    virtual ~DevArena() {}
+    virtual cudaError_t alloc(void **p, size_t bytes) = 0;
+    virtual void release(void *p) = 0;
+};
+
 class SolverBase {
   public:
     virtual ~SolverBase() {}
@@ -23,8 +32,30 @@ class SolverBase {
     virtual void set_schedule(const int *c, int n) = 0;
     virtual void set_timing(int on) = 0;
     virtual void set_tuning(int sweeps_per_launch, int shape, int vec_staging) = 0;
+    virtual int deformation(double *out, std::string &err) = 0;
     int last_nsteps = 0;
 };
+
+// A set of lattices stepped together (ehdlb_batch.cuh).
+class BatchBase {
+  public:
+    virtual ~BatchBase() {}
+    virtual int add(int nx, int ny, const ehdlb_params &p, int *id, std::string &err) = 0;
+    virtual int remove(int id, std::string &err) = 0;
+    virtual int step(int nsteps, ehdlb_batch_stats *st, std::string &err) = 0;
+    virtual int get_fields(int id, unsigned mask, double *dst, std::string &err) = 0;
+    virtual int get_state(int id, double *dst, std::string &err) = 0;
+    virtual int case_size(int id, int *nx, int *ny) const = 0;
+    virtual int deformation(int n, const int *ids, double *out, std::string &err) = 0;
+    virtual int set_tuning(int sweeps_per_launch, int shape, int use_graphs) = 0;
+    virtual int autotune(int steps, int *best_chunk, int *best_shape, double *best_ms, std::string &err) = 0;
+    virtual void info(int *cases, size_t *in_use, size_t *capacity) const = 0;
+};
+
+BatchBase *make_batch_fp32(size_t budget, int sweeps, cudaStream_t s, int *status, std::string &err);
+BatchBase *make_batch_fp16s(size_t budget, int sweeps, cudaStream_t s, int *status, std::string &err);
+size_t footprint_fp32(int nx, int ny);
+size_t footprint_fp16s(int nx, int ny);
 
 SolverBase *make_solver_fp32(int nx, int ny, cudaStream_t s, int *status, std::string &err);
 SolverBase *make_solver_fp64(int nx, int ny, cudaStream_t s, int *status, std::string &err);

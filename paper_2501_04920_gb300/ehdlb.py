@@ -15,9 +15,9 @@ from . import build as _build
 
 FIELDS = ["phi", "ux", "uy", "p", "psi", "Ex", "Ey", "cp", "cm", "q"]
 FP64, FP32, FP16S = 0, 1, 2
-OK, WNOTCONV, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ESTATE = 0, 1, -1, -2, -3, -4, -5
+OK, WNOTCONV, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ESTATE, EFULL = 0, 1, -1, -2, -3, -4, -5, -6
 STATUS_NAMES = {0: "OK", 1: "WNOTCONV", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA",
-                -4: "EUNSTABLE", -5: "ESTATE"}
+                -4: "EUNSTABLE", -5: "ESTATE", -6: "EFULL"}
 
 _PARAM_FIELDS = [
     ("size", C.c_size_t),
@@ -60,6 +60,14 @@ class ehdlb_stats(C.Structure):
     ]
 
 
+class ehdlb_batch_stats(C.Structure):
+    _fields_ = [
+        ("steps", C.c_longlong), ("cases", C.c_int), ("unstable_cases", C.c_int),
+        ("seconds", C.c_double), ("device_ms", C.c_double), ("mlups", C.c_double),
+        ("launches", C.c_longlong), ("sweeps_per_launch", C.c_int), ("tile_shape", C.c_int),
+    ]
+
+
 class EhdlbError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -96,6 +104,22 @@ def lib():
         L.ehdlb_set_tuning.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.ehdlb_potential_noalloc.argtypes = [C.c_int, C.c_int, C.POINTER(ehdlb_params), vp, vp,
                                               C.c_int, vp, vp, vp, dp, vp]
+        L.ehdlb_deformation.argtypes = [vp, dp]
+        L.ehdlb_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.c_size_t, C.c_int, vp]
+        L.ehdlb_batch_footprint.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]
+        L.ehdlb_batch_add.argtypes = [vp, C.c_int, C.c_int, C.POINTER(ehdlb_params), ip]
+        L.ehdlb_batch_remove.argtypes = [vp, C.c_int]
+        L.ehdlb_batch_step.argtypes = [vp, C.c_int, C.POINTER(ehdlb_batch_stats)]
+        L.ehdlb_batch_get_fields.argtypes = [vp, C.c_int, C.c_uint, dp, C.c_size_t]
+        L.ehdlb_batch_get_state.argtypes = [vp, C.c_int, dp, C.c_size_t]
+        L.ehdlb_batch_deformation.argtypes = [vp, C.c_int, ip, dp]
+        L.ehdlb_batch_set_tuning.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+        L.ehdlb_batch_autotune.argtypes = [vp, C.c_int, ip, ip, dp]
+        L.ehdlb_batch_info.argtypes = [vp, ip, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+        L.ehdlb_batch_last_error.argtypes = [vp]
+        L.ehdlb_batch_last_error.restype = C.c_char_p
+        L.ehdlb_batch_destroy.argtypes = [vp]
+        L.ehdlb_batch_destroy.restype = None
         L.ehdlb_destroy.argtypes = [vp]
         L.ehdlb_destroy.restype = None
         L.ehdlb_last_error.argtypes = [vp]
@@ -223,8 +247,97 @@ def ehdlb_set_tuning(ctx, sweeps_per_launch: int = -1, tile_shape: int = -1, mai
                   "ehdlb_set_tuning")
 
 
+def ehdlb_deformation(ctx) -> float:
+    d = C.c_double()
+    _check(ctx, lib().ehdlb_deformation(ctx, C.byref(d)), "ehdlb_deformation")
+    return d.value
+
+
 def ehdlb_destroy(ctx):
     lib().ehdlb_destroy(ctx)
+
+
+# ---- batches ---------------------------------------------------------------------
+
+def _bcheck(b, status, what):
+    if status < 0:
+        msg = lib().ehdlb_batch_last_error(b).decode() if b else ""
+        raise EhdlbError(status, f"{what}: {msg}")
+    return status
+
+
+def ehdlb_batch_create(precision: int, budget_bytes: int, sweeps: int, cuda_stream: int | None = None):
+    h = C.c_void_p()
+    _bcheck(None, lib().ehdlb_batch_create(C.byref(h), precision, budget_bytes, sweeps,
+                                           C.c_void_p(cuda_stream) if cuda_stream else None),
+            "ehdlb_batch_create")
+    return h
+
+
+def ehdlb_batch_footprint(precision: int, nx: int, ny: int) -> int:
+    b = C.c_size_t()
+    _bcheck(None, lib().ehdlb_batch_footprint(precision, nx, ny, C.byref(b)), "ehdlb_batch_footprint")
+    return b.value
+
+
+def ehdlb_batch_add(b, nx: int, ny: int, p: ehdlb_params):
+    """Returns (status, id); status EFULL (no room) is returned, not raised."""
+    i = C.c_int(-1)
+    st = lib().ehdlb_batch_add(b, nx, ny, C.byref(p), C.byref(i))
+    if st != EFULL:
+        _bcheck(b, st, "ehdlb_batch_add")
+    return st, i.value
+
+
+def ehdlb_batch_remove(b, case_id: int):
+    return _bcheck(b, lib().ehdlb_batch_remove(b, case_id), "ehdlb_batch_remove")
+
+
+def ehdlb_batch_step(b, nsteps: int):
+    st = ehdlb_batch_stats()
+    status = _bcheck(b, lib().ehdlb_batch_step(b, nsteps, C.byref(st)), "ehdlb_batch_step")
+    return status, st
+
+
+def ehdlb_batch_get_fields(b, case_id: int, mask: int, out: np.ndarray):
+    assert out.dtype == np.float64 and out.flags["C_CONTIGUOUS"]
+    return _bcheck(b, lib().ehdlb_batch_get_fields(b, case_id, mask, _dp(out), out.size),
+                   "ehdlb_batch_get_fields")
+
+
+def ehdlb_batch_get_state(b, case_id: int, out: np.ndarray):
+    assert out.dtype == np.float64 and out.flags["C_CONTIGUOUS"]
+    return _bcheck(b, lib().ehdlb_batch_get_state(b, case_id, _dp(out), out.size), "ehdlb_batch_get_state")
+
+
+def ehdlb_batch_deformation(b, ids) -> np.ndarray:
+    ids = np.ascontiguousarray(np.asarray(ids, dtype=np.int32))
+    out = np.zeros(ids.size)
+    _bcheck(b, lib().ehdlb_batch_deformation(b, ids.size, ids.ctypes.data_as(C.POINTER(C.c_int)), _dp(out)),
+            "ehdlb_batch_deformation")
+    return out
+
+
+def ehdlb_batch_set_tuning(b, sweeps_per_launch=-1, tile_shape=-1, use_graphs=-1):
+    return _bcheck(b, lib().ehdlb_batch_set_tuning(b, sweeps_per_launch, tile_shape, use_graphs),
+                   "ehdlb_batch_set_tuning")
+
+
+def ehdlb_batch_autotune(b, steps: int):
+    spl, shape, ms = C.c_int(), C.c_int(), C.c_double()
+    _bcheck(b, lib().ehdlb_batch_autotune(b, steps, C.byref(spl), C.byref(shape), C.byref(ms)),
+            "ehdlb_batch_autotune")
+    return spl.value, shape.value, ms.value
+
+
+def ehdlb_batch_info(b):
+    n, used, cap = C.c_int(), C.c_size_t(), C.c_size_t()
+    _bcheck(b, lib().ehdlb_batch_info(b, C.byref(n), C.byref(used), C.byref(cap)), "ehdlb_batch_info")
+    return n.value, used.value, cap.value
+
+
+def ehdlb_batch_destroy(b):
+    lib().ehdlb_batch_destroy(b)
 
 
 def ehdlb_last_error(ctx) -> str:
@@ -269,10 +382,75 @@ class Lattice:
     def set_state(self, s):
         ehdlb_set_state(self.ctx, np.asarray(s, dtype=np.float64).reshape(self.ny, self.nx, 35))
 
+    def deformation(self) -> float:
+        return ehdlb_deformation(self.ctx)
+
     def close(self):
         if self.ctx:
             ehdlb_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many lattices stepped together (see ehdlb_batch_create)."""
+
+    def __init__(self, budget_bytes: int, sweeps: int = 20, precision=FP32, cuda_stream=None):
+        self.precision = precision
+        self.b = ehdlb_batch_create(precision, budget_bytes, sweeps, cuda_stream)
+        self.sizes = {}
+
+    def add(self, nx, ny, params: dict | ehdlb_params):
+        """Case id, or None if the budget has no room."""
+        p = params if isinstance(params, ehdlb_params) else ehdlb_params_default(params)
+        st, cid = ehdlb_batch_add(self.b, nx, ny, p)
+        if st == EFULL:
+            return None
+        self.sizes[cid] = (nx, ny)
+        return cid
+
+    def remove(self, cid):
+        ehdlb_batch_remove(self.b, cid)
+        del self.sizes[cid]
+
+    def step(self, nsteps: int):
+        return ehdlb_batch_step(self.b, nsteps)
+
+    def fields(self, cid, names=None) -> dict:
+        nx, ny = self.sizes[cid]
+        names = FIELDS if names is None else list(names)
+        idx = sorted(FIELDS.index(n) for n in names)
+        out = np.zeros((len(idx), ny, nx))
+        ehdlb_batch_get_fields(self.b, cid, sum(1 << i for i in idx), out)
+        return {FIELDS[i]: out[j] for j, i in enumerate(idx)}
+
+    def state(self, cid) -> np.ndarray:
+        nx, ny = self.sizes[cid]
+        out = np.zeros((ny, nx, 35))
+        ehdlb_batch_get_state(self.b, cid, out)
+        return out
+
+    def deformation(self, ids) -> np.ndarray:
+        return ehdlb_batch_deformation(self.b, ids)
+
+    def set_tuning(self, sweeps_per_launch=-1, tile_shape=-1, use_graphs=-1):
+        ehdlb_batch_set_tuning(self.b, sweeps_per_launch, tile_shape, use_graphs)
+
+    def autotune(self, steps: int):
+        return ehdlb_batch_autotune(self.b, steps)
+
+    def info(self):
+        return ehdlb_batch_info(self.b)
+
+    def close(self):
+        if self.b:
+            ehdlb_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -82,3 +82,26 @@ def test_null_and_bad_arguments_are_rejected_without_a_device():
     assert not h.value
     L.ehdlb_destroy(None)
     assert ehdlb.ehdlb_version() == 2
+
+
+def test_batch_entry_points_reject_null_without_a_device():
+    L = ehdlb.lib()
+    h = C.c_void_p()
+    assert L.ehdlb_batch_create(None, ehdlb.FP32, 1 << 20, 20, None) == ehdlb.EINVAL
+    assert L.ehdlb_batch_create(C.byref(h), ehdlb.FP64, 1 << 20, 20, None) == ehdlb.EINVAL
+    assert L.ehdlb_batch_create(C.byref(h), ehdlb.FP32, 1 << 20, 0, None) == ehdlb.EINVAL
+    assert L.ehdlb_batch_step(None, 1, None) == ehdlb.EINVAL
+    assert L.ehdlb_batch_remove(None, 0) == ehdlb.EINVAL
+    assert L.ehdlb_batch_info(None, None, None, None) == ehdlb.EINVAL
+    L.ehdlb_batch_destroy(None)
+
+
+def test_batch_footprint_grows_with_the_lattice_and_halves_with_fp16_storage():
+    f = ehdlb.ehdlb_batch_footprint
+    a, b = f(ehdlb.FP32, 128, 128), f(ehdlb.FP32, 256, 256)
+    assert 3.5 * a < b < 4.5 * a
+    # per node: about 348 B in FP32 (two time levels of 27 populations,
+    # g, auxiliary planes, snapshot, staging)
+    assert 300 * 256 * 256 < b < 420 * 256 * 256
+    assert f(ehdlb.FP16S, 256, 256) < 0.8 * b
+
