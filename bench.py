@@ -59,6 +59,12 @@ def parse():
                     help="step kernel staging, 0 per node, 1 16-byte segments (default: the library's)")
     ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS),
                     help="fp32 (the headline form), fp16s (FP16 storage) or fp64")
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve"],
+                    help="step: the 2048^2 case (the headline); batch: the 96 uneven cases, batched "
+                         "against one by one; serve: a stream of arriving cases, continuous batching "
+                         "against one by one")
+    ap.add_argument("--serve-cases", type=int, default=64)
+    ap.add_argument("--serve-max-steps", type=int, default=4000)
     return ap.parse_args()
 
 
@@ -321,10 +327,118 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batch(args):
+    """Cases per hour of the 96 uneven cases (10000 steps each): one batch
+    against the same cases run one at a time."""
+    import torch
+    from paper_2501_04920_gb300 import ehdlb, workloads
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    prec = {"fp32": ehdlb.FP32, "fp16s": ehdlb.FP16S}[args.precision]
+    cases = workloads.uneven_cases()
+    total_steps = workloads.STEPS["uneven"]
+    params = [ehdlb.ehdlb_params_from_physical(c["nx"], c["ny"], c["d_mm"], c["dpsi_kV"], c["eps_r"], c["mu_r"])
+              for c in cases]
+    budget = int(1.05 * sum(ehdlb.ehdlb_batch_footprint(prec, c["nx"], c["ny"]) for c in cases)) + (64 << 20)
+    # autotune on a scratch copy of the batch
+    b = ehdlb.Batch(budget, 20, precision=prec)
+    for c, p in zip(cases, params):
+        b.add(c["nx"], c["ny"], p)
+    spl, shape, tune_ms = b.autotune(3)
+    b.close()
+    # the timed batch
+    t0 = time.perf_counter()
+    b = ehdlb.Batch(budget, 20, precision=prec)
+    for c, p in zip(cases, params):
+        b.add(c["nx"], c["ny"], p)
+    b.set_tuning(spl, shape)
+    setup_b = time.perf_counter() - t0
+    b.step(max(3, args.warmup))
+    with ClockSampler(local) as clk:
+        _, st = b.step(args.steps)
+    per_step_b = st.device_ms / 1e3 / args.steps
+    batch_mlups = st.mlups
+    b.close()
+    total_b = setup_b + per_step_b * total_steps
+    # one case at a time
+    total_p, k = 0.0, 20
+    for c, p in zip(cases, params):
+        t0 = time.perf_counter()
+        lat = ehdlb.Lattice(c["nx"], c["ny"], p, precision=prec)
+        setup = time.perf_counter() - t0
+        lat.step(2)
+        _, s1 = lat.step(k)
+        total_p += setup + s1.seconds / k * total_steps
+        lat.close()
+    nodes = sum(c["nx"] * c["ny"] for c in cases)
+    out = {
+        "metric": "served cases/h vs plain (uneven batch)", "mode": "batch",
+        "value": round(len(cases) * 3600 / total_b, 1), "unit": "cases/h", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+        "plain_value": round(len(cases) * 3600 / total_p, 1),
+        "speedup_vs_plain": round(total_p / total_b, 3),
+        "ms_per_batch_step": per_step_b * 1e3, "batch_mlups": round(batch_mlups, 1),
+        "autotune": {"sweeps_per_launch": spl, "tile_shape": shape, "ms_per_step": tune_ms},
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{len(cases)} uneven droplet cases (nx 128-768, ny in [nx, 2nx], physical "
+                               f"mapping), {total_steps} steps each, 20 sweeps/step, "
+                               f"{'FP16 storage' if args.precision == 'fp16s' else 'FP32'}",
+                   "nodes": nodes, "projection": f"setup + {total_steps} x measured time per step"},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_serve(args):
+    """Continuous batching of a Poisson stream of cases against serving them
+    one by one: latency percentiles and completed cases per hour."""
+    import torch
+    from paper_2501_04920_gb300 import ehdlb, workloads
+    from paper_2501_04920_gb300.serve import Case, Server, percentile, serve_one_by_one
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    n, max_steps, check = args.serve_cases, args.serve_max_steps, 500
+    raw = workloads.arrivals(n, rate_per_s=1.0)
+    # offered load ~1.2x the batch's capacity at the throughput of the
+    # 2048^2 case: rate = 1.2 * node updates per s / mean node updates per case
+    mean_work = sum(a["nx"] * a["ny"] for a in raw) / n * max_steps
+    rate = 1.2 * 6.5e9 / mean_work
+    cases = [Case(t=a["t"] / rate, nx=a["nx"], ny=a["ny"], d_mm=a["d_mm"], dpsi_kV=a["dpsi_kV"],
+                  eps_r=a["eps_r"], mu_r=a["mu_r"], key=i) for i, a in enumerate(raw)]
+    budget = 150 << 30
+    b = ehdlb.Batch(budget, 20)
+    t0 = time.perf_counter()
+    res = Server(b, check_every=check, max_steps=max_steps, tol=1e-6).run(cases)
+    span_b = time.perf_counter() - t0
+    b.close()
+    t0 = time.perf_counter()
+    res_p = serve_one_by_one(cases, check_every=check, max_steps=max_steps, tol=1e-6)
+    span_p = time.perf_counter() - t0
+    lb, lp = [r.latency for r in res], [r.latency for r in res_p]
+    out = {
+        "metric": "served cases/h vs plain, p99 latency (continuous batching)", "mode": "serve",
+        "value": round(n * 3600 / span_b, 1), "unit": "cases/h", "n_gpus": 1, "higher_is_better": True,
+        "plain_value": round(n * 3600 / span_p, 1), "speedup_vs_plain": round(span_p / span_b, 3),
+        "latency_s": {"p50": percentile(lb, 50), "p99": percentile(lb, 99)},
+        "plain_latency_s": {"p50": percentile(lp, 50), "p99": percentile(lp, 99)},
+        "steady_fraction": sum(r.steady for r in res) / n,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{n} Poisson arrivals at {rate:.3f}/s (offered ~1.2x capacity), square "
+                               f"sides 128*8^U rounded to 64, physical parameters as the uneven batch; "
+                               f"steady when |dD|/{check} steps < 1e-6, at most {max_steps} steps; "
+                               f"budget 150 GB", "rate_per_s": rate},
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "batch":
+        run_batch(args)
+    elif args.mode == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

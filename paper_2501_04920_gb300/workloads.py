@@ -11,6 +11,8 @@ here.  Cases:
   b = sqrt(|E|); eps_r = 2, Kq = W0 / 64^2 with W0 = 5.6893 (d = 2 mm,
   1 kV); potential swept to a relative change of 1e-8 (cap 200) every step,
   the initial potential solved to the same tolerance; 2000 steps.
+* ``uneven_cases()``: 96 physical cases of uneven size for the batch engine.
+* ``arrivals()``: a Poisson stream of cases for the serving loop.
 * ``droplet(n)``: the plain FP32 case on an n x n lattice (n = 2048 for the
   throughput case, n = 256 for its oracle-sized copy): R = n / 8, eps_r = 4,
   mu_r = 2, dpsi = 2, b = 0.5 sqrt(|E|), Kq = 5.6893 / n^2 (W0 at d = 2 mm,
@@ -45,4 +47,41 @@ def droplet(n: int = 2048) -> dict:
     return d
 
 
-STEPS = {"droplet64": 2000, "droplet2048": 20000}
+def uneven_cases(n: int = 96, seed: int = 20250109) -> list[dict]:
+    """The uneven batch: n physical cases drawn with numpy's default_rng(seed).
+    nx from {128, 192, ..., 768}; ny uniform over the multiples of 64 in
+    [nx, 2 nx]; electrode gap d ~ U[0.5, 2] mm; dpsi ~ U[0.5, 4] kV; eps_r from
+    {0.5, 1, 2, 4}; mu_r from {0.5, 1, 2}.  Each entry holds the arguments of
+    ehdlb_params_from_physical (R = nx / 5 there); 10000 steps each."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        nx = int(rng.choice(np.arange(128, 769, 64)))
+        ny = int(rng.choice(np.arange(nx, 2 * nx + 1, 64)))
+        out.append(dict(nx=nx, ny=ny, d_mm=float(rng.uniform(0.5, 2.0)),
+                        dpsi_kV=float(rng.uniform(0.5, 4.0)),
+                        eps_r=float(rng.choice([0.5, 1.0, 2.0, 4.0])),
+                        mu_r=float(rng.choice([0.5, 1.0, 2.0]))))
+    return out
+
+
+def arrivals(n: int = 1000, rate_per_s: float = 1.0, seed: int = 20250109,
+             side_min: int = 128, side_max_factor: float = 8.0) -> list[dict]:
+    """A stream of served cases: Poisson arrival times at rate_per_s, square
+    lattices of side side_min * side_max_factor^U (U ~ U[0, 1]) rounded to a
+    multiple of 64, physical parameters drawn as in uneven_cases."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
+    out = []
+    for i in range(n):
+        side = int(max(64, round(side_min * side_max_factor ** rng.uniform() / 64) * 64))
+        out.append(dict(t=float(t[i]), nx=side, ny=side, d_mm=float(rng.uniform(0.5, 2.0)),
+                        dpsi_kV=float(rng.uniform(0.5, 4.0)),
+                        eps_r=float(rng.choice([0.5, 1.0, 2.0, 4.0])),
+                        mu_r=float(rng.choice([0.5, 1.0, 2.0]))))
+    return out
+
+
+STEPS = {"droplet64": 2000, "droplet2048": 20000, "uneven": 10000}
