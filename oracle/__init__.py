@@ -21,7 +21,7 @@ SRC = os.path.join(HERE, "ehd_oracle.c")
 LIB = os.path.join(HERE, "libehd_oracle.so")
 
 FIELDS = ["phi", "ux", "uy", "p", "psi", "Ex", "Ey", "cp", "cm", "q"]
-STATE_PER_NODE = 35  # f9 h9 p5 n5 g5 phiu2
+STATE_PER_NODE = 35  # f9 h9 p5 n5 g5 phiu2 (43 with ions on D2Q9: p9 n9)
 
 _PARAM_FIELDS = [
     ("tau_f", C.c_double), ("rho_ratio", C.c_double), ("eta_ratio", C.c_double),
@@ -44,7 +44,7 @@ _PARAM_FIELDS = [
     ("init_psi_zero", C.c_int),
     ("freeze_E", C.c_int), ("E_frozen_x", C.c_double), ("E_frozen_y", C.c_double),
     ("s_free", C.c_double), ("bgk", C.c_int),
-    ("side_walls", C.c_int),
+    ("ion_lattice", C.c_int), ("side_walls", C.c_int),
 ]
 
 
@@ -60,7 +60,7 @@ DEFAULTS = dict(
     Kq=5.6893 / 64**2, vartheta=0.3, psi_src_literal=0, psi_anode=1.0, psi_cathode=0.0,
     sweeps_min=1, sweeps_max=200, sweep_tol=1e-8, init_sweeps_max=100000,
     init_sweeps_fixed=-1, init_psi_zero=0, freeze_E=0, E_frozen_x=0.0,
-    E_frozen_y=0.0, s_free=1.0, bgk=0, side_walls=0,
+    E_frozen_y=0.0, s_free=1.0, bgk=0, ion_lattice=5, side_walls=0,
 )
 
 
@@ -105,6 +105,9 @@ def lib():
         L.orc_heq.argtypes = [C.c_double] * 3 + [dp]
         L.orc_Hsrc.argtypes = [C.c_double] * 7 + [dp]
         L.orc_ion_eq.argtypes = [C.c_double] * 3 + [dp]
+        L.orc_ion_eq9.argtypes = [C.c_double] * 3 + [dp]
+        L.orc_state_per_node.argtypes = [C.c_void_p]
+        L.orc_state_per_node.restype = C.c_int
         L.orc_geq.argtypes = [C.c_double, dp]
         L.orc_mrt.argtypes = [C.c_int, dp, dp, dp, dp, dp]
         L.orc_onsager.argtypes = [C.c_double, C.c_int]
@@ -187,13 +190,13 @@ class Oracle:
         return {k: out[i] for i, k in enumerate(FIELDS)}
 
     def state(self) -> np.ndarray:
-        out = np.zeros((self.ny, self.nx, STATE_PER_NODE))
+        out = np.zeros((self.ny, self.nx, lib().orc_state_per_node(self._h)))
         lib().orc_get_state(self._h, _dp(out))
         return out
 
     def set_state(self, s: np.ndarray):
         s = np.ascontiguousarray(s, dtype=np.float64)
-        assert s.shape == (self.ny, self.nx, STATE_PER_NODE)
+        assert s.shape == (self.ny, self.nx, lib().orc_state_per_node(self._h))
         lib().orc_set_state(self._h, _dp(s))
 
     def sum_phi(self) -> float:
@@ -228,8 +231,10 @@ def Hsrc(phi, W, dpux, dpuy, gx, gy, eps=0.0):
     o = np.zeros(9); lib().orc_Hsrc(phi, W, dpux, dpuy, gx, gy, eps, _dp(o)); return o
 
 
-def ion_eq(c, ux, uy):
-    o = np.zeros(5); lib().orc_ion_eq(c, ux, uy, _dp(o)); return o
+def ion_eq(c, ux, uy, q=5):
+    o = np.zeros(q)
+    (lib().orc_ion_eq9 if q == 9 else lib().orc_ion_eq)(c, ux, uy, _dp(o))
+    return o
 
 
 def geq(psi):

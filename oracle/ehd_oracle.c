@@ -23,7 +23,8 @@
  *   O10 p, n collisions (Eq. 34-40).  O11 streaming with wall rules (Eq. 64).
  *
  * Readings of points the paper leaves open (all shared with the GPU library):
- *  - ions on D2Q5 with the matrix N of Eq. 46 and weights of Eq. 26;
+ *  - ions on D2Q5 with the matrix N of Eq. 46 and weights of Eq. 26
+ *    (ion_lattice = 9: on D2Q9 with M and the weights of Eq. 25, as printed);
  *  - NS: the viscous rates are those of the second-order moments (rows 3-5 of
  *    Eq. 28) besides the s1 = s2 of Eq. 55; every other rate is s_free;
  *  - variable permittivity: the potential source is
@@ -243,6 +244,19 @@ void orc_ion_eq(double c, double ux, double uy, double *out)
         out[i] = w5[i] * c * (1.0 + (cx5[i] * ux + cy5[i] * uy) / cs2);
 }
 
+void orc_ion_eq9(double c, double ux, double uy, double *out)
+{
+    for (int i = 0; i < 9; ++i)
+        out[i] = w9[i] * c * (1.0 + (cx9[i] * ux + cy9[i] * uy) / cs2);
+}
+
+/* Eq. 38 on the ion lattice of the context (Q = 5 or 9). */
+static void ion_eq(int Q, double c, double ux, double uy, double *out)
+{
+    if (Q == 9) orc_ion_eq9(c, ux, uy, out);
+    else orc_ion_eq(c, ux, uy, out);
+}
+
 /* Eq. 45 */
 void orc_geq(double psi, double *out)
 {
@@ -296,6 +310,7 @@ struct orc_ctx {
     long nn;
     orc_params P;
     double tau_g;
+    int qi;                         /* ion lattice: 5 or 9 */
     double *f, *h, *p, *n, *g;      /* post-streaming populations */
     double *fs, *hs, *ps, *ns, *gs; /* post-collision populations */
     double *phiu_prev;              /* (phi u)(t - 1), 2 per node */
@@ -366,13 +381,14 @@ orc_ctx *orc_create(int nx, int ny, const orc_params *P)
     long nn = c->nn;
     c->f = alloc(9 * nn);
     c->h = alloc(9 * nn);
-    c->p = alloc(5 * nn);
-    c->n = alloc(5 * nn);
+    c->qi = P->ion_lattice == 9 ? 9 : 5;
+    c->p = alloc(9 * nn);
+    c->n = alloc(9 * nn);
     c->g = alloc(5 * nn);
     c->fs = alloc(9 * nn);
     c->hs = alloc(9 * nn);
-    c->ps = alloc(5 * nn);
-    c->ns = alloc(5 * nn);
+    c->ps = alloc(9 * nn);
+    c->ns = alloc(9 * nn);
     c->gs = alloc(5 * nn);
     c->phiu_prev = alloc(2 * nn);
     c->phi = alloc(nn);
@@ -456,6 +472,46 @@ static void stream5(const orc_ctx *c, const double *post, double *out,
         }
 }
 
+/* Pull-stream a D2Q9 ion field: a link crossing the bottom (top) wall takes
+ * anti-bounce-back out_i = -post_opp(i) + 2 w_i v_wall (mode 0) or
+ * bounce-back (mode 1), as stream5 does; a link that crosses only a side
+ * wall bounces back; a diagonal link through a corner takes the electrode's
+ * rule. */
+static void stream9_ion(const orc_ctx *c, const double *post, double *out,
+                        int mode_bot, const double *vbot, int mode_top,
+                        const double *vtop)
+{
+    const int walls = c->P.side_walls;
+#pragma omp parallel for
+    for (int y = 0; y < c->ny; ++y)
+        for (int x = 0; x < c->nx; ++x) {
+            long k = idx(c, x, y);
+            for (int i = 0; i < 9; ++i) {
+                int sy = y - cy9[i], sx = x - cx9[i];
+                if (sy < 0 || sy >= c->ny) {
+                    int bottom = sy < 0;
+                    int mode = bottom ? mode_bot : mode_top;
+                    double v = bottom ? vbot[x] : vtop[x];
+                    double a = post[k * 9 + opp9[i]];
+                    out[k * 9 + i] = mode == 0 ? -a + 2.0 * w9[i] * v : a;
+                } else if (walls && (sx < 0 || sx >= c->nx)) {
+                    out[k * 9 + i] = post[k * 9 + opp9[i]];
+                } else {
+                    out[k * 9 + i] = post[idx(c, wrapx(c, sx), sy) * 9 + i];
+                }
+            }
+        }
+}
+
+/* Ion streaming on the context's lattice. */
+static void stream_ion(const orc_ctx *c, const double *post, double *out,
+                       int mode_bot, const double *vbot, int mode_top,
+                       const double *vtop)
+{
+    if (c->qi == 9) stream9_ion(c, post, out, mode_bot, vbot, mode_top, vtop);
+    else stream5(c, post, out, mode_bot, vbot, mode_top, vtop);
+}
+
 /* ---- potential (Eq. 44-50) --------------------------------------------- */
 
 static double psi_of(const double *g) /* Eq. 49 */
@@ -479,6 +535,14 @@ static void E_of(const double *g, double tau_g, double *Ex, double *Ey) /* Eq. 5
 static void rates5(const orc_params *P, double tau, double *s)
 {
     for (int k = 0; k < 5; ++k) s[k] = P->bgk ? 1.0 / tau : P->s_free;
+    s[1] = s[2] = 1.0 / tau;
+}
+
+/* Ion rates of Eq. 36-37 on Q = 5 or 9: the first moments (rows 1, 2 of N or
+ * M) relax at 1/tau, the others at s_free (all at 1/tau with bgk). */
+static void rates_ion(const orc_params *P, int Q, double tau, double *s)
+{
+    for (int k = 0; k < Q; ++k) s[k] = P->bgk ? 1.0 / tau : P->s_free;
     s[1] = s[2] = 1.0 / tau;
 }
 
@@ -554,9 +618,9 @@ static void macro_phi_q(orc_ctx *c)
         for (int i = 0; i < 9; ++i) s += c->h[9 * k + i]; /* Eq. 33 */
         c->phi[k] = s;
         double sp = 0.0, sn = 0.0;
-        for (int i = 0; i < 5; ++i) {
-            sp += c->p[5 * k + i];
-            sn += c->n[5 * k + i];
+        for (int i = 0; i < c->qi; ++i) {
+            sp += c->p[c->qi * k + i];
+            sn += c->n[c->qi * k + i];
         }
         c->q[k] = sp - sn;
     }
@@ -589,7 +653,7 @@ int orc_init(orc_ctx *c)
             orc_heq(phi0, 0.0, 0.0, c->h + 9 * k);
             double rho = 1.0 + (P->rho_ratio - 1.0) * phi0;
             orc_feq(0.0, rho, 0.0, 0.0, c->f + 9 * k);
-            for (int i = 0; i < 5; ++i) c->p[5 * k + i] = c->n[5 * k + i] = 0.0;
+            for (int i = 0; i < c->qi; ++i) c->p[c->qi * k + i] = c->n[c->qi * k + i] = 0.0;
             c->phiu_prev[2 * k] = c->phiu_prev[2 * k + 1] = 0.0;
             /* potential: linear profile between the half-way electrodes with
              * the first-order non-equilibrium part that makes Eq. 50 return
@@ -624,12 +688,12 @@ int orc_init(orc_ctx *c)
             E_of(c->g + 5 * k, c->tau_g, &Ex, &Ey);
         }
         double ceq = P->c_init_scale * n_eq_of(P, sqrt(Ex * Ex + Ey * Ey));
-        orc_ion_eq(ceq, 0.0, 0.0, c->p + 5 * k);
-        orc_ion_eq(ceq, 0.0, 0.0, c->n + 5 * k);
+        ion_eq(c->qi, ceq, 0.0, 0.0, c->p + c->qi * k);
+        ion_eq(c->qi, ceq, 0.0, 0.0, c->n + c->qi * k);
         double sp = 0.0, sn = 0.0;
-        for (int i = 0; i < 5; ++i) {
-            sp += c->p[5 * k + i];
-            sn += c->n[5 * k + i];
+        for (int i = 0; i < c->qi; ++i) {
+            sp += c->p[c->qi * k + i];
+            sn += c->n[c->qi * k + i];
         }
         c->snap[ORC_PHI * c->nn + k] = c->phi[k];
         c->snap[ORC_UX * c->nn + k] = 0.0;
@@ -679,7 +743,8 @@ static int step_once(orc_ctx *c, int forced, int *used, double *resid)
 #pragma omp parallel for
     for (long k = 0; k < nn; ++k) {
         const double *f = c->f + 9 * k, *h = c->h + 9 * k;
-        const double *pp = c->p + 5 * k, *np = c->n + 5 * k;
+        const int Q = c->qi;
+        const double *pp = c->p + Q * k, *np = c->n + Q * k;
         double phi = c->phi[k];
         double gx = c->gpx[k], gy = c->gpy[k], lap = c->lap[k];
 
@@ -706,7 +771,7 @@ static int step_once(orc_ctx *c, int forced, int *used, double *resid)
 
         /* O5: Onsager F and the implicit reaction, Eq. 5, 42-43 */
         double sp = 0.0, sn = 0.0;
-        for (int i = 0; i < 5; ++i) {
+        for (int i = 0; i < Q; ++i) {
             sp += pp[i];
             sn += np[i];
         }
@@ -769,38 +834,42 @@ static int step_once(orc_ctx *c, int forced, int *used, double *resid)
         c->phiu_prev[2 * k] = phi * ux;
         c->phiu_prev[2 * k + 1] = phi * uy;
 
-        /* O10: ions, Eq. 34-40 (G of Eq. 40 with grad psi = -E) */
+        /* O10: ions, Eq. 34-40 (G of Eq. 40 with grad psi = -E), on the
+         * D2Q5 lattice (N of Eq. 46, weights of Eq. 26) or, ion_lattice = 9,
+         * on D2Q9 (M of Eq. 28, weights of Eq. 25); s1 = s2 = 1/tau (Eq. 37) */
+        const int *cxq = Q == 9 ? cx9 : cx5, *cyq = Q == 9 ? cy9 : cy5;
+        const double *wq = Q == 9 ? w9 : w5;
         double gpsx = -Ex, gpsy = -Ey;
-        double s5p[5], s5n[5];
-        rates5(P, 0.5 + Dp / cs2, s5p); /* Eq. 37 */
-        rates5(P, 0.5 + Dm / cs2, s5n);
-        double eq5[5], G5[5], RL[5], d5[5], a5[5], b5[5], c5[5];
-        orc_ion_eq(cp, ux, uy, eq5);
-        for (int i = 0; i < 5; ++i) {
-            double cg = cx5[i] * gpsx + cy5[i] * gpsy;
-            double cF = cx5[i] * Fx + cy5[i] * Fy;
-            G5[i] = w5[i] * cg * mup * cp / cs2;
-            RL[i] = w5[i] * R + (P->ion_L_term ? w5[i] * cF * cp / cs2 : 0.0);
-            d5[i] = pp[i] - eq5[i];
+        double sqp[9], sqn[9];
+        rates_ion(P, Q, 0.5 + Dp / cs2, sqp);
+        rates_ion(P, Q, 0.5 + Dm / cs2, sqn);
+        double eqq[9], Gq[9], RL[9], dq[9], aq[9], bq[9], cq[9];
+        ion_eq(Q, cp, ux, uy, eqq);
+        for (int i = 0; i < Q; ++i) {
+            double cg = cxq[i] * gpsx + cyq[i] * gpsy;
+            double cF = cxq[i] * Fx + cyq[i] * Fy;
+            Gq[i] = wq[i] * cg * mup * cp / cs2;
+            RL[i] = wq[i] * R + (P->ion_L_term ? wq[i] * cF * cp / cs2 : 0.0);
+            dq[i] = pp[i] - eqq[i];
         }
-        msm(5, s5p, d5, a5);
-        msm_half(5, s5p, RL, b5);
-        msm(5, s5p, G5, c5);
-        for (int i = 0; i < 5; ++i)
-            c->ps[5 * k + i] = pp[i] - a5[i] + b5[i] - c5[i];   /* Eq. 34 */
-        orc_ion_eq(cm, ux, uy, eq5);
-        for (int i = 0; i < 5; ++i) {
-            double cg = cx5[i] * gpsx + cy5[i] * gpsy;
-            double cF = cx5[i] * Fx + cy5[i] * Fy;
-            G5[i] = w5[i] * cg * mum * cm / cs2;
-            RL[i] = w5[i] * R + (P->ion_L_term ? w5[i] * cF * cm / cs2 : 0.0);
-            d5[i] = np[i] - eq5[i];
+        msm(Q, sqp, dq, aq);
+        msm_half(Q, sqp, RL, bq);
+        msm(Q, sqp, Gq, cq);
+        for (int i = 0; i < Q; ++i)
+            c->ps[Q * k + i] = pp[i] - aq[i] + bq[i] - cq[i];   /* Eq. 34 */
+        ion_eq(Q, cm, ux, uy, eqq);
+        for (int i = 0; i < Q; ++i) {
+            double cg = cxq[i] * gpsx + cyq[i] * gpsy;
+            double cF = cxq[i] * Fx + cyq[i] * Fy;
+            Gq[i] = wq[i] * cg * mum * cm / cs2;
+            RL[i] = wq[i] * R + (P->ion_L_term ? wq[i] * cF * cm / cs2 : 0.0);
+            dq[i] = np[i] - eqq[i];
         }
-        msm(5, s5n, d5, a5);
-        msm_half(5, s5n, RL, b5);
-        msm(5, s5n, G5, c5);
-        for (int i = 0; i < 5; ++i)
-            c->ns[5 * k + i] = np[i] - a5[i] + b5[i] + c5[i];   /* Eq. 35 */
+        msm(Q, sqn, dq, aq);
+        msm_half(Q, sqn, RL, bq);
+        msm(Q, sqn, Gq, cq);
+        for (int i = 0; i < Q; ++i)
+            c->ns[Q * k + i] = np[i] - aq[i] + bq[i] + cq[i];   /* Eq. 35 */
 
         /* snapshot of time t */
         c->snap[ORC_PHI * nn + k] = phi;
@@ -824,20 +893,20 @@ static int step_once(orc_ctx *c, int forced, int *used, double *resid)
     double *tmp_t = (double *)malloc(sizeof(double) * c->nx);
     for (int x = 0; x < c->nx; ++x) zero[x] = zero2[x] = 0.0;
     if (P->ion_bc == 2) {
-        stream5(c, c->ps, c->p, 1, zero, 1, zero2);
-        stream5(c, c->ns, c->n, 1, zero, 1, zero2);
+        stream_ion(c, c->ps, c->p, 1, zero, 1, zero2);
+        stream_ion(c, c->ns, c->n, 1, zero, 1, zero2);
     } else if (P->ion_bc == 1) {
-        stream5(c, c->ps, c->p, 0, zero, 0, zero2);
-        stream5(c, c->ns, c->n, 0, zero, 0, zero2);
+        stream_ion(c, c->ps, c->p, 0, zero, 0, zero2);
+        stream_ion(c, c->ns, c->n, 0, zero, 0, zero2);
     } else {
         /* cations: repelled by the anode (c = 0), attracted by the cathode
          * (zero gradient, wall value from the node) */
         for (int x = 0; x < c->nx; ++x)
             tmp_t[x] = cpf[idx(c, x, c->ny - 1)];
-        stream5(c, c->ps, c->p, 0, zero, 0, tmp_t);
+        stream_ion(c, c->ps, c->p, 0, zero, 0, tmp_t);
         /* anions: attracted by the anode, repelled by the cathode */
         for (int x = 0; x < c->nx; ++x) tmp_b[x] = cmf[idx(c, x, 0)];
-        stream5(c, c->ns, c->n, 0, tmp_b, 0, zero2);
+        stream_ion(c, c->ns, c->n, 0, tmp_b, 0, zero2);
     }
     free(tmp_b);
     free(tmp_t);
@@ -864,29 +933,33 @@ void orc_get_fields(const orc_ctx *c, double *out)
     memcpy(out, c->snap, sizeof(double) * ORC_NFIELDS * c->nn);
 }
 
+int orc_state_per_node(const orc_ctx *c) { return 25 + 2 * c->qi; }
+
 void orc_get_state(const orc_ctx *c, double *out)
 {
+    const int Q = c->qi, S = 25 + 2 * Q;
     for (long k = 0; k < c->nn; ++k) {
-        double *o = out + 35 * k;
+        double *o = out + S * k;
         memcpy(o, c->f + 9 * k, 9 * sizeof(double));
         memcpy(o + 9, c->h + 9 * k, 9 * sizeof(double));
-        memcpy(o + 18, c->p + 5 * k, 5 * sizeof(double));
-        memcpy(o + 23, c->n + 5 * k, 5 * sizeof(double));
-        memcpy(o + 28, c->g + 5 * k, 5 * sizeof(double));
-        memcpy(o + 33, c->phiu_prev + 2 * k, 2 * sizeof(double));
+        memcpy(o + 18, c->p + Q * k, Q * sizeof(double));
+        memcpy(o + 18 + Q, c->n + Q * k, Q * sizeof(double));
+        memcpy(o + 18 + 2 * Q, c->g + 5 * k, 5 * sizeof(double));
+        memcpy(o + 23 + 2 * Q, c->phiu_prev + 2 * k, 2 * sizeof(double));
     }
 }
 
 void orc_set_state(orc_ctx *c, const double *in)
 {
+    const int Q = c->qi, S = 25 + 2 * Q;
     for (long k = 0; k < c->nn; ++k) {
-        const double *o = in + 35 * k;
+        const double *o = in + S * k;
         memcpy(c->f + 9 * k, o, 9 * sizeof(double));
         memcpy(c->h + 9 * k, o + 9, 9 * sizeof(double));
-        memcpy(c->p + 5 * k, o + 18, 5 * sizeof(double));
-        memcpy(c->n + 5 * k, o + 23, 5 * sizeof(double));
-        memcpy(c->g + 5 * k, o + 28, 5 * sizeof(double));
-        memcpy(c->phiu_prev + 2 * k, o + 33, 2 * sizeof(double));
+        memcpy(c->p + Q * k, o + 18, Q * sizeof(double));
+        memcpy(c->n + Q * k, o + 18 + Q, Q * sizeof(double));
+        memcpy(c->g + 5 * k, o + 18 + 2 * Q, 5 * sizeof(double));
+        memcpy(c->phiu_prev + 2 * k, o + 23 + 2 * Q, 2 * sizeof(double));
     }
 }
 
@@ -933,6 +1006,7 @@ void orc_params_from_physical(orc_params *P, int nx, int ny, double d_mm,
     P->init_sweeps_max = 0; P->init_sweeps_fixed = 0; P->init_psi_zero = 0;
     P->freeze_E = 0;
     P->s_free = 1.0; P->bgk = 0;
+    P->ion_lattice = 5; P->side_walls = 0;
 }
 
 /* ---- deformation factor, Eq. 63 ------------------------------------------ *

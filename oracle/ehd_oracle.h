@@ -72,6 +72,10 @@ typedef struct orc_params {
     double s_free;       /* the free relaxation rates (1.0 in Sec. 6) */
     int bgk;             /* 1: every rate equals the hydrodynamic one */
     /* geometry */
+    int ion_lattice;     /* 5: ions on D2Q5 with N (Eq. 46) and the weights of
+                            Eq. 26 (the reading used by default); 9: on D2Q9
+                            with M (Eq. 28) and the weights of Eq. 25, as
+                            Eq. 34-36 print them */
     int side_walls;      /* 0: periodic x; 1: solid walls half-way left of
                             x = 0 and right of x = nx - 1 with the "other
                             boundaries" rules of Eq. 64: u = 0, zero normal
@@ -100,6 +104,9 @@ int orc_step(orc_ctx *c, int nsteps, const int *forced, int *counts, double *res
  * out[ORC_NFIELDS * ny * nx]. */
 void orc_get_fields(const orc_ctx *c, double *out);
 /* Raw populations: f[9], h[9], p[5], n[5], g[5], phiu_prev[2] per node. */
+/* State per node: f9 h9 p[Q] n[Q] g5 (phi u)2, Q = ion_lattice: 35 doubles
+ * (Q = 5) or 43 (Q = 9). */
+int orc_state_per_node(const orc_ctx *c);
 void orc_get_state(const orc_ctx *c, double *out);
 void orc_set_state(orc_ctx *c, const double *in);
 double orc_sum_phi(const orc_ctx *c);   /* sum of phi = sum h over all nodes */
@@ -114,6 +121,8 @@ void orc_heq(double phi, double ux, double uy, double *out9);
 void orc_Hsrc(double phi, double W, double dphiux, double dphiuy,
               double gx, double gy, double eps, double *out9);
 void orc_ion_eq(double c, double ux, double uy, double *out5);
+/* Eq. 38 on D2Q9 (weights of Eq. 25). */
+void orc_ion_eq9(double c, double ux, double uy, double *out9);
 void orc_geq(double psi, double *out5);
 /* One MRT collision x* = x - Minv S M (x - xeq) + Minv (I - S/2) M src,
  * Q = 9 (matrix of Eq. 28) or 5 (Eq. 46). */

@@ -582,3 +582,75 @@ def test_side_walls_keep_a_centred_case_mirror_symmetric_and_conserve_phi():
                                    atol=1e-12 * max(1e-12, np.max(np.abs(a))), err_msg=k)
     # no flux through the side walls: the wall columns do not leak ions
     assert np.max(np.abs(f["ux"])) > 0
+
+
+# ---- ions on D2Q9 (Eq. 34-38 as printed, ion_lattice = 9) -------------------------------
+
+def _ion_slices(q):
+    return slice(18, 18 + q), slice(18 + q, 18 + 2 * q)
+
+
+def test_d2q9_ion_equilibrium_moments():
+    c, ux, uy = 1.3, 0.02, -0.01
+    e = O.ion_eq(c, ux, uy, q=9)
+    assert abs(e.sum() - c) < 1e-15
+    assert abs((CX9 * e).sum() - c * ux) < 1e-15 and abs((CY9 * e).sum() - c * uy) < 1e-15
+    # the second moments of Eq. 38 on D2Q9 are those of D2Q5: c cs^2 along
+    # each axis, no cross term
+    assert abs((CX9**2 * e).sum() - c * CS2) < 1e-15 and abs((CX9 * CY9 * e).sum()) < 1e-15
+    assert np.allclose(W9, [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+@pytest.mark.parametrize("scale", [0.0, 2.0])
+def test_d2q9_ions_reach_n_eq_in_a_uniform_field(scale):
+    E0, cb = 0.3, 1.0
+    o = O.Oracle(8, 8, dict(QUIET, ion_lattice=9, onsager_form=0, k_d=1.0, k_r=1.0, onsager_cb=cb,
+                            ion_bc=2, E_frozen_x=E0, c_init_scale=scale))
+    o.step(200)
+    f = o.fields()
+    neq = np.sqrt(special.i1(4 * cb * np.sqrt(E0)) / (2 * cb * np.sqrt(E0)))
+    np.testing.assert_allclose(f["cp"], neq, rtol=1e-12)
+    np.testing.assert_allclose(f["cm"], neq, rtol=1e-12)
+
+
+def test_d2q9_and_d2q5_ions_share_centroid_and_spread_of_a_drifting_blob():
+    # for a profile that varies along y only (x periodic), the cy moments of
+    # Eq. 34-37 up to second order are the same on both lattices, and the
+    # electrode bounce-back maps the cy = +1 group to the cy = -1 group on
+    # both, so the mean and the variance of the blob evolve identically
+    # (the mean at mu E, Eq. 40)
+    nx, ny, E0 = 4, 64, 0.02
+    y = np.arange(ny)
+    bump = np.exp(-0.5 * ((y - 24.0) / 3.0) ** 2)
+    moments = {}
+    for q, w in ((5, W5), (9, W9)):
+        o = O.Oracle(nx, ny, dict(QUIET, ion_lattice=q, ion_bc=2, E_frozen_y=E0, einstein_D=0))
+        s = o.state()
+        sp, sn = _ion_slices(q)
+        s[:, :, sp] += w[None, None, :] * bump[:, None, None]
+        o.set_state(s)
+        o.step(150)
+        st = o.state()
+        cp = st[:, :, sp].sum(-1).sum(1)
+        m0 = cp.sum()
+        m1 = (cp * y).sum() / m0
+        m2 = (cp * (y - m1) ** 2).sum() / m0
+        moments[q] = (m0, m1, m2)
+    for a, b in zip(moments[5], moments[9]):
+        assert abs(a - b) <= 1e-11 * max(1.0, abs(a))
+    assert moments[9][2] > 9.0 + 2 * 0.01 * 100      # it does spread (D = 0.01)
+
+
+def test_d2q9_ions_conserved_between_zero_flux_electrodes():
+    # ion_bc = 2 (bounce-back at both electrodes), no reaction: every
+    # population, diagonal ones included, comes back at the wall
+    o = O.Oracle(16, 12, dict(QUIET, ion_lattice=9, ion_bc=2, freeze_E=1, E_frozen_y=0.05,
+                              E_frozen_x=0.01, k_d=0.0, k_r=0.0, c0=1.0, onsager_form=2))
+    sp, sn = _ion_slices(9)
+    s0 = o.state()
+    m0 = s0[:, :, sp].sum()
+    o.step(300)
+    s1 = o.state()
+    assert abs(s1[:, :, sp].sum() - m0) <= 1e-12 * m0
+    f = o.fields()
+    assert f["cp"][-1].mean() > f["cp"][0].mean()   # cations pile up downfield (E_y > 0)
