@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define EHDLB_ABI_VERSION 2
+#define EHDLB_ABI_VERSION 3
 
 typedef struct ehdlb_ctx ehdlb_ctx;
 
@@ -128,6 +128,14 @@ typedef struct ehdlb_params {
     /* collision */
     double s_free;       /* the free MRT rates, in (0, 2); 1.0 in Sec. 6 */
     int bgk;             /* 1: all rates equal the hydrodynamic one */
+    /* ion lattice */
+    int ion_lattice;     /* 5 (default): ions on D2Q5 with N (Eq. 46) and the
+                            weights of Eq. 26; 9: on D2Q9 with M (Eq. 28) and
+                            the weights of Eq. 25, as Eq. 34-36 print them
+                            (s1 = s2 = 1/tau, Eq. 37, other rates free; a link
+                            through an electrode, corners included, takes the
+                            electrode's rule).  The state then holds 43 doubles
+                            per node instead of 35. */
     /* geometry */
     int side_walls;      /* 0: periodic x (default); 1: solid walls half-way
                             left of x = 0 and right of x = nx - 1 with the
@@ -220,10 +228,13 @@ int ehdlb_get_fields(ehdlb_ctx *c, unsigned mask, double *dst,
 /* Sweep counts of the steps of the last ehdlb_step call, n <= its nsteps. */
 int ehdlb_get_sweep_counts(ehdlb_ctx *c, int *dst, int n);
 
-/* Raw state as 35 doubles per node, node-major [ny][nx][35]: f0..f8, h0..h8,
- * p0..p4, n0..n4, g0..g4 (Eq. 25-26 order), (phi u)(t-1) x and y.  The
- * library does not store f0 and g0 (no other quantity depends on them):
- * get_state writes 0 there and set_state ignores them.  len in doubles. */
+/* Raw state as S doubles per node, node-major [ny][nx][S]: f0..f8, h0..h8,
+ * the ion populations p and n (Eq. 25-26 order), g0..g4, (phi u)(t-1) x and
+ * y; S = 35 with ions on D2Q5 (p0..p4, n0..n4) and 43 on D2Q9 (p0..p8,
+ * n0..n8); ehdlb_state_len gives S nx ny for the ion lattice of the last
+ * ehdlb_set_params.  The library does not store f0 and g0 (no other quantity
+ * depends on them): get_state writes 0 there and set_state ignores them.
+ * len in doubles. */
 size_t ehdlb_state_len(const ehdlb_ctx *c);
 int ehdlb_get_state(ehdlb_ctx *c, double *dst, size_t len);
 int ehdlb_set_state(ehdlb_ctx *c, const double *src, size_t len);
@@ -344,7 +355,8 @@ int ehdlb_batch_step(ehdlb_batch *b, int nsteps, ehdlb_batch_stats *st);
  * [field][ny][nx] for the fields of mask in order). */
 int ehdlb_batch_get_fields(ehdlb_batch *b, int id, unsigned mask, double *dst, size_t dst_len);
 
-/* State of case id as ehdlb_get_state (35 doubles per node). */
+/* State of case id as ehdlb_get_state (35 doubles per node: batch cases
+ * have ions on D2Q5). */
 int ehdlb_batch_get_state(ehdlb_batch *b, int id, double *dst, size_t len);
 
 /* D of Eq. 63 (as ehdlb_deformation) of n cases from their last snapshots,

@@ -73,6 +73,7 @@ std::string validate(const ehdlb_params *p)
     if (!(p->s_free > 0.0 && p->s_free < 2.0)) return "s_free must lie in (0, 2)";
     if (!(p->c_init_scale >= 0.0) || !(p->c0 >= 0.0)) return "initial concentrations must be >= 0";
     if (p->side_walls != 0 && p->side_walls != 1) return "side_walls must be 0 or 1";
+    if (p->ion_lattice != 5 && p->ion_lattice != 9) return "ion_lattice must be 5 or 9";
     return "";
 }
 
@@ -101,6 +102,7 @@ int ehdlb_params_default(ehdlb_params *p)
     p->freeze_E = 0; p->E_frozen_x = 0.0; p->E_frozen_y = 0.0;
     p->s_free = 1.0; p->bgk = 0;
     p->side_walls = 0;
+    p->ion_lattice = 5;
     return EHDLB_OK;
 }
 
@@ -206,7 +208,10 @@ int ehdlb_get_sweep_counts(ehdlb_ctx *c, int *dst, int n)
     return c->solver->get_counts(dst, n, c->err);
 }
 
-size_t ehdlb_state_len(const ehdlb_ctx *c) { return c ? (size_t)35 * c->nx * c->ny : 0; }
+size_t ehdlb_state_len(const ehdlb_ctx *c)
+{
+    return c ? (size_t)c->solver->state_per_node() * c->nx * c->ny : 0;
+}
 
 int ehdlb_get_state(ehdlb_ctx *c, double *dst, size_t len)
 {

@@ -278,8 +278,8 @@ template <typename T, typename S> class Batch : public BatchBase {
             err = "batch cases take the batch's fixed sweeps per step (sweeps_min = sweeps_max)";
             return EHDLB_EINVAL;
         }
-        if (p.freeze_E || p.side_walls || p.init_sweeps_fixed < 0) {
-            err = "batch cases need freeze_E = 0, side_walls = 0 and init_sweeps_fixed >= 0";
+        if (p.freeze_E || p.side_walls || p.init_sweeps_fixed < 0 || p.ion_lattice == 9) {
+            err = "batch cases need freeze_E = 0, side_walls = 0, ions on D2Q5 and init_sweeps_fixed >= 0";
             return EHDLB_EINVAL;
         }
         if (Sv::footprint(nx, ny) > arena_.largest_free()) {

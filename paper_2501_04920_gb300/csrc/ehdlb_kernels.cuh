@@ -13,7 +13,7 @@
 //        reference's gradient and chemical potential are evaluated once, in
 //        double; near equilibrium the chemical potential of Eq. 13 is a small
 //        residual of O(1) terms, which float cannot resolve from phi ~ 1 itself.
-//   p, n : 5 planes each (Eq. 34-35, D2Q5).
+//   p, n : 5 planes each (Eq. 34-35, D2Q5), or 9 each on D2Q9 (QI = 9).
 //   g  : 4 planes, g1..g4 of Eq. 44, stored as g_i - w_i psi_lin(y) where
 //        psi_lin is the linear profile between the electrodes; g0 is not
 //        stored (psi (Eq. 49) and E (Eq. 50) do not read it, and the diagonal
@@ -112,7 +112,8 @@ struct Control {
                        // read by the batched kernels, the single-lattice host tracks its own)
 };
 
-// One allocation of 27 planes: f at +0, h at +8 nn, p at +17 nn, n at +22 nn.
+// One allocation of 17 + 2 QI planes (QI = 5 or 9 ion populations): f at +0,
+// h at +8 nn, p at +17 nn, n at +(17 + QI) nn.
 template <typename S> struct Pops {
     S *f;   // 8 planes
     S *h;   // 9 planes (h_i - w_i phi_ref)
@@ -357,7 +358,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // the main kernel).  With init_ctl the first thread also opens the step in
 // the control block.
 // Body of k_prep for the block at (bx, by) of the lattice's grid.
-template <typename T, typename S>
+template <typename T, typename S, int QI = 5>
 __device__ __forceinline__ void prep_body(const DevP<T> &P, const S *__restrict__ h, const S *__restrict__ p,
                                           const S *__restrict__ n, const PhiRef<T> &R, T *__restrict__ phig,
                                           T *__restrict__ q, Control *ctl, int fixedK, int kmin, int kmax,
@@ -375,17 +376,17 @@ __device__ __forceinline__ void prep_body(const DevP<T> &P, const S *__restrict_
     }
     if (x >= P.nx || y >= P.ny) return;
     const long long nn = P.nn, k = (long long)y * P.nx + x;
-    S hv[9], pv[5], nv[5];
+    S hv[9], pv[QI], nv[QI];
 #pragma unroll
     for (int i = 0; i < 9; ++i) hv[i] = h[i * nn + k];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) { pv[i] = p[i * nn + k]; nv[i] = n[i * nn + k]; }
+    for (int i = 0; i < QI; ++i) { pv[i] = p[i * nn + k]; nv[i] = n[i * nn + k]; }
     // pairwise: rest, axis pairs, diagonal pairs
     T d = raw<S, T>(hv[0]) + ((((raw<S, T>(hv[1]) + raw<S, T>(hv[3])) + (raw<S, T>(hv[2]) + raw<S, T>(hv[4])))) +
                               ((raw<S, T>(hv[5]) + raw<S, T>(hv[7])) + (raw<S, T>(hv[6]) + raw<S, T>(hv[8]))));
     T sp = T(0), sn = T(0);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) { sp += raw<S, T>(pv[i]); sn += raw<S, T>(nv[i]); }
+    for (int i = 0; i < QI; ++i) { sp += raw<S, T>(pv[i]); sn += raw<S, T>(nv[i]); }
     T qv = sp - sn;   // the rest concentrations of stored p and n cancel
     if constexpr (!kSame<S, T>) { d *= P.isc_h; qv *= P.isc_c; }
     const long long gk = (long long)(y + 1) * P.nx + x;
@@ -401,13 +402,13 @@ __device__ __forceinline__ void prep_body(const DevP<T> &P, const S *__restrict_
 }
 
 // Launch: blockDim (64, 4) over the lattice.
-template <typename T, typename S>
+template <typename T, typename S, int QI = 5>
 __global__ void __launch_bounds__(256) k_prep(const DevP<T> P, const S *__restrict__ h,
                                               const S *__restrict__ p, const S *__restrict__ n,
                                               const PhiRef<T> R, T *__restrict__ phig, T *__restrict__ q,
                                               Control *ctl, int fixedK, int kmin, int kmax, int flips)
 {
-    prep_body<T, S>(P, h, p, n, R, phig, q, ctl, fixedK, kmin, kmax, flips, blockIdx.x, blockIdx.y);
+    prep_body<T, S, QI>(P, h, p, n, R, phig, q, ctl, fixedK, kmin, kmax, flips, blockIdx.x, blockIdx.y);
 }
 
 // One pseudo-time sweep of the potential (Eq. 44-50) at every node: E and
@@ -1021,13 +1022,14 @@ static __global__ void __launch_bounds__(256) k_sweep_decide(const double *__res
     if (j >= ctl->kmax) ctl->done = 1;
 }
 
-// Planes k_main stages per node: f1..f8, h0..h8, p0..p4, n0..n4 (one
-// allocation of 27 planes) and (phi u)(t-1) x, y of type S, then g1..g4 of
-// type T.
-constexpr int MAIN_SPLANES = 27 + 2, MAIN_TPLANES = 4;
-template <typename T, typename S> __host__ __device__ constexpr size_t main_smem_bytes()
+// Planes k_main stages per node: f1..f8, h0..h8, the QI planes of p and of
+// n (one allocation of 17 + 2 QI planes) and (phi u)(t-1) x, y of type S,
+// then g1..g4 of type T.
+template <int QI> __host__ __device__ constexpr int main_splanes() { return 17 + 2 * QI + 2; }
+constexpr int MAIN_TPLANES = 4;
+template <typename T, typename S, int QI = 5> __host__ __device__ constexpr size_t main_smem_bytes()
 {
-    return (sizeof(S) * MAIN_SPLANES + sizeof(T) * MAIN_TPLANES) * 256;
+    return (sizeof(S) * main_splanes<QI>() + sizeof(T) * MAIN_TPLANES) * 256;
 }
 
 // Copy NPL planes of the block's 64 x 4 nodes (x0, y0) to st[plane][256]
@@ -1077,7 +1079,7 @@ __device__ __forceinline__ void stage_planes(E *st, PlaneF plane, int nx, int ny
 // Launch: blockDim (64, 4), dynamic shared memory main_smem_bytes<T, S>().
 // Body of k_main for the block at (bx, by) of the lattice's grid; slot: its
 // partials.
-template <typename T, typename S, bool SNAP, bool FROZEN, bool RESID, bool VEC>
+template <typename T, typename S, bool SNAP, bool FROZEN, bool RESID, bool VEC, int QI = 5>
 __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, const Pops<S> &dst,
                                           const T *__restrict__ gA, const T *__restrict__ gB,
                                           const Control *__restrict__ ctl, const PhiRef<T> &Rf,
@@ -1087,7 +1089,8 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S *st = reinterpret_cast<S *>(smem_raw);
-    T *stg = reinterpret_cast<T *>(smem_raw + sizeof(S) * MAIN_SPLANES * 256);
+    constexpr int NSP = main_splanes<QI>(), NPOP = 17 + 2 * QI;
+    T *stg = reinterpret_cast<T *>(smem_raw + sizeof(S) * NSP * 256);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int x = bx * blockDim.x + threadIdx.x;
     const int y = by * blockDim.y + threadIdx.y;
@@ -1098,8 +1101,9 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
         const T *__restrict__ g = ((ctl->cur0 + ctl->flips) & 1) ? gB : gA;
         const S *pops = src.f, *pu = phiu;
         const int x0 = bx * blockDim.x, y0 = by * blockDim.y;
-        stage_planes<S, MAIN_SPLANES, VEC>(
-            st, [=](int i) { return i < 27 ? pops + i * nn : pu + (i - 27) * nn; }, P.nx, P.ny, x0, y0, tid, inside, k);
+        stage_planes<S, NSP, VEC>(
+            st, [=](int i) { return i < NPOP ? pops + i * nn : pu + (i - NPOP) * nn; }, P.nx, P.ny, x0, y0, tid, inside,
+            k);
         stage_planes<T, MAIN_TPLANES, VEC>(stg, [=](int i) { return g + i * nn; }, P.nx, P.ny, x0, y0, tid, inside, k);
     }
     const T pprev = (RESID && inside) ? psi_prev[k] : T(0);
@@ -1164,19 +1168,27 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
         }
 
         // ---- O5: Onsager dissociation and the implicit reaction (Eq. 5, 42-43) ----
-        T pv[5], nv[5];
+        T pv[QI], nv[QI];
 #pragma unroll
-        for (int i = 0; i < 5; ++i) {
+        for (int i = 0; i < QI; ++i) {
             pv[i] = lds(st + (17 + i) * 256 + tid, P.isc_c);
-            nv[i] = lds(st + (22 + i) * 256 + tid, P.isc_c);
+            nv[i] = lds(st + (17 + QI + i) * 256 + tid, P.isc_c);
             if constexpr (!kSame<S, T>) {
-                const T wc = (i == 0 ? T(1.0 / 3.0) : T(1.0 / 6.0)) * P.cref;
+                const T wc = (QI == 9 ? w9<T>(i) : (i == 0 ? T(1.0 / 3.0) : T(1.0 / 6.0))) * P.cref;
                 pv[i] += wc;
                 nv[i] += wc;
             }
         }
-        const T sp = (((pv[0] + pv[1]) + pv[2]) + pv[3]) + pv[4];
-        const T sn = (((nv[0] + nv[1]) + nv[2]) + nv[3]) + nv[4];
+        T sp, sn;
+        if constexpr (QI == 5) {
+            sp = (((pv[0] + pv[1]) + pv[2]) + pv[3]) + pv[4];
+            sn = (((nv[0] + nv[1]) + nv[2]) + nv[3]) + nv[4];
+        } else {
+            sp = T(0);
+            sn = T(0);
+#pragma unroll
+            for (int i = 0; i < QI; ++i) { sp += pv[i]; sn += nv[i]; }
+        }
         const T q = sp - sn;
         T cp, cm, R;
         if (P.onsager_form == 2) {
@@ -1263,7 +1275,7 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
 #pragma unroll
             for (int i = 0; i < 9; ++i) hv[i] = lds(st + (8 + i) * 256 + tid, P.isc_h);
             const T pux = phi * ux, puy = phi * uy;
-            const T dpx = pux - lds(st + 27 * 256 + tid, P.isc_u), dpy = puy - lds(st + 28 * 256 + tid, P.isc_u);
+            const T dpx = pux - lds(st + NPOP * 256 + tid, P.isc_u), dpy = puy - lds(st + (NPOP + 1) * 256 + tid, P.isc_u);
             sts(phiu + k, pux, P.sc_u);
             sts(phiu + nn + k, puy, P.sc_u);
             // normal of Eq. 32, regularised: grad phi / sqrt(|grad phi|^2 + eps^2)
@@ -1322,7 +1334,7 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
         }
 
         // ---- O10-O11: ions (Eq. 34-40) on D2Q5, push with Eq. 64 ----
-        {
+        if constexpr (QI == 5) {
             T sv_p = P.s_p0, sv_n = P.s_n0;
             if (!(sv_p > T(0))) {
                 const T Dp = P.einstein_D ? P.D * mup * P.inv_mu_v : P.D;
@@ -1399,6 +1411,74 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
             sts_sr(dst.n + o2, bn2, P.sc_c, rng);
             sts_sr(dst.p + o4, bp4, P.sc_c, rng);
             sts_sr(dst.n + o4, bn4, P.sc_c, rng);
+        } else {
+            // ---- ions on D2Q9 as Eq. 34-38 print them: M of Eq. 28, the
+            // weights of Eq. 25, s1 = s2 = 1/tau (Eq. 37), the other rates free.
+            // In the basis of Eq. 28 the moments of p_eq, of the drift G and of
+            // R_i + L_i are (with a = mu c grad psi, the drift of Eq. 40):
+            //   M p_eq  = c (1, ux, uy, 1/3, 1/3, 0, ux/3, uy/3, 1/9)
+            //   M G     = (0, ax, ay, 0, 0, 0, ax/3, ay/3, 0)
+            //   M (R+L) = (R, c Lx, c Ly, R/3, R/3, 0, c Lx/3, c Ly/3, R/9)
+            T sv_p = P.s_p0, sv_n = P.s_n0;
+            if (!(sv_p > T(0))) {
+                const T Dp = P.einstein_D ? P.D * mup * P.inv_mu_v : P.D;
+                const T Dm = P.einstein_D ? P.D * mum * P.inv_mu_v : P.D;
+                sv_p = T(1) / (T(0.5) + T(3) * Dp);
+                sv_n = T(1) / (T(0.5) + T(3) * Dm);
+            }
+            const T Lx = P.ion_L_term ? Fx : T(0), Ly = P.ion_L_term ? Fy : T(0);
+            const T ninth = T(1.0 / 9.0);
+            // post-collision populations; the drift enters as m - m_eq + a with
+            // a = -mu+ c+ E for cations (Eq. 34) and a = +mu- c- E for anions
+            // (Eq. 35, the sign of its G term)
+            auto collide = [&](const T (&v)[9], T c, T ax, T ay, T sv, T (&o)[9]) {
+                const T fr = P.bgk ? sv : P.s_free;
+                const T hf = T(1) - T(0.5) * fr, hv = T(1) - T(0.5) * sv;
+                T m[9], dm[9], dl[9];
+                moments9<T>(v, m);
+                const T cLx = c * Lx, cLy = c * Ly;
+                dm[0] = fr * (m[0] - c) - hf * R;
+                dm[1] = sv * ((m[1] - c * ux) + ax) - hv * cLx;
+                dm[2] = sv * ((m[2] - c * uy) + ay) - hv * cLy;
+                dm[3] = fr * (m[3] - c * third) - hf * R * third;
+                dm[4] = fr * (m[4] - c * third) - hf * R * third;
+                dm[5] = fr * m[5];
+                dm[6] = fr * ((m[6] - c * ux * third) + ax * third) - hf * cLx * third;
+                dm[7] = fr * ((m[7] - c * uy * third) + ay * third) - hf * cLy * third;
+                dm[8] = fr * (m[8] - c * ninth) - hf * R * ninth;
+                inverse9<T>(dm, dl);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) o[i] = v[i] - dl[i];
+            };
+            T po[9], no[9];
+            collide(pv, cp, -mup * cp * Ex, -mup * cp * Ey, sv_p, po);
+            collide(nv, cm, mum * cm * Ex, mum * cm * Ey, sv_n, no);
+            // push; an electrode link (which also decides a corner link) takes
+            // anti-bounce-back to the wall value (the attracted species keeps
+            // the node's concentration, the repelled one 0; ion_bc 1: 0 for
+            // both, 2: bounce-back), a side-wall link bounces back
+            auto push = [&](S *base, T (&o)[9], bool cation) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const int cx = cx9(i), cy = cy9(i);
+                    T v = o[i];
+                    long long off;
+                    if ((cy > 0 && top) || (cy < 0 && bot)) {
+                        const bool attracted = cation ? (cy > 0) : (cy < 0);
+                        const T cw = (P.ion_bc == 0 && attracted) ? (cation ? cp : cm) : T(0);
+                        if (P.ion_bc != 2) v = -v + T(2) * w9<T>(i) * cw;
+                        off = opp9(i) * nn + rowC;
+                    } else if ((cx > 0 && rwall) || (cx < 0 && lwall)) {
+                        off = opp9(i) * nn + rowC;
+                    } else {
+                        off = i * nn + dest(cx, cy);
+                    }
+                    if constexpr (!kSame<S, T>) v -= w9<T>(i) * P.cref;   // stored relative to w_i c_ref
+                    sts_sr(base + off, v, P.sc_c, rng);
+                }
+            };
+            push(dst.p, po, true);
+            push(dst.n, no, false);
         }
 
         if (SNAP) {
@@ -1421,7 +1501,7 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
     if (SNAP || RESID) block_sum_store_at<T, 4>(red, part, slot);
 }
 
-template <typename T, typename S, bool SNAP, bool FROZEN, bool RESID, bool VEC>
+template <typename T, typename S, bool SNAP, bool FROZEN, bool RESID, bool VEC, int QI = 5>
 __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<S> src, const Pops<S> dst,
                                                  const T *__restrict__ gA, const T *__restrict__ gB,
                                                  const Control *__restrict__ ctl, const PhiRef<T> Rf,
@@ -1429,7 +1509,7 @@ __global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<S> 
                                                  T *__restrict__ snap, double *__restrict__ part,
                                                  int *__restrict__ unstable)
 {
-    main_body<T, S, SNAP, FROZEN, RESID, VEC>(P, src, dst, gA, gB, ctl, Rf, phiu, psi_prev, snap, part, unstable,
+    main_body<T, S, SNAP, FROZEN, RESID, VEC, QI>(P, src, dst, gA, gB, ctl, Rf, phiu, psi_prev, snap, part, unstable,
                                               blockIdx.x, blockIdx.y, blockIdx.x + (long long)blockIdx.y * gridDim.x);
 }
 
@@ -1482,7 +1562,7 @@ static __global__ void __launch_bounds__(256) k_step_end(const double *__restric
 
 // ---- initial state (Sec. 6 set-up) ------------------------------------------------
 
-template <typename T, typename S>
+template <typename T, typename S, int QI = 5>
 __global__ void __launch_bounds__(256) k_init_state(const DevP<T> P, Pops<S> pops, T *__restrict__ g,
                                                     S *__restrict__ phiu, PhiRef<T> Rf, double xc, double yc,
                                                     double R, double Wi, int shape, int psi_zero)
@@ -1504,7 +1584,7 @@ __global__ void __launch_bounds__(256) k_init_state(const DevP<T> P, Pops<S> pop
     for (int i = 0; i < 8; ++i) sts(pops.f + i * nn + k, T(0), P.sc_f);
     // p, n are set by k_init_ions
 #pragma unroll
-    for (int i = 0; i < 5; ++i) { sts(pops.p + i * nn + k, T(0), P.sc_c); sts(pops.n + i * nn + k, T(0), P.sc_c); }
+    for (int i = 0; i < QI; ++i) { sts(pops.p + i * nn + k, T(0), P.sc_c); sts(pops.n + i * nn + k, T(0), P.sc_c); }
     sts(phiu + k, T(0), P.sc_u);
     sts(phiu + nn + k, T(0), P.sc_u);
     const T w = T(1) / T(6);
@@ -1544,7 +1624,7 @@ __global__ void __launch_bounds__(256) k_init_ref(const DevP<T> P, PhiRef<T> Rf,
     Rf.mur[k] = (T)(4.0 * beta * c * (c - 1.0) * (c - 0.5) - kappa * lap);
 }
 
-template <typename T, typename S>
+template <typename T, typename S, int QI = 5>
 __global__ void __launch_bounds__(256) k_init_ions(const DevP<T> P, Pops<S> pops, const T *__restrict__ gA,
                                                    const T *__restrict__ gB, const Control *__restrict__ ctl,
                                                    const T *__restrict__ phig, T *__restrict__ snap,
@@ -1568,12 +1648,12 @@ __global__ void __launch_bounds__(256) k_init_ions(const DevP<T> P, Pops<S> pops
         ceq = (T)c0;
     }
     ceq = (T)c_scale * ceq;
-    const T wv[5] = {T(1) / T(3), T(1) / T(6), T(1) / T(6), T(1) / T(6), T(1) / T(6)};
     T sp = T(0), sn = T(0);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        const T v = wv[i] * ceq;
-        const T vs = kSame<S, T> ? v : v - wv[i] * P.cref;
+    for (int i = 0; i < QI; ++i) {
+        const T wi = QI == 9 ? w9<T>(i) : (i == 0 ? T(1) / T(3) : T(1) / T(6));
+        const T v = wi * ceq;
+        const T vs = kSame<S, T> ? v : v - wi * P.cref;
         sts(pops.p + i * nn + k, vs, P.sc_c);
         sts(pops.n + i * nn + k, vs, P.sc_c);
         sp += v;
@@ -1593,58 +1673,61 @@ __global__ void __launch_bounds__(256) k_init_ions(const DevP<T> P, Pops<S> pops
 }
 
 // ---- state transfer (checkpoint / test hook) ---------------------------------------
-// Packs rows [y0, y0 + rows) of the state into 35 doubles per node.
-template <typename T, typename S>
+// Packs rows [y0, y0 + rows) of the state into 25 + 2 QI doubles per node:
+// f0..f8, h0..h8, p (QI), n (QI), g0..g4, (phi u)(t-1) x, y.
+template <typename T, typename S, int QI = 5>
 __global__ void k_pack_state(const DevP<T> P, const Pops<S> pops, const T *__restrict__ g,
                              const S *__restrict__ phiu, const T *__restrict__ phir, double *__restrict__ out,
                              int y0, int rows)
 {
+    constexpr int SPN = 25 + 2 * QI, G0 = 18 + 2 * QI;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long cnt = (long long)rows * P.nx;
     if (i >= cnt) return;
     const int y = y0 + (int)(i / P.nx);
     const long long nn = P.nn, k = (long long)y0 * P.nx + i;
-    double *o = out + 35 * i;
+    double *o = out + SPN * i;
     o[0] = 0.0;
     for (int q = 1; q < 9; ++q) o[q] = (double)lds(pops.f + (q - 1) * nn + k, P.isc_f);
     const double pr = (double)phir[(long long)(y + 1) * P.nx + (k - (long long)y * P.nx)];
     for (int q = 0; q < 9; ++q) o[9 + q] = (double)lds(pops.h + q * nn + k, P.isc_h) + (double)w9<T>(q) * pr;
     const double cr = (double)P.cref;
-    for (int q = 0; q < 5; ++q) {
-        const double wc = (q == 0 ? 1.0 / 3.0 : 1.0 / 6.0) * cr;
-        o[18 + q] = (double)lds(pops.p + q * nn + k, P.isc_c) + wc;
-        o[23 + q] = (double)lds(pops.n + q * nn + k, P.isc_c) + wc;
+    for (int q = 0; q < QI; ++q) {
+        const double wq = QI == 9 ? (double)w9<double>(q) : (q == 0 ? 1.0 / 3.0 : 1.0 / 6.0);
+        o[18 + q] = (double)lds(pops.p + q * nn + k, P.isc_c) + wq * cr;
+        o[18 + QI + q] = (double)lds(pops.n + q * nn + k, P.isc_c) + wq * cr;
     }
     const double pl = (double)psi_lin(P, y);
-    o[28] = 0.0;
-    for (int q = 0; q < 4; ++q) o[29 + q] = (double)g[q * nn + k] + pl / 6.0;
-    o[33] = (double)lds(phiu + k, P.isc_u);
-    o[34] = (double)lds(phiu + nn + k, P.isc_u);
+    o[G0] = 0.0;
+    for (int q = 0; q < 4; ++q) o[G0 + 1 + q] = (double)g[q * nn + k] + pl / 6.0;
+    o[G0 + 5] = (double)lds(phiu + k, P.isc_u);
+    o[G0 + 6] = (double)lds(phiu + nn + k, P.isc_u);
 }
 
-template <typename T, typename S>
+template <typename T, typename S, int QI = 5>
 __global__ void k_unpack_state(const DevP<T> P, Pops<S> pops, T *__restrict__ g, S *__restrict__ phiu,
                                const T *__restrict__ phir, const double *__restrict__ in, int y0, int rows)
 {
+    constexpr int SPN = 25 + 2 * QI, G0 = 18 + 2 * QI;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long cnt = (long long)rows * P.nx;
     if (i >= cnt) return;
     const int y = y0 + (int)(i / P.nx);
     const long long nn = P.nn, k = (long long)y0 * P.nx + i;
-    const double *o = in + 35 * i;
+    const double *o = in + SPN * i;
     for (int q = 1; q < 9; ++q) sts(pops.f + (q - 1) * nn + k, (T)o[q], P.sc_f);
     const double pr = (double)phir[(long long)(y + 1) * P.nx + (k - (long long)y * P.nx)];
     for (int q = 0; q < 9; ++q) sts(pops.h + q * nn + k, (T)(o[9 + q] - (double)w9<T>(q) * pr), P.sc_h);
     const double cr = (double)P.cref;
-    for (int q = 0; q < 5; ++q) {
-        const double wc = (q == 0 ? 1.0 / 3.0 : 1.0 / 6.0) * cr;
-        sts(pops.p + q * nn + k, (T)(o[18 + q] - wc), P.sc_c);
-        sts(pops.n + q * nn + k, (T)(o[23 + q] - wc), P.sc_c);
+    for (int q = 0; q < QI; ++q) {
+        const double wq = QI == 9 ? (double)w9<double>(q) : (q == 0 ? 1.0 / 3.0 : 1.0 / 6.0);
+        sts(pops.p + q * nn + k, (T)(o[18 + q] - wq * cr), P.sc_c);
+        sts(pops.n + q * nn + k, (T)(o[18 + QI + q] - wq * cr), P.sc_c);
     }
     const double pl = (double)psi_lin(P, y);
-    for (int q = 0; q < 4; ++q) g[q * nn + k] = (T)(o[29 + q] - pl / 6.0);
-    sts(phiu + k, (T)o[33], P.sc_u);
-    sts(phiu + nn + k, (T)o[34], P.sc_u);
+    for (int q = 0; q < 4; ++q) g[q * nn + k] = (T)(o[G0 + 1 + q] - pl / 6.0);
+    sts(phiu + k, (T)o[G0 + 5], P.sc_u);
+    sts(phiu + nn + k, (T)o[G0 + 6], P.sc_u);
 }
 
 template <typename T>

@@ -57,12 +57,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         nb_ = (long long)grid_.x * grid_.y;
         const size_t plane = sizeof(T) * (size_t)nn_, splane = sizeof(S) * (size_t)nn_;
         for (int b = 0; b < 2; ++b) {
-            S *base;
-            EHDLB_CK(alloc((void **)&base, splane * 27));
-            pops_[b].f = base;
-            pops_[b].h = base + 8 * nn_;
-            pops_[b].p = base + 17 * nn_;
-            pops_[b].n = base + 22 * nn_;
+            EHDLB_CK(alloc_pops(b, 5));
             EHDLB_CK(alloc((void **)&g_[b], plane * 4));
         }
         // 16-byte staging of the main kernel: every row starts on a 16-byte boundary
@@ -112,6 +107,12 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     {
         P_ = p;
         make_devp();
+        const int qi = p.ion_lattice == 9 ? 9 : 5;
+        if (qi != qi_) {   // the ion lattice sets the size of the population blocks
+            EHDLB_CK(cudaStreamSynchronize(stream_));
+            EHDLB_CK(alloc_pops(0, qi));
+            EHDLB_CK(alloc_pops(1, qi));
+        }
         Control c{};
         c.cur0 = 0;
         c.tol = p.sweep_tol;
@@ -120,8 +121,12 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         ctl_h_ = c;
         EHDLB_CK(cudaMemcpyAsync(ctl_, &ctl_h_, sizeof(Control), cudaMemcpyHostToDevice, stream_));
         const double Wi = p.W_init > 0.0 ? p.W_init : p.W;
-        k_init_state<T, S><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[0], g_[0], phiu_, ref_, p.xc, p.yc,
-                                                             p.R, Wi, p.init_shape, p.init_psi_zero);
+        if (qi_ == 9)
+            k_init_state<T, S, 9><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[0], g_[0], phiu_, ref_, p.xc, p.yc,
+                                                                      p.R, Wi, p.init_shape, p.init_psi_zero);
+        else
+            k_init_state<T, S, 5><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[0], g_[0], phiu_, ref_, p.xc, p.yc,
+                                                                      p.R, Wi, p.init_shape, p.init_psi_zero);
         EHDLB_CK(cudaGetLastError());
         k_init_ref<T><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, ref_, 12.0 * p.sigma / p.W, 1.5 * p.sigma * p.W);
         EHDLB_CK(cudaGetLastError());
@@ -147,8 +152,12 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             }
         }
         EHDLB_CK(cudaGetLastError());
-        k_init_ions<T, S><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[0], g_[0], g_[1], ctl_, phig_, snap_,
-                                                            p.c_init_scale, p.c0);
+        if (qi_ == 9)
+            k_init_ions<T, S, 9><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[0], g_[0], g_[1], ctl_, phig_, snap_,
+                                                                     p.c_init_scale, p.c0);
+        else
+            k_init_ions<T, S, 5><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[0], g_[0], g_[1], ctl_, phig_, snap_,
+                                                                     p.c_init_scale, p.c0);
         EHDLB_CK(cudaGetLastError());
         EHDLB_CK(cudaMemcpyAsync(&ctl_h_, ctl_, sizeof(Control), cudaMemcpyDeviceToHost, stream_));
         EHDLB_CK(cudaStreamSynchronize(stream_));
@@ -293,7 +302,32 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         return e;
     }
 
+    // f, h, p, n of time level b for QI ion populations per species (the
+    // previous block, if any, is released first)
+    cudaError_t alloc_pops(int b, int qi)
+    {
+        if (pops_[b].f) {
+            void *old = pops_[b].f;
+            for (auto it = allocs_.begin(); it != allocs_.end(); ++it)
+                if (*it == old) { allocs_.erase(it); break; }
+            if (arena_) arena_->release(old);
+            else cudaFree(old);
+            pops_[b] = Pops<S>{};
+        }
+        S *base;
+        const cudaError_t e = alloc((void **)&base, sizeof(S) * (size_t)nn_ * (17 + 2 * qi));
+        if (e != cudaSuccess) return e;
+        pops_[b].f = base;
+        pops_[b].h = base + 8 * nn_;
+        pops_[b].p = base + 17 * nn_;
+        pops_[b].n = base + (17 + qi) * nn_;
+        qi_ = qi;
+        return cudaSuccess;
+    }
+
   public:
+    int state_per_node() const override { return 25 + 2 * qi_; }
+
     // Device bytes of one lattice of nx x ny nodes (what allocate() takes,
     // rounded up to 256-byte blocks; the per-call counters excluded).
     static size_t footprint(int nx, int ny)
@@ -417,8 +451,12 @@ template <typename T, typename S = T> class Solver : public SolverBase {
 
     void launch_prep(int par, int fixedK, int kmin, int kmax, int flips)
     {
-        k_prep<T, S><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n, ref_,
-                                                       phig_, q_, ctl_, fixedK, kmin, kmax, flips);
+        if (qi_ == 9)
+            k_prep<T, S, 9><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n, ref_,
+                                                                phig_, q_, ctl_, fixedK, kmin, kmax, flips);
+        else
+            k_prep<T, S, 5><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n, ref_,
+                                                                phig_, q_, ctl_, fixedK, kmin, kmax, flips);
         ++launches_;
     }
 
@@ -448,11 +486,17 @@ template <typename T, typename S = T> class Solver : public SolverBase {
 
     template <bool SN, bool F, bool R> cudaError_t main_attr()
     {
-        cudaError_t e = cudaFuncSetAttribute(k_main<T, S, SN, F, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)main_smem_bytes<T, S>());
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_main<T, S, SN, F, R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)main_smem_bytes<T, S>());
+        cudaError_t e = cudaSuccess;
+        for (cudaError_t x :
+             {cudaFuncSetAttribute(k_main<T, S, SN, F, R, true, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)main_smem_bytes<T, S, 5>()),
+              cudaFuncSetAttribute(k_main<T, S, SN, F, R, false, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)main_smem_bytes<T, S, 5>()),
+              cudaFuncSetAttribute(k_main<T, S, SN, F, R, true, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)main_smem_bytes<T, S, 9>()),
+              cudaFuncSetAttribute(k_main<T, S, SN, F, R, false, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)main_smem_bytes<T, S, 9>())})
+            if (x != cudaSuccess) e = x;
         return e;
     }
 
@@ -616,16 +660,19 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         const int resid_mode = main_resid ? 1 : ((fused && last) ? 2 : 0);
         const dim3 b(BX, BY);
         int *unstable = &ctl_->unstable;
+#define EHDLB_MAIN1(SN, F, R, V, Q)                                                                      \
+    k_main<T, S, SN, F, R, V, Q><<<grid_, b, main_smem_bytes<T, S, Q>(), stream_>>>(                       \
+        dp_, pops_[par], pops_[par ^ 1], g_[0], g_[1], ctl_, ref_, phiu_, psi_prev_, snap_, part_, unstable)
 #define EHDLB_MAIN(SN, F, R)                                                                             \
     do {                                                                                                 \
-        if (vec_ok_ && vec_)                                                                             \
-            k_main<T, S, SN, F, R, true><<<grid_, b, main_smem_bytes<T, S>(), stream_>>>(                   \
-                dp_, pops_[par], pops_[par ^ 1], g_[0], g_[1], ctl_, ref_, phiu_, psi_prev_, snap_, part_, \
-                unstable);                                                                               \
-        else                                                                                             \
-            k_main<T, S, SN, F, R, false><<<grid_, b, main_smem_bytes<T, S>(), stream_>>>(                  \
-                dp_, pops_[par], pops_[par ^ 1], g_[0], g_[1], ctl_, ref_, phiu_, psi_prev_, snap_, part_, \
-                unstable);                                                                               \
+        const bool v_ = vec_ok_ && vec_;                                                                 \
+        if (qi_ == 9) {                                                                                  \
+            if (v_) EHDLB_MAIN1(SN, F, R, true, 9);                                                      \
+            else EHDLB_MAIN1(SN, F, R, false, 9);                                                        \
+        } else {                                                                                         \
+            if (v_) EHDLB_MAIN1(SN, F, R, true, 5);                                                      \
+            else EHDLB_MAIN1(SN, F, R, false, 5);                                                        \
+        }                                                                                                \
     } while (0)
         if (last) {
             if (frozen) EHDLB_MAIN(true, true, false);
@@ -637,6 +684,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             else EHDLB_MAIN(false, false, false);
         }
 #undef EHDLB_MAIN
+#undef EHDLB_MAIN1
         long long nb2 = 0;
         if (resid_mode == 2) {
             const dim3 g = tb_grid(std::min(chunk, fixedK - (nk - 1) * chunk), tb_shape_, nx_, ny_);
@@ -654,7 +702,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         EHDLB_CK(cudaMemcpyAsync(&ctl_h_, ctl_, sizeof(Control), cudaMemcpyDeviceToHost, stream_));
         EHDLB_CK(cudaStreamSynchronize(stream_));
         const int cur = ctl_h_.cur0;
-        const size_t per_row = (size_t)35 * nx_;
+        const size_t per_row = (size_t)state_per_node() * nx_;
         int rows = (int)std::max<size_t>(1, std::min<size_t>((size_t)ny_, ((size_t)nn_) / per_row));
         double *stage = nullptr;
         EHDLB_CK(cudaMalloc((void **)&stage, sizeof(double) * per_row * rows));
@@ -665,8 +713,12 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             const unsigned nblk = (unsigned)((cnt + 255) / 256);
             cudaError_t e = cudaSuccess;
             if (dst) {
-                k_pack_state<T, S><<<nblk, 256, 0, stream_>>>(dp_, pops_[ctl_h_.tpar & 1], g_[cur], phiu_, ref_.phir, stage,
-                                                            y0, r);
+                if (qi_ == 9)
+                    k_pack_state<T, S, 9><<<nblk, 256, 0, stream_>>>(dp_, pops_[ctl_h_.tpar & 1], g_[cur], phiu_,
+                                                                     ref_.phir, stage, y0, r);
+                else
+                    k_pack_state<T, S, 5><<<nblk, 256, 0, stream_>>>(dp_, pops_[ctl_h_.tpar & 1], g_[cur], phiu_,
+                                                                     ref_.phir, stage, y0, r);
                 e = cudaGetLastError();
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(dst + per_row * y0, stage, sizeof(double) * per_row * r,
@@ -675,8 +727,14 @@ template <typename T, typename S = T> class Solver : public SolverBase {
                 e = cudaMemcpyAsync(stage, src + per_row * y0, sizeof(double) * per_row * r,
                                     cudaMemcpyHostToDevice, stream_);
                 if (e == cudaSuccess)
-                    k_unpack_state<T, S><<<nblk, 256, 0, stream_>>>(dp_, pops_[ctl_h_.tpar & 1], g_[cur], phiu_, ref_.phir,
-                                                              stage, y0, r);
+                {
+                    if (qi_ == 9)
+                        k_unpack_state<T, S, 9><<<nblk, 256, 0, stream_>>>(dp_, pops_[ctl_h_.tpar & 1], g_[cur],
+                                                                           phiu_, ref_.phir, stage, y0, r);
+                    else
+                        k_unpack_state<T, S, 5><<<nblk, 256, 0, stream_>>>(dp_, pops_[ctl_h_.tpar & 1], g_[cur],
+                                                                           phiu_, ref_.phir, stage, y0, r);
+                }
                 if (e == cudaSuccess) e = cudaGetLastError();
             }
             if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
@@ -707,6 +765,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     int tb_chunk_ = sizeof(T) == 4 ? 5 : 2;  // sweeps fused per launch (0: one per launch)
     int tb_shape_ = 0;                        // region shape of the fused sweep kernel
     int tb_m_ = 0;                            // launch index within the step
+    int qi_ = 0;                              // ion populations per species (5 or 9) of pops_
     T *coef_ = nullptr;                       // source coefficients A, Bx, By of the step
     Control *ctl_ = nullptr;
     Control ctl_h_{};

@@ -41,7 +41,7 @@ _PARAM_FIELDS = [
     ("init_psi_zero", C.c_int),
     ("freeze_E", C.c_int), ("E_frozen_x", C.c_double), ("E_frozen_y", C.c_double),
     ("s_free", C.c_double), ("bgk", C.c_int),
-    ("side_walls", C.c_int),
+    ("ion_lattice", C.c_int), ("side_walls", C.c_int),
 ]
 
 
@@ -124,7 +124,7 @@ def lib():
         L.ehdlb_destroy.restype = None
         L.ehdlb_last_error.argtypes = [vp]
         L.ehdlb_last_error.restype = C.c_char_p
-        if L.ehdlb_version() != 2:
+        if L.ehdlb_version() != 3:
             raise ImportError("libehdlb ABI version mismatch")
         _lib = L
     return _lib
@@ -375,12 +375,14 @@ class Lattice:
         return ehdlb_get_sweep_counts(self.ctx, n)
 
     def state(self) -> np.ndarray:
-        out = np.zeros((self.ny, self.nx, 35))
+        spn = lib().ehdlb_state_len(self.ctx) // (self.nx * self.ny)
+        out = np.zeros((self.ny, self.nx, spn))
         ehdlb_get_state(self.ctx, out)
         return out
 
     def set_state(self, s):
-        ehdlb_set_state(self.ctx, np.asarray(s, dtype=np.float64).reshape(self.ny, self.nx, 35))
+        spn = lib().ehdlb_state_len(self.ctx) // (self.nx * self.ny)
+        ehdlb_set_state(self.ctx, np.asarray(s, dtype=np.float64).reshape(self.ny, self.nx, spn))
 
     def deformation(self) -> float:
         return ehdlb_deformation(self.ctx)

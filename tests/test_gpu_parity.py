@@ -119,6 +119,9 @@ VARIANTS = {
     "wide_interface": dict(W_init=6.0, eps_r=0.5, mu_r=5.0),
     "printed_normal": dict(nhat_eps=0.0),
     "side_walls": dict(side_walls=1),
+    "d2q9_ions": dict(ion_lattice=9),
+    "d2q9_ions_walls_bc1": dict(ion_lattice=9, side_walls=1, ion_bc=1),
+    "d2q9_ions_bc2_bgk": dict(ion_lattice=9, ion_bc=2, bgk=1),
     "side_walls_bgk_ionbc1": dict(side_walls=1, bgk=1, ion_bc=1),
 }
 
@@ -174,6 +177,33 @@ def test_fp32_side_walls_match_oracle():
     err = field_errors(got, ref)
     assert_close(err, FP32_TOL, keys=["phi", "psi", "q", "cp", "cm"])
     assert_close(err, FP32_U_TOL, keys=["u"])
+
+
+def test_fp32_d2q9_ions_match_oracle():
+    # the ion lattice as Eq. 34-36 print it
+    n, steps = 128, 100
+    prm = dict(workloads.droplet(n), ion_lattice=9)
+    got, ref, *_ = run_pair(n, n, prm, steps, precision=ehdlb.FP32)
+    err = field_errors(got, ref)
+    assert_close(err, FP32_TOL, keys=["phi", "psi", "q", "cp", "cm"])
+    assert_close(err, FP32_U_TOL, keys=["u"])
+
+
+def test_d2q9_ion_state_round_trips_through_the_oracle():
+    prm = dict(workloads.droplet64(), ion_lattice=9, sweeps_min=10, sweeps_max=10)
+    orc = oracle.Oracle(64, 64, prm)
+    orc.step(20)
+    s = orc.state()
+    assert s.shape[-1] == 43
+    lat = ehdlb.Lattice(64, 64, dict(prm, init_sweeps_fixed=0), precision=ehdlb.FP64)
+    lat.set_state(s)
+    got = lat.state()
+    keep = np.ones(43, bool)
+    keep[[0, 36]] = False                       # f0 and g0 are not stored
+    assert np.max(np.abs(got[:, :, keep] - s[:, :, keep])) <= 1e-15
+    orc.step(10)
+    lat.step(10)
+    assert_close(field_errors(lat.fields(), orc.fields()), FP64_TOL)
 
 
 def test_fp64_droplet256_matches_oracle():
