@@ -248,10 +248,10 @@ int ehdlb_set_timing(ehdlb_ctx *c, int on);
  *     1..5 (the double-precision solver uses at most 2), 0 for one sweep per
  *     launch; default 5 (float) / 2 (double);
  *   tile_shape: blocks of the fused sweep kernel, 0: 64 x 32 region per
- *     block (512 threads, default), 1: 64 x 32 (256 threads), 2: clusters of
- *     2 x 4 blocks of 64 x 32 that exchange populations through distributed
- *     shared memory every sweep; 1 and 2 float only (the double solver keeps
- *     0);
+ *     block (512 threads; the double solver's only shape), 1: 64 x 32 (256
+ *     threads; default for float), 2: clusters of 2 x 4 blocks of 64 x 32
+ *     that exchange populations through distributed shared memory every
+ *     sweep; 1 and 2 float only;
  *   main_staging: how the step kernel copies its block's populations to
  *     shared memory, 0: one asynchronous copy per node and plane, 1: 16-byte
  *     copies of row segments (default; used only when nx times the element
@@ -364,7 +364,7 @@ int ehdlb_batch_get_state(ehdlb_batch *b, int id, double *dst, size_t len);
 int ehdlb_batch_deformation(ehdlb_batch *b, int n, const int *ids, double *D);
 
 /* Sweeps fused per launch (1..5; default 5), tile shape of the fused sweep
- * kernel (0: 512 threads, default; 1: 256 threads) and whether steps replay
+ * kernel (0: 512 threads; 1: 256 threads, default) and whether steps replay
  * a captured graph (default 1); -1 keeps a setting. */
 int ehdlb_batch_set_tuning(ehdlb_batch *b, int sweeps_per_launch, int tile_shape, int use_graphs);
 

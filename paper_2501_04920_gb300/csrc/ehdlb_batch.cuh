@@ -114,9 +114,17 @@ template <typename T, typename S> struct CaseDev {
     Control *ctl;
     long long nb_main;       // partial slots of the step kernel
     long long nb_tb;         // partial slots of the last sweep launch
+    int gxm, gym;            // grid of 64 x 4 blocks of the step kernel
+    int pad_[2];
 };
 
-// x: case index, y, z: block column and row in the case's grid, w: partials slot
+// Block rows of the step and prep kernels one work item covers (one
+// descriptor load per item).
+constexpr int KB_ROWS = 4;
+
+// x: case index, y, z: block column and row in the case's grid, w: partials
+// slot (step and prep kernels: z is the first of KB_ROWS block rows and the
+// slot follows from the row)
 using WorkItem = int4;
 
 // Copy the descriptor of case c to shared memory (all threads; no barrier).
@@ -145,8 +153,10 @@ __global__ void __launch_bounds__(256) kb_prep(const CaseDev<T, S> *__restrict__
         load_case(C, cases, w.x);
         __syncthreads();
         const Pops<S> &cur = C.pops[C.ctl->tpar & 1];
-        prep_body<T, S>(C.P, cur.h, cur.p, cur.n, C.ref, C.phig, C.q, C.ctl, fixedK, fixedK, fixedK, flips, w.y,
-                        w.z);
+        const int by1 = min(w.z + KB_ROWS, C.gym);
+        for (int by = w.z; by < by1; ++by)
+            prep_body<T, S>(C.P, cur.h, cur.p, cur.n, C.ref, C.phig, C.q, C.ctl, fixedK, fixedK, fixedK, flips, w.y,
+                            by);
         __syncthreads();
     }
 }
@@ -181,10 +191,13 @@ __global__ void __launch_bounds__(256, 3) kb_main(const CaseDev<T, S> *__restric
         load_case(C, cases, w.x);
         __syncthreads();
         const int par = C.ctl->tpar & 1;
-        main_body<T, S, SNAP, false, false, true>(C.P, C.pops[par], C.pops[par ^ 1], C.g[0], C.g[1], C.ctl, C.ref,
-                                                  C.phiu, C.psi_prev, C.snap, C.part, &C.ctl->unstable, w.y, w.z,
-                                                  w.w);
-        __syncthreads();
+        const int by1 = min(w.z + KB_ROWS, C.gym);
+        for (int by = w.z; by < by1; ++by) {
+            main_body<T, S, SNAP, false, false, true>(C.P, C.pops[par], C.pops[par ^ 1], C.g[0], C.g[1], C.ctl,
+                                                      C.ref, C.phiu, C.psi_prev, C.snap, C.part, &C.ctl->unstable,
+                                                      w.y, by, (long long)by * C.gxm + w.y);
+            __syncthreads();
+        }
     }
 }
 
@@ -577,9 +590,11 @@ template <typename T, typename S> class Batch : public BatchBase {
             const int gx = (nx + 63) / 64, gy = (ny + 3) / 4;
             d.nb_main = (long long)gx * gy;
             d.nb_tb = 0;
+            d.gxm = gx;
+            d.gym = gy;
             host_cases_.push_back(d);
             index_of_[kv.first] = c;
-            for (int by = 0; by < gy; ++by)
+            for (int by = 0; by < gy; by += KB_ROWS)
                 for (int bx = 0; bx < gx; ++bx) node.push_back(make_int4(c, bx, by, by * gx + bx));
             for (int nsw = 1; nsw <= TBMAX; ++nsw) {
                 const int tx = 64 - 2 * nsw, ty = 32 - 2 * nsw;
@@ -625,7 +640,7 @@ template <typename T, typename S> class Batch : public BatchBase {
     int ncases_ = 0;
     long long nodes_ = 0;
     bool dirty_ = true;
-    int chunk_ = 5, shape_ = 0;
+    int chunk_ = 5, shape_ = 1;
     bool graphs_ = true;
     int sms_ = 1;
     long long launches_ = 0;

@@ -485,24 +485,29 @@ __global__ void __launch_bounds__(256) k_sweep(const DevP<T> P, S *__restrict__ 
 // lattice stay empty, the electrode rules act on the wall links).  Every
 // sweep collides and pushes the whole region; values at distance < s from
 // the region edge are incomplete after sweep s, so after NSW sweeps the
-// output tile is exact.  One buffer of four planes holds the populations: a
-// sweep reads every node's populations into registers, the block
-// synchronises, then every node pushes its post-collision values in place.
-// The planes carry a one-node pad on every side that absorbs pushes leaving
-// the region.  The source coefficients of each node stay in registers:
-// X/3 = A - Bx m1 - By m2 with m1, m2 the first moments (E = 3 m / tau_g),
-// A = th Kq q / (3 eps), B = th (eps_r - 1) grad phi / (tau_g eps),
-// th = vartheta (times 1/(1 - w0)).
+// output tile is exact.  The four population planes are stored in a moving
+// frame: after s sweeps the population g_i of node (lx, ly) sits at
+// (lx, ly) - s c_i, so the value a node pushes to its neighbour lands in the
+// cell the node itself has just read.  Every thread therefore reads and
+// writes the same four cells per node and a sweep needs one block barrier;
+// the planes moving along x are NSW cells wider, those moving along y NSW
+// cells taller.  An electrode link writes the bounced value into the node's
+// own cell of the opposite plane for the next sweep.  The source
+// coefficients of each node stay in registers: X/3 = A - Bx m1 - By m2 with
+// m1, m2 the first moments (E = 3 m / tau_g), A = th Kq q / (3 eps),
+// B = th (eps_r - 1) grad phi / (tau_g eps), th = vartheta (times 1/(1 - w0)).
 //   FIRST: first launch of the step; the coefficients come from phi (with
 //          its ring of neighbours) and q, and the output tile's are written
 //          to coef (three planes A, Bx, By) for the later launches, which
 //          load them instead.
 //   RESID: the last sweep of the step; residual partials of the output tile.
 // Launch: blockDim (32, BY), dynamic shared memory
-// tb_smem_bytes<T, RW, RH>(FIRST).
+// tb_smem_bytes<T, RW, RH>(FIRST) (sized for up to TB_NSW_MAX sweeps).
+constexpr int TB_NSW_MAX = 5;
 template <typename T, int RW, int RH> __host__ __device__ constexpr size_t tb_smem_bytes(bool first)
 {
-    return sizeof(T) * (first ? 6 : 4) * (size_t)(RH + 2) * (RW + 2);
+    return sizeof(T) * ((size_t)2 * RH * (RW + TB_NSW_MAX) + (size_t)2 * (RH + TB_NSW_MAX) * RW +
+                        (first ? (size_t)(RH + 2) * (RW + 2) + (size_t)RH * RW : 0));
 }
 
 // x mod nx for x within one lattice width of [0, nx) (wide == true) or any x.
@@ -521,12 +526,17 @@ __device__ __forceinline__ void tb_body(const DevP<T> &P, S *__restrict__ gA, S 
                                         int by, long long slot)
 {
     constexpr int H = NSW, TX = RW - 2 * H, TY = RH - 2 * H;
-    constexpr int PW = RW + 2, PH = RH + 2, PL = PW * PH;
+    constexpr int W1 = RW + H;                    // width of the planes moving along x
+    constexpr int P1 = RH * W1, P2 = (RH + H) * RW;
+    constexpr int FW = RW + 2;                    // phi with its one-node ring
     constexpr int NB = RW / 32, NA = RH / BY;
     static_assert(RW % 32 == 0 && RH % BY == 0, "region must tile the block");
-    static_assert(TX > 0 && TY > 0 && NA >= 1, "tile too small for NSW");
+    static_assert(TX > 0 && TY > 0 && NA >= 1 && H <= TB_NSW_MAX, "tile too small for NSW");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sg = reinterpret_cast<T *>(smem_raw);   // [4][PH][PW], then (FIRST) phi ring and q
+    // planes g1 (+x), g3 (-x), g2 (+y), g4 (-y); then (FIRST) phi ring and q
+    T *const s1 = reinterpret_cast<T *>(smem_raw);
+    T *const s3 = s1 + P1, *const s2 = s1 + 2 * P1, *const s4 = s2 + P2;
+    T *const sphi = s4 + P2, *const sq = sphi + (RH + 2) * FW;
     const int par = (ctl->cur0 + m) & 1;
     const S *__restrict__ src = par ? gB : gA;
     S *__restrict__ dst = par ? gA : gB;
@@ -540,10 +550,10 @@ __device__ __forceinline__ void tb_body(const DevP<T> &P, S *__restrict__ gA, S 
 #pragma unroll
     for (int b = 0; b < NB; ++b) gxs[b] = wrap_x(x0 - H + tx + 32 * b, nx, wide);
 
-    // ---- load the region: g (async) into the buffer; the coefficients from
-    // coef into registers, or (FIRST) phi with a one-node ring and q (async) ----
+    // ---- load the region: g (async) into the frame of sweep 0; the
+    // coefficients from coef into registers, or (FIRST) phi with a one-node
+    // ring and q (async) ----
     T cA[NA][NB], cBx[NA][NB], cBy[NA][NB];
-    T *const sphi = sg + 4 * PL, *const sq = sg + 5 * PL;
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
         const int ly = ty + BY * a, gy = y0 - H + ly;
@@ -553,17 +563,23 @@ __device__ __forceinline__ void tb_body(const DevP<T> &P, S *__restrict__ gA, S 
         const long long row = (long long)gy * nx;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
+            const int lx = tx + 32 * b;
             const long long k = row + gxs[b];
-            const int li = (ly + 1) * PW + tx + 32 * b + 1;
+            T *c1 = s1 + ly * W1 + lx + H, *c3 = s3 + ly * W1 + lx, *c2 = s2 + (ly + H) * RW + lx,
+              *c4 = s4 + ly * RW + lx;
             if constexpr (kSame<S, T>) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) cp_async(sg + i * PL + li, src + i * nn + k);
+                cp_async(c1, src + k);
+                cp_async(c2, src + nn + k);
+                cp_async(c3, src + 2 * nn + k);
+                cp_async(c4, src + 3 * nn + k);
             } else {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) sg[i * PL + li] = lds(src + i * nn + k, P.isc_g);
+                *c1 = lds(src + k, P.isc_g);
+                *c2 = lds(src + nn + k, P.isc_g);
+                *c3 = lds(src + 2 * nn + k, P.isc_g);
+                *c4 = lds(src + 3 * nn + k, P.isc_g);
             }
             if (FIRST) {
-                cp_async(sq + li, q + k);
+                cp_async(sq + ly * RW + lx, q + k);
             } else {
                 cA[a][b] = coef[k];
                 cBx[a][b] = coef[nn + k];
@@ -573,8 +589,9 @@ __device__ __forceinline__ void tb_body(const DevP<T> &P, S *__restrict__ gA, S 
     }
     if (FIRST) {
         // phi rows gy = y0 - H - 1 .. y0 - H + RH, of which phig holds -1 .. ny
-        for (int e = tx + 32 * ty; e < PL; e += 32 * BY) {
-            const int py = e / PW, px = e - py * PW;
+        constexpr int FL = (RH + 2) * FW;
+        for (int e = tx + 32 * ty; e < FL; e += 32 * BY) {
+            const int py = e / FW, px = e - py * FW;
             const int gy = y0 - H - 1 + py;
             if (gy < -1 || gy > ny) continue;
             const int gx = wrap_x(x0 - H - 1 + px, nx, wide);
@@ -582,16 +599,18 @@ __device__ __forceinline__ void tb_body(const DevP<T> &P, S *__restrict__ gA, S 
         }
     }
     cp_async_wait_all();
-    __syncthreads();
+    // every thread reads the cells of sweep 0 it copied itself; the ring of
+    // phi was copied by all threads
     if (FIRST) {
+        __syncthreads();
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
             const int ly = ty + BY * a, gy = y0 - H + ly;
             if (gy < 0 || gy >= ny) continue;
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-                const int li = (ly + 1) * PW + tx + 32 * b + 1;
-                const T *r1 = sphi + li, *r0 = r1 - PW, *r2 = r1 + PW;
+                const int lx = tx + 32 * b;
+                const T *r1 = sphi + (ly + 1) * FW + lx + 1, *r0 = r1 - FW, *r2 = r1 + FW;
                 const T phi = r1[0];
                 const T gxs_ = (r1[1] - r1[-1]) * T(1.0 / 3.0) +
                                ((r2[1] - r2[-1]) + (r0[1] - r0[-1])) * T(1.0 / 12.0);
@@ -599,7 +618,7 @@ __device__ __forceinline__ void tb_body(const DevP<T> &P, S *__restrict__ gA, S 
                                ((r2[1] + r2[-1]) - (r0[1] + r0[-1])) * T(1.0 / 12.0);
                 const T inv = T(1) / (T(1) + P.er1 * phi);
                 const T bb = P.src_norm * P.er1 * inv / P.tau_g;
-                cA[a][b] = P.src_norm * P.Kq * sq[li] * inv * T(1.0 / 3.0);
+                cA[a][b] = P.src_norm * P.Kq * sq[ly * RW + lx] * inv * T(1.0 / 3.0);
                 cBx[a][b] = bb * gxs_;
                 cBy[a][b] = bb * gys_;
             }
@@ -612,92 +631,37 @@ __device__ __forceinline__ void tb_body(const DevP<T> &P, S *__restrict__ gA, S 
     const T kf = T(0.5) * (T(1) - P.s_free_g);       // second moments
     const T ke = T(0.25) * P.s_free_g;               // their equilibrium psi/3, psi = 1.5 (m3 + m4)
     const T wG = P.wG;
-    int li[NA][NB];
-#pragma unroll
-    for (int a = 0; a < NA; ++a)
-#pragma unroll
-        for (int b = 0; b < NB; ++b) li[a][b] = (ty + BY * a + 1) * PW + tx + 32 * b + 1;
     const bool interior = y0 - H >= 0 && y0 - H + RH <= ny;
-    if (interior) {
-        // no wall and no empty row in the region: the same update everywhere
 #pragma unroll 1
-        for (int s = 0; s < NSW; ++s) {
-            T o1[NA][NB], o2[NA][NB], o3[NA][NB], o4[NA][NB];
+    for (int s = 0; s < NSW; ++s) {
 #pragma unroll
-            for (int a = 0; a < NA; ++a)
+        for (int a = 0; a < NA; ++a) {
+            const int ly = ty + BY * a, gy = y0 - H + ly;
+            if (!interior && (gy < 0 || gy >= ny)) continue;
+            const bool top = !interior && gy + 1 >= ny, bot = !interior && gy == 0;
 #pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    const int l = li[a][b];
-                    const T g1 = sg[l], g2 = sg[PL + l], g3 = sg[2 * PL + l], g4 = sg[3 * PL + l];
-                    const T m1 = g1 - g3, m2 = g2 - g4, m3 = g1 + g3, m4 = g2 + g4;
-                    if (RESID) psi_before[a][b] = T(1.5) * (m3 + m4);
-                    const T X6 = T(0.5) * (cA[a][b] - cBx[a][b] * m1 - cBy[a][b] * m2);
-                    const T e = ke * (m3 + m4) + X6;                 // half of s psi/3 + X/3
-                    const T h3 = kf * m3 + e, h4 = kf * m4 + e;      // half of n3, n4
-                    const T h1 = k1 * m1, h2 = k1 * m2;              // half of n1, n2
-                    o1[a][b] = h3 + h1;
-                    o3[a][b] = h3 - h1;
-                    o2[a][b] = (h4 + h2) - wG;
-                    o4[a][b] = (h4 - h2) + wG;
-                }
-            __syncthreads();
-#pragma unroll
-            for (int a = 0; a < NA; ++a)
-#pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    const int l = li[a][b];
-                    sg[l + 1] = o1[a][b];
-                    sg[2 * PL + l - 1] = o3[a][b];
-                    sg[PL + l + PW] = o2[a][b];
-                    sg[3 * PL + l - PW] = o4[a][b];
-                }
-            __syncthreads();
-        }
-    } else {
-#pragma unroll 1
-        for (int s = 0; s < NSW; ++s) {
-            T o1[NA][NB], o2[NA][NB], o3[NA][NB], o4[NA][NB];
-#pragma unroll
-            for (int a = 0; a < NA; ++a) {
-                const int gy = y0 - H + ty + BY * a;
-                if (gy < 0 || gy >= ny) continue;
-#pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    const int l = li[a][b];
-                    const T g1 = sg[l], g2 = sg[PL + l], g3 = sg[2 * PL + l], g4 = sg[3 * PL + l];
-                    const T psit = T(1.5) * ((g1 + g3) + (g2 + g4));
-                    if (RESID) psi_before[a][b] = psit;
-                    const T m1 = g1 - g3, m2 = g2 - g4, m3 = g1 + g3, m4 = g2 + g4;
-                    const T X3 = cA[a][b] - cBx[a][b] * m1 - cBy[a][b] * m2;
-                    const T eq = psit * T(1.0 / 3.0);
-                    const T n1 = (T(1) - P.s_g) * m1, n2 = (T(1) - P.s_g) * m2;
-                    const T n3 = m3 - P.s_free_g * (m3 - eq) + X3;
-                    const T n4 = m4 - P.s_free_g * (m4 - eq) + X3;
-                    o1[a][b] = T(0.5) * (n3 + n1);
-                    o3[a][b] = T(0.5) * (n3 - n1);
-                    o2[a][b] = T(0.5) * (n4 + n2);
-                    o4[a][b] = T(0.5) * (n4 - n2);
-                }
+            for (int b = 0; b < NB; ++b) {
+                const int lx = tx + 32 * b;
+                // this node's cells after s sweeps
+                T *c1 = s1 + ly * W1 + lx - s + H, *c3 = s3 + ly * W1 + lx + s;
+                T *c2 = s2 + (ly - s + H) * RW + lx, *c4 = s4 + (ly + s) * RW + lx;
+                const T g1 = *c1, g2 = *c2, g3 = *c3, g4 = *c4;
+                const T m1 = g1 - g3, m2 = g2 - g4, m3 = g1 + g3, m4 = g2 + g4;
+                if (RESID) psi_before[a][b] = T(1.5) * (m3 + m4);
+                const T X6 = T(0.5) * (cA[a][b] - cBx[a][b] * m1 - cBy[a][b] * m2);
+                const T e = ke * (m3 + m4) + X6;                 // half of s psi/3 + X/3
+                const T h3 = kf * m3 + e, h4 = kf * m4 + e;      // half of n3, n4
+                const T h1 = k1 * m1, h2 = k1 * m2;              // half of n1, n2
+                const T p2 = h4 + h2, p4 = h4 - h2;
+                *c1 = h3 + h1;
+                *c3 = h3 - h1;
+                if (top) c4[RW] = -p2 + wG;         // cathode: ABB to psi_c, this node's g4 next sweep
+                else *c2 = p2 - wG;
+                if (bot) c2[-RW] = -p4 - wG;        // anode: ABB to psi_a, this node's g2 next sweep
+                else *c4 = p4 + wG;
             }
-            __syncthreads();
-#pragma unroll
-            for (int a = 0; a < NA; ++a) {
-                const int gy = y0 - H + ty + BY * a;
-                if (gy < 0 || gy >= ny) continue;
-                const bool top = gy + 1 >= ny, bot = gy == 0;
-#pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    const int l = li[a][b];
-                    sg[l + 1] = o1[a][b];
-                    sg[2 * PL + l - 1] = o3[a][b];
-                    if (!top) sg[PL + l + PW] = o2[a][b] - P.wG;
-                    else sg[3 * PL + l] = -o2[a][b] + P.wG;       // cathode: ABB to psi_c
-                    if (!bot) sg[3 * PL + l - PW] = o4[a][b] + P.wG;
-                    else sg[PL + l] = -o4[a][b] - P.wG;           // anode: ABB to psi_a
-                }
-            }
-            __syncthreads();
         }
+        __syncthreads();
     }
 
     // ---- store the output tile (and, FIRST, its coefficients) ----
@@ -711,9 +675,10 @@ __device__ __forceinline__ void tb_body(const DevP<T> &P, S *__restrict__ gA, S 
         for (int b = 0; b < NB; ++b) {
             const int lx = tx + 32 * b, gx = x0 - H + lx;
             if (lx < H || lx >= H + TX || gx >= nx) continue;
-            const int l = li[a][b];
             const long long k = row + gx;
-            const T g1 = sg[l], g2 = sg[PL + l], g3 = sg[2 * PL + l], g4 = sg[3 * PL + l];
+            // cells after NSW = H sweeps
+            const T g1 = s1[ly * W1 + lx], g3 = s3[ly * W1 + lx + H];
+            const T g2 = s2[ly * RW + lx], g4 = s4[(ly + H) * RW + lx];
             sts(dst + k, g1, P.sc_g);
             sts(dst + nn + k, g2, P.sc_g);
             sts(dst + 2 * nn + k, g3, P.sc_g);

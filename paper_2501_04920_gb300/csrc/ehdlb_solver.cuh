@@ -763,7 +763,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     PhiRef<T> ref_{};
     double *part_ = nullptr, *part2_ = nullptr, *stage_ = nullptr;
     int tb_chunk_ = sizeof(T) == 4 ? 5 : 2;  // sweeps fused per launch (0: one per launch)
-    int tb_shape_ = 0;                        // region shape of the fused sweep kernel
+    int tb_shape_ = sizeof(T) == 4 ? 1 : 0;   // region shape of the fused sweep kernel
     int tb_m_ = 0;                            // launch index within the step
     int qi_ = 0;                              // ion populations per species (5 or 9) of pops_
     T *coef_ = nullptr;                       // source coefficients A, Bx, By of the step
