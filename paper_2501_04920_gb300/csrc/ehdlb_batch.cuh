@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(32 * BY, MINB) kb_sweep(const CaseDev<T, S> *_
 
 // O5-O11 of every case.  blockDim (64, 4), dynamic shared memory main_smem_bytes<T, S>().
 template <typename T, typename S, bool SNAP>
-__global__ void __launch_bounds__(256, 3) kb_main(const CaseDev<T, S> *__restrict__ cases,
+__global__ void __launch_bounds__(256, MAIN_MINB<T>) kb_main(const CaseDev<T, S> *__restrict__ cases,
                                                   const WorkItem *__restrict__ items, const int *__restrict__ nitems)
 {
     __shared__ CaseDev<T, S> C;

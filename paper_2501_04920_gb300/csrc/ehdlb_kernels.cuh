@@ -632,7 +632,7 @@ __device__ __forceinline__ void tb_body(const DevP<T> &P, S *__restrict__ gA, S 
     const T ke = T(0.25) * P.s_free_g;               // their equilibrium psi/3, psi = 1.5 (m3 + m4)
     const T wG = P.wG;
     const bool interior = y0 - H >= 0 && y0 - H + RH <= ny;
-#pragma unroll 1
+#pragma unroll
     for (int s = 0; s < NSW; ++s) {
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
@@ -991,6 +991,10 @@ static __global__ void __launch_bounds__(256) k_sweep_decide(const double *__res
 // n (one allocation of 17 + 2 QI planes) and (phi u)(t-1) x, y of type S,
 // then g1..g4 of type T.
 template <int QI> __host__ __device__ constexpr int main_splanes() { return 17 + 2 * QI + 2; }
+// Blocks of 256 per SM the step kernel's registers are sized for: 4 in float
+// (64 registers; measured 9 % faster at 2048^2 than 3 blocks at 80 registers,
+// though a few bytes spill), 3 in double.
+template <typename T> constexpr int MAIN_MINB = sizeof(T) == 4 ? 4 : 3;
 constexpr int MAIN_TPLANES = 4;
 template <typename T, typename S, int QI = 5> __host__ __device__ constexpr size_t main_smem_bytes()
 {
@@ -1467,7 +1471,7 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
 }
 
 template <typename T, typename S, bool SNAP, bool FROZEN, bool RESID, bool VEC, int QI = 5>
-__global__ void __launch_bounds__(256, 3) k_main(const DevP<T> P, const Pops<S> src, const Pops<S> dst,
+__global__ void __launch_bounds__(256, MAIN_MINB<T>) k_main(const DevP<T> P, const Pops<S> src, const Pops<S> dst,
                                                  const T *__restrict__ gA, const T *__restrict__ gB,
                                                  const Control *__restrict__ ctl, const PhiRef<T> Rf,
                                                  S *__restrict__ phiu, const T *__restrict__ psi_prev,
