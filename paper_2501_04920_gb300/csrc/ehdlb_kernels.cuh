@@ -1010,13 +1010,21 @@ __device__ __forceinline__ void stage_planes(E *st, PlaneF plane, int nx, int ny
                                              bool inside, long long k)
 {
     if constexpr (VEC) {
-        constexpr int NE = 16 / (int)sizeof(E), CH = 64 / NE, NCH = NPL * 4 * CH;
-        for (int c = tid; c < NCH; c += 256) {
-            const int pl = c / (4 * CH), r = c - pl * (4 * CH);
-            const int row = r / CH, ch = r - row * CH;
-            const int y = y0 + row, x = x0 + ch * NE;
-            if (y >= ny || x >= nx) continue;
-            cp_async16(st + pl * 256 + row * 64 + ch * NE, plane(pl) + (long long)y * nx + x);
+        // a plane's 4 rows of 64 take PER 16-byte chunks; 256 / PER planes per
+        // pass of the block, so each thread keeps its row and chunk and steps
+        // through the planes
+        constexpr int NE = 16 / (int)sizeof(E), CH = 64 / NE, PER = 4 * CH, STEP = 256 / PER;
+        static_assert(256 % PER == 0, "staging pass");
+        const int r = tid % PER, row = r / CH, ch = r - row * CH;
+        const int y = y0 + row, x = x0 + ch * NE;
+        if (y < ny && x < nx) {
+            const long long off = (long long)y * nx + x;
+            E *d = st + row * 64 + ch * NE;
+#pragma unroll
+            for (int j = 0; j < (NPL + STEP - 1) / STEP; ++j) {
+                const int pl = tid / PER + j * STEP;
+                if (pl < NPL) cp_async16(d + pl * 256, plane(pl) + off);
+            }
         }
     } else {
         if (!inside) return;
