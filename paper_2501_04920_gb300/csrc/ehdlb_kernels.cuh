@@ -559,6 +559,11 @@ __device__ __forceinline__ void tb_body(const DevP<T> &P, S *__restrict__ gA, S 
         const int ly = ty + BY * a, gy = y0 - H + ly;
 #pragma unroll
         for (int b = 0; b < NB; ++b) cA[a][b] = cBx[a][b] = cBy[a][b] = T(0);
+        if (FIRST && gy >= -1 && gy <= ny) {   // phi of this node (the ghost rows included)
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+                cp_async(sphi + (ly + 1) * FW + tx + 32 * b + 1, phig + (long long)(gy + 1) * nx + gxs[b]);
+        }
         if (gy < 0 || gy >= ny) continue;
         const long long row = (long long)gy * nx;
 #pragma unroll
@@ -588,14 +593,24 @@ __device__ __forceinline__ void tb_body(const DevP<T> &P, S *__restrict__ gA, S 
         }
     }
     if (FIRST) {
-        // phi rows gy = y0 - H - 1 .. y0 - H + RH, of which phig holds -1 .. ny
-        constexpr int FL = (RH + 2) * FW;
-        for (int e = tx + 32 * ty; e < FL; e += 32 * BY) {
-            const int py = e / FW, px = e - py * FW;
+        // the ring of phi around the region: the rows below and above it
+        // (2 FW cells), then its left and right columns (2 RH cells); phig
+        // holds the rows -1 .. ny
+        constexpr int NR = 2 * FW + 2 * RH;
+        for (int e = tx + 32 * ty; e < NR; e += 32 * BY) {
+            int py, px;
+            if (e < 2 * FW) {
+                py = e < FW ? 0 : RH + 1;
+                px = e < FW ? e : e - FW;
+            } else {
+                const int c = e - 2 * FW;
+                py = 1 + (c < RH ? c : c - RH);
+                px = c < RH ? 0 : RW + 1;
+            }
             const int gy = y0 - H - 1 + py;
             if (gy < -1 || gy > ny) continue;
             const int gx = wrap_x(x0 - H - 1 + px, nx, wide);
-            cp_async(sphi + e, phig + (long long)(gy + 1) * nx + gx);
+            cp_async(sphi + py * FW + px, phig + (long long)(gy + 1) * nx + gx);
         }
     }
     cp_async_wait_all();
