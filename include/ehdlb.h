@@ -251,7 +251,7 @@ int ehdlb_set_timing(ehdlb_ctx *c, int on);
  *     block (512 threads; the double solver's only shape), 1: 64 x 32 (256
  *     threads; default for float), 2: clusters of 2 x 4 blocks of 64 x 32
  *     that exchange populations through distributed shared memory every
- *     sweep; 1 and 2 float only;
+ *     sweep, 3: 64 x 64 (512 threads); 1, 2 and 3 float only;
  *   main_staging: how the step kernel copies its block's populations to
  *     shared memory, 0: one asynchronous copy per node and plane, 1: 16-byte
  *     copies of row segments (default; used only when nx times the element

@@ -465,11 +465,13 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     // sweeps one launch fuses.
     struct TbShape { int rw, rh, by, minb; };
     // float: shape 2 is the cluster kernel (k_sweep_cl), 2 x 4 CTAs of 64 x 32
-    static constexpr int TB_NSHAPES = sizeof(T) == 4 ? 3 : 1;
+    static constexpr int TB_NSHAPES = sizeof(T) == 4 ? 4 : 1;
     static constexpr int CL_X = 2, CL_Y = 4, CL_BY = 16;
     static constexpr TbShape tb_shape(int i)
     {
-        return sizeof(T) == 4 ? (i == 1 ? TbShape{64, 32, 8, 4} : TbShape{64, 32, 16, 3}) : TbShape{64, 16, 16, 2};
+        return sizeof(T) == 4
+                   ? (i == 1 ? TbShape{64, 32, 8, 4} : (i == 3 ? TbShape{64, 64, 16, 2} : TbShape{64, 32, 16, 3}))
+                   : TbShape{64, 16, 16, 2};
     }
     static constexpr int TB_MAX = sizeof(T) == 4 ? 5 : 2;
 
@@ -528,6 +530,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         cudaError_t e = tb_attr1<NSW, 0>();
         if constexpr (TB_NSHAPES > 1) {
             if (e == cudaSuccess) e = tb_attr1<NSW, 1>();
+            if (e == cudaSuccess) e = tb_attr1<NSW, 3>();
             if (e == cudaSuccess) e = cl_attr2<NSW, false, false>();
             if (e == cudaSuccess) e = cl_attr2<NSW, false, true>();
             if (e == cudaSuccess) e = cl_attr2<NSW, true, false>();
@@ -580,6 +583,8 @@ template <typename T, typename S = T> class Solver : public SolverBase {
                 }
             } else if (tb_shape_ == 1) {
                 tb_launch1<NSW, 1>(first, resid);
+            } else if (tb_shape_ == 3) {
+                tb_launch1<NSW, 3>(first, resid);
             } else {
                 tb_launch1<NSW, 0>(first, resid);
             }

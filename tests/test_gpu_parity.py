@@ -221,7 +221,7 @@ def test_fp32_every_sweep_tuning_matches_oracle():
     orc = oracle.Oracle(nx, ny, prm)
     orc.step(steps)
     ref = orc.fields()
-    for shape in range(3):
+    for shape in range(4):
         for spl in (0, 1, 2, 3, 4, 5):
             lat = ehdlb.Lattice(nx, ny, prm, precision=ehdlb.FP32)
             ehdlb.ehdlb_set_tuning(lat.ctx, spl, shape, spl % 2)
@@ -303,7 +303,7 @@ def test_error_codes():
                                            sweep_tol=0.0, init_sweeps_max=10))
     assert L.ehdlb_set_params(h, ehdlb.C.byref(good)) == ehdlb.OK
     assert L.ehdlb_set_tuning(h, 6, 0, 0) == ehdlb.EINVAL
-    assert L.ehdlb_set_tuning(h, 2, 3, 0) == ehdlb.EINVAL
+    assert L.ehdlb_set_tuning(h, 2, 4, 0) == ehdlb.EINVAL
     assert L.ehdlb_set_tuning(h, 2, 0, 2) == ehdlb.EINVAL
     assert L.ehdlb_set_tuning(h, -1, -1, -1) == ehdlb.OK
     assert L.ehdlb_step(h, 2, ehdlb.C.byref(st)) == ehdlb.WNOTCONV
