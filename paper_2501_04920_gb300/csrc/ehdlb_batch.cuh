@@ -214,14 +214,33 @@ __global__ void __launch_bounds__(256) kb_step_end(const CaseDev<T, S> *__restri
     }
 }
 
-// Every case of a batch (launch: any number of blocks of 256).
+// Slice sums of every case of a batch, item (case, slice) at parts[3 * item]
+// with DEF_MAX_SLICES items per case
+// (launch: any number of blocks of 256).
 template <typename T, typename S>
-__global__ void __launch_bounds__(256) kb_deformation(const CaseDev<T, S> *__restrict__ cases,
-                                                      const int *__restrict__ ncases, double *out)
+__global__ void __launch_bounds__(256) kb_deform_sums(const CaseDev<T, S> *__restrict__ cases,
+                                                      const int *__restrict__ ncases, double *parts)
 {
+    __shared__ double red[256][3];
+    const long long n = (long long)*ncases * DEF_MAX_SLICES;
+    for (long long i = blockIdx.x; i < n; i += gridDim.x) {
+        const CaseDev<T, S> *C = cases + i / DEF_MAX_SLICES;
+        const int j = (int)(i % DEF_MAX_SLICES), nsl = deform_slices(C->P.nx, C->P.ny);
+        if (j < nsl) deform_slice_sums(C->snap, C->P.nx, C->P.ny, j, nsl, red, parts + 3 * i);
+    }
+}
+
+// D of every case of a batch from its slice sums (launch: any number of blocks of 256).
+template <typename T, typename S>
+__global__ void __launch_bounds__(256) kb_deform_finish(const CaseDev<T, S> *__restrict__ cases,
+                                                        const int *__restrict__ ncases,
+                                                        const double *__restrict__ parts, double *out)
+{
+    __shared__ double red[256][3];
     const int n = *ncases;
     for (int c = blockIdx.x; c < n; c += gridDim.x)
-        deformation_body(cases[c].snap, cases[c].P.nx, cases[c].P.ny, out + c);
+        deform_finish(cases[c].snap, cases[c].P.nx, cases[c].P.ny, parts + (long long)3 * DEF_MAX_SLICES * c, red,
+                      out + c);
 }
 
 }  // namespace ehdlb
@@ -407,7 +426,10 @@ template <typename T, typename S> class Batch : public BatchBase {
             const int r = rebuild(err);
             if (r != EHDLB_OK) return r;
         }
-        kb_deformation<T, S><<<std::min(ncases_, 4 * sms_), 256, 0, stream_>>>(d_cases_, d_nitems_ + 6, d_D_);
+        kb_deform_sums<T, S><<<(int)std::min<long long>((long long)ncases_ * DEF_MAX_SLICES, 8LL * sms_), 256, 0,
+                               stream_>>>(d_cases_, d_nitems_ + 6, d_Dpart_);
+        kb_deform_finish<T, S><<<std::min(ncases_, 4 * sms_), 256, 0, stream_>>>(d_cases_, d_nitems_ + 6, d_Dpart_,
+                                                                                 d_D_);
         EHDLB_CK(cudaGetLastError());
         std::vector<double> all(ncases_);
         EHDLB_CK(cudaMemcpyAsync(all.data(), d_D_, sizeof(double) * ncases_, cudaMemcpyDeviceToHost, stream_));
@@ -608,6 +630,7 @@ template <typename T, typename S> class Batch : public BatchBase {
         ncases_ = c;
         EHDLB_CK(ensure(d_cases_, cap_cases_, host_cases_.size()));
         EHDLB_CK(ensure(d_D_, cap_D_, host_cases_.size()));
+        EHDLB_CK(ensure(d_Dpart_, cap_Dpart_, host_cases_.size() * 3 * DEF_MAX_SLICES));
         EHDLB_CK(ensure(d_items_node_, cap_node_, node.size()));
         for (int nsw = 1; nsw <= TBMAX; ++nsw) EHDLB_CK(ensure(d_items_tb_[nsw], cap_tb_[nsw], tb[nsw].size()));
         EHDLB_CK(cudaMemcpyAsync(d_cases_, host_cases_.data(), sizeof(CaseDev<T, S>) * host_cases_.size(),
@@ -647,11 +670,12 @@ template <typename T, typename S> class Batch : public BatchBase {
     std::vector<void *> dev_;
     CaseDev<T, S> *d_cases_ = nullptr;
     double *d_D_ = nullptr;
+    double *d_Dpart_ = nullptr;   // slice sums of the deformation factor
     WorkItem *d_items_node_ = nullptr;
     WorkItem *d_items_tb_[TBMAX + 1] = {};
     int *d_nitems_ = nullptr;   // [0] node items, [1..5] sweep items by NSW, [6] cases
     int host_nitems_[8] = {};
-    size_t cap_cases_ = 0, cap_D_ = 0, cap_node_ = 0, cap_tb_[TBMAX + 1] = {};
+    size_t cap_cases_ = 0, cap_D_ = 0, cap_Dpart_ = 0, cap_node_ = 0, cap_tb_[TBMAX + 1] = {};
     cudaGraphExec_t gexec_ = nullptr;
     cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;
 };

@@ -112,6 +112,16 @@ struct Control {
                        // read by the batched kernels, the single-lattice host tracks its own)
 };
 
+// Opens an ehdlb_step call: zeroes its per-call counters (launch: 1 thread).
+static __global__ void k_open_call(Control *c)
+{
+    c->tloc = 0;
+    c->sweeps_total = 0;
+    c->sweeps_max = 0;
+    c->notconv = 0;
+    c->unstable = 0;
+}
+
 // One allocation of 17 + 2 QI planes (QI = 5 or 9 ion populations): f at +0,
 // h at +8 nn, p at +17 nn, n at +(17 + QI) nn.
 template <typename S> struct Pops {
@@ -1509,6 +1519,34 @@ __global__ void __launch_bounds__(256, MAIN_MINB<T>) k_main(const DevP<T> P, con
 // reduced), the step's residual, counters, the next step's g parity.
 //   resid: 0 none; 1 from the main kernel's partials (columns 2, 3 of 4);
 //          2 from the fused sweep kernel's partials (2 per block in part2).
+// First stage of a two-stage sum of NV-wide block partials in a fixed order:
+// thread t of block b adds the partials b * 256 + t + k * 256 G (G = gridDim.x),
+// the block's tree sum goes to out[NV * b].  The end of step then sums the G
+// results in one block.
+template <int NV>
+__global__ void __launch_bounds__(256) k_partials(const double *__restrict__ part, long long nb, double *out)
+{
+    __shared__ double red[256][NV];
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < nb; i += 256LL * gridDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] += part[NV * i + k];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) red[threadIdx.x][k] += red[threadIdx.x + s][k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[NV * blockIdx.x + k] = red[0][k];
+}
+
 __device__ __forceinline__ void step_end_body(const double *__restrict__ part, long long nb,
                                               const double *__restrict__ part2, long long nb2, Control *ctl,
                                               int *counts, int resid, int sums)
@@ -1732,11 +1770,11 @@ __global__ void k_to_double(const T *__restrict__ a, double *__restrict__ out, l
 // ---- deformation factor (Eq. 63) ------------------------------------------------
 
 // Deformation factor D = (L - H) / (L + H) (Eq. 63) of the phi field (the
-// first plane of a snapshot), one block of 256 per lattice: L is the extent
-// of phi >= 1/2 along the field (y) through the phi-weighted centroid, H
-// the same across it (x); the line is sampled by bilinear interpolation of
-// the nodes (x periodic, rows clamped at the walls) and each end is the
-// crossing of 1/2 interpolated linearly between consecutive samples.
+// first plane of a snapshot): L is the extent of phi >= 1/2 along the field
+// (y) through the phi-weighted centroid, H the same across it (x); the line
+// is sampled by bilinear interpolation of the nodes (x periodic, rows clamped
+// at the walls) and each end is the crossing of 1/2 interpolated linearly
+// between consecutive samples.
 template <typename T>
 __device__ __forceinline__ double phi_sample(const T *phi, int nx, int ny, double x, double y)
 {
@@ -1752,67 +1790,178 @@ __device__ __forceinline__ double phi_sample(const T *phi, int nx, int ny, doubl
     return a * (1.0 - fy) + b * fy;
 }
 
-template <typename T>
-__device__ __forceinline__ double phi_extent(const T *phi, int nx, int ny, double xc, double yc, bool along_y)
+// The phi-weighted sums of the centroid are taken over slices of the nodes in
+// row-major order, deform_slices(nx, ny) of them of (near) equal size, each
+// reduced by one block in a fixed order, so one lattice and the same lattice
+// inside a batch give the same bits.
+constexpr int DEF_MAX_SLICES = 1024;
+constexpr int DEF_SLICE_NODES = 4096;
+
+__host__ __device__ inline int deform_slices(int nx, int ny)
 {
-    const int lim = along_y ? ny : nx;
-    double e[2];
-    for (int dir = 0; dir < 2; ++dir) {
-        const double sgn = dir ? 1.0 : -1.0;
-        double pt = 0.0, pv = phi_sample(phi, nx, ny, xc, yc), end = sgn * lim;
-        for (int s = 1; s < lim; ++s) {
-            const double tt = sgn * s;
-            const double v = along_y ? phi_sample(phi, nx, ny, xc, yc + tt) : phi_sample(phi, nx, ny, xc + tt, yc);
-            if (pv >= 0.5 && v < 0.5) {
-                end = pt + (tt - pt) * (pv - 0.5) / (pv - v);
-                break;
-            }
-            pt = tt;
-            pv = v;
-        }
-        e[dir] = end;
-    }
-    return e[1] - e[0];
+    const long long s = (long long)nx * ny / DEF_SLICE_NODES;
+    return (int)(s < 1 ? 1 : (s > DEF_MAX_SLICES ? DEF_MAX_SLICES : s));
 }
 
-template <typename T>
-__device__ __forceinline__ void deformation_body(const T *__restrict__ phi, int nx, int ny, double *out)
+// Error-free sum of two floats (Knuth's TwoSum): returns s = fl(a + b) and
+// sets e with s + e == a + b exactly.
+__device__ __forceinline__ float two_sum(float a, float b, float &e)
 {
-    __shared__ double red[256][3];
-    double a[3] = {0.0, 0.0, 0.0};
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
+// (sum phi, sum phi x, sum phi y) over slice j of nsl (one block of 256);
+// thread 0 writes the three sums to dst.
+template <typename T>
+__device__ __forceinline__ void deform_slice_sums(const T *__restrict__ phi, int nx, int ny, int j, int nsl,
+                                                  double (*red)[3], double *dst)
+{
     const long long nn = (long long)nx * ny;
-    for (long long k = threadIdx.x; k < nn; k += blockDim.x) {
-        const double v = (double)phi[k];
-        a[0] += v;
-        a[1] += v * (double)(k % nx);
-        a[2] += v * (double)(k / nx);
+    const long long k0 = j * nn / nsl, k1 = (j + 1) * nn / nsl;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    // FP32 fields: each thread keeps its sums as unevaluated float pairs
+    // (hi + lo; exact products by fmaf, TwoSum additions), about 48 bits, and
+    // hands them to double per row (sum phi, sum phi y) and at the end (sum
+    // phi x): the FP32 pipe does the per-node work.
+    float h1 = 0.f, l1 = 0.f;
+    int y = (int)(k0 / nx);
+    for (long long rowk = (long long)y * nx; rowk < k1; ++y, rowk += nx) {
+        const int xs = (int)(k0 > rowk ? k0 - rowk : 0), xe = (int)(k1 - rowk < nx ? k1 - rowk : nx);
+        const T *row = phi + rowk;
+        const double fy = (double)y;
+        if constexpr (sizeof(T) == 4) {
+            const int x0 = xs + (int)threadIdx.x;
+            if (x0 >= xe) continue;   // no node of this row for this thread
+            float rh = 0.f, rl = 0.f;
+            float xf = (float)x0;   // exact: x < 2^24
+#pragma unroll 4
+            for (int x = x0; x < xe; x += 256, xf = __fadd_rn(xf, 256.f)) {
+                const float v = (float)row[x];
+                float e;
+                rh = two_sum(rh, v, e);
+                rl = __fadd_rn(rl, e);
+                const float p = __fmul_rn(v, xf), pe = __fmaf_rn(v, xf, -p);
+                h1 = two_sum(h1, p, e);
+                l1 = __fadd_rn(l1, __fadd_rn(e, pe));
+            }
+            const double r = (double)rh + (double)rl;
+            a0 += r;
+            a2 += r * fy;
+        } else {
+#pragma unroll 4
+            for (int x = xs + (int)threadIdx.x; x < xe; x += 256) {
+                const double v = (double)row[x];
+                a0 += v;
+                a1 += v * (double)x;
+                a2 += v * fy;
+            }
+        }
     }
-    for (int i = 0; i < 3; ++i) red[threadIdx.x][i] = a[i];
+    a1 += (double)h1 + (double)l1;
+    red[threadIdx.x][0] = a0;
+    red[threadIdx.x][1] = a1;
+    red[threadIdx.x][2] = a2;
     __syncthreads();
     for (int s = 128; s > 0; s >>= 1) {
         if ((int)threadIdx.x < s)
             for (int i = 0; i < 3; ++i) red[threadIdx.x][i] += red[threadIdx.x + s][i];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        const double sphi = red[0][0];
-        if (!(sphi > 0.0)) {
-            *out = 0.0;
-        } else {
-            const double xc = red[0][1] / sphi, yc = red[0][2] / sphi;
-            const double L = phi_extent(phi, nx, ny, xc, yc, true);
-            const double H = phi_extent(phi, nx, ny, xc, yc, false);
-            *out = (L - H) / (L + H);
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 3; ++i) dst[i] = red[0][i];
+    __syncthreads();
+}
+
+// End of the phi >= 1/2 run through (xc, yc) in direction sgn along y or x,
+// searched by one warp 32 samples at a time: the first s = 1 .. lim-1 whose
+// sample drops below 1/2 after one at or above it, interpolated linearly
+// between the two; sgn * lim when there is none.
+template <typename T>
+__device__ __forceinline__ double phi_run_end(const T *phi, int nx, int ny, double xc, double yc, bool along_y,
+                                              double sgn)
+{
+    const int lane = threadIdx.x & 31, lim = along_y ? ny : nx;
+    double carry = phi_sample(phi, nx, ny, xc, yc);
+    for (int base = 1; base < lim; base += 32) {
+        const int s = base + lane;
+        const double tt = sgn * (double)s;
+        double v = 0.0;
+        if (s < lim) v = along_y ? phi_sample(phi, nx, ny, xc, yc + tt) : phi_sample(phi, nx, ny, xc + tt, yc);
+        double pv = __shfl_up_sync(0xffffffffu, v, 1);
+        if (lane == 0) pv = carry;
+        const bool hit = s < lim && pv >= 0.5 && v < 0.5;
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (m) {
+            const int first = __ffs(m) - 1;
+            double end = 0.0;
+            if (lane == first) {
+                const double pt = s == 1 ? 0.0 : sgn * (double)(s - 1);
+                end = pt + (tt - pt) * (pv - 0.5) / (pv - v);
+            }
+            return __shfl_sync(0xffffffffu, end, first);
         }
+        carry = __shfl_sync(0xffffffffu, v, 31);
+    }
+    return sgn * lim;
+}
+
+// D = (L - H) / (L + H) from the deform_slices(nx, ny) slice sums at parts
+// (one block of 256; four warps search the four ends of the two axes).
+template <typename T>
+__device__ __forceinline__ void deform_finish(const T *__restrict__ phi, int nx, int ny, const double *parts,
+                                              double (*red)[3], double *out)
+{
+    __shared__ double ends[4];
+    const int nsl = deform_slices(nx, ny);
+    for (int i = 0; i < 3; ++i) {
+        double acc = 0.0;
+        for (int j = threadIdx.x; j < nsl; j += 256) acc += parts[3 * j + i];
+        red[threadIdx.x][i] = acc;
+    }
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int i = 0; i < 3; ++i) red[threadIdx.x][i] += red[threadIdx.x + s][i];
+        __syncthreads();
+    }
+    const double sphi = red[0][0];
+    if (!(sphi > 0.0)) {
+        if (threadIdx.x == 0) *out = 0.0;
+        __syncthreads();
+        return;
+    }
+    const double xc = red[0][1] / sphi, yc = red[0][2] / sphi;
+    const int w = threadIdx.x >> 5;
+    if (w < 4) {
+        const double e = phi_run_end(phi, nx, ny, xc, yc, w >= 2, (w & 1) ? 1.0 : -1.0);
+        if ((threadIdx.x & 31) == 0) ends[w] = e;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double L = ends[3] - ends[2], H = ends[1] - ends[0];
+        *out = (L - H) / (L + H);
     }
     __syncthreads();
 }
 
-// One lattice (launch: 1 block of 256).
+// Slice sums of one lattice (launch: deform_slices(nx, ny) blocks of 256).
 template <typename T>
-__global__ void __launch_bounds__(256) k_deformation(const T *__restrict__ phi, int nx, int ny, double *out)
+__global__ void __launch_bounds__(256) k_deform_sums(const T *__restrict__ phi, int nx, int ny, double *parts)
 {
-    deformation_body(phi, nx, ny, out);
+    __shared__ double red[256][3];
+    deform_slice_sums(phi, nx, ny, blockIdx.x, gridDim.x, red, parts + 3 * blockIdx.x);
+}
+
+// D of one lattice from its slice sums (launch: 1 block of 256).
+template <typename T>
+__global__ void __launch_bounds__(256) k_deform_finish(const T *__restrict__ phi, int nx, int ny,
+                                                       const double *__restrict__ parts, double *out)
+{
+    __shared__ double red[256][3];
+    deform_finish(phi, nx, ny, parts, red, out);
 }
 
 }  // namespace ehdlb

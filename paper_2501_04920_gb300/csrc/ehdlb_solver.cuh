@@ -44,6 +44,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             else cudaFree(p);
         }
         for (cudaEvent_t e : events_) cudaEventDestroy(e);
+        if (pin_) cudaFreeHost(pin_);
         if (own_stream_) cudaStreamDestroy(stream_);
     }
 
@@ -98,6 +99,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             EHDLB_CK(tb_attr<5>());
         }
         EHDLB_CK(alloc((void **)&stage_, sizeof(double) * (size_t)nn_));
+        EHDLB_CK(alloc((void **)&red_, sizeof(double) * (6 * PSUM + 3 * DEF_MAX_SLICES)));
         EHDLB_CK(cudaMemsetAsync(snap_, 0, plane * EHDLB_NFIELDS, stream_));
         EHDLB_CK(cudaStreamSynchronize(stream_));
         return EHDLB_OK;
@@ -193,18 +195,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             counts_ = nc;
             counts_cap_ = nsteps;
         }
-        // open the call: per-call counters
-        ctl_h_.tloc = 0;
-        ctl_h_.sweeps_total = 0;
-        ctl_h_.sweeps_max = 0;
-        ctl_h_.notconv = 0;
-        ctl_h_.unstable = 0;
-        EHDLB_CK(cudaMemcpyAsync(&ctl_->tloc, &ctl_h_.tloc, sizeof(long long), cudaMemcpyHostToDevice, stream_));
-        EHDLB_CK(cudaMemcpyAsync(&ctl_->sweeps_total, &ctl_h_.sweeps_total, sizeof(long long),
-                                 cudaMemcpyHostToDevice, stream_));
-        EHDLB_CK(cudaMemsetAsync(&ctl_->unstable, 0, sizeof(int), stream_));
-        EHDLB_CK(cudaMemsetAsync(&ctl_->notconv, 0, sizeof(int), stream_));
-        EHDLB_CK(cudaMemsetAsync(&ctl_->sweeps_max, 0, sizeof(int), stream_));
+        EHDLB_CK(pinned());
         if (timing_ && (int)events_.size() < 4 * nsteps) {
             while ((int)events_.size() < 4 * nsteps) {
                 cudaEvent_t e;
@@ -214,13 +205,17 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         }
         launches_ = 0;
         sweep_launches_ = 0;
+        // open the call: per-call counters
+        k_open_call<<<1, 1, 0, stream_>>>(ctl_);
+        ++launches_;
         for (int s = 0; s < nsteps; ++s) {
             enqueue_step(s, s == nsteps - 1);
             EHDLB_CK(cudaGetLastError());
         }
-        EHDLB_CK(cudaMemcpyAsync(&ctl_h_, ctl_, sizeof(Control), cudaMemcpyDeviceToHost, stream_));
+        EHDLB_CK(cudaMemcpyAsync(&pin_->c, ctl_, sizeof(Control), cudaMemcpyDeviceToHost, stream_));
         EHDLB_CK(cudaStreamSynchronize(stream_));
         EHDLB_CK(cudaGetLastError());
+        ctl_h_ = pin_->c;
         last_nsteps = nsteps;
         const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (st) {
@@ -286,15 +281,27 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     // D of Eq. 63 from the phi of the last snapshot
     int deformation(double *out, std::string &err) override
     {
-        k_deformation<T><<<1, 256, 0, stream_>>>(snap_, nx_, ny_, stage_);
+        double *parts = red_ + 6 * PSUM;
+        k_deform_sums<T><<<deform_slices(nx_, ny_), 256, 0, stream_>>>(snap_, nx_, ny_, parts);
+        k_deform_finish<T><<<1, 256, 0, stream_>>>(snap_, nx_, ny_, parts, stage_);
         EHDLB_CK(cudaGetLastError());
-        EHDLB_CK(cudaMemcpyAsync(out, stage_, sizeof(double), cudaMemcpyDeviceToHost, stream_));
+        EHDLB_CK(pinned());
+        EHDLB_CK(cudaMemcpyAsync(&pin_->D, stage_, sizeof(double), cudaMemcpyDeviceToHost, stream_));
         EHDLB_CK(cudaStreamSynchronize(stream_));
+        *out = pin_->D;
         return EHDLB_OK;
     }
     int set_state(const double *src, std::string &err) override { return transfer_state(nullptr, src, err); }
 
   private:
+    // page-locked host copy of the control block and D, read back by every
+    // step call and deformation (allocated on first use: cases of a batch
+    // never need it)
+    cudaError_t pinned()
+    {
+        return pin_ ? cudaSuccess : cudaHostAlloc((void **)&pin_, sizeof(HostMirror), cudaHostAllocDefault);
+    }
+
     cudaError_t alloc(void **p, size_t bytes)
     {
         cudaError_t e = arena_ ? arena_->alloc(p, bytes) : cudaMalloc(p, bytes);
@@ -345,7 +352,8 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         const size_t b[] = {27 * nn * s, 4 * nn * t, 27 * nn * s, 4 * nn * t,
                             planes_row * t, planes_row * t, planes_row * t,
                             nn * t, nn * t, nn * t, nn * t, 3 * nn * t, 2 * nn * s, nn * t,
-                            EHDLB_NFIELDS * nn * t, 4 * gx * gy * 8, sizeof(Control), 2 * nbmax * 8, nn * 8};
+                            EHDLB_NFIELDS * nn * t, 4 * gx * gy * 8, sizeof(Control), 2 * nbmax * 8, nn * 8,
+                            (size_t)(6 * PSUM + 3 * DEF_MAX_SLICES) * 8};
         size_t tot = 0;
         for (size_t v : b) tot += (v + 255) / 256 * 256;
         return tot;
@@ -695,7 +703,22 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             const dim3 g = tb_grid(std::min(chunk, fixedK - (nk - 1) * chunk), tb_shape_, nx_, ny_);
             nb2 = (long long)g.x * g.y;
         }
-        k_step_end<<<1, 256, 0, stream_>>>(part_, nb_, part2_, nb2, ctl_, counts_, resid_mode, last ? 1 : 0);
+        // sums of the block partials in two stages (PSUM blocks, then one)
+        const double *p4 = part_, *p2 = part2_;
+        long long n4 = nb_, n2 = nb2;
+        if ((resid_mode == 1 || last) && nb_ > PSUM) {
+            k_partials<4><<<PSUM, 256, 0, stream_>>>(part_, nb_, red_);
+            p4 = red_;
+            n4 = PSUM;
+            ++launches_;
+        }
+        if (resid_mode == 2 && nb2 > PSUM) {
+            k_partials<2><<<PSUM, 256, 0, stream_>>>(part2_, nb2, red_ + 4 * PSUM);
+            p2 = red_ + 4 * PSUM;
+            n2 = PSUM;
+            ++launches_;
+        }
+        k_step_end<<<1, 256, 0, stream_>>>(p4, n4, p2, n2, ctl_, counts_, resid_mode, last ? 1 : 0);
         launches_ += 2;
         if (timing_) cudaEventRecord(events_[4 * s + 3], stream_);
         tpar_ ^= 1;
@@ -771,8 +794,15 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     int tb_shape_ = sizeof(T) == 4 ? 1 : 0;   // region shape of the fused sweep kernel
     int tb_m_ = 0;                            // launch index within the step
     int qi_ = 0;                              // ion populations per species (5 or 9) of pops_
+    static constexpr int PSUM = 64;           // blocks of the first stage of the partial sums
+    double *red_ = nullptr;                   // their results: 4 PSUM, then 2 PSUM doubles, then the
+                                              // slice sums of the deformation factor
     T *coef_ = nullptr;                       // source coefficients A, Bx, By of the step
     Control *ctl_ = nullptr;
+    struct HostMirror {
+        Control c;
+        double D;
+    } *pin_ = nullptr;
     Control ctl_h_{};
     int *counts_ = nullptr;
     int counts_cap_ = 0;

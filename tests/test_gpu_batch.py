@@ -99,8 +99,9 @@ def test_batch_rejects_cases_it_does_not_take():
     b.close()
 
 
-def test_device_deformation_is_eq63_of_the_fields():
-    nx, ny = 128, 192
+@pytest.mark.parametrize("nx,ny", [(64, 96), (128, 192), (300, 520), (2048, 2048)])
+def test_device_deformation_is_eq63_of_the_fields(nx, ny):
+    # one slice of the device sums, a few, slices ending inside rows, the most slices
     lat = ehdlb.Lattice(nx, ny, case_params(nx, ny, 1.0, 4.0, 0.5, 5.0))
     lat.step(40)
     phi = lat.fields(["phi"])["phi"]
