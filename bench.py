@@ -42,6 +42,15 @@ def sweep_bytes_per_node(storage_bytes: int) -> int:
 # bytes of the control block ehdlb_step reads back after every call (sums,
 # residual, counters)
 CONTROL_BYTES = 120
+# fused sweep kernel of each tile shape (ehdlb_set_tuning)
+SWEEP_KERNELS = {
+    0: ("k_sweep_tb", "potential sweeps fused in shared memory, 64 x 32 regions"),
+    1: ("k_sweep_tb", "potential sweeps fused in shared memory, 64 x 32 regions"),
+    2: ("k_sweep_cl", "potential sweeps fused across clusters of 2 x 4 blocks"),
+    3: ("k_sweep_tb", "potential sweeps fused in shared memory, 64 x 64 regions"),
+    4: ("k_sweep_tbr", "potential sweeps fused in registers, persistent, 64 x 32 regions"),
+    5: ("k_sweep_tbr", "potential sweeps fused in registers, persistent, 64 x 40 regions"),
+}
 
 PRECISIONS = {"fp32": ("FP32", 4, "f32"), "fp16s": ("FP16 storage, FP32 arithmetic", 2, "f32"),
               "fp64": ("FP64", 8, "f64")}
@@ -270,7 +279,9 @@ def run_ours(args):
     hbm = float(peaks["hbm_gbs"])
     unit_bytes = sweep_bytes_per_node(sbytes)
     achieved = unit_bytes * sweeps_per_launch * nn / (sweep_launch_ms / 1e3) / 1e9
-    traffic = measured_traffic("k_sweep_tb" if args.precision == "fp32" else f"k_sweep_tb_{args.precision}", n)
+    sweep_kernel = SWEEP_KERNELS.get(int(st.tile_shape), SWEEP_KERNELS[1])
+    tkey = sweep_kernel[0] if args.precision == "fp32" else f"{sweep_kernel[0]}_{args.precision}"
+    traffic = measured_traffic(tkey, n)
     launches = int(st.launches)
     ehdlb.ehdlb_set_timing(lat.ctx, False)
 
@@ -320,7 +331,7 @@ def run_ours(args):
                    "nx": n, "ny": n, "sweeps_per_step": SWEEPS, "storage_bytes": sbytes,
                    "l2": "inputs larger than L2 (state ~1.35 GB), no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-        "roofline": {"bound": "hbm", "kernel": "k_sweep_tb (potential sweeps fused in shared memory)",
+        "roofline": {"bound": "hbm", "kernel": f"{sweep_kernel[0]} ({sweep_kernel[1]})",
                      "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "peak_source": peak_kind,
                      "traffic": traffic,

@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define EHDLB_ABI_VERSION 3
+#define EHDLB_ABI_VERSION 4
 
 typedef struct ehdlb_ctx ehdlb_ctx;
 
@@ -160,6 +160,8 @@ typedef struct ehdlb_stats {
                                             timing is on (ehdlb_set_timing) */
     long long launches;       /* kernels launched by the call */
     long long sweep_launches; /* of which potential-sweep kernels */
+    int sweeps_per_launch;    /* fused sweeps per launch (0: one sweep per launch) */
+    int tile_shape;           /* tile shape of the fused sweep kernel (ehdlb_set_tuning) */
 } ehdlb_stats;
 
 /* Counters of one ehdlb_batch_step() call. */
@@ -249,9 +251,13 @@ int ehdlb_set_timing(ehdlb_ctx *c, int on);
  *     launch; default 5 (float) / 2 (double);
  *   tile_shape: blocks of the fused sweep kernel, 0: 64 x 32 region per
  *     block (512 threads; the double solver's only shape), 1: 64 x 32 (256
- *     threads; default for float), 2: clusters of 2 x 4 blocks of 64 x 32
- *     that exchange populations through distributed shared memory every
- *     sweep, 3: 64 x 64 (512 threads); 1, 2 and 3 float only;
+ *     threads), 2: clusters of 2 x 4 blocks of 64 x 32 that exchange
+ *     populations through distributed shared memory every sweep, 3: 64 x 64
+ *     (512 threads), 4: 64 x 32 and 5: 64 x 40 (persistent blocks of 256
+ *     threads, each thread holding the populations of 2 x 4 or 2 x 5 nodes
+ *     in registers; populations cross lanes by warp shuffles and warps
+ *     through shared memory; 5 is the default for float); 1 to 5 float
+ *     only;
  *   main_staging: how the step kernel copies its block's populations to
  *     shared memory, 0: one asynchronous copy per node and plane, 1: 16-byte
  *     copies of row segments (default; used only when nx times the element

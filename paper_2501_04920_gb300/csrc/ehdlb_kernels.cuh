@@ -358,6 +358,16 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+// Asynchronous copy of two consecutive elements; both addresses aligned to
+// twice the element size.
+template <typename T> __device__ __forceinline__ void cp_async_pair(T *smem, const T *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ---- kernels -----------------------------------------------------------------
@@ -733,6 +743,299 @@ __global__ void __launch_bounds__(32 * BY, MINB)
 {
     tb_body<T, S, NSW, RW, RH, BY, FIRST, RESID>(P, gA, gB, phig, q, coef, part, ctl, m, blockIdx.x, blockIdx.y,
                                                  blockIdx.x + (long long)blockIdx.y * gridDim.x);
+}
+
+// a * b + c rounded once.
+template <typename T> __device__ __forceinline__ T fma_t(T a, T b, T c)
+{
+    if constexpr (sizeof(T) == 4) return __fmaf_rn(a, b, c);
+    else return __fma_rn(a, b, c);
+}
+
+// ---- register-blocked fused sweeps ----------------------------------------------
+
+// The NSW fused sweeps of tb_body on 64 x 8R regions, computed in registers
+// by a persistent block (blockDim (32, 8)) that walks the tiles of the grid:
+// lane l of warp w holds the nodes 2l and 2l + 1 of the region rows
+// wR .. wR + R - 1, their four populations and their source coefficients.
+// After each collision the populations moving along x cross lanes by one
+// warp shuffle per node (lane 0's left and lane 31's right neighbours are
+// outside the region: those cells are incomplete, as is every cell at
+// distance < s from the region edge after s sweeps); those moving along y
+// stay in the thread between its own rows and cross to the warps above and
+// below through shared memory, one row per band edge, double buffered by
+// sweep parity, so a sweep needs one block barrier.  While a tile is swept,
+// the next one is copied to shared memory (cp.async), each thread copying
+// the cells it will read itself.  Collision, electrode links, FIRST and
+// RESID as in tb_body; the residual partials go to the tile's slot.  The
+// region's left and right halos are HL = NSW rounded up to even nodes, so a
+// lane's two nodes sit at an even lattice column: for even nx they are one
+// aligned 8-byte pair in every plane, copied and stored as one.
+template <typename T> struct Vec2T;
+template <> struct Vec2T<float> { using type = float2; };
+template <> struct Vec2T<double> { using type = double2; };
+
+constexpr int TBR_NW = 8;   // warps per block (bands of R rows)
+
+// Planes of one staged tile: g1..g4 and A, Bx, By, or (FIRST) g1..g4, q and
+// phi with its one-node ring.
+__host__ __device__ constexpr int tbr_halo_x(int nsw) { return nsw + (nsw & 1); }
+
+template <typename T, int R> __host__ __device__ constexpr size_t tbr_smem_bytes(bool first)
+{
+    return sizeof(T) * (first ? (size_t)5 * TBR_NW * R * 64 + (size_t)(TBR_NW * R + 2) * 66
+                              : (size_t)7 * TBR_NW * R * 64);
+}
+
+template <typename T, int NSW, int R, bool FIRST, bool RESID>
+__global__ void __launch_bounds__(32 * TBR_NW, 2)
+    k_sweep_tbr(const DevP<T> P, T *__restrict__ gA, T *__restrict__ gB, const T *__restrict__ phig,
+                const T *__restrict__ q, T *__restrict__ coef, double *__restrict__ part,
+                const Control *__restrict__ ctl, int m, int tiles_x, int ntiles)
+{
+    using V2 = typename Vec2T<T>::type;
+    constexpr int NW = TBR_NW, H = NSW, HL = tbr_halo_x(NSW), RW = 64, RH = NW * R, TX = RW - 2 * HL,
+                  TY = RH - 2 * H;
+    constexpr int FW = RW + 2, PL = RH * RW;
+    static_assert(TX > 0 && TY > 0 && H <= TB_NSW_MAX, "region too small for NSW");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *const stg = reinterpret_cast<T *>(smem_raw);           // planes of the staged tile
+    T *const sphi = stg + 5 * PL;                               // FIRST: phi with its ring
+    __shared__ __align__(16) T xup[2][NW][RW];   // p2 of each warp's top row, for the warp above
+    __shared__ __align__(16) T xdn[2][NW][RW];   // p4 of each warp's bottom row, for the warp below
+    const int par = (ctl->cur0 + m) & 1;
+    const T *__restrict__ src = par ? gB : gA;
+    T *__restrict__ dst = par ? gA : gB;
+    const int nx = P.nx, ny = P.ny;
+    const long long nn = P.nn;
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int lx0 = 2 * lane, ly0 = w * R;
+    const bool wide = nx >= RW + 2;
+
+    const bool pairs = (nx & 1) == 0;   // a lane's two nodes are one aligned pair
+    constexpr int NPL = FIRST ? 5 : 7;
+    // plane pl of the staged inputs: g1..g4, then q or A, Bx, By
+    auto plane = [&](int pl) -> const T * {
+        return pl < 4 ? src + pl * nn : (FIRST ? q : coef + (pl - 4) * nn);
+    };
+
+    // copy tile t to the stage: this thread's own cells (zeros outside the
+    // lattice rows), and (FIRST) a share of phi with its ring
+    auto issue = [&](int t) {
+        const int x0 = (t % tiles_x) * TX, y0 = (t / tiles_x) * TY;
+        const int gx = wrap_x(x0 - HL + lx0, nx, wide);
+        const int gx1 = pairs ? gx + 1 : wrap_x(x0 - HL + lx0 + 1, nx, wide);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int gy = y0 - H + ly0 + r;
+            T *c = stg + (ly0 + r) * RW + lx0;
+            if (gy < 0 || gy >= ny) {
+#pragma unroll
+                for (int pl = 0; pl < NPL; ++pl) *reinterpret_cast<V2 *>(c + pl * PL) = V2{T(0), T(0)};
+                continue;
+            }
+            const int k = gy * nx + gx, k1 = gy * nx + gx1;   // < nn <= 2^31
+            if (pairs) {
+#pragma unroll
+                for (int pl = 0; pl < NPL; ++pl) cp_async_pair(c + pl * PL, plane(pl) + k);
+            } else {
+#pragma unroll
+                for (int pl = 0; pl < NPL; ++pl) {
+                    cp_async(c + pl * PL, plane(pl) + k);
+                    cp_async(c + pl * PL + 1, plane(pl) + k1);
+                }
+            }
+        }
+        if (FIRST) {
+            for (int e = lane + 32 * w; e < (RH + 2) * FW; e += 32 * NW) {
+                const int py = e / FW, px = e - py * FW;
+                const int gy = y0 - H - 1 + py;   // phig holds the rows -1 .. ny
+                if (gy >= -1 && gy <= ny)
+                    cp_async(sphi + e, phig + (long long)(gy + 1) * nx + wrap_x(x0 - HL - 1 + px, nx, wide));
+                else
+                    sphi[e] = T(0);
+            }
+        }
+    };
+
+    const T k1 = T(0.5) * (T(1) - P.s_g);
+    const T kf = T(0.5) * (T(1) - P.s_free_g);
+    const T ke = T(0.25) * P.s_free_g;
+    const T wG = P.wG;
+    int sw = 0;   // sweeps done by this block: parity of the exchange rows
+
+    // NSW sweeps of the tile in registers; EDGE: the region reaches an
+    // electrode row (block-uniform), which adds the wall links.  ch = half of
+    // the coefficients A, Bx, By (exact), so X/6 = chA - chBx m1 - chBy m2.
+    auto sweeps = [&](auto edge, int gy0, T (&g1)[R][2], T (&g2)[R][2], T (&g3)[R][2], T (&g4)[R][2],
+                      const T (&chA)[R][2], const T (&chBx)[R][2], const T (&chBy)[R][2], T (&psi_before)[R][2]) {
+        constexpr bool EDGE = decltype(edge)::value;
+#pragma unroll
+        for (int s = 0; s < NSW; ++s, ++sw) {
+            T o1[R][2], o3[R][2], p2[R][2], p4[R][2];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const T m1 = g1[r][j] - g3[r][j], m2 = g2[r][j] - g4[r][j];
+                    const T m3 = g1[r][j] + g3[r][j], m4 = g2[r][j] + g4[r][j];
+                    const T m34 = m3 + m4;
+                    if (RESID) psi_before[r][j] = T(1.5) * m34;
+                    const T X6 = fma_t(-chBy[r][j], m2, fma_t(-chBx[r][j], m1, chA[r][j]));
+                    const T e = fma_t(ke, m34, X6);
+                    const T h3 = fma_t(kf, m3, e), h4 = fma_t(kf, m4, e);   // halves of n3, n4
+                    o1[r][j] = fma_t(k1, m1, h3);
+                    o3[r][j] = fma_t(-k1, m1, h3);
+                    p2[r][j] = fma_t(k1, m2, h4);
+                    p4[r][j] = fma_t(-k1, m2, h4);
+                }
+            }
+            const int b = sw & 1;
+            *reinterpret_cast<V2 *>(&xup[b][w][lx0]) = V2{p2[R - 1][0], p2[R - 1][1]};
+            *reinterpret_cast<V2 *>(&xdn[b][w][lx0]) = V2{p4[0][0], p4[0][1]};
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                g1[r][1] = o1[r][0];
+                g1[r][0] = __shfl_up_sync(0xffffffffu, o1[r][1], 1);
+                g3[r][0] = o3[r][1];
+                g3[r][1] = __shfl_down_sync(0xffffffffu, o3[r][0], 1);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    if (r > 0) g2[r][j] = p2[r - 1][j] - wG;
+                    if (r < R - 1) g4[r][j] = p4[r + 1][j] + wG;
+                }
+            }
+            __syncthreads();
+            if (w > 0) {
+                const V2 v = *reinterpret_cast<const V2 *>(&xup[b][w - 1][lx0]);
+                g2[0][0] = v.x - wG;
+                g2[0][1] = v.y - wG;
+            } else {
+                g2[0][0] = g2[0][1] = T(0);   // below the region
+            }
+            if (w < NW - 1) {
+                const V2 v = *reinterpret_cast<const V2 *>(&xdn[b][w + 1][lx0]);
+                g4[R - 1][0] = v.x + wG;
+                g4[R - 1][1] = v.y + wG;
+            } else {
+                g4[R - 1][0] = g4[R - 1][1] = T(0);   // above the region
+            }
+            if (EDGE) {
+                // electrodes: ABB of the wall links into the node's own cell
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int gy = gy0 + r;
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        if (gy == 0) g2[r][j] = -p4[r][j] - wG;        // anode, psi_a
+                        if (gy == ny - 1) g4[r][j] = -p2[r][j] + wG;   // cathode, psi_c
+                    }
+                }
+            }
+        }
+    };
+
+    if ((int)blockIdx.x < ntiles) issue(blockIdx.x);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int x0 = (t % tiles_x) * TX, y0 = (t / tiles_x) * TY;
+        const int gy0 = y0 - H + ly0;   // lattice row of this thread's row 0
+        cp_async_wait_all();
+        if (FIRST) __syncthreads();      // phi was copied by all threads
+
+        T g1[R][2], g2[R][2], g3[R][2], g4[R][2], cA[R][2], cBx[R][2], cBy[R][2];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const T *c = stg + (ly0 + r) * RW + lx0;
+            auto ld2 = [&](int pl, T(&v)[R][2]) {
+                const V2 u = *reinterpret_cast<const V2 *>(c + pl * PL);
+                v[r][0] = u.x;
+                v[r][1] = u.y;
+            };
+            ld2(0, g1);
+            ld2(1, g2);
+            ld2(2, g3);
+            ld2(3, g4);
+            if (FIRST) {
+                ld2(4, cA);   // q until the coefficients are formed
+                const int gy = gy0 + r;
+                const bool in = gy >= 0 && gy < ny;
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const T *r1 = sphi + (ly0 + r + 1) * FW + lx0 + j + 1, *r0 = r1 - FW, *r2 = r1 + FW;
+                    const T phi = r1[0];
+                    const T gxs_ = (r1[1] - r1[-1]) * T(1.0 / 3.0) + ((r2[1] - r2[-1]) + (r0[1] - r0[-1])) * T(1.0 / 12.0);
+                    const T gys_ = (r2[0] - r0[0]) * T(1.0 / 3.0) + ((r2[1] + r2[-1]) - (r0[1] + r0[-1])) * T(1.0 / 12.0);
+                    const T inv = T(1) / (T(1) + P.er1 * phi);
+                    const T bb = P.src_norm * P.er1 * inv / P.tau_g;
+                    cA[r][j] = in ? P.src_norm * P.Kq * cA[r][j] * inv * T(1.0 / 3.0) : T(0);
+                    cBx[r][j] = in ? bb * gxs_ : T(0);
+                    cBy[r][j] = in ? bb * gys_ : T(0);
+                }
+            } else {
+                ld2(4, cA);
+                ld2(5, cBx);
+                ld2(6, cBy);
+            }
+        }
+        if (FIRST) __syncthreads();      // phi read by all before it is refilled
+        if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+
+        T chA[R][2], chBx[R][2], chBy[R][2], psi_before[R][2];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                chA[r][j] = T(0.5) * cA[r][j];
+                chBx[r][j] = T(0.5) * cBx[r][j];
+                chBy[r][j] = T(0.5) * cBy[r][j];
+            }
+        if (y0 - H <= 0 || y0 - H + RH >= ny)
+            sweeps(std::true_type{}, gy0, g1, g2, g3, g4, chA, chBx, chBy, psi_before);
+        else
+            sweeps(std::false_type{}, gy0, g1, g2, g3, g4, chA, chBx, chBy, psi_before);
+
+        // ---- the output tile (and, FIRST, its coefficients); lx0 and HL
+        // are even, so a lane's two nodes are both in the tile or both out ----
+        T red[2] = {T(0), T(0)};
+        const int gxo = x0 - HL + lx0;
+        const bool xin = lx0 >= HL && lx0 < HL + TX && gxo < nx;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int ly = ly0 + r, gy = gy0 + r;
+            if (!xin || ly < H || ly >= H + TY || gy >= ny) continue;
+            const int k = gy * nx + gxo;
+            auto st2 = [&](T *base, const T(&v)[R][2]) {
+                if (pairs) {
+                    *reinterpret_cast<V2 *>(base + k) = V2{v[r][0], v[r][1]};
+                } else {
+                    base[k] = v[r][0];
+                    if (gxo + 1 < nx) base[k + 1] = v[r][1];
+                }
+            };
+            st2(dst, g1);
+            st2(dst + nn, g2);
+            st2(dst + 2 * nn, g3);
+            st2(dst + 3 * nn, g4);
+            if (FIRST) {
+                st2(coef, cA);
+                st2(coef + nn, cBx);
+                st2(coef + 2 * nn, cBy);
+            }
+            if (RESID) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    if (j == 1 && gxo + 1 >= nx) continue;
+                    const T psit = T(1.5) * ((g1[r][j] + g3[r][j]) + (g2[r][j] + g4[r][j]));
+                    const T d = psit - psi_before[r][j];
+                    const T ps = psit + psi_lin(P, gy);
+                    red[0] += d * d;
+                    red[1] += ps * ps;
+                }
+            }
+        }
+        if (RESID) block_sum_store_at<T, 2>(red, part, t);
+    }
+    cp_async_wait_all();
 }
 
 // ---- thread-block clusters -------------------------------------------------------

@@ -56,6 +56,11 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         }
         grid_ = dim3((nx_ + BX - 1) / BX, (ny_ + BY - 1) / BY);
         nb_ = (long long)grid_.x * grid_.y;
+        {
+            int dev = 0;
+            EHDLB_CK(cudaGetDevice(&dev));
+            EHDLB_CK(cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev));
+        }
         const size_t plane = sizeof(T) * (size_t)nn_, splane = sizeof(S) * (size_t)nn_;
         for (int b = 0; b < 2; ++b) {
             EHDLB_CK(alloc_pops(b, 5));
@@ -243,6 +248,8 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             }
             st->launches = launches_;
             st->sweep_launches = sweep_launches_;
+            st->sweeps_per_launch = tb_chunk();
+            st->tile_shape = tb_shape_;
         }
         if (ctl_h_.unstable) {
             err = "NaN or Inf in the fields";
@@ -471,15 +478,23 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     // Fused sweep kernel: region shapes (width, height, threads per column,
     // blocks per SM the registers are sized for) and the largest number of
     // sweeps one launch fuses.
-    struct TbShape { int rw, rh, by, minb; };
-    // float: shape 2 is the cluster kernel (k_sweep_cl), 2 x 4 CTAs of 64 x 32
-    static constexpr int TB_NSHAPES = sizeof(T) == 4 ? 4 : 1;
+    // r: rows per thread of the register-blocked kernel (k_sweep_tbr), 0 for
+    // the shared-memory one (k_sweep_tb).
+    struct TbShape { int rw, rh, by, minb, r; };
+    // float: shape 2 is the cluster kernel (k_sweep_cl), 2 x 4 CTAs of 64 x 32;
+    // shapes 4 and 5 are register-blocked, 64 x 32 and 64 x 40
+    static constexpr int TB_NSHAPES = sizeof(T) == 4 ? 6 : 1;
     static constexpr int CL_X = 2, CL_Y = 4, CL_BY = 16;
     static constexpr TbShape tb_shape(int i)
     {
-        return sizeof(T) == 4
-                   ? (i == 1 ? TbShape{64, 32, 8, 4} : (i == 3 ? TbShape{64, 64, 16, 2} : TbShape{64, 32, 16, 3}))
-                   : TbShape{64, 16, 16, 2};
+        if (sizeof(T) != 4) return TbShape{64, 16, 16, 2, 0};
+        switch (i) {
+        case 1: return TbShape{64, 32, 8, 4, 0};
+        case 3: return TbShape{64, 64, 16, 2, 0};
+        case 4: return TbShape{64, 32, 8, 2, 4};
+        case 5: return TbShape{64, 40, 8, 2, 5};
+        default: return TbShape{64, 32, 16, 3, 0};
+        }
     }
     static constexpr int TB_MAX = sizeof(T) == 4 ? 5 : 2;
 
@@ -490,7 +505,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             return dim3(CL_X * ((nx + tx - 1) / tx), CL_Y * ((ny + ty - 1) / ty));
         }
         const TbShape sh = tb_shape(shape);
-        const int tx = sh.rw - 2 * nsw, ty = sh.rh - 2 * nsw;
+        const int tx = sh.rw - 2 * (sh.r ? tbr_halo_x(nsw) : nsw), ty = sh.rh - 2 * nsw;
         return dim3((nx + tx - 1) / tx, (ny + ty - 1) / ty);
     }
 
@@ -539,6 +554,8 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         if constexpr (TB_NSHAPES > 1) {
             if (e == cudaSuccess) e = tb_attr1<NSW, 1>();
             if (e == cudaSuccess) e = tb_attr1<NSW, 3>();
+            if (e == cudaSuccess) e = tbr_attr1<NSW, 4>();
+            if (e == cudaSuccess) e = tbr_attr1<NSW, 5>();
             if (e == cudaSuccess) e = cl_attr2<NSW, false, false>();
             if (e == cudaSuccess) e = cl_attr2<NSW, false, true>();
             if (e == cudaSuccess) e = cl_attr2<NSW, true, false>();
@@ -563,6 +580,51 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         k_sweep_tb<T, T, NSW, sh.rw, sh.rh, sh.by, sh.minb, FIRST, RESID>
             <<<g, dim3(32, sh.by), tb_smem_bytes<T, sh.rw, sh.rh>(FIRST), stream_>>>(
                 dp_, g_[0], g_[1], phig_, q_, coef_, part2_, ctl_, tb_m_);
+    }
+
+    template <int NSW, int SH, bool FIRST, bool RESID> cudaError_t tbr_attr2()
+    {
+        constexpr TbShape sh = tb_shape(SH);
+        const size_t smem = tbr_smem_bytes<T, sh.r>(FIRST);
+        cudaError_t e = cudaFuncSetAttribute(k_sweep_tbr<T, NSW, sh.r, FIRST, RESID>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per = 0;
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_tbr<T, NSW, sh.r, FIRST, RESID>,
+                                                              32 * TBR_NW, smem);
+        // persistent grid: the fewest resident blocks per SM of any variant
+        if (e == cudaSuccess) tbr_per_sm_[SH - 4] = std::max(1, std::min(tbr_per_sm_[SH - 4], per));
+        return e;
+    }
+
+    template <int NSW, int SH> cudaError_t tbr_attr1()
+    {
+        cudaError_t e = tbr_attr2<NSW, SH, false, false>();
+        if (e == cudaSuccess) e = tbr_attr2<NSW, SH, false, true>();
+        if (e == cudaSuccess) e = tbr_attr2<NSW, SH, true, false>();
+        if (e == cudaSuccess) e = tbr_attr2<NSW, SH, true, true>();
+        return e;
+    }
+
+    template <int NSW, int SH, bool FIRST, bool RESID> void tbr_launch2()
+    {
+        constexpr TbShape sh = tb_shape(SH);
+        const dim3 g = tb_grid(NSW, SH, nx_, ny_);
+        const int ntiles = (int)(g.x * g.y);
+        const int grid = std::min(ntiles, tbr_per_sm_[SH - 4] * sms_);
+        k_sweep_tbr<T, NSW, sh.r, FIRST, RESID><<<grid, dim3(32, TBR_NW), tbr_smem_bytes<T, sh.r>(FIRST), stream_>>>(
+            dp_, g_[0], g_[1], phig_, q_, coef_, part2_, ctl_, tb_m_, (int)g.x, ntiles);
+    }
+
+    template <int NSW, int SH> void tbr_launch1(bool first, bool resid)
+    {
+        if (first) {
+            if (resid) tbr_launch2<NSW, SH, true, true>();
+            else tbr_launch2<NSW, SH, true, false>();
+        } else {
+            if (resid) tbr_launch2<NSW, SH, false, true>();
+            else tbr_launch2<NSW, SH, false, false>();
+        }
     }
 
     template <int NSW, int SH> void tb_launch1(bool first, bool resid)
@@ -593,6 +655,10 @@ template <typename T, typename S = T> class Solver : public SolverBase {
                 tb_launch1<NSW, 1>(first, resid);
             } else if (tb_shape_ == 3) {
                 tb_launch1<NSW, 3>(first, resid);
+            } else if (tb_shape_ == 4) {
+                tbr_launch1<NSW, 4>(first, resid);
+            } else if (tb_shape_ == 5) {
+                tbr_launch1<NSW, 5>(first, resid);
             } else {
                 tb_launch1<NSW, 0>(first, resid);
             }
@@ -791,7 +857,9 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     PhiRef<T> ref_{};
     double *part_ = nullptr, *part2_ = nullptr, *stage_ = nullptr;
     int tb_chunk_ = sizeof(T) == 4 ? 5 : 2;  // sweeps fused per launch (0: one per launch)
-    int tb_shape_ = sizeof(T) == 4 ? 1 : 0;   // region shape of the fused sweep kernel
+    int tb_shape_ = sizeof(T) == 4 ? 5 : 0;   // region shape of the fused sweep kernel
+    int tbr_per_sm_[2] = {1 << 20, 1 << 20};  // resident blocks per SM of the register-blocked shapes
+    int sms_ = 1;                             // SMs of the device
     int tb_m_ = 0;                            // launch index within the step
     int qi_ = 0;                              // ion populations per species (5 or 9) of pops_
     static constexpr int PSUM = 64;           // blocks of the first stage of the partial sums

@@ -57,6 +57,7 @@ class ehdlb_stats(C.Structure):
         ("seconds", C.c_double), ("mlups", C.c_double),
         ("ms_prep", C.c_double), ("ms_sweeps", C.c_double), ("ms_main", C.c_double),
         ("launches", C.c_longlong), ("sweep_launches", C.c_longlong),
+        ("sweeps_per_launch", C.c_int), ("tile_shape", C.c_int),
     ]
 
 
@@ -124,7 +125,7 @@ def lib():
         L.ehdlb_destroy.restype = None
         L.ehdlb_last_error.argtypes = [vp]
         L.ehdlb_last_error.restype = C.c_char_p
-        if L.ehdlb_version() != 3:
+        if L.ehdlb_version() != 4:
             raise ImportError("libehdlb ABI version mismatch")
         _lib = L
     return _lib

@@ -81,7 +81,7 @@ def test_null_and_bad_arguments_are_rejected_without_a_device():
     assert L.ehdlb_create(C.byref(h), 64, 64, 7, None) == ehdlb.EINVAL
     assert not h.value
     L.ehdlb_destroy(None)
-    assert ehdlb.ehdlb_version() == 3
+    assert ehdlb.ehdlb_version() == 4
 
 
 def test_batch_entry_points_reject_null_without_a_device():

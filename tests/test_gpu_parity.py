@@ -221,7 +221,7 @@ def test_fp32_every_sweep_tuning_matches_oracle():
     orc = oracle.Oracle(nx, ny, prm)
     orc.step(steps)
     ref = orc.fields()
-    for shape in range(4):
+    for shape in range(6):
         for spl in (0, 1, 2, 3, 4, 5):
             lat = ehdlb.Lattice(nx, ny, prm, precision=ehdlb.FP32)
             ehdlb.ehdlb_set_tuning(lat.ctx, spl, shape, spl % 2)
@@ -232,6 +232,30 @@ def test_fp32_every_sweep_tuning_matches_oracle():
                 assert_close(err, FP32_U_TOL, keys=["u"])
             except AssertionError as e:
                 raise AssertionError(f"shape {shape}, {spl} sweeps per launch: {e}") from None
+
+
+@pytest.mark.parametrize("nx,ny", [(40, 70), (66, 45), (45, 66), (137, 50)])
+def test_fp32_register_blocked_sweeps_on_narrow_lattices(nx, ny):
+    # lattices narrower than the 64-node region (x wraps inside it) or just
+    # wider, odd widths (no aligned node pairs), and fewer rows than two
+    # regions: the register-blocked shapes against the oracle, five sweeps
+    # per launch
+    steps = 8
+    prm = workloads.droplet(64)
+    prm.update(xc=(nx - 1) / 2, yc=(ny - 1) / 2, R=min(nx, ny) / 4, Kq=5.6893 / (nx * ny))
+    orc = oracle.Oracle(nx, ny, prm)
+    orc.step(steps)
+    ref = orc.fields()
+    for shape in (1, 4, 5):
+        lat = ehdlb.Lattice(nx, ny, prm, precision=ehdlb.FP32)
+        ehdlb.ehdlb_set_tuning(lat.ctx, 5, shape, -1)
+        lat.step(steps)
+        err = field_errors(lat.fields(), ref)
+        try:
+            assert_close(err, FP32_TOL, keys=["phi", "psi", "q", "cp", "cm"])
+            assert_close(err, FP32_U_TOL, keys=["u"])
+        except AssertionError as e:
+            raise AssertionError(f"shape {shape}: {e}") from None
 
 
 @pytest.mark.slow
@@ -303,7 +327,7 @@ def test_error_codes():
                                            sweep_tol=0.0, init_sweeps_max=10))
     assert L.ehdlb_set_params(h, ehdlb.C.byref(good)) == ehdlb.OK
     assert L.ehdlb_set_tuning(h, 6, 0, 0) == ehdlb.EINVAL
-    assert L.ehdlb_set_tuning(h, 2, 4, 0) == ehdlb.EINVAL
+    assert L.ehdlb_set_tuning(h, 2, 6, 0) == ehdlb.EINVAL
     assert L.ehdlb_set_tuning(h, 2, 0, 2) == ehdlb.EINVAL
     assert L.ehdlb_set_tuning(h, -1, -1, -1) == ehdlb.OK
     assert L.ehdlb_step(h, 2, ehdlb.C.byref(st)) == ehdlb.WNOTCONV
