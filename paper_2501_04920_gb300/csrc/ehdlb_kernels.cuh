@@ -755,7 +755,7 @@ template <typename T> __device__ __forceinline__ T fma_t(T a, T b, T c)
 // ---- register-blocked fused sweeps ----------------------------------------------
 
 // The NSW fused sweeps of tb_body on 64 x 8R regions, computed in registers
-// by a persistent block (blockDim (32, 8)) that walks the tiles of the grid:
+// by a persistent block (blockDim (32, NW)) that walks the tiles of the grid:
 // lane l of warp w holds the nodes 2l and 2l + 1 of the region rows
 // wR .. wR + R - 1, their four populations and their source coefficients.
 // After each collision the populations moving along x cross lanes by one
@@ -775,26 +775,25 @@ template <typename T> struct Vec2T;
 template <> struct Vec2T<float> { using type = float2; };
 template <> struct Vec2T<double> { using type = double2; };
 
-constexpr int TBR_NW = 8;   // warps per block (bands of R rows)
-
-// Planes of one staged tile: g1..g4 and A, Bx, By, or (FIRST) g1..g4, q and
-// phi with its one-node ring.
 __host__ __device__ constexpr int tbr_halo_x(int nsw) { return nsw + (nsw & 1); }
 
-template <typename T, int R> __host__ __device__ constexpr size_t tbr_smem_bytes(bool first)
+// Planes of one staged tile (NW warps, bands of R rows): g1..g4 and A, Bx,
+// By, or (FIRST) g1..g4, q and phi with its one-node ring.
+template <typename T, int R, int NW> __host__ __device__ constexpr size_t tbr_smem_bytes(bool first)
 {
-    return sizeof(T) * (first ? (size_t)5 * TBR_NW * R * 64 + (size_t)(TBR_NW * R + 2) * 66
-                              : (size_t)7 * TBR_NW * R * 64);
+    return sizeof(T) * (first ? (size_t)5 * NW * R * 64 + (size_t)(NW * R + 2) * 66 : (size_t)7 * NW * R * 64);
 }
 
-template <typename T, int NSW, int R, bool FIRST, bool RESID>
-__global__ void __launch_bounds__(32 * TBR_NW, 2)
+// Launch: blockDim (32, NW), dynamic shared memory tbr_smem_bytes<T, R, NW>(FIRST),
+// grid = min(tiles, resident blocks); tiles_x x (ntiles / tiles_x) tiles.
+template <typename T, int NSW, int R, int NW, int MINB, bool FIRST, bool RESID>
+__global__ void __launch_bounds__(32 * NW, MINB)
     k_sweep_tbr(const DevP<T> P, T *__restrict__ gA, T *__restrict__ gB, const T *__restrict__ phig,
                 const T *__restrict__ q, T *__restrict__ coef, double *__restrict__ part,
                 const Control *__restrict__ ctl, int m, int tiles_x, int ntiles)
 {
     using V2 = typename Vec2T<T>::type;
-    constexpr int NW = TBR_NW, H = NSW, HL = tbr_halo_x(NSW), RW = 64, RH = NW * R, TX = RW - 2 * HL,
+    constexpr int H = NSW, HL = tbr_halo_x(NSW), RW = 64, RH = NW * R, TX = RW - 2 * HL,
                   TY = RH - 2 * H;
     constexpr int FW = RW + 2, PL = RH * RW;
     static_assert(TX > 0 && TY > 0 && H <= TB_NSW_MAX, "region too small for NSW");

@@ -482,7 +482,8 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     // the shared-memory one (k_sweep_tb).
     struct TbShape { int rw, rh, by, minb, r; };
     // float: shape 2 is the cluster kernel (k_sweep_cl), 2 x 4 CTAs of 64 x 32;
-    // shapes 4 and 5 are register-blocked, 64 x 32 and 64 x 40
+    // shapes 4 and 5 are register-blocked (by = warps, r = rows per warp),
+    // 64 x 32 and 64 x 40
     static constexpr int TB_NSHAPES = sizeof(T) == 4 ? 6 : 1;
     static constexpr int CL_X = 2, CL_Y = 4, CL_BY = 16;
     static constexpr TbShape tb_shape(int i)
@@ -585,13 +586,11 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     template <int NSW, int SH, bool FIRST, bool RESID> cudaError_t tbr_attr2()
     {
         constexpr TbShape sh = tb_shape(SH);
-        const size_t smem = tbr_smem_bytes<T, sh.r>(FIRST);
-        cudaError_t e = cudaFuncSetAttribute(k_sweep_tbr<T, NSW, sh.r, FIRST, RESID>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const size_t smem = tbr_smem_bytes<T, sh.r, sh.by>(FIRST);
+        auto kern = k_sweep_tbr<T, NSW, sh.r, sh.by, sh.minb, FIRST, RESID>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per = 0;
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_tbr<T, NSW, sh.r, FIRST, RESID>,
-                                                              32 * TBR_NW, smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * sh.by, smem);
         // persistent grid: the fewest resident blocks per SM of any variant
         if (e == cudaSuccess) tbr_per_sm_[SH - 4] = std::max(1, std::min(tbr_per_sm_[SH - 4], per));
         return e;
@@ -612,8 +611,9 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         const dim3 g = tb_grid(NSW, SH, nx_, ny_);
         const int ntiles = (int)(g.x * g.y);
         const int grid = std::min(ntiles, tbr_per_sm_[SH - 4] * sms_);
-        k_sweep_tbr<T, NSW, sh.r, FIRST, RESID><<<grid, dim3(32, TBR_NW), tbr_smem_bytes<T, sh.r>(FIRST), stream_>>>(
-            dp_, g_[0], g_[1], phig_, q_, coef_, part2_, ctl_, tb_m_, (int)g.x, ntiles);
+        k_sweep_tbr<T, NSW, sh.r, sh.by, sh.minb, FIRST, RESID>
+            <<<grid, dim3(32, sh.by), tbr_smem_bytes<T, sh.r, sh.by>(FIRST), stream_>>>(
+                dp_, g_[0], g_[1], phig_, q_, coef_, part2_, ctl_, tb_m_, (int)g.x, ntiles);
     }
 
     template <int NSW, int SH> void tbr_launch1(bool first, bool resid)
@@ -659,6 +659,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
                 tbr_launch1<NSW, 4>(first, resid);
             } else if (tb_shape_ == 5) {
                 tbr_launch1<NSW, 5>(first, resid);
+
             } else {
                 tb_launch1<NSW, 0>(first, resid);
             }
