@@ -1316,16 +1316,24 @@ static __global__ void __launch_bounds__(256) k_sweep_decide(const double *__res
 
 // Planes k_main stages per node: f1..f8, h0..h8, the QI planes of p and of
 // n (one allocation of 17 + 2 QI planes) and (phi u)(t-1) x, y of type S,
-// then g1..g4 of type T.
+// then g1..g4 of type T.  With FP16 storage it also stages the chemical
+// potential of phi_ref (a fifth plane of type T) and phi_ref on the block's
+// 64 x 4 nodes with a one-node ring (6 x 66), which the h push reads; with
+// S = T those two come from global memory after the staging (measured at
+// 2048^2: staging them costs FP32 0.031 ms per step and saves FP16
+// storage 0.008 ms).
 template <int QI> __host__ __device__ constexpr int main_splanes() { return 17 + 2 * QI + 2; }
 // Blocks of 256 per SM the step kernel's registers are sized for: 4 in float
 // (64 registers; measured 9 % faster at 2048^2 than 3 blocks at 80 registers,
 // though a few bytes spill), 3 in double.
 template <typename T> constexpr int MAIN_MINB = sizeof(T) == 4 ? 4 : 3;
-constexpr int MAIN_TPLANES = 4;
+template <typename T, typename S> constexpr bool MAIN_STAGE_REF = !std::is_same<S, T>::value;
+template <typename T, typename S> constexpr int MAIN_TPLANES = MAIN_STAGE_REF<T, S> ? 5 : 4;
+constexpr int MAIN_RING_W = 66, MAIN_RING = 6 * MAIN_RING_W;
 template <typename T, typename S, int QI = 5> __host__ __device__ constexpr size_t main_smem_bytes()
 {
-    return (sizeof(S) * main_splanes<QI>() + sizeof(T) * MAIN_TPLANES) * 256;
+    return (sizeof(S) * main_splanes<QI>() + sizeof(T) * MAIN_TPLANES<T, S>) * 256 +
+           (MAIN_STAGE_REF<T, S> ? sizeof(T) * MAIN_RING : 0);
 }
 
 // Copy NPL planes of the block's 64 x 4 nodes (x0, y0) to st[plane][256]
@@ -1408,7 +1416,19 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
         stage_planes<S, NSP, VEC>(
             st, [=](int i) { return i < NPOP ? pops + i * nn : pu + (i - NPOP) * nn; }, P.nx, P.ny, x0, y0, tid, inside,
             k);
-        stage_planes<T, MAIN_TPLANES, VEC>(stg, [=](int i) { return g + i * nn; }, P.nx, P.ny, x0, y0, tid, inside, k);
+        const T *mur = Rf.mur;
+        stage_planes<T, MAIN_TPLANES<T, S>, VEC>(stg, [=](int i) { return i < 4 ? g + i * nn : mur; }, P.nx, P.ny,
+                                                 x0, y0, tid, inside, k);
+        // phi_ref of rows y0 - 1 .. y0 + 4 (phir holds the rows -1 .. ny),
+        // columns x0 - 1 .. x0 + 64 (periodic); rows above ny are never read
+        T *ring = stg + MAIN_TPLANES<T, S> * 256;
+        for (int e = tid; MAIN_STAGE_REF<T, S> && e < MAIN_RING; e += 256) {
+            const int ry = e / MAIN_RING_W, rx = e - ry * MAIN_RING_W;
+            const int gy = y0 - 1 + ry;
+            int gx = x0 - 1 + rx;
+            gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx % P.nx : gx);
+            if (gy <= P.ny) cp_async(ring + e, Rf.phir + (long long)(gy + 1) * P.nx + gx);
+        }
     }
     const T pprev = (RESID && inside) ? psi_prev[k] : T(0);
     const int nx = P.nx, ny = P.ny;
@@ -1435,7 +1455,7 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
         lapd = T(2.0 / 3.0) * ((dE + dW) + (dN + dS)) + T(1.0 / 6.0) * ((dNE + dSW) + (dNW + dSE));
     }
     cp_async_wait_all();
-    if constexpr (VEC) __syncthreads();
+    if constexpr (VEC || MAIN_STAGE_REF<T, S>) __syncthreads();   // copies of all threads
     if (inside) {
         SRng rng(k, kSame<S, T> ? 0 : ctl->t, 0x1b873593u);
         // in-plane offsets of the push targets: rows below / at / above, the
@@ -1513,7 +1533,7 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
         // ---- O6: forces (Eq. 12-14) ----
         // mu_phi - mu_ref: the cubic of Eq. 13 as (phi - phi_ref) times
         // (phi^2 + phi phi_ref + phi_ref^2 - 1.5 (phi + phi_ref) + 0.5)
-        const T mu_phi = Rf.mur[rowC] +
+        const T mu_phi = (MAIN_STAGE_REF<T, S> ? stg[4 * 256 + tid] : Rf.mur[rowC]) +
                          T(4) * P.beta * dphi * ((phi * phi + phi * phir + phir * phir) - T(1.5) * (phi + phir) + T(0.5)) -
                          P.kappa * lapd;
         const T E2 = Ex * Ex + Ey * Ey;
@@ -1623,7 +1643,9 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
             inverse9<T>(mc, dl);
             // push, re-based on the destination's reference:
             // + w_i (phi_ref(x) - phi_ref(x + c_i)); a bounced population stays
-            const T *qr = Rf.phir + nx;   // phi_ref without its ghost row
+            const T *qr = MAIN_STAGE_REF<T, S>
+                              ? stg + MAIN_TPLANES<T, S> * 256 + (threadIdx.y + 1) * MAIN_RING_W + threadIdx.x + 1
+                              : Rf.phir + nx;   // phi_ref without its ghost row
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const T v = hv[i] - dl[i];
@@ -1631,7 +1653,9 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
                     sts_sr(dst.h + opp9(i) * nn + rowC, v, P.sc_h, rng);
                 } else {
                     const int o = dest(cx9(i), cy9(i));
-                    const T shift = i == 0 ? T(0) : w9<T>(i) * (phir - qr[o]);
+                    const T shift =
+                        i == 0 ? T(0)
+                               : w9<T>(i) * (phir - qr[MAIN_STAGE_REF<T, S> ? cy9(i) * MAIN_RING_W + cx9(i) : o]);
                     sts_sr(dst.h + i * nn + o, v + shift, P.sc_h, rng);
                 }
             }
