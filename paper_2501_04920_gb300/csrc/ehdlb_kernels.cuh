@@ -83,6 +83,7 @@ template <typename T> struct DevP {
     T s_f0;                        // 1/tau_f when rho and eta are uniform, else 0
     T s_p0, s_n0;                  // ion rates (Eq. 37) when D is uniform, else 0
     T inv_mu_v, three_over_tau_g, inv_W;
+    T src_a, src_b;                // fused sweeps: src_norm Kq / 3, src_norm (eps_r - 1) / tau_g
     // storage scales (value x sc is stored, stored x isc is the value) and
     // the rest concentration of the stored p, n; 1, 1 and 0 unless S != T
     T sc_f, isc_f, sc_h, isc_h, sc_c, isc_c, sc_g, isc_g, sc_u, isc_u;  // sc_g: g stored as S
@@ -523,6 +524,19 @@ __global__ void __launch_bounds__(256) k_sweep(const DevP<T> P, S *__restrict__ 
 //   RESID: the last sweep of the step; residual partials of the output tile.
 // Launch: blockDim (32, BY), dynamic shared memory
 // tb_smem_bytes<T, RW, RH>(FIRST) (sized for up to TB_NSW_MAX sweeps).
+// Source coefficients of Eq. 44 at a node for the fused sweeps, from phi,
+// q and grad phi (Eq. 59): A = th Kq q / (3 eps), (Bx, By) = th (eps_r - 1)
+// grad phi / (tau_g eps), eps = 1 + (eps_r - 1) phi.
+template <typename T>
+__device__ __forceinline__ void src_coefs(const DevP<T> &P, T phi, T q, T gx, T gy, T &A, T &Bx, T &By)
+{
+    const T inv = T(1) / (T(1) + P.er1 * phi);
+    const T bb = P.src_b * inv;
+    A = P.src_a * q * inv;
+    Bx = bb * gx;
+    By = bb * gy;
+}
+
 constexpr int TB_NSW_MAX = 5;
 template <typename T, int RW, int RH> __host__ __device__ constexpr size_t tb_smem_bytes(bool first)
 {
@@ -651,11 +665,7 @@ __device__ __forceinline__ void tb_body(const DevP<T> &P, S *__restrict__ gA, S 
                                ((r2[1] - r2[-1]) + (r0[1] - r0[-1])) * T(1.0 / 12.0);
                 const T gys_ = (r2[0] - r0[0]) * T(1.0 / 3.0) +
                                ((r2[1] + r2[-1]) - (r0[1] + r0[-1])) * T(1.0 / 12.0);
-                const T inv = T(1) / (T(1) + P.er1 * phi);
-                const T bb = P.src_norm * P.er1 * inv / P.tau_g;
-                cA[a][b] = P.src_norm * P.Kq * sq[ly * RW + lx] * inv * T(1.0 / 3.0);
-                cBx[a][b] = bb * gxs_;
-                cBy[a][b] = bb * gys_;
+                src_coefs(P, phi, sq[ly * RW + lx], gxs_, gys_, cA[a][b], cBx[a][b], cBy[a][b]);
             }
         }
     }
@@ -779,9 +789,12 @@ __host__ __device__ constexpr int tbr_halo_x(int nsw) { return nsw + (nsw & 1); 
 
 // Planes of one staged tile (NW warps, bands of R rows): g1..g4 and A, Bx,
 // By, or (FIRST) g1..g4, q and phi with its one-node ring.
+// phi with its ring is kept in rows of 68: region column lx at lx + 2, so a
+// lane's node pair is 8-byte aligned there too.
+constexpr int TBR_FW = 68;
 template <typename T, int R, int NW> __host__ __device__ constexpr size_t tbr_smem_bytes(bool first)
 {
-    return sizeof(T) * (first ? (size_t)5 * NW * R * 64 + (size_t)(NW * R + 2) * 66 : (size_t)7 * NW * R * 64);
+    return sizeof(T) * (first ? (size_t)5 * NW * R * 64 + (size_t)(NW * R + 2) * TBR_FW : (size_t)7 * NW * R * 64);
 }
 
 // Launch: blockDim (32, NW), dynamic shared memory tbr_smem_bytes<T, R, NW>(FIRST),
@@ -795,7 +808,7 @@ __global__ void __launch_bounds__(32 * NW, MINB)
     using V2 = typename Vec2T<T>::type;
     constexpr int H = NSW, HL = tbr_halo_x(NSW), RW = 64, RH = NW * R, TX = RW - 2 * HL,
                   TY = RH - 2 * H;
-    constexpr int FW = RW + 2, PL = RH * RW;
+    constexpr int FW = TBR_FW, PL = RH * RW;
     static_assert(TX > 0 && TY > 0 && H <= TB_NSW_MAX, "region too small for NSW");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *const stg = reinterpret_cast<T *>(smem_raw);           // planes of the staged tile
@@ -846,13 +859,41 @@ __global__ void __launch_bounds__(32 * NW, MINB)
             }
         }
         if (FIRST) {
-            for (int e = lane + 32 * w; e < (RH + 2) * FW; e += 32 * NW) {
-                const int py = e / FW, px = e - py * FW;
-                const int gy = y0 - H - 1 + py;   // phig holds the rows -1 .. ny
+            // phi (phig holds the rows -1 .. ny): this thread's node pairs,
+            // then the ring (rows -1 and RH, columns -1 and 64) by all
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int gy = y0 - H + ly0 + r;
+                T *c = sphi + (ly0 + r + 1) * FW + lx0 + 2;
+                if (gy < -1 || gy > ny) {
+                    *reinterpret_cast<V2 *>(c) = V2{T(0), T(0)};
+                    continue;
+                }
+                const T *row = phig + (long long)(gy + 1) * nx;
+                if (pairs) {
+                    cp_async_pair(c, row + gx);
+                } else {
+                    cp_async(c, row + gx);
+                    cp_async(c + 1, row + gx1);
+                }
+            }
+            constexpr int NRING = 2 * (RW + 2) + 2 * RH;
+            for (int e = lane + 32 * w; e < NRING; e += 32 * NW) {
+                int ly, lx;
+                if (e < 2 * (RW + 2)) {
+                    ly = e < RW + 2 ? -1 : RH;
+                    lx = (e < RW + 2 ? e : e - (RW + 2)) - 1;
+                } else {
+                    const int c = e - 2 * (RW + 2);
+                    ly = c < RH ? c : c - RH;
+                    lx = c < RH ? -1 : RW;
+                }
+                const int gy = y0 - H + ly;
+                T *d = sphi + (ly + 1) * FW + lx + 2;
                 if (gy >= -1 && gy <= ny)
-                    cp_async(sphi + e, phig + (long long)(gy + 1) * nx + wrap_x(x0 - HL - 1 + px, nx, wide));
+                    cp_async(d, phig + (long long)(gy + 1) * nx + wrap_x(x0 - HL + lx, nx, wide));
                 else
-                    sphi[e] = T(0);
+                    *d = T(0);
             }
         }
     };
@@ -956,27 +997,51 @@ __global__ void __launch_bounds__(32 * NW, MINB)
             ld2(3, g4);
             if (FIRST) {
                 ld2(4, cA);   // q until the coefficients are formed
-                const int gy = gy0 + r;
-                const bool in = gy >= 0 && gy < ny;
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const T *r1 = sphi + (ly0 + r + 1) * FW + lx0 + j + 1, *r0 = r1 - FW, *r2 = r1 + FW;
-                    const T phi = r1[0];
-                    const T gxs_ = (r1[1] - r1[-1]) * T(1.0 / 3.0) + ((r2[1] - r2[-1]) + (r0[1] - r0[-1])) * T(1.0 / 12.0);
-                    const T gys_ = (r2[0] - r0[0]) * T(1.0 / 3.0) + ((r2[1] + r2[-1]) - (r0[1] + r0[-1])) * T(1.0 / 12.0);
-                    const T inv = T(1) / (T(1) + P.er1 * phi);
-                    const T bb = P.src_norm * P.er1 * inv / P.tau_g;
-                    cA[r][j] = in ? P.src_norm * P.Kq * cA[r][j] * inv * T(1.0 / 3.0) : T(0);
-                    cBx[r][j] = in ? bb * gxs_ : T(0);
-                    cBy[r][j] = in ? bb * gys_ : T(0);
-                }
             } else {
                 ld2(4, cA);
                 ld2(5, cBx);
                 ld2(6, cBy);
             }
         }
-        if (FIRST) __syncthreads();      // phi read by all before it is refilled
+        if (FIRST) {
+            // the coefficients from phi: columns lx0 - 1 .. lx0 + 2 of the
+            // rows around each of this thread's rows, read once per row
+            T win[3][4];
+            auto ldrow = [&](int ly, T(&v)[4]) {
+                const T *c = sphi + (ly + 1) * FW + lx0 + 1;
+                const V2 u = *reinterpret_cast<const V2 *>(c + 1);
+                v[0] = c[0];
+                v[1] = u.x;
+                v[2] = u.y;
+                v[3] = c[3];
+            };
+            ldrow(ly0 - 1, win[0]);
+            ldrow(ly0, win[1]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                ldrow(ly0 + r + 1, win[(r + 2) % 3]);
+                const T(&w0)[4] = win[r % 3];
+                const T(&w1)[4] = win[(r + 1) % 3];
+                const T(&w2)[4] = win[(r + 2) % 3];
+                const int gy = gy0 + r;
+                const bool in = gy >= 0 && gy < ny;
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    // r0, r1, r2: the rows below, at and above; [j + 1] is the node
+                    const T phi = w1[j + 1];
+                    const T gxs_ = (w1[j + 2] - w1[j]) * T(1.0 / 3.0) +
+                                   ((w2[j + 2] - w2[j]) + (w0[j + 2] - w0[j])) * T(1.0 / 12.0);
+                    const T gys_ = (w2[j + 1] - w0[j + 1]) * T(1.0 / 3.0) +
+                                   ((w2[j + 2] + w2[j]) - (w0[j + 2] + w0[j])) * T(1.0 / 12.0);
+                    T a, bx, by;
+                    src_coefs(P, phi, cA[r][j], gxs_, gys_, a, bx, by);
+                    cA[r][j] = in ? a : T(0);
+                    cBx[r][j] = in ? bx : T(0);
+                    cBy[r][j] = in ? by : T(0);
+                }
+            }
+            __syncthreads();      // phi read by all before it is refilled
+        }
         if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
 
         T chA[R][2], chBx[R][2], chBy[R][2], psi_before[R][2];
@@ -1186,11 +1251,7 @@ __global__ void __cluster_dims__(CX, CY, 1) __launch_bounds__(32 * BY, 3)
                                ((r2[1] - r2[-1]) + (r0[1] - r0[-1])) * T(1.0 / 12.0);
                 const T gys_ = (r2[0] - r0[0]) * T(1.0 / 3.0) +
                                ((r2[1] + r2[-1]) - (r0[1] + r0[-1])) * T(1.0 / 12.0);
-                const T inv = T(1) / (T(1) + P.er1 * phi);
-                const T bb = P.src_norm * P.er1 * inv / P.tau_g;
-                cA[a][b] = P.src_norm * P.Kq * sq[li] * inv * T(1.0 / 3.0);
-                cBx[a][b] = bb * gxs_;
-                cBy[a][b] = bb * gys_;
+                src_coefs(P, phi, sq[li], gxs_, gys_, cA[a][b], cBx[a][b], cBy[a][b]);
             }
         }
     }

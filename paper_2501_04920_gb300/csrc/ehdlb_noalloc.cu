@@ -172,6 +172,8 @@ extern "C" int ehdlb_potential_noalloc(int nx, int ny, const ehdlb_params *p, co
     d.src_norm = p->vartheta * (p->psi_src_literal ? 1.0 : 1.5);
     d.Kq = p->Kq;
     d.er1 = p->eps_r - 1.0;
+    d.src_a = d.src_norm * p->Kq / 3.0;
+    d.src_b = d.src_norm * (p->eps_r - 1.0) / tau_g;
     d.psi_a = p->psi_anode;
     d.psi_c = p->psi_cathode;
     d.G = (p->psi_cathode - p->psi_anode) / ny;

@@ -410,9 +410,12 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         d.tau_g = (T)tau_g;
         d.s_g = (T)(1.0 / tau_g);
         d.s_free_g = (T)(p.bgk ? 1.0 / tau_g : p.s_free);
-        d.src_norm = (T)(p.vartheta * (p.psi_src_literal ? 1.0 : 1.5));
+        const double src_norm = p.vartheta * (p.psi_src_literal ? 1.0 : 1.5);
+        d.src_norm = (T)src_norm;
         d.Kq = (T)p.Kq;
         d.er1 = (T)(p.eps_r - 1.0);
+        d.src_a = (T)(src_norm * p.Kq / 3.0);
+        d.src_b = (T)(src_norm * (p.eps_r - 1.0) / tau_g);
         d.psi_a = (T)p.psi_anode;
         d.psi_c = (T)p.psi_cathode;
         d.G = (T)((p.psi_cathode - p.psi_anode) / ny_);
