@@ -174,7 +174,7 @@ typedef struct ehdlb_batch_stats {
     double mlups;             /* sum over cases of nx ny, times steps, / device time / 1e6 */
     long long launches;       /* kernels (graph nodes included) launched by the call */
     int sweeps_per_launch;    /* fused potential sweeps per launch used */
-    int tile_shape;           /* block shape of the fused sweep kernel used (0, 1) */
+    int tile_shape;           /* tile shape of the fused sweep kernel used (0, 1, 2) */
 } ehdlb_batch_stats;
 
 /* ABI version of the loaded library (EHDLB_ABI_VERSION). */
@@ -370,13 +370,15 @@ int ehdlb_batch_get_state(ehdlb_batch *b, int id, double *dst, size_t len);
 int ehdlb_batch_deformation(ehdlb_batch *b, int n, const int *ids, double *D);
 
 /* Sweeps fused per launch (1..5; default 5), tile shape of the fused sweep
- * kernel (0: 512 threads; 1: 256 threads, default) and whether steps replay
- * a captured graph (default 1); -1 keeps a setting. */
+ * kernel (0: 64 x 32 regions in shared memory, 512 threads; 1: the same with
+ * 256 threads; 2: 64 x 40 regions in registers, as tile shape 5 of
+ * ehdlb_set_tuning, default) and whether steps replay a captured graph (default 1);
+ * -1 keeps a setting; EINVAL outside these ranges. */
 int ehdlb_batch_set_tuning(ehdlb_batch *b, int sweeps_per_launch, int tile_shape, int use_graphs);
 
 /* Autotuner: time `steps` batch steps of the current cases for every sweeps
- * per launch in 3..5 and both tile shapes, keep the fastest and report it.
- * The timed steps are real steps: the cases advance by 6 (steps + 1). */
+ * per launch in 3..5 and the three tile shapes, keep the fastest and report
+ * it.  The timed steps are real steps: the cases advance by 9 (steps + 1). */
 int ehdlb_batch_autotune(ehdlb_batch *b, int steps, int *sweeps_per_launch, int *tile_shape,
                          double *ms_per_step);
 

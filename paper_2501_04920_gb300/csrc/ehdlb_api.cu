@@ -357,7 +357,7 @@ int ehdlb_batch_set_tuning(ehdlb_batch *b, int sweeps_per_launch, int tile_shape
     if (!b) return EHDLB_EINVAL;
     if (sweeps_per_launch < -1 || sweeps_per_launch == 0 || sweeps_per_launch > 5)
         return bfail(b, EHDLB_EINVAL, "sweeps_per_launch must lie in 1..5 (or -1)");
-    if (tile_shape < -1 || tile_shape > 1) return bfail(b, EHDLB_EINVAL, "tile_shape must lie in -1..1");
+    if (tile_shape < -1 || tile_shape > 2) return bfail(b, EHDLB_EINVAL, "tile_shape must lie in -1..2");
     if (use_graphs < -1 || use_graphs > 1) return bfail(b, EHDLB_EINVAL, "use_graphs must lie in -1..1");
     return b->batch->set_tuning(sweeps_per_launch, tile_shape, use_graphs);
 }

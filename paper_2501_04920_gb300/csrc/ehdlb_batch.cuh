@@ -179,6 +179,33 @@ __global__ void __launch_bounds__(32 * BY, MINB) kb_sweep(const CaseDev<T, S> *_
     }
 }
 
+// The tiles of a batch's register-blocked sweep launch m: item (case, tile
+// column, tile row, index) of the case's grid of tiles.
+template <typename T, typename S> struct TbrBatchTiles {
+    const CaseDev<T, S> *cases;
+    const WorkItem *items;
+    int n, m;
+    __device__ int count() const { return n; }
+    __device__ TbrTile<T> tile(int i, int TX, int TY) const
+    {
+        const WorkItem w = items[i];
+        const CaseDev<T, S> &C = cases[w.x];
+        const int par = (C.ctl->cur0 + m) & 1;
+        return TbrTile<T>{&C.P, C.g[par], C.g[par ^ 1], C.phig, C.q, C.coef, C.part2, w.w, w.y * TX, w.z * TY};
+    }
+};
+
+// Sweep launch m of every case, register-blocked (k_sweep_tbr's tiles of
+// 64 x 8R).  blockDim (32, 8), dynamic shared memory tbr_smem_bytes<T, R, 8>(FIRST).
+template <typename T, typename S, int NSW, int R, bool FIRST>
+__global__ void __launch_bounds__(256, 2) kb_sweep_r(const CaseDev<T, S> *__restrict__ cases,
+                                                     const WorkItem *__restrict__ items,
+                                                     const int *__restrict__ nitems, int m)
+{
+    const TbrBatchTiles<T, S> J{cases, items, *nitems, m};
+    tbr_run<T, NSW, R, 8, FIRST, false>(J);
+}
+
 // O5-O11 of every case.  blockDim (64, 4), dynamic shared memory main_smem_bytes<T, S>().
 template <typename T, typename S, bool SNAP>
 __global__ void __launch_bounds__(256, MAIN_MINB<T>) kb_main(const CaseDev<T, S> *__restrict__ cases,
@@ -264,6 +291,7 @@ __global__ void kb_open(const CaseDev<T, S> *__restrict__ cases, const int *__re
 template <typename T, typename S> class Batch : public BatchBase {
   public:
     static constexpr int TBMAX = 5;
+    static constexpr int TBR_R = 5;   // rows per thread of the register-blocked sweeps (64 x 40 regions)
     using Sv = Solver<T, S>;
 
     Batch(int sweeps, cudaStream_t s) : S_(sweeps), stream_(s) {}
@@ -287,7 +315,7 @@ template <typename T, typename S> class Batch : public BatchBase {
         EHDLB_CK(arena_.init(budget));
         EHDLB_CK(cudaEventCreate(&ev0_));
         EHDLB_CK(cudaEventCreate(&ev1_));
-        EHDLB_CK(dalloc((void **)&d_nitems_, sizeof(int) * 8));
+        EHDLB_CK(dalloc((void **)&d_nitems_, sizeof(host_nitems_)));
         int dev = 0;
         EHDLB_CK(cudaGetDevice(&dev));
         EHDLB_CK(cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev));
@@ -445,7 +473,7 @@ template <typename T, typename S> class Batch : public BatchBase {
     int set_tuning(int sweeps_per_launch, int shape, int use_graphs) override
     {
         if (sweeps_per_launch >= 1) chunk_ = std::min(TBMAX, sweeps_per_launch);
-        if (shape >= 0) shape_ = shape ? 1 : 0;
+        if (shape >= 0) shape_ = std::min(shape, 2);
         if (use_graphs >= 0) graphs_ = use_graphs != 0;
         drop_graph();
         return EHDLB_OK;
@@ -457,7 +485,7 @@ template <typename T, typename S> class Batch : public BatchBase {
         // (they advance); the fastest per step is kept
         double best = 1e300;
         int bc = chunk_, bs = shape_;
-        for (int sh = 0; sh < 2; ++sh)
+        for (int sh = 0; sh < 3; ++sh)
             for (int ch = 3; ch <= TBMAX; ++ch) {
                 set_tuning(ch, sh, -1);
                 ehdlb_batch_stats st{};
@@ -492,6 +520,13 @@ template <typename T, typename S> class Batch : public BatchBase {
     template <int NSW> cudaError_t sweep_attr()
     {
         cudaError_t e = cudaSuccess;
+        for (cudaError_t x : {cudaFuncSetAttribute(kb_sweep_r<T, S, NSW, TBR_R, true>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)tbr_smem_bytes<T, TBR_R, 8>(true)),
+                              cudaFuncSetAttribute(kb_sweep_r<T, S, NSW, TBR_R, false>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)tbr_smem_bytes<T, TBR_R, 8>(false))})
+            if (x != cudaSuccess) e = x;
         const int sm = (int)tb_smem_bytes<T, 64, 32>(true);
         for (cudaError_t x : {cudaFuncSetAttribute(kb_sweep<T, S, NSW, 16, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm),
                               cudaFuncSetAttribute(kb_sweep<T, S, NSW, 16, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm),
@@ -526,9 +561,25 @@ template <typename T, typename S> class Batch : public BatchBase {
         }
     }
 
+    template <int NSW> void sweep_launch_r(int m)
+    {
+        const size_t sm = tbr_smem_bytes<T, TBR_R, 8>(m == 0);
+        const int items = host_nitems_[8 + NSW];
+        if (m == 0) {
+            const int g = pgrid(kb_sweep_r<T, S, NSW, TBR_R, true>, 256, sm, items);
+            kb_sweep_r<T, S, NSW, TBR_R, true><<<g, dim3(32, 8), sm, stream_>>>(d_cases_, d_items_tbr_[NSW],
+                                                                               d_nitems_ + 8 + NSW, m);
+        } else {
+            const int g = pgrid(kb_sweep_r<T, S, NSW, TBR_R, false>, 256, sm, items);
+            kb_sweep_r<T, S, NSW, TBR_R, false><<<g, dim3(32, 8), sm, stream_>>>(d_cases_, d_items_tbr_[NSW],
+                                                                                d_nitems_ + 8 + NSW, m);
+        }
+    }
+
     template <int NSW> void sweep_launch_shape(int m)
     {
-        if (shape_ == 1) sweep_launch<NSW, 8, 4>(m);
+        if (shape_ == 2) sweep_launch_r<NSW>(m);
+        else if (shape_ == 1) sweep_launch<NSW, 8, 4>(m);
         else sweep_launch<NSW, 16, 3>(m);
     }
 
@@ -600,7 +651,7 @@ template <typename T, typename S> class Batch : public BatchBase {
         host_cases_.clear();
         index_of_.clear();
         std::vector<WorkItem> node;
-        std::vector<WorkItem> tb[TBMAX + 1];
+        std::vector<WorkItem> tb[TBMAX + 1], tbr[TBMAX + 1];
         nodes_ = 0;
         int c = 0;
         for (auto &kv : cases_) {
@@ -623,6 +674,10 @@ template <typename T, typename S> class Batch : public BatchBase {
                 const int tgx = (nx + tx - 1) / tx, tgy = (ny + ty - 1) / ty;
                 for (int by = 0; by < tgy; ++by)
                     for (int bx = 0; bx < tgx; ++bx) tb[nsw].push_back(make_int4(c, bx, by, by * tgx + bx));
+                const int rx = 64 - 2 * tbr_halo_x(nsw), ry = 8 * TBR_R - 2 * nsw;
+                const int rgx = (nx + rx - 1) / rx, rgy = (ny + ry - 1) / ry;
+                for (int by = 0; by < rgy; ++by)
+                    for (int bx = 0; bx < rgx; ++bx) tbr[nsw].push_back(make_int4(c, bx, by, by * rgx + bx));
             }
             nodes_ += (long long)nx * ny;
             ++c;
@@ -632,16 +687,25 @@ template <typename T, typename S> class Batch : public BatchBase {
         EHDLB_CK(ensure(d_D_, cap_D_, host_cases_.size()));
         EHDLB_CK(ensure(d_Dpart_, cap_Dpart_, host_cases_.size() * 3 * DEF_MAX_SLICES));
         EHDLB_CK(ensure(d_items_node_, cap_node_, node.size()));
-        for (int nsw = 1; nsw <= TBMAX; ++nsw) EHDLB_CK(ensure(d_items_tb_[nsw], cap_tb_[nsw], tb[nsw].size()));
+        for (int nsw = 1; nsw <= TBMAX; ++nsw) {
+            EHDLB_CK(ensure(d_items_tb_[nsw], cap_tb_[nsw], tb[nsw].size()));
+            EHDLB_CK(ensure(d_items_tbr_[nsw], cap_tbr_[nsw], tbr[nsw].size()));
+        }
         EHDLB_CK(cudaMemcpyAsync(d_cases_, host_cases_.data(), sizeof(CaseDev<T, S>) * host_cases_.size(),
                                  cudaMemcpyHostToDevice, stream_));
         EHDLB_CK(cudaMemcpyAsync(d_items_node_, node.data(), sizeof(WorkItem) * node.size(), cudaMemcpyHostToDevice,
                                  stream_));
         for (int nsw = 1; nsw <= TBMAX; ++nsw)
+            EHDLB_CK(cudaMemcpyAsync(d_items_tbr_[nsw], tbr[nsw].data(), sizeof(WorkItem) * tbr[nsw].size(),
+                                     cudaMemcpyHostToDevice, stream_));
+        for (int nsw = 1; nsw <= TBMAX; ++nsw)
             EHDLB_CK(cudaMemcpyAsync(d_items_tb_[nsw], tb[nsw].data(), sizeof(WorkItem) * tb[nsw].size(),
                                      cudaMemcpyHostToDevice, stream_));
         host_nitems_[0] = (int)node.size();
-        for (int nsw = 1; nsw <= TBMAX; ++nsw) host_nitems_[nsw] = (int)tb[nsw].size();
+        for (int nsw = 1; nsw <= TBMAX; ++nsw) {
+            host_nitems_[nsw] = (int)tb[nsw].size();
+            host_nitems_[8 + nsw] = (int)tbr[nsw].size();
+        }
         host_nitems_[6] = ncases_;
         host_nitems_[7] = 0;
         EHDLB_CK(cudaMemcpyAsync(d_nitems_, host_nitems_, sizeof(host_nitems_), cudaMemcpyHostToDevice, stream_));
@@ -663,7 +727,7 @@ template <typename T, typename S> class Batch : public BatchBase {
     int ncases_ = 0;
     long long nodes_ = 0;
     bool dirty_ = true;
-    int chunk_ = 5, shape_ = 1;
+    int chunk_ = 5, shape_ = 2;
     bool graphs_ = true;
     int sms_ = 1;
     long long launches_ = 0;
@@ -673,9 +737,10 @@ template <typename T, typename S> class Batch : public BatchBase {
     double *d_Dpart_ = nullptr;   // slice sums of the deformation factor
     WorkItem *d_items_node_ = nullptr;
     WorkItem *d_items_tb_[TBMAX + 1] = {};
-    int *d_nitems_ = nullptr;   // [0] node items, [1..5] sweep items by NSW, [6] cases
-    int host_nitems_[8] = {};
-    size_t cap_cases_ = 0, cap_D_ = 0, cap_Dpart_ = 0, cap_node_ = 0, cap_tb_[TBMAX + 1] = {};
+    WorkItem *d_items_tbr_[TBMAX + 1] = {};   // tiles of the register-blocked sweeps
+    int *d_nitems_ = nullptr;   // [0] node items, [1..5] sweep items by NSW, [6] cases, [9..13] register-blocked sweep items
+    int host_nitems_[16] = {};
+    size_t cap_cases_ = 0, cap_D_ = 0, cap_Dpart_ = 0, cap_node_ = 0, cap_tb_[TBMAX + 1] = {}, cap_tbr_[TBMAX + 1] = {};
     cudaGraphExec_t gexec_ = nullptr;
     cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;
 };

@@ -797,13 +797,43 @@ template <typename T, int R, int NW> __host__ __device__ constexpr size_t tbr_sm
     return sizeof(T) * (first ? (size_t)5 * NW * R * 64 + (size_t)(NW * R + 2) * TBR_FW : (size_t)7 * NW * R * 64);
 }
 
+// One tile of the register-blocked sweeps: its lattice (constants, g buffer
+// read and written, phi with ghost rows, q, the coefficient planes, the
+// residual partials and the tile's slot in them) and its first output node.
+template <typename T> struct TbrTile {
+    const DevP<T> *P;
+    const T *src;
+    T *dst;
+    const T *phig, *q;
+    T *coef;
+    double *part;
+    long long slot;
+    int x0, y0;
+};
+
+// The tiles of one lattice, tiles_x per row, row by row (sweep launch m).
+template <typename T> struct TbrLatticeTiles {
+    const DevP<T> *P;
+    T *gA, *gB;
+    const T *phig, *q;
+    T *coef;
+    double *part;
+    const Control *ctl;
+    int m, tiles_x, ntiles;
+    __device__ int count() const { return ntiles; }
+    __device__ TbrTile<T> tile(int t, int TX, int TY) const
+    {
+        const int par = (ctl->cur0 + m) & 1;
+        return TbrTile<T>{P, par ? gB : gA, par ? gA : gB, phig, q, coef, part, t, (t % tiles_x) * TX,
+                          (t / tiles_x) * TY};
+    }
+};
+
+// The persistent loop over the tiles J gives (count(), tile(i, TX, TY)).
 // Launch: blockDim (32, NW), dynamic shared memory tbr_smem_bytes<T, R, NW>(FIRST),
-// grid = min(tiles, resident blocks); tiles_x x (ntiles / tiles_x) tiles.
-template <typename T, int NSW, int R, int NW, int MINB, bool FIRST, bool RESID>
-__global__ void __launch_bounds__(32 * NW, MINB)
-    k_sweep_tbr(const DevP<T> P, T *__restrict__ gA, T *__restrict__ gB, const T *__restrict__ phig,
-                const T *__restrict__ q, T *__restrict__ coef, double *__restrict__ part,
-                const Control *__restrict__ ctl, int m, int tiles_x, int ntiles)
+// grid = min(tiles, resident blocks).
+template <typename T, int NSW, int R, int NW, bool FIRST, bool RESID, typename Tiles>
+__device__ __forceinline__ void tbr_run(const Tiles &J)
 {
     using V2 = typename Vec2T<T>::type;
     constexpr int H = NSW, HL = tbr_halo_x(NSW), RW = 64, RH = NW * R, TX = RW - 2 * HL,
@@ -815,26 +845,23 @@ __global__ void __launch_bounds__(32 * NW, MINB)
     T *const sphi = stg + 5 * PL;                               // FIRST: phi with its ring
     __shared__ __align__(16) T xup[2][NW][RW];   // p2 of each warp's top row, for the warp above
     __shared__ __align__(16) T xdn[2][NW][RW];   // p4 of each warp's bottom row, for the warp below
-    const int par = (ctl->cur0 + m) & 1;
-    const T *__restrict__ src = par ? gB : gA;
-    T *__restrict__ dst = par ? gA : gB;
-    const int nx = P.nx, ny = P.ny;
-    const long long nn = P.nn;
     const int lane = threadIdx.x, w = threadIdx.y;
     const int lx0 = 2 * lane, ly0 = w * R;
-    const bool wide = nx >= RW + 2;
-
-    const bool pairs = (nx & 1) == 0;   // a lane's two nodes are one aligned pair
     constexpr int NPL = FIRST ? 5 : 7;
-    // plane pl of the staged inputs: g1..g4, then q or A, Bx, By
-    auto plane = [&](int pl) -> const T * {
-        return pl < 4 ? src + pl * nn : (FIRST ? q : coef + (pl - 4) * nn);
-    };
 
-    // copy tile t to the stage: this thread's own cells (zeros outside the
+    // copy tile tl to the stage: this thread's own cells (zeros outside the
     // lattice rows), and (FIRST) a share of phi with its ring
-    auto issue = [&](int t) {
-        const int x0 = (t % tiles_x) * TX, y0 = (t / tiles_x) * TY;
+    auto issue = [&](const TbrTile<T> &tl) {
+        const int nx = tl.P->nx, ny = tl.P->ny;
+        const long long nn = tl.P->nn;
+        const bool wide = nx >= RW + 2;
+        const bool pairs = (nx & 1) == 0;   // a lane's two nodes are one aligned pair
+        const T *__restrict__ phig = tl.phig;
+        // plane pl of the staged inputs: g1..g4, then q or A, Bx, By
+        auto plane = [&](int pl) -> const T * {
+            return pl < 4 ? tl.src + pl * nn : (FIRST ? tl.q : tl.coef + (pl - 4) * nn);
+        };
+        const int x0 = tl.x0, y0 = tl.y0;
         const int gx = wrap_x(x0 - HL + lx0, nx, wide);
         const int gx1 = pairs ? gx + 1 : wrap_x(x0 - HL + lx0 + 1, nx, wide);
 #pragma unroll
@@ -898,11 +925,9 @@ __global__ void __launch_bounds__(32 * NW, MINB)
         }
     };
 
-    const T k1 = T(0.5) * (T(1) - P.s_g);
-    const T kf = T(0.5) * (T(1) - P.s_free_g);
-    const T ke = T(0.25) * P.s_free_g;
-    const T wG = P.wG;
-    int sw = 0;   // sweeps done by this block: parity of the exchange rows
+    T k1, kf, ke, wG;   // collision constants of the current tile's lattice
+    int ny;
+    int sw = 0;         // sweeps done by this block: parity of the exchange rows
 
     // NSW sweeps of the tile in registers; EDGE: the region reaches an
     // electrode row (block-uniform), which adds the wall links.  ch = half of
@@ -975,9 +1000,23 @@ __global__ void __launch_bounds__(32 * NW, MINB)
         }
     };
 
-    if ((int)blockIdx.x < ntiles) issue(blockIdx.x);
+    const int ntiles = J.count();
+    TbrTile<T> cur;
+    if ((int)blockIdx.x < ntiles) {
+        cur = J.tile(blockIdx.x, TX, TY);
+        issue(cur);
+    }
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int x0 = (t % tiles_x) * TX, y0 = (t / tiles_x) * TY;
+        const DevP<T> &P = *cur.P;
+        const int nx = P.nx;
+        const long long nn = P.nn;
+        const bool pairs = (nx & 1) == 0;
+        ny = P.ny;
+        k1 = T(0.5) * (T(1) - P.s_g);
+        kf = T(0.5) * (T(1) - P.s_free_g);
+        ke = T(0.25) * P.s_free_g;
+        wG = P.wG;
+        const int x0 = cur.x0, y0 = cur.y0;
         const int gy0 = y0 - H + ly0;   // lattice row of this thread's row 0
         cp_async_wait_all();
         if (FIRST) __syncthreads();      // phi was copied by all threads
@@ -1042,7 +1081,11 @@ __global__ void __launch_bounds__(32 * NW, MINB)
             }
             __syncthreads();      // phi read by all before it is refilled
         }
-        if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+        TbrTile<T> nxt = cur;
+        if (t + (int)gridDim.x < ntiles) {
+            nxt = J.tile(t + gridDim.x, TX, TY);
+            issue(nxt);
+        }
 
         T chA[R][2], chBx[R][2], chBy[R][2], psi_before[R][2];
 #pragma unroll
@@ -1076,14 +1119,14 @@ __global__ void __launch_bounds__(32 * NW, MINB)
                     if (gxo + 1 < nx) base[k + 1] = v[r][1];
                 }
             };
-            st2(dst, g1);
-            st2(dst + nn, g2);
-            st2(dst + 2 * nn, g3);
-            st2(dst + 3 * nn, g4);
+            st2(cur.dst, g1);
+            st2(cur.dst + nn, g2);
+            st2(cur.dst + 2 * nn, g3);
+            st2(cur.dst + 3 * nn, g4);
             if (FIRST) {
-                st2(coef, cA);
-                st2(coef + nn, cBx);
-                st2(coef + 2 * nn, cBy);
+                st2(cur.coef, cA);
+                st2(cur.coef + nn, cBx);
+                st2(cur.coef + 2 * nn, cBy);
             }
             if (RESID) {
 #pragma unroll
@@ -1097,9 +1140,20 @@ __global__ void __launch_bounds__(32 * NW, MINB)
                 }
             }
         }
-        if (RESID) block_sum_store_at<T, 2>(red, part, t);
+        if (RESID) block_sum_store_at<T, 2>(red, cur.part, cur.slot);
+        cur = nxt;
     }
     cp_async_wait_all();
+}
+
+template <typename T, int NSW, int R, int NW, int MINB, bool FIRST, bool RESID>
+__global__ void __launch_bounds__(32 * NW, MINB)
+    k_sweep_tbr(const __grid_constant__ DevP<T> P, T *__restrict__ gA, T *__restrict__ gB,
+                const T *__restrict__ phig, const T *__restrict__ q, T *__restrict__ coef,
+                double *__restrict__ part, const Control *__restrict__ ctl, int m, int tiles_x, int ntiles)
+{
+    const TbrLatticeTiles<T> J{&P, gA, gB, phig, q, coef, part, ctl, m, tiles_x, ntiles};
+    tbr_run<T, NSW, R, NW, FIRST, RESID>(J);
 }
 
 // ---- thread-block clusters -------------------------------------------------------

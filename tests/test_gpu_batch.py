@@ -35,9 +35,12 @@ def alone(nx, ny, p, steps, precision):
     return f, d
 
 
+@pytest.mark.parametrize("shape", [1, 2])
 @pytest.mark.parametrize("precision", [ehdlb.FP32, ehdlb.FP16S])
-def test_batched_cases_equal_the_same_cases_alone(precision):
+def test_batched_cases_equal_the_same_cases_alone(precision, shape):
+    # tile shape 1: the sweeps in shared memory; 2: in registers
     b = ehdlb.Batch(2 << 30, SWEEPS, precision=precision)
+    ehdlb.ehdlb_batch_set_tuning(b.b, -1, shape, -1)
     ids = [b.add(nx, ny, case_params(nx, ny, *c)) for nx, ny, *c in CASES]
     steps = 30
     b.step(steps - 7)
@@ -114,7 +117,7 @@ def test_autotuner_picks_a_valid_schedule():
     for nx, ny, *c in CASES[:2]:
         b.add(nx, ny, case_params(nx, ny, *c))
     spl, shape, ms = b.autotune(3)
-    assert spl in (3, 4, 5) and shape in (0, 1) and ms > 0
+    assert spl in (3, 4, 5) and shape in (0, 1, 2) and ms > 0
     _, st = b.step(2)
     assert st.sweeps_per_launch == spl and st.tile_shape == shape
     b.close()
