@@ -800,13 +800,19 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         EHDLB_CK(cudaMemcpyAsync(&ctl_h_, ctl_, sizeof(Control), cudaMemcpyDeviceToHost, stream_));
         EHDLB_CK(cudaStreamSynchronize(stream_));
         const int cur = ctl_h_.cur0;
+        // rows of the state per chunk through the solver's staging buffer
+        // (nn doubles); the chunks follow one another on the stream, which
+        // is synchronised once at the end
         const size_t per_row = (size_t)state_per_node() * nx_;
-        int rows = (int)std::max<size_t>(1, std::min<size_t>((size_t)ny_, ((size_t)nn_) / per_row));
-        double *stage = nullptr;
-        EHDLB_CK(cudaMalloc((void **)&stage, sizeof(double) * per_row * rows));
+        const int rows = (int)std::min<size_t>((size_t)ny_, ((size_t)nn_) / per_row);
+        double *stage = stage_;
         int status = EHDLB_OK;
-        for (int y0 = 0; y0 < ny_ && status == EHDLB_OK; y0 += rows) {
-            const int r = std::min(rows, ny_ - y0);
+        if (rows < 1) {   // a row of the state exceeds the staging buffer (nn < per_row)
+            EHDLB_CK(cudaMalloc((void **)&stage, sizeof(double) * per_row));
+        }
+        const int crows = std::max(1, rows);
+        for (int y0 = 0; y0 < ny_ && status == EHDLB_OK; y0 += crows) {
+            const int r = std::min(crows, ny_ - y0);
             const long long cnt = (long long)r * nx_;
             const unsigned nblk = (unsigned)((cnt + 255) / 256);
             cudaError_t e = cudaSuccess;
@@ -835,13 +841,17 @@ template <typename T, typename S = T> class Solver : public SolverBase {
                 }
                 if (e == cudaSuccess) e = cudaGetLastError();
             }
-            if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
             if (e != cudaSuccess) {
                 err = std::string("state transfer: ") + cudaGetErrorString(e);
                 status = EHDLB_ECUDA;
             }
         }
-        cudaFree(stage);
+        const cudaError_t e = cudaStreamSynchronize(stream_);
+        if (e != cudaSuccess && status == EHDLB_OK) {
+            err = std::string("state transfer: ") + cudaGetErrorString(e);
+            status = EHDLB_ECUDA;
+        }
+        if (stage != stage_) cudaFree(stage);
         return status;
     }
 
