@@ -39,6 +39,24 @@ def sweep_bytes_per_node(storage_bytes: int) -> int:
     return 10 * storage_bytes + 8
 
 
+def prep_bytes_per_node(storage_bytes: int) -> int:
+    """k_prep: h (9), p (5), n (5) populations read; phi, dphi (with ghost
+    rows) and q written as float."""
+    return 19 * storage_bytes + 12
+
+
+def main_bytes_per_node(storage_bytes: int) -> int:
+    """k_main: f (8), h (9), p (5), n (5) read and written, (phi u)(t-1)
+    read and written, g (4 float) read, dphi, phi_ref, grad phi_ref (2) and
+    mu_ref read as float."""
+    return 2 * 27 * storage_bytes + 2 * 2 * storage_bytes + 16 + 20
+
+
+def step_model_bytes(storage_bytes: int, sweeps: int) -> int:
+    """Whole-step byte model of the unfused method: 56 s + 24 + (10 s + 8) S."""
+    return 56 * storage_bytes + 24 + (10 * storage_bytes + 8) * sweeps
+
+
 # bytes of the control block ehdlb_step reads back after every call (sums,
 # residual, counters)
 CONTROL_BYTES = 120
@@ -285,6 +303,30 @@ def run_ours(args):
     launches = int(st.launches)
     ehdlb.ehdlb_set_timing(lat.ctx, False)
 
+    # every kernel class of a step against the measured copy bandwidth:
+    # algorithmic bytes per step / device time per step, and the DRAM bytes
+    # ncu measured for it (profiles/traffic.json) while its source is unchanged
+    launches_per_step = max(1, st.sweep_launches) / args.steps
+    suffix = "" if args.precision == "fp32" else f"_{args.precision}"
+
+    def kernel_line(alg_bytes_per_node, ms_per_step, dram_key, dram_launches=1.0):
+        achieved_k = alg_bytes_per_node * nn / (ms_per_step / 1e3) / 1e9
+        t = measured_traffic(dram_key + suffix, n)
+        return {"algorithmic_bytes_per_node": alg_bytes_per_node, "ms_per_step": round(ms_per_step, 4),
+                "achieved": round(achieved_k, 1), "frac": round(achieved_k / hbm, 4),
+                "dram_bytes_per_node": (round(t * dram_launches / nn, 1) if t else None)}
+
+    roofline_kernels = {
+        "unit": "GB/s", "peak": hbm,
+        "k_prep": kernel_line(prep_bytes_per_node(sbytes), st.ms_prep / args.steps, "k_prep"),
+        sweep_kernel[0]: kernel_line(unit_bytes * SWEEPS, st.ms_sweeps / args.steps, sweep_kernel[0],
+                                     launches_per_step),
+        "k_main": kernel_line(main_bytes_per_node(sbytes), st.ms_main / args.steps, "k_main"),
+        "step": {"model_bytes_per_node_step": step_model_bytes(sbytes, SWEEPS),
+                 "achieved": round(step_model_bytes(sbytes, SWEEPS) * value * 1e6 / world / 1e9, 1),
+                 "frac": round(step_model_bytes(sbytes, SWEEPS) * value * 1e6 / world / 1e9 / hbm, 4)},
+    }
+
     # end to end through the public API with host buffers: the job's input,
     # a full state (35 doubles per node with D2Q5 ions) in pinned host memory, goes to the
     # device (ehdlb_set_state), then every step is one ehdlb_step call (its
@@ -346,6 +388,7 @@ def run_ours(args):
                      "sweeps_per_launch": sweeps_per_launch, "launch_ms": sweep_launch_ms,
                      "dram_achieved": (round(traffic / (sweep_launch_ms / 1e3) / 1e9, 1)
                                        if traffic else None)},
+        "roofline_kernels": roofline_kernels,
         "gpu_launches": launches,
         "kernel_ms": {"prep": st.ms_prep / args.steps, "sweeps": st.ms_sweeps / args.steps,
                       "main": st.ms_main / args.steps},
