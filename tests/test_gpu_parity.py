@@ -189,6 +189,26 @@ def test_fp32_d2q9_ions_match_oracle():
     assert_close(err, FP32_U_TOL, keys=["u"])
 
 
+@pytest.mark.parametrize("nx,ny,precision", [(8, 8, ehdlb.FP64), (13, 7, ehdlb.FP32), (70, 40, ehdlb.FP64)])
+def test_state_round_trips_on_lattices_of_any_size(nx, ny, precision):
+    # a row of the state (35 values per node) longer than the solver's
+    # staging buffer (8 x 8, 13 x 7), and a state moved in 40 chunks (70 x 40)
+    prm = dict(workloads.droplet64(), xc=(nx - 1) / 2, yc=(ny - 1) / 2, R=min(nx, ny) / 4,
+               sweeps_min=5, sweeps_max=5)
+    orc = oracle.Oracle(nx, ny, prm)
+    orc.step(3)
+    s = orc.state()
+    assert s.shape == (ny, nx, 35)
+    lat = ehdlb.Lattice(nx, ny, dict(prm, init_sweeps_fixed=0), precision=precision)
+    lat.set_state(s)
+    got = lat.state()
+    keep = np.ones(35, bool)
+    keep[[0, 28]] = False                       # f0 and g0 are not stored
+    tol = 1e-15 if precision == ehdlb.FP64 else 1e-6 * np.max(np.abs(s))
+    assert np.max(np.abs(got[:, :, keep] - s[:, :, keep])) <= tol
+    lat.close()
+
+
 def test_d2q9_ion_state_round_trips_through_the_oracle():
     prm = dict(workloads.droplet64(), ion_lattice=9, sweeps_min=10, sweeps_max=10)
     orc = oracle.Oracle(64, 64, prm)
