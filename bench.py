@@ -220,6 +220,16 @@ def oracle_rate(n: int, steps: int, budget_s: float):
     return n * n * done / dt / 1e6, done, dt, threads
 
 
+def workload_config(n: int, precision: str, world: int) -> dict:
+    """The config of the timed workload (both arms report it)."""
+    label, sbytes, _ = PRECISIONS[precision]
+    return {"workload": f"droplet {n}x{n} {label}, 20 potential sweeps per step "
+                        f"(R = {n // 8}, eps_r = 4, mu_r = 2, dpsi = 2)",
+            "nx": n, "ny": n, "sweeps_per_step": SWEEPS, "storage_bytes": sbytes,
+            "l2": "inputs larger than L2 (state ~1.35 GB), no flush",
+            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -235,15 +245,14 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     value = n * n * args.steps / dt / 1e6
-    sample = (f"FP64 CPU oracle, {n}x{n} copy of the 2048^2 droplet case (R = {n // 8}, "
+    sample = (f"FP64 CPU oracle on a {n}x{n} copy of the {args.n}^2 droplet case (R = {n // 8}, "
               f"{SWEEPS} sweeps/step), {args.steps} timed steps after {args.warmup} warm-up")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"droplet {n}x{n} (sample of the 2048x2048 case)", "nx": n, "ny": n,
-                   "sweeps_per_step": SWEEPS},
+        "config": workload_config(args.n, args.precision, world),
         "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": threads,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
@@ -375,11 +384,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
         "data": "synthetic",
-        "config": {"workload": f"droplet {n}x{n} {label}, 20 potential sweeps per step "
-                               f"(R = {n // 8}, eps_r = 4, mu_r = 2, dpsi = 2)",
-                   "nx": n, "ny": n, "sweeps_per_step": SWEEPS, "storage_bytes": sbytes,
-                   "l2": "inputs larger than L2 (state ~1.35 GB), no flush",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "config": workload_config(n, args.precision, world),
         "roofline": {"bound": "hbm", "kernel": f"{sweep_kernel[0]} ({sweep_kernel[1]})",
                      "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "peak_source": peak_kind,
