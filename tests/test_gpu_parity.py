@@ -254,12 +254,12 @@ def test_fp32_every_sweep_tuning_matches_oracle():
                 raise AssertionError(f"shape {shape}, {spl} sweeps per launch: {e}") from None
 
 
-@pytest.mark.parametrize("nx,ny", [(40, 70), (66, 45), (45, 66), (137, 50)])
+@pytest.mark.parametrize("nx,ny", [(8, 8), (13, 7), (40, 70), (66, 45), (45, 66), (137, 50)])
 def test_fp32_register_blocked_sweeps_on_narrow_lattices(nx, ny):
     # lattices narrower than the 64-node region (x wraps inside it) or just
-    # wider, odd widths (no aligned node pairs), and fewer rows than two
-    # regions: the register-blocked shapes against the oracle, five sweeps
-    # per launch
+    # wider, odd widths (no aligned node pairs), fewer rows than two regions
+    # and tiny lattices that one mostly empty region covers: the
+    # register-blocked shapes against the oracle, five sweeps per launch
     steps = 8
     prm = workloads.droplet(64)
     prm.update(xc=(nx - 1) / 2, yc=(ny - 1) / 2, R=min(nx, ny) / 4, Kq=5.6893 / (nx * ny))
