@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define EHDLB_ABI_VERSION 4
+#define EHDLB_ABI_VERSION 5
 
 typedef struct ehdlb_ctx ehdlb_ctx;
 
@@ -162,6 +162,8 @@ typedef struct ehdlb_stats {
     long long sweep_launches; /* of which potential-sweep kernels */
     int sweeps_per_launch;    /* fused sweeps per launch (0: one sweep per launch) */
     int tile_shape;           /* tile shape of the fused sweep kernel (ehdlb_set_tuning) */
+    double deformation;       /* D (Eq. 63) of the last step when ehdlb_set_reporting asked
+                                 for it, else NaN */
 } ehdlb_stats;
 
 /* Counters of one ehdlb_batch_step() call. */
@@ -226,6 +228,17 @@ int ehdlb_step(ehdlb_ctx *c, int nsteps, ehdlb_stats *out);
  * [ny][nx], into dst of dst_len doubles (>= popcount(mask) nx ny). */
 int ehdlb_get_fields(ehdlb_ctx *c, unsigned mask, double *dst,
                      size_t dst_len);
+
+/* What the last step of every ehdlb_step call reports.  snapshot_mask
+ * (bits EHDLB_PHI ...) selects the fields its snapshot captures for
+ * ehdlb_get_fields (default: all); asking ehdlb_get_fields for a field
+ * outside the last capture returns EHDLB_ESTATE.  deformation = 1 makes every
+ * call also compute the deformation factor D of Eq. 63 from that snapshot
+ * (phi is then captured whatever the mask) and return it in
+ * ehdlb_stats.deformation, read back with the call's counters.  The initial
+ * fields after ehdlb_set_params are always captured whole.  EINVAL for a
+ * mask with bits at or above EHDLB_NFIELDS or deformation outside 0, 1. */
+int ehdlb_set_reporting(ehdlb_ctx *c, unsigned snapshot_mask, int deformation);
 
 /* Sweep counts of the steps of the last ehdlb_step call, n <= its nsteps. */
 int ehdlb_get_sweep_counts(ehdlb_ctx *c, int *dst, int n);

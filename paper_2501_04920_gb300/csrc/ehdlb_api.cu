@@ -236,6 +236,15 @@ int ehdlb_set_timing(ehdlb_ctx *c, int on)
     return EHDLB_OK;
 }
 
+int ehdlb_set_reporting(ehdlb_ctx *c, unsigned snapshot_mask, int deformation)
+{
+    if (!c) return EHDLB_EINVAL;
+    if (snapshot_mask >> EHDLB_NFIELDS) return fail(c, EHDLB_EINVAL, "snapshot_mask has bits beyond the fields");
+    if (deformation != 0 && deformation != 1) return fail(c, EHDLB_EINVAL, "deformation must be 0 or 1");
+    c->solver->set_reporting(snapshot_mask, deformation);
+    return EHDLB_OK;
+}
+
 int ehdlb_set_tuning(ehdlb_ctx *c, int sweeps_per_launch, int tile_shape, int main_staging)
 {
     if (!c) return EHDLB_EINVAL;

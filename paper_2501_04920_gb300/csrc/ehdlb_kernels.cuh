@@ -84,6 +84,7 @@ template <typename T> struct DevP {
     T s_p0, s_n0;                  // ion rates (Eq. 37) when D is uniform, else 0
     T inv_mu_v, three_over_tau_g, inv_W;
     T src_a, src_b;                // fused sweeps: src_norm Kq / 3, src_norm (eps_r - 1) / tau_g
+    unsigned snap_mask;            // fields the step kernel's snapshot writes (bit f: field f)
     // storage scales (value x sc is stored, stored x isc is the value) and
     // the rest concentration of the stored p, n; 1, 1 and 0 unless S != T
     T sc_f, isc_f, sc_h, isc_h, sc_c, isc_c, sc_g, isc_g, sc_u, isc_u;  // sc_g: g stored as S
@@ -1925,16 +1926,17 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
         }
 
         if (SNAP) {
-            snap[k] = phi;
-            snap[nn + k] = ux;
-            snap[2 * nn + k] = uy;
-            snap[3 * nn + k] = pr;
-            snap[4 * nn + k] = psi;
-            snap[5 * nn + k] = Ex;
-            snap[6 * nn + k] = Ey;
-            snap[7 * nn + k] = cp;
-            snap[8 * nn + k] = cm;
-            snap[9 * nn + k] = q;
+            const unsigned sm = P.snap_mask;   // block-uniform
+            if (sm & 1u) snap[k] = phi;
+            if (sm & 2u) snap[nn + k] = ux;
+            if (sm & 4u) snap[2 * nn + k] = uy;
+            if (sm & 8u) snap[3 * nn + k] = pr;
+            if (sm & 16u) snap[4 * nn + k] = psi;
+            if (sm & 32u) snap[5 * nn + k] = Ex;
+            if (sm & 64u) snap[6 * nn + k] = Ey;
+            if (sm & 128u) snap[7 * nn + k] = cp;
+            if (sm & 256u) snap[8 * nn + k] = cm;
+            if (sm & 512u) snap[9 * nn + k] = q;
             red[0] = phi;
             red[1] = q;
         }

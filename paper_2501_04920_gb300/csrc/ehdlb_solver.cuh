@@ -114,6 +114,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     {
         P_ = p;
         make_devp();
+        snap_valid_ = (1u << EHDLB_NFIELDS) - 1;   // the initial fields are captured whole
         const int qi = p.ion_lattice == 9 ? 9 : 5;
         if (qi != qi_) {   // the ion lattice sets the size of the population blocks
             EHDLB_CK(cudaStreamSynchronize(stream_));
@@ -217,10 +218,15 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             enqueue_step(s, s == nsteps - 1);
             EHDLB_CK(cudaGetLastError());
         }
+        if (deform_each_) {   // D of the last step, read back with the control block
+            EHDLB_CK(enqueue_deformation());
+            launches_ += 2;
+        }
         EHDLB_CK(cudaMemcpyAsync(&pin_->c, ctl_, sizeof(Control), cudaMemcpyDeviceToHost, stream_));
         EHDLB_CK(cudaStreamSynchronize(stream_));
         EHDLB_CK(cudaGetLastError());
         ctl_h_ = pin_->c;
+        if (nsteps > 0) snap_valid_ = snap_mask_;
         last_nsteps = nsteps;
         const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (st) {
@@ -250,6 +256,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             st->sweep_launches = sweep_launches_;
             st->sweeps_per_launch = tb_chunk();
             st->tile_shape = tb_shape_;
+            st->deformation = deform_each_ && nsteps > 0 ? pin_->D : NAN;
         }
         if (ctl_h_.unstable) {
             err = "NaN or Inf in the fields";
@@ -260,6 +267,10 @@ template <typename T, typename S = T> class Solver : public SolverBase {
 
     int get_fields(unsigned mask, double *dst, std::string &err) override
     {
+        if (mask & ~snap_valid_) {
+            err = "a requested field was not captured by the last step (ehdlb_set_reporting)";
+            return EHDLB_ESTATE;
+        }
         size_t off = 0;
         const int nthr = 256;
         const unsigned nblk = (unsigned)((nn_ + nthr - 1) / nthr);
@@ -288,19 +299,38 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     // D of Eq. 63 from the phi of the last snapshot
     int deformation(double *out, std::string &err) override
     {
-        double *parts = red_ + 6 * PSUM;
-        k_deform_sums<T><<<deform_slices(nx_, ny_), 256, 0, stream_>>>(snap_, nx_, ny_, parts);
-        k_deform_finish<T><<<1, 256, 0, stream_>>>(snap_, nx_, ny_, parts, stage_);
-        EHDLB_CK(cudaGetLastError());
+        if (!(snap_valid_ & 1u)) {
+            err = "phi was not captured by the last step (ehdlb_set_reporting)";
+            return EHDLB_ESTATE;
+        }
         EHDLB_CK(pinned());
-        EHDLB_CK(cudaMemcpyAsync(&pin_->D, stage_, sizeof(double), cudaMemcpyDeviceToHost, stream_));
+        EHDLB_CK(enqueue_deformation());
         EHDLB_CK(cudaStreamSynchronize(stream_));
         *out = pin_->D;
         return EHDLB_OK;
     }
+
+    void set_reporting(unsigned snap_mask, int deformation) override
+    {
+        deform_each_ = deformation != 0;
+        snap_mask_ = (snap_mask & ((1u << EHDLB_NFIELDS) - 1)) | (deform_each_ ? 1u : 0u);
+        dp_.snap_mask = snap_mask_;
+    }
     int set_state(const double *src, std::string &err) override { return transfer_state(nullptr, src, err); }
 
   private:
+    // D of Eq. 63 from the snapshot's phi into the page-locked mirror (on
+    // the stream; the caller synchronises)
+    cudaError_t enqueue_deformation()
+    {
+        double *parts = red_ + 6 * PSUM;
+        k_deform_sums<T><<<deform_slices(nx_, ny_), 256, 0, stream_>>>(snap_, nx_, ny_, parts);
+        k_deform_finish<T><<<1, 256, 0, stream_>>>(snap_, nx_, ny_, parts, stage_);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&pin_->D, stage_, sizeof(double), cudaMemcpyDeviceToHost, stream_);
+        return e;
+    }
+
     // page-locked host copy of the control block and D, read back by every
     // step call and deformation (allocated on first use: cases of a batch
     // never need it)
@@ -414,6 +444,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         d.src_norm = (T)src_norm;
         d.Kq = (T)p.Kq;
         d.er1 = (T)(p.eps_r - 1.0);
+        d.snap_mask = snap_mask_;
         d.src_a = (T)(src_norm * p.Kq / 3.0);
         d.src_b = (T)(src_norm * (p.eps_r - 1.0) / tau_g);
         d.psi_a = (T)p.psi_anode;
@@ -873,6 +904,9 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     int tb_chunk_ = sizeof(T) == 4 ? 5 : 2;  // sweeps fused per launch (0: one per launch)
     int tb_shape_ = sizeof(T) == 4 ? 5 : 0;   // region shape of the fused sweep kernel
     int tbr_per_sm_[2] = {1 << 20, 1 << 20};  // resident blocks per SM of the register-blocked shapes
+    unsigned snap_mask_ = (1u << EHDLB_NFIELDS) - 1;   // fields the reporting step captures
+    unsigned snap_valid_ = (1u << EHDLB_NFIELDS) - 1;  // fields the snapshot holds now
+    bool deform_each_ = false;                        // every step call also computes D
     int sms_ = 1;                             // SMs of the device
     int tb_m_ = 0;                            // launch index within the step
     int qi_ = 0;                              // ion populations per species (5 or 9) of pops_

@@ -33,6 +33,9 @@ class SolverBase {
     virtual void set_timing(int on) = 0;
     virtual void set_tuning(int sweeps_per_launch, int shape, int vec_staging) = 0;
     virtual int deformation(double *out, std::string &err) = 0;
+    // fields the last step of each call captures, and whether each call
+    // also computes D of Eq. 63 (stats->deformation)
+    virtual void set_reporting(unsigned snap_mask, int deformation) = 0;
     virtual int state_per_node() const = 0;   // doubles per node of get_state / set_state
     int last_nsteps = 0;
 };

@@ -57,7 +57,7 @@ class ehdlb_stats(C.Structure):
         ("seconds", C.c_double), ("mlups", C.c_double),
         ("ms_prep", C.c_double), ("ms_sweeps", C.c_double), ("ms_main", C.c_double),
         ("launches", C.c_longlong), ("sweep_launches", C.c_longlong),
-        ("sweeps_per_launch", C.c_int), ("tile_shape", C.c_int),
+        ("sweeps_per_launch", C.c_int), ("tile_shape", C.c_int), ("deformation", C.c_double),
     ]
 
 
@@ -103,6 +103,7 @@ def lib():
         L.ehdlb_set_state.argtypes = [vp, dp, C.c_size_t]
         L.ehdlb_set_timing.argtypes = [vp, C.c_int]
         L.ehdlb_set_tuning.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+        L.ehdlb_set_reporting.argtypes = [vp, C.c_uint, C.c_int]
         L.ehdlb_potential_noalloc.argtypes = [C.c_int, C.c_int, C.POINTER(ehdlb_params), vp, vp,
                                               C.c_int, vp, vp, vp, dp, vp]
         L.ehdlb_deformation.argtypes = [vp, dp]
@@ -125,7 +126,7 @@ def lib():
         L.ehdlb_destroy.restype = None
         L.ehdlb_last_error.argtypes = [vp]
         L.ehdlb_last_error.restype = C.c_char_p
-        if L.ehdlb_version() != 4:
+        if L.ehdlb_version() != 5:
             raise ImportError("libehdlb ABI version mismatch")
         _lib = L
     return _lib
@@ -241,6 +242,10 @@ def ehdlb_potential_noalloc(nx, ny, p: ehdlb_params, phi_dev: int, q_dev: int, n
         C.c_void_p(psi_dev), C.c_void_p(ex_dev), C.c_void_p(ey_dev), C.byref(r),
         C.c_void_p(cuda_stream) if cuda_stream else None)
     return status, r.value
+
+
+def ehdlb_set_reporting(ctx, snapshot_mask: int, deformation: int = 0):
+    return _check(ctx, lib().ehdlb_set_reporting(ctx, snapshot_mask, deformation), "ehdlb_set_reporting")
 
 
 def ehdlb_set_tuning(ctx, sweeps_per_launch: int = -1, tile_shape: int = -1, main_staging: int = -1):

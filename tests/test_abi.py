@@ -76,12 +76,13 @@ def test_null_and_bad_arguments_are_rejected_without_a_device():
     assert L.ehdlb_set_params(None, None) == ehdlb.EINVAL
     assert L.ehdlb_get_fields(None, 1, None, 0) == ehdlb.EINVAL
     assert L.ehdlb_params_default(None) == ehdlb.EINVAL
+    assert L.ehdlb_set_reporting(None, 1, 0) == ehdlb.EINVAL
     h = C.c_void_p()
     assert L.ehdlb_create(C.byref(h), 3, 64, ehdlb.FP32, None) == ehdlb.EINVAL
     assert L.ehdlb_create(C.byref(h), 64, 64, 7, None) == ehdlb.EINVAL
     assert not h.value
     L.ehdlb_destroy(None)
-    assert ehdlb.ehdlb_version() == 4
+    assert ehdlb.ehdlb_version() == 5
 
 
 def test_batch_entry_points_reject_null_without_a_device():

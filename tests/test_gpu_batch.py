@@ -112,6 +112,32 @@ def test_device_deformation_is_eq63_of_the_fields(nx, ny):
     lat.close()
 
 
+def test_reporting_captures_the_asked_fields_and_returns_D():
+    nx, ny = 128, 192
+    lat = ehdlb.Lattice(nx, ny, case_params(nx, ny, 1.0, 4.0, 0.5, 5.0))
+    lat.step(20)
+    phi_bit = 1 << ehdlb.FIELDS.index("phi")
+    ehdlb.ehdlb_set_reporting(lat.ctx, phi_bit, 1)
+    _, st = lat.step(20)
+    # D read back with the step's counters is D of the captured phi
+    assert st.deformation == lat.deformation()
+    assert abs(st.deformation - oracle.deformation(lat.fields(["phi"])["phi"])) <= 1e-12
+    with pytest.raises(ehdlb.EhdlbError):
+        lat.fields(["ux"])                      # not captured by the last step
+    ehdlb.ehdlb_set_reporting(lat.ctx, 0, 1)    # D alone still captures phi
+    _, st = lat.step(1)
+    assert st.deformation == lat.deformation()
+    ehdlb.ehdlb_set_reporting(lat.ctx, (1 << len(ehdlb.FIELDS)) - 1, 0)
+    _, st = lat.step(1)
+    assert np.isnan(st.deformation)
+    assert set(lat.fields()) >= {"phi", "ux", "q"}
+    with pytest.raises(ehdlb.EhdlbError):
+        ehdlb.ehdlb_set_reporting(lat.ctx, 1 << len(ehdlb.FIELDS), 0)
+    with pytest.raises(ehdlb.EhdlbError):
+        ehdlb.ehdlb_set_reporting(lat.ctx, phi_bit, 2)
+    lat.close()
+
+
 def test_autotuner_picks_a_valid_schedule():
     b = ehdlb.Batch(1 << 30, SWEEPS)
     for nx, ny, *c in CASES[:2]:
