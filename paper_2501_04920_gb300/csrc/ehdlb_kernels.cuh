@@ -2228,9 +2228,14 @@ __device__ __forceinline__ double phi_sample(const T *phi, int nx, int ny, doubl
     x1 = ((x1 % nx) + nx) % nx;
     y0 = min(max(y0, 0), ny - 1);
     y1 = min(max(y1, 0), ny - 1);
-    const double a = (double)phi[(long long)y0 * nx + x0] * (1.0 - fx) + (double)phi[(long long)y0 * nx + x1] * fx;
-    const double b = (double)phi[(long long)y1 * nx + x0] * (1.0 - fx) + (double)phi[(long long)y1 * nx + x1] * fx;
-    return a * (1.0 - fy) + b * fy;
+    // every product and sum rounded on its own, so that all kernels that
+    // sample a line (one lattice, a batch) give the same bits
+    const double gx = 1.0 - fx, gy = 1.0 - fy;
+    const double a = __dadd_rn(__dmul_rn((double)phi[(long long)y0 * nx + x0], gx),
+                               __dmul_rn((double)phi[(long long)y0 * nx + x1], fx));
+    const double b = __dadd_rn(__dmul_rn((double)phi[(long long)y1 * nx + x0], gx),
+                               __dmul_rn((double)phi[(long long)y1 * nx + x1], fx));
+    return __dadd_rn(__dmul_rn(a, gy), __dmul_rn(b, fy));
 }
 
 // The phi-weighted sums of the centroid are taken over slices of the nodes in
@@ -2265,6 +2270,8 @@ __device__ __forceinline__ void deform_slice_sums(const T *__restrict__ phi, int
     const long long nn = (long long)nx * ny;
     const long long k0 = j * nn / nsl, k1 = (j + 1) * nn / nsl;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    // (every product and sum is rounded on its own: the slice sums of one
+    // lattice and of a batch come from different kernels and must agree)
     // FP32 fields: each thread keeps its sums as unevaluated float pairs
     // (hi + lo; exact products by fmaf, TwoSum additions), about 48 bits, and
     // hands them to double per row (sum phi, sum phi y) and at the end (sum
@@ -2290,20 +2297,20 @@ __device__ __forceinline__ void deform_slice_sums(const T *__restrict__ phi, int
                 h1 = two_sum(h1, p, e);
                 l1 = __fadd_rn(l1, __fadd_rn(e, pe));
             }
-            const double r = (double)rh + (double)rl;
-            a0 += r;
-            a2 += r * fy;
+            const double r = __dadd_rn((double)rh, (double)rl);
+            a0 = __dadd_rn(a0, r);
+            a2 = __dadd_rn(a2, __dmul_rn(r, fy));
         } else {
 #pragma unroll 4
             for (int x = xs + (int)threadIdx.x; x < xe; x += 256) {
                 const double v = (double)row[x];
-                a0 += v;
-                a1 += v * (double)x;
-                a2 += v * fy;
+                a0 = __dadd_rn(a0, v);
+                a1 = __dadd_rn(a1, __dmul_rn(v, (double)x));
+                a2 = __dadd_rn(a2, __dmul_rn(v, fy));
             }
         }
     }
-    a1 += (double)h1 + (double)l1;
+    a1 = __dadd_rn(a1, __dadd_rn((double)h1, (double)l1));
     red[threadIdx.x][0] = a0;
     red[threadIdx.x][1] = a1;
     red[threadIdx.x][2] = a2;
