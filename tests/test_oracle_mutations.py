@@ -1,0 +1,91 @@
+"""Planted mistakes in a copy of the oracle (CPU only).
+
+Each case compiles a copy of the oracle's C source with one plausible
+mistake (a dropped term, a wrong sign, a transposed operand, a wrong weight
+or factor), loads it as a separate instance of the `oracle` package and runs
+one of the pins of test_oracle_pins.py against it: the pin must fail.  The
+oracle itself is not modified.
+"""
+import importlib.util
+import os
+import shutil
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+# (what, text in ehd_oracle.c, its mistaken form, a pin that must fail)
+MUTATIONS = [
+    ("Eq. 53: the -u^2 / (2 cs2) term of r_i(u) dropped",
+     "return w9[i] * (cu / cs2 + cu * cu / (2.0 * cs2 * cs2) - uu / (2.0 * cs2));",
+     "return w9[i] * (cu / cs2 + cu * cu / (2.0 * cs2 * cs2));",
+     "test_p2_equilibrium_moments"),
+    ("Eq. 54: sign of the cs2 u.grad(rho) part of the tensor term",
+     "double tens = uc * gc - cs2 * ugr;",
+     "double tens = uc * gc + cs2 * ugr;",
+     "test_p4_momentum_and_ion_sources_exact_for_any_rates"),
+    ("Eq. 59: c_x in place of c_y in the y gradient",
+     "sy += w9[i] * cy9[i] * v;",
+     "sy += w9[i] * cx9[i] * v;",
+     "test_p5_stencil_exact_on_low_degree_polynomials"),
+    ("Eq. 25: a diagonal weight 1/18 instead of 1/36",
+     "1.0 / 9.0,  1.0 / 36.0,\n",
+     "1.0 / 9.0,  1.0 / 18.0,\n",
+     "test_p2_equilibrium_moments"),
+    ("Eq. 32: sign of the sharpening flux",
+     "double vx = dphiux + cs2 * lam * nx;",
+     "double vx = dphiux - cs2 * lam * nx;",
+     "test_p12_static_droplet_obeys_laplace_law"),
+    ("Eq. 38: sign of the advective part of the ion equilibrium",
+     "out[i] = w5[i] * c * (1.0 + (cx5[i] * ux + cy5[i] * uy) / cs2);",
+     "out[i] = w5[i] * c * (1.0 - (cx5[i] * ux + cy5[i] * uy) / cs2);",
+     "test_p2_equilibrium_moments"),
+    ("Eq. 5: (k + 2) in place of (k + 1) in the series of I1",
+     "term *= y / ((double)k * (double)(k + 1));",
+     "term *= y / ((double)k * (double)(k + 2));",
+     "test_p6_onsager_full_form_matches_bessel_i1"),
+    ("Eq. 47: vartheta times cs2 in tau_g",
+     "c->tau_g = 0.5 + P->vartheta / cs2; /* Eq. 47 */",
+     "c->tau_g = 0.5 + P->vartheta * cs2; /* Eq. 47 */",
+     "test_p9_uniform_charge_gives_the_poisson_parabola"),
+    ("Eq. 50: tau_g dropped from E_x",
+     "*Ex = sx / (cs2 * tau_g);",
+     "*Ex = sx / cs2;",
+     "test_p9_field_is_minus_grad_psi_for_a_charge_wave"),
+    ("Eq. 55: cs2 dropped from the viscosity",
+     "const double eta_v = cs2 * (P->tau_f - 0.5);",
+     "const double eta_v = (P->tau_f - 0.5);",
+     "test_shear_wave_decays_at_the_viscosity_of_tau_f"),
+]
+
+
+def mutant(tmp_path, old, new):
+    """A separate instance of the oracle package built from the mutated source."""
+    with open(oracle.SRC) as f:
+        src = f.read()
+    assert src.count(old) == 1, f"mutation site not unique: {old!r}"
+    d = str(tmp_path)
+    with open(os.path.join(d, "ehd_oracle.c"), "w") as f:
+        f.write(src.replace(old, new))
+    shutil.copy(os.path.join(oracle.HERE, "ehd_oracle.h"), d)
+    spec = importlib.util.spec_from_file_location(f"oracle_mutant_{tmp_path.name}",
+                                                  os.path.join(oracle.HERE, "__init__.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.HERE, mod.SRC, mod.LIB = d, os.path.join(d, "ehd_oracle.c"), os.path.join(d, "libehd_oracle.so")
+    return mod
+
+
+@pytest.mark.parametrize("what,old,new,pin", MUTATIONS, ids=[m[3] + "/" + str(i) for i, m in enumerate(MUTATIONS)])
+def test_planted_mistake_fails_a_pin(what, old, new, pin, tmp_path, monkeypatch):
+    monkeypatch.setattr(pins, "O", mutant(tmp_path, old, new))
+    with pytest.raises(AssertionError):
+        getattr(pins, pin)()
+
+
+def test_the_unmutated_copy_passes_the_same_pins(tmp_path, monkeypatch):
+    # the machinery itself: a copy built the same way without a mistake passes
+    monkeypatch.setattr(pins, "O", mutant(tmp_path, "/* Eq. 52 */", "/* Eq. 52 */"))
+    for pin in sorted({m[3] for m in MUTATIONS}):
+        getattr(pins, pin)()

@@ -118,6 +118,15 @@ def test_p4_momentum_and_ion_sources_exact_for_any_rates():
         Fi = O.forcing_f(ux, uy, F[0], F[1], gr[0], gr[1])
         # the forcing term carries exactly the force in its first moment
         np.testing.assert_allclose([CX9 @ Fi, CY9 @ Fi], F, atol=1e-16)
+        # zeroth and second moments of Eq. 54 in closed form (isotropy of the
+        # weights): sum F_i = u.grad rho, sum c_a c_b F_i = cs2 [(u.grad rho)
+        # delta_ab + u_a d_b rho + u_b d_a rho]
+        ugr = ux * gr[0] + uy * gr[1]
+        cs2 = 1.0 / 3.0
+        assert abs(Fi.sum() - ugr) < 1e-17
+        np.testing.assert_allclose([CX9 * CX9 @ Fi, CY9 * CY9 @ Fi, CX9 * CY9 @ Fi],
+                                   [cs2 * (ugr + 2 * ux * gr[0]), cs2 * (ugr + 2 * uy * gr[1]),
+                                    cs2 * (ux * gr[1] + uy * gr[0])], atol=1e-17)
         out = O.mrt(rng.uniform(0.2, 1.9, 9), f, fe, Fi)
         np.testing.assert_allclose([CX9 @ out, CY9 @ out],
                                    [CX9 @ f + F[0], CY9 @ f + F[1]], atol=1e-15)
@@ -263,6 +272,29 @@ def test_p9_linear_potential_between_electrodes():
     np.testing.assert_allclose(f["psi"], np.tile(ref[:, None], (1, 4)), atol=1e-9)
     np.testing.assert_allclose(f["Ey"], 1.0 / ny, atol=1e-9)
     np.testing.assert_allclose(f["Ex"], 0.0, atol=1e-12)
+
+
+def test_p9_field_is_minus_grad_psi_for_a_charge_wave():
+    # q = cos(2 pi x / nx) between grounded electrodes: E from the populations
+    # (Eq. 50) against the central differences of the same psi (Eq. 49); both
+    # components nonzero, agreement to the second-order error of the lattice
+    nx, ny, kq = 64, 24, 1e-3
+    o = O.Oracle(nx, ny, dict(QUIET, freeze_E=0, Kq=kq, psi_anode=0.0, psi_cathode=0.0,
+                              sweeps_min=1, sweeps_max=4000000, sweep_tol=1e-15))
+    s = o.state()
+    wave = np.cos(2 * np.pi * np.arange(nx) / nx)[None, :, None]
+    s[:, :, 18:23] = W5 * (1.0 + 0.5 * wave)     # cations
+    s[:, :, 23:28] = W5 * (1.0 - 0.5 * wave)     # anions: q = cos(k x)
+    o.set_state(s)
+    o.step(1)
+    f = o.fields()
+    psi, Ex, Ey = f["psi"], f["Ex"], f["Ey"]
+    dx = -(np.roll(psi, -1, axis=1) - np.roll(psi, 1, axis=1)) / 2
+    dy = -(psi[2:, :] - psi[:-2, :]) / 2
+    inner = slice(2, ny - 2)
+    assert np.max(np.abs(Ex)) > 0.1 * np.max(np.abs(Ey)) > 0
+    assert np.max(np.abs(Ex[inner] - dx[inner])) < 2e-2 * np.max(np.abs(Ex))
+    assert np.max(np.abs(Ey[inner] - dy[1:-1][:ny - 4])) < 2e-2 * np.max(np.abs(Ey))
 
 
 def _parabola_error(ny, kq):
