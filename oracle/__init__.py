@@ -103,6 +103,9 @@ def lib():
         L.orc_feq.argtypes = [C.c_double] * 4 + [dp]
         L.orc_forcing_f.argtypes = [C.c_double] * 6 + [dp]
         L.orc_heq.argtypes = [C.c_double] * 3 + [dp]
+        L.orc_pressure.argtypes = [dp] + [C.c_double] * 5
+        L.orc_pressure.restype = C.c_double
+        L.orc_ion_src.argtypes = [C.c_int] + [C.c_double] * 4 + [C.c_int, dp]
         L.orc_Hsrc.argtypes = [C.c_double] * 7 + [dp]
         L.orc_ion_eq.argtypes = [C.c_double] * 3 + [dp]
         L.orc_ion_eq9.argtypes = [C.c_double] * 3 + [dp]
@@ -221,6 +224,15 @@ def feq(p, rho, ux, uy):
 
 def forcing_f(ux, uy, Fx, Fy, grx, gry):
     o = np.zeros(9); lib().orc_forcing_f(ux, uy, Fx, Fy, grx, gry, _dp(o)); return o
+
+
+def pressure(f, rho, ux, uy, grx, gry):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    return lib().orc_pressure(_dp(f), rho, ux, uy, grx, gry)
+
+
+def ion_src(R, c, Fx, Fy, L_term=1, q=5):
+    o = np.zeros(q); lib().orc_ion_src(q, R, c, Fx, Fy, L_term, _dp(o)); return o
 
 
 def heq(phi, ux, uy):

@@ -207,6 +207,27 @@ void orc_forcing_f(double ux, double uy, double Fx, double Fy, double grx,
     }
 }
 
+/* Eq. 57: the pressure from the populations f (f0 not used), rho, u and
+ * grad rho */
+double orc_pressure(const double *f, double rho, double ux, double uy, double grx, double gry)
+{
+    double s_ne0 = 0.0;
+    for (int i = 1; i < 9; ++i) s_ne0 += f[i];
+    return cs2 / (1.0 - w9[0]) * (s_ne0 + 0.5 * (ux * grx + uy * gry) + rho * r_u(0, ux, uy));
+}
+
+/* Eq. 39 and the reaction source of Eq. 34-35 on the Q-lattice (5 or 9):
+ * w_i R plus, with L_term, L_i = w_i (c_i . F) c / cs2 */
+void orc_ion_src(int Q, double R, double c, double Fx, double Fy, int L_term, double *out)
+{
+    const int *cxq = Q == 9 ? cx9 : cx5, *cyq = Q == 9 ? cy9 : cy5;
+    const double *wq = Q == 9 ? w9 : w5;
+    for (int i = 0; i < Q; ++i) {
+        double cF = cxq[i] * Fx + cyq[i] * Fy;
+        out[i] = wq[i] * R + (L_term ? wq[i] * cF * c / cs2 : 0.0);
+    }
+}
+
 /* Eq. 31 */
 void orc_heq(double phi, double ux, double uy, double *out)
 {
@@ -794,16 +815,14 @@ static int step_once(orc_ctx *c, int forced, int *used, double *resid)
         double Fy = mu_phi * gy + P->Kq * q * Ey - 0.5 * E2 * dey;
 
         /* O7: velocity and pressure, Eq. 56-57 */
-        double jx = 0.0, jy = 0.0, s_ne0 = 0.0;
+        double jx = 0.0, jy = 0.0;
         for (int i = 0; i < 9; ++i) {
             jx += cx9[i] * f[i];
             jy += cy9[i] * f[i];
-            if (i) s_ne0 += f[i];
         }
         double ux = (jx + 0.5 * Fx) / rho;
         double uy = (jy + 0.5 * Fy) / rho;
-        double pr = cs2 / (1.0 - w9[0]) *
-                    (s_ne0 + 0.5 * (ux * grx + uy * gry) + rho * r_u(0, ux, uy));
+        double pr = orc_pressure(f, rho, ux, uy, grx, gry);
 
         /* O8: f, Eq. 51 */
         double sf[9];
@@ -845,11 +864,10 @@ static int step_once(orc_ctx *c, int forced, int *used, double *resid)
         rates_ion(P, Q, 0.5 + Dm / cs2, sqn);
         double eqq[9], Gq[9], RL[9], dq[9], aq[9], bq[9], cq[9];
         ion_eq(Q, cp, ux, uy, eqq);
+        orc_ion_src(Q, R, cp, Fx, Fy, P->ion_L_term, RL);
         for (int i = 0; i < Q; ++i) {
             double cg = cxq[i] * gpsx + cyq[i] * gpsy;
-            double cF = cxq[i] * Fx + cyq[i] * Fy;
             Gq[i] = wq[i] * cg * mup * cp / cs2;
-            RL[i] = wq[i] * R + (P->ion_L_term ? wq[i] * cF * cp / cs2 : 0.0);
             dq[i] = pp[i] - eqq[i];
         }
         msm(Q, sqp, dq, aq);
@@ -858,11 +876,10 @@ static int step_once(orc_ctx *c, int forced, int *used, double *resid)
         for (int i = 0; i < Q; ++i)
             c->ps[Q * k + i] = pp[i] - aq[i] + bq[i] - cq[i];   /* Eq. 34 */
         ion_eq(Q, cm, ux, uy, eqq);
+        orc_ion_src(Q, R, cm, Fx, Fy, P->ion_L_term, RL);
         for (int i = 0; i < Q; ++i) {
             double cg = cxq[i] * gpsx + cyq[i] * gpsy;
-            double cF = cxq[i] * Fx + cyq[i] * Fy;
             Gq[i] = wq[i] * cg * mum * cm / cs2;
-            RL[i] = wq[i] * R + (P->ion_L_term ? wq[i] * cF * cm / cs2 : 0.0);
             dq[i] = np[i] - eqq[i];
         }
         msm(Q, sqn, dq, aq);

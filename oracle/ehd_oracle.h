@@ -117,6 +117,8 @@ void orc_matrices(double *M, double *Minv, double *N, double *Ninv);
 void orc_feq(double p, double rho, double ux, double uy, double *out9);
 void orc_forcing_f(double ux, double uy, double Fx, double Fy,
                    double grx, double gry, double *out9);
+double orc_pressure(const double *f9, double rho, double ux, double uy, double grx, double gry);
+void orc_ion_src(int Q, double R, double c, double Fx, double Fy, int L_term, double *outQ);
 void orc_heq(double phi, double ux, double uy, double *out9);
 void orc_Hsrc(double phi, double W, double dphiux, double dphiuy,
               double gx, double gy, double eps, double *out9);

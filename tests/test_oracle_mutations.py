@@ -1,8 +1,8 @@
 """Planted mistakes in a copy of the oracle (CPU only).
 
 Each case compiles a copy of the oracle's C source with one plausible
-mistake (a dropped term, a wrong sign, a transposed operand, a wrong weight
-or factor), loads it as a separate instance of the `oracle` package and runs
+mistake (a dropped term, a wrong sign, a transposed operand, a wrong weight,
+factor or boundary rule), loads it as a separate instance of the `oracle` package and runs
 one of the pins of test_oracle_pins.py against it: the pin must fail.  The
 oracle itself is not modified.
 """
@@ -53,11 +53,63 @@ MUTATIONS = [
      "*Ex = sx / (cs2 * tau_g);",
      "*Ex = sx / cs2;",
      "test_p9_field_is_minus_grad_psi_for_a_charge_wave"),
+    ("Eq. 14: sign of the x part of -1/2 |E|^2 grad eps",
+     "double Fx = mu_phi * gx + P->Kq * q * Ex - 0.5 * E2 * dex;",
+     "double Fx = mu_phi * gx + P->Kq * q * Ex + 0.5 * E2 * dex;",
+     "test_polarization_force_across_a_tangential_field"),
+    ("Eq. 39: cs2 dropped from the L source",
+     "out[i] = wq[i] * R + (L_term ? wq[i] * cF * c / cs2 : 0.0);",
+     "out[i] = wq[i] * R + (L_term ? wq[i] * cF * c : 0.0);",
+     "test_p15_ion_sources_carry_R_and_c_F"),
+    ("Eq. 57: the 1/2 u.grad rho term dropped",
+     "return cs2 / (1.0 - w9[0]) * (s_ne0 + 0.5 * (ux * grx + uy * gry) + rho * r_u(0, ux, uy));",
+     "return cs2 / (1.0 - w9[0]) * (s_ne0 + rho * r_u(0, ux, uy));",
+     "test_p14_pressure_of_eq57_round_trips_with_forcing"),
+    ("Eq. 56: the half force dropped from u",
+     "double ux = (jx + 0.5 * Fx) / rho;",
+     "double ux = (jx) / rho;",
+     "test_p12_static_droplet_obeys_laplace_law"),
+    ("Eq. 13: sign of the kappa laplacian in the chemical potential",
+     "double mu_phi = 4.0 * beta * phi * (phi - 1.0) * (phi - 0.5) - kappa * lap;",
+     "double mu_phi = 4.0 * beta * phi * (phi - 1.0) * (phi - 0.5) + kappa * lap;",
+     "test_p12_static_droplet_obeys_laplace_law"),
+    ("Eq. 43: sign of the recombination in R",
+     "*R = k_d * F - k_r * (*cp) * (*cm);",
+     "*R = k_d * F + k_r * (*cp) * (*cm);",
+     "test_p7_reaction_satisfies_eq41_with_eq5"),
+    ("Eq. 34: sign of the cation drift",
+     "c->ps[Q * k + i] = pp[i] - aq[i] + bq[i] - cq[i];   /* Eq. 34 */",
+     "c->ps[Q * k + i] = pp[i] - aq[i] + bq[i] + cq[i];   /* Eq. 34 */",
+     "test_ion_drift_moves_the_centroid_at_mobility_times_field"),
+    ("Eq. 64: a wall link returning the same population instead of the opposite",
+     "                    out[k * 9 + i] = post[k * 9 + opp9[i]];\n                else",
+     "                    out[k * 9 + i] = post[k * 9 + i];\n                else",
+     "test_p8_sum_phi_conserved_with_electrodes_and_walls"),
+    ("Eq. 64: sign of the anti-bounce-back at the electrodes",
+     "out[k * 5 + i] = mode == 0 ? -a + 2.0 * w5[i] * v : a;",
+     "out[k * 5 + i] = mode == 0 ? a + 2.0 * w5[i] * v : a;",
+     "test_p9_linear_potential_between_electrodes"),
+    ("Eq. 30: M_phi times cs2 in tau_h",
+     "double tau_h = 0.5 + P->M_phi / cs2; /* Eq. 30 */",
+     "double tau_h = 0.5 + P->M_phi * cs2; /* Eq. 30 */",
+     "test_p11_flat_interface_relaxes_to_tanh"),
+    ("Eq. 2: 2 in place of 4 in lambda",
+     "double lam = 4.0 * phi * (1.0 - phi) / W;",
+     "double lam = 2.0 * phi * (1.0 - phi) / W;",
+     "test_p11_flat_interface_relaxes_to_tanh"),
     ("Eq. 55: cs2 dropped from the viscosity",
      "const double eta_v = cs2 * (P->tau_f - 0.5);",
      "const double eta_v = (P->tau_f - 0.5);",
      "test_shear_wave_decays_at_the_viscosity_of_tau_f"),
 ]
+
+
+# arguments of the parametrised pins
+PIN_ARGS = {"test_p15_ion_sources_carry_R_and_c_F": dict(q=5)}
+
+
+def run_pin(pin):
+    getattr(pins, pin)(**PIN_ARGS.get(pin, {}))
 
 
 def mutant(tmp_path, old, new):
@@ -81,11 +133,11 @@ def mutant(tmp_path, old, new):
 def test_planted_mistake_fails_a_pin(what, old, new, pin, tmp_path, monkeypatch):
     monkeypatch.setattr(pins, "O", mutant(tmp_path, old, new))
     with pytest.raises(AssertionError):
-        getattr(pins, pin)()
+        run_pin(pin)
 
 
 def test_the_unmutated_copy_passes_the_same_pins(tmp_path, monkeypatch):
     # the machinery itself: a copy built the same way without a mistake passes
     monkeypatch.setattr(pins, "O", mutant(tmp_path, "/* Eq. 52 */", "/* Eq. 52 */"))
     for pin in sorted({m[3] for m in MUTATIONS}):
-        getattr(pins, pin)()
+        run_pin(pin)

@@ -144,6 +144,37 @@ def test_p4_momentum_and_ion_sources_exact_for_any_rates():
         assert abs(outh.sum() - phi) < 1e-15
 
 
+def test_p14_pressure_of_eq57_round_trips_with_forcing():
+    # f = f_eq(p, rho, u) - F_i / 2 are the populations whose Eq. 56 velocity
+    # is u; Eq. 57 must return p for any grad rho (its 1/2 u.grad rho term
+    # cancels the half forcing of the non-rest populations)
+    rng = np.random.default_rng(14)
+    for _ in range(25):
+        p, rho = rng.normal(scale=1e-3), rng.uniform(0.5, 2)
+        ux, uy = rng.normal(scale=1e-2, size=2)
+        Fx, Fy = rng.normal(scale=1e-3, size=2)
+        grx, gry = rng.normal(scale=1e-1, size=2)
+        f = O.feq(p, rho, ux, uy) - 0.5 * O.forcing_f(ux, uy, Fx, Fy, grx, gry)
+        np.testing.assert_allclose((np.array([CX9 @ f, CY9 @ f]) + 0.5 * np.array([Fx, Fy])) / rho,
+                                   [ux, uy], atol=1e-16)
+        assert abs(O.pressure(f, rho, ux, uy, grx, gry) - p) < 1e-16
+
+
+@pytest.mark.parametrize("q", [5, 9])
+def test_p15_ion_sources_carry_R_and_c_F(q):
+    # Eq. 39 and the reaction term: sum_i = R, sum_i c_i = c F (L term on),
+    # 0 (L term off), on D2Q5 and D2Q9
+    cx, cy = (CX9, CY9) if q == 9 else (CX9[:5], CY9[:5])
+    rng = np.random.default_rng(15)
+    for _ in range(25):
+        R, c = rng.normal(scale=1e-2), rng.uniform(0.1, 2)
+        Fx, Fy = rng.normal(scale=1e-3, size=2)
+        on, off = O.ion_src(R, c, Fx, Fy, 1, q), O.ion_src(R, c, Fx, Fy, 0, q)
+        assert abs(on.sum() - R) < 1e-17 and abs(off.sum() - R) < 1e-17
+        np.testing.assert_allclose([cx @ on, cy @ on], [c * Fx, c * Fy], atol=1e-18)
+        np.testing.assert_allclose([cx @ off, cy @ off], [0.0, 0.0], atol=1e-18)
+
+
 # ---- P5: isotropic stencils (Eq. 59 and the Laplacian) ---------------------
 
 def test_p5_stencil_exact_on_low_degree_polynomials():
@@ -475,6 +506,31 @@ def test_polarization_force_sets_the_pressure_jump():
     ref = 0.5 * D * D * (1 / eps_r - 1)
     assert abs(jump / ref - 1) < 0.03, (jump, ref)
     assert np.max(np.abs(f["uy"])) < 1e-6
+
+
+def test_polarization_force_across_a_tangential_field():
+    # the x part of -1/2 |E|^2 grad eps: a dielectric slab |x - xc| < R in a
+    # frozen field E0 along y (tangential to its faces) comes to rest with a
+    # pressure inside lower by E0^2 (eps_r - 1) / 2 (no surface tension, no
+    # charge force; tau_f = 2 damps the acoustic sloshing)
+    nx, ny, eps_r, E0, R = 64, 4, 4.0, 0.1, 16.0
+    xc = (nx - 1) / 2
+    o = O.Oracle(nx, ny, dict(QUIET, freeze_E=1, E_frozen_x=0.0, E_frozen_y=E0, sigma=0.0, tau_f=2.0,
+                              eps_r=eps_r, Kq=0.0, W=6.0))
+    s = o.state()
+    x = np.arange(nx)
+    phi = 0.5 * (1.0 + np.tanh(2.0 * (R - np.abs(x - xc)) / 6.0))
+    s[:, :, 9:18] = W9[None, None, :] * phi[None, :, None]     # h at rest: w_i phi
+    s[:, :, 0:9] = 0.0
+    s[:, :, 33:35] = 0.0
+    o.set_state(s)
+    o.step(4000)
+    f = o.fields()
+    pr = f["p"][ny // 2]
+    jump = pr[int(xc)] - 0.5 * (pr[4] + pr[nx - 5])
+    ref = -0.5 * E0 * E0 * (eps_r - 1.0)
+    assert abs(jump / ref - 1) < 0.03, (jump, ref)
+    assert np.max(np.abs(f["ux"])) < 1e-6
 
 
 # ---- Coulomb force (Eq. 14) in a 1D column with heterocharge layers ----------
