@@ -97,6 +97,50 @@ MUTATIONS = [
      "double lam = 4.0 * phi * (1.0 - phi) / W;",
      "double lam = 2.0 * phi * (1.0 - phi) / W;",
      "test_p11_flat_interface_relaxes_to_tanh"),
+    ("Eq. 49: psi without the 1/(1 - w0) of the non-rest sum",
+     "    return s / (1.0 - w5[0]);",
+     "    return s;",
+     "test_p9_linear_potential_between_electrodes"),
+    ("Eq. 44: the source not divided by eps",
+     "double rho_t = (P->Kq * c->q[k] - (dex * Ex + dey * Ey)) / eps;",
+     "double rho_t = (P->Kq * c->q[k] - (dex * Ex + dey * Ey));",
+     "test_polarization_force_sets_the_pressure_jump"),
+    ("Eq. 7: sign of the grad eps . E part of the source",
+     "double rho_t = (P->Kq * c->q[k] - (dex * Ex + dey * Ey)) / eps;",
+     "double rho_t = (P->Kq * c->q[k] + (dex * Ex + dey * Ey)) / eps;",
+     "test_polarization_force_sets_the_pressure_jump"),
+    ("Eq. 6: the linear Onsager form with b^2 for 2 b^2",
+     "if (form == 1) return 1.0 + 2.0 * b * b;",
+     "if (form == 1) return 1.0 + b * b;",
+     "test_p6_onsager_full_form_matches_bessel_i1"),
+    ("Eq. 52: the rest population with w0 instead of w0 - 1",
+     "double a = (i == 0) ? (w9[0] - 1.0) * p / cs2 : w9[i] * p / cs2;",
+     "double a = (i == 0) ? w9[0] * p / cs2 : w9[i] * p / cs2;",
+     "test_p2_equilibrium_moments"),
+    ("Eq. 45: the rest population with w0 instead of w0 - 1",
+     "out[i] = (i == 0) ? (w5[0] - 1.0) * psi : w5[i] * psi;",
+     "out[i] = (i == 0) ? w5[0] * psi : w5[i] * psi;",
+     "test_p2_equilibrium_moments"),
+    ("Eq. 38 on D2Q9: sign of the advective part",
+     "out[i] = w9[i] * c * (1.0 + (cx9[i] * ux + cy9[i] * uy) / cs2);",
+     "out[i] = w9[i] * c * (1.0 - (cx9[i] * ux + cy9[i] * uy) / cs2);",
+     "test_d2q9_ion_equilibrium_moments"),
+    ("Eq. 32: cs2 dropped from the interface source",
+     "out[i] = w9[i] * (cx9[i] * vx + cy9[i] * vy) / cs2;",
+     "out[i] = w9[i] * (cx9[i] * vx + cy9[i] * vy);",
+     "test_p11_flat_interface_relaxes_to_tanh"),
+    ("Eq. 31: cs2 dropped from the advective part of h_eq",
+     "out[i] = w9[i] * phi * (1.0 + (cx9[i] * ux + cy9[i] * uy) / cs2);",
+     "out[i] = w9[i] * phi * (1.0 + (cx9[i] * ux + cy9[i] * uy));",
+     "test_p2_equilibrium_moments"),
+    ("the Laplacian stencil without its factor 2",
+     "sl += 2.0 * w9[i] * (v - c0);",
+     "sl += w9[i] * (v - c0);",
+     "test_p5_stencil_exact_on_low_degree_polynomials"),
+    ("Eq. 64: the ghost row below the lattice mirrored from row 1",
+     "if (yn < 0) yn = 0;          /* mirror ghost row: zero normal */",
+     "if (yn < 0) yn = 1;          /* mirror ghost row: zero normal */",
+     "test_p5_stencil_periodic_x_and_mirror_rows"),
     ("Eq. 55: cs2 dropped from the viscosity",
      "const double eta_v = cs2 * (P->tau_f - 0.5);",
      "const double eta_v = (P->tau_f - 0.5);",
