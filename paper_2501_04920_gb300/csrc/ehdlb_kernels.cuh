@@ -778,7 +778,8 @@ template <typename T> __device__ __forceinline__ T fma_t(T a, T b, T c)
 // sweep parity, so a sweep needs one block barrier.  While a tile is swept,
 // the next one is copied to shared memory (cp.async), each thread copying
 // the cells it will read itself.  Collision, electrode links, FIRST and
-// RESID as in tb_body; the residual partials go to the tile's slot.  The
+// RESID as in tb_body (except that the coefficient planes hold halves of A,
+// Bx, By here); the residual partials go to the tile's slot.  The
 // region's left and right halos are HL = NSW rounded up to even nodes, so a
 // lane's two nodes sit at an even lattice column: for even nx they are one
 // aligned 8-byte pair in every plane, copied and stored as one.
@@ -812,21 +813,20 @@ template <typename T> struct TbrTile {
     int x0, y0;
 };
 
-// The tiles of one lattice, tiles_x per row, row by row (sweep launch m).
+// The tiles of one lattice, tiles_x per row, row by row; src / dst: the g
+// buffers the launch reads and writes.
 template <typename T> struct TbrLatticeTiles {
     const DevP<T> *P;
-    T *gA, *gB;
+    const T *src;
+    T *dst;
     const T *phig, *q;
     T *coef;
     double *part;
-    const Control *ctl;
-    int m, tiles_x, ntiles;
+    int tiles_x, ntiles;
     __device__ int count() const { return ntiles; }
     __device__ TbrTile<T> tile(int t, int TX, int TY) const
     {
-        const int par = (ctl->cur0 + m) & 1;
-        return TbrTile<T>{P, par ? gB : gA, par ? gA : gB, phig, q, coef, part, t, (t % tiles_x) * TX,
-                          (t / tiles_x) * TY};
+        return TbrTile<T>{P, src, dst, phig, q, coef, part, t, (t % tiles_x) * TX, (t / tiles_x) * TY};
     }
 };
 
@@ -1088,14 +1088,17 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
             issue(nxt);
         }
 
+        // halves of the coefficients (exact); the first launch stores them
+        // so that the later ones load halves
         T chA[R][2], chBx[R][2], chBy[R][2], psi_before[R][2];
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                chA[r][j] = T(0.5) * cA[r][j];
-                chBx[r][j] = T(0.5) * cBx[r][j];
-                chBy[r][j] = T(0.5) * cBy[r][j];
+                const T f = FIRST ? T(0.5) : T(1);
+                chA[r][j] = f * cA[r][j];
+                chBx[r][j] = f * cBx[r][j];
+                chBy[r][j] = f * cBy[r][j];
             }
         if (y0 - H <= 0 || y0 - H + RH >= ny)
             sweeps(std::true_type{}, gy0, g1, g2, g3, g4, chA, chBx, chBy, psi_before);
@@ -1125,9 +1128,9 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
             st2(cur.dst + 2 * nn, g3);
             st2(cur.dst + 3 * nn, g4);
             if (FIRST) {
-                st2(cur.coef, cA);
-                st2(cur.coef + nn, cBx);
-                st2(cur.coef + 2 * nn, cBy);
+                st2(cur.coef, chA);
+                st2(cur.coef + nn, chBx);
+                st2(cur.coef + 2 * nn, chBy);
             }
             if (RESID) {
 #pragma unroll
@@ -1153,7 +1156,8 @@ __global__ void __launch_bounds__(32 * NW, MINB)
                 const T *__restrict__ phig, const T *__restrict__ q, T *__restrict__ coef,
                 double *__restrict__ part, const Control *__restrict__ ctl, int m, int tiles_x, int ntiles)
 {
-    const TbrLatticeTiles<T> J{&P, gA, gB, phig, q, coef, part, ctl, m, tiles_x, ntiles};
+    const int par = (ctl->cur0 + m) & 1;
+    const TbrLatticeTiles<T> J{&P, par ? gB : gA, par ? gA : gB, phig, q, coef, part, tiles_x, ntiles};
     tbr_run<T, NSW, R, NW, FIRST, RESID>(J);
 }
 
