@@ -117,7 +117,10 @@ void orc_matrices(double *M, double *Minv, double *N, double *Ninv);
 void orc_feq(double p, double rho, double ux, double uy, double *out9);
 void orc_forcing_f(double ux, double uy, double Fx, double Fy,
                    double grx, double gry, double *out9);
+/* Eq. 57: pressure from the populations f9 (f0 unused), rho, u, grad rho. */
 double orc_pressure(const double *f9, double rho, double ux, double uy, double grx, double gry);
+/* Source of Eq. 34-35 on the Q-lattice (5 or 9): w_i R plus, with L_term,
+ * L_i = w_i (c_i . F) c / cs2 of Eq. 39. */
 void orc_ion_src(int Q, double R, double c, double Fx, double Fy, int L_term, double *outQ);
 void orc_heq(double phi, double ux, double uy, double *out9);
 void orc_Hsrc(double phi, double W, double dphiux, double dphiuy,
