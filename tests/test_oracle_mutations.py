@@ -141,6 +141,30 @@ MUTATIONS = [
      "if (yn < 0) yn = 0;          /* mirror ghost row: zero normal */",
      "if (yn < 0) yn = 1;          /* mirror ghost row: zero normal */",
      "test_p5_stencil_periodic_x_and_mirror_rows"),
+    ("Eq. 64 on D2Q9 ions: D2Q5 weights in the electrode anti-bounce-back",
+     "out[k * 9 + i] = mode == 0 ? -a + 2.0 * w9[i] * v : a;",
+     "out[k * 9 + i] = mode == 0 ? -a + 2.0 * w5[i % 5] * v : a;",
+     "test_uniform_ions_stay_uniform_at_zero_gradient_electrodes_and_side_walls"),
+    ("Eq. 64 on D2Q9 ions: sign of the electrode anti-bounce-back",
+     "out[k * 9 + i] = mode == 0 ? -a + 2.0 * w9[i] * v : a;",
+     "out[k * 9 + i] = mode == 0 ? a + 2.0 * w9[i] * v : a;",
+     "test_ions_decay_in_the_slowest_mode_between_absorbing_electrodes"),
+    ("Eq. 64 on D2Q9 ions: anti-bounce-back instead of bounce-back at a side wall",
+     "                } else if (walls && (sx < 0 || sx >= c->nx)) {\n                    out[k * 9 + i] = post[k * 9 + opp9[i]];",
+     "                } else if (walls && (sx < 0 || sx >= c->nx)) {\n                    out[k * 9 + i] = -post[k * 9 + opp9[i]];",
+     "test_uniform_ions_stay_uniform_at_zero_gradient_electrodes_and_side_walls"),
+    ("Eq. 64 on D2Q5: a side-wall link keeping its own direction",
+     "                if (walls && (sx < 0 || sx >= c->nx)) {\n                    out[k * 5 + i] = post[k * 5 + opp5[i]];",
+     "                if (walls && (sx < 0 || sx >= c->nx)) {\n                    out[k * 5 + i] = post[k * 5 + i];",
+     "test_side_walls_potential_equals_the_mirrored_periodic_lattice"),
+    ("Eq. 64: f and h periodic through the side walls",
+     "if (sy < 0 || sy >= c->ny || (walls && (sx < 0 || sx >= c->nx)))",
+     "if (sy < 0 || sy >= c->ny)",
+     "test_side_walls_and_electrode_walls_act_alike_on_the_fluid"),
+    ("Eq. 50: tau_g dropped from E_y",
+     "*Ey = sy / (cs2 * tau_g);",
+     "*Ey = sy / cs2;",
+     "test_p9_linear_potential_between_electrodes"),
     ("Eq. 55: cs2 dropped from the viscosity",
      "const double eta_v = cs2 * (P->tau_f - 0.5);",
      "const double eta_v = (P->tau_f - 0.5);",
@@ -149,7 +173,9 @@ MUTATIONS = [
 
 
 # arguments of the parametrised pins
-PIN_ARGS = {"test_p15_ion_sources_carry_R_and_c_F": dict(q=5)}
+PIN_ARGS = {"test_p15_ion_sources_carry_R_and_c_F": dict(q=5),
+            "test_ions_decay_in_the_slowest_mode_between_absorbing_electrodes": dict(q=9),
+            "test_uniform_ions_stay_uniform_at_zero_gradient_electrodes_and_side_walls": dict(q=9)}
 
 
 def run_pin(pin):

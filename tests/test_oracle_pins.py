@@ -678,6 +678,48 @@ def _ion_slices(q):
     return slice(18, 18 + q), slice(18 + q, 18 + 2 * q)
 
 
+def _ion_state(o, q, cp_y, cm_y):
+    # ions at rest in equilibrium, w_i c(y) for both species (p then n)
+    s = o.state()
+    w = W9 if q == 9 else W5
+    s[:, :, 18:18 + q] = w[None, None, :] * cp_y[:, None, None]
+    s[:, :, 18 + q:18 + 2 * q] = w[None, None, :] * cm_y[:, None, None]
+    return s
+
+
+@pytest.mark.parametrize("q", [5, 9])
+def test_ions_decay_in_the_slowest_mode_between_absorbing_electrodes(q):
+    # c = 0 at both half-way electrode walls (anti-bounce-back of Eq. 64):
+    # sin(pi (y + 1/2) / ny) decays as exp(-D (pi / ny)^2 t), on D2Q5 and D2Q9
+    nx, ny, steps, D = 4, 32, 4001, 0.01
+    o = O.Oracle(nx, ny, dict(QUIET, ion_bc=1, ion_lattice=q, D=D))
+    mode = np.sin(np.pi * (np.arange(ny) + 0.5) / ny)
+    o.set_state(_ion_state(o, q, mode, 0.5 * mode))
+    o.step(steps)
+    t = steps - 1                      # the snapshot precedes the last streaming
+    decay = np.exp(-D * (np.pi / ny) ** 2 * t)
+    f = o.fields()
+    np.testing.assert_allclose(f["cp"][:, 0] / mode, decay, rtol=3e-3)
+    np.testing.assert_allclose(f["cm"][:, 0] / (0.5 * mode), decay, rtol=3e-3)
+
+
+@pytest.mark.parametrize("q", [5, 9])
+def test_uniform_ions_stay_uniform_at_zero_gradient_electrodes_and_side_walls(q):
+    # Eq. 64: the attracted species takes the node's own value at its
+    # electrode (anions at the anode below, cations at the cathode above) and
+    # every species bounces back at the side walls; a uniform concentration
+    # at rest is then stationary there, on D2Q5 and D2Q9 (populations move one
+    # node per step, so after 5 streamings the repelled species' absorption at
+    # the other electrode has not reached the rows checked)
+    nx, ny, steps, c0 = 8, 24, 6, 0.7
+    o = O.Oracle(nx, ny, dict(QUIET, ion_bc=0, ion_lattice=q, side_walls=1))
+    o.set_state(_ion_state(o, q, np.full(ny, c0), np.full(ny, c0)))
+    o.step(steps)
+    f = o.fields()
+    np.testing.assert_allclose(f["cm"][:ny - 8], c0, rtol=1e-13)
+    np.testing.assert_allclose(f["cp"][8:], c0, rtol=1e-13)
+
+
 def test_d2q9_ion_equilibrium_moments():
     c, ux, uy = 1.3, 0.02, -0.01
     e = O.ion_eq(c, ux, uy, q=9)
