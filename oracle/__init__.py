@@ -120,6 +120,8 @@ def lib():
         L.orc_stencil_walls.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, dp]
         L.orc_params_from_physical.argtypes = [C.POINTER(OrcParams), C.c_int,
                                                C.c_int] + [C.c_double] * 4
+        L.orc_sample.argtypes = [C.c_int, C.c_int, dp, C.c_double, C.c_double]
+        L.orc_sample.restype = C.c_double
         L.orc_deformation.argtypes = [C.c_int, C.c_int, dp]
         L.orc_deformation.restype = C.c_double
         _lib = L
@@ -282,6 +284,12 @@ def stencil(chi: np.ndarray, side_walls: int = 0):
     else:
         lib().orc_stencil(nx, ny, _dp(chi), _dp(gx), _dp(gy), _dp(lap))
     return gx, gy, lap
+
+
+def sample(phi, x, y):
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    ny, nx = phi.shape
+    return lib().orc_sample(nx, ny, _dp(phi), x, y)
 
 
 def deformation(phi: np.ndarray) -> float:

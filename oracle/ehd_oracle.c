@@ -1030,7 +1030,7 @@ void orc_params_from_physical(orc_params *P, int nx, int ny, double d_mm,
  * L: extent of phi >= 1/2 along the field (y) through the phi-weighted
  * centroid, H: the same across it (x); crossings by linear interpolation
  * along the line, the line itself sampled by linear interpolation. */
-static double sample(int nx, int ny, const double *phi, double x, double y)
+double orc_sample(int nx, int ny, const double *phi, double x, double y)
 {
     int x0 = (int)floor(x), y0 = (int)floor(y);
     double fx = x - x0, fy = y - y0;
@@ -1053,13 +1053,13 @@ static double extent(int nx, int ny, const double *phi, double xc, double yc,
     for (int dir = 0; dir < 2; ++dir) {
         double sgn = dir ? 1.0 : -1.0;
         double prev_t = 0.0;
-        double prev_v = along_y ? sample(nx, ny, phi, xc, yc)
-                                : sample(nx, ny, phi, xc, yc);
+        double prev_v = along_y ? orc_sample(nx, ny, phi, xc, yc)
+                                : orc_sample(nx, ny, phi, xc, yc);
         double end = sgn * lim;
         for (int s = 1; s < lim; ++s) {
             double tt = sgn * s;
-            double v = along_y ? sample(nx, ny, phi, xc, yc + tt)
-                               : sample(nx, ny, phi, xc + tt, yc);
+            double v = along_y ? orc_sample(nx, ny, phi, xc, yc + tt)
+                               : orc_sample(nx, ny, phi, xc + tt, yc);
             if (prev_v >= 0.5 && v < 0.5) {
                 end = prev_t + (tt - prev_t) * (prev_v - 0.5) / (prev_v - v);
                 break;

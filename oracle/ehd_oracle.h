@@ -147,6 +147,9 @@ void orc_stencil_walls(int nx, int ny, int side_walls, const double *chi, double
 void orc_params_from_physical(orc_params *P, int nx, int ny, double d_mm,
                               double dpsi_kV, double eps_r, double mu_r);
 /* Deformation factor of Eq. 63 from a phi field [ny][nx]. */
+/* phi at (x, y) by bilinear interpolation of the nodes (x periodic, rows
+ * clamped at the walls), as Eq. 63's extents sample it. */
+double orc_sample(int nx, int ny, const double *phi, double x, double y);
 double orc_deformation(int nx, int ny, const double *phi);
 
 #ifdef __cplusplus

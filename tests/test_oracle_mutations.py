@@ -165,6 +165,30 @@ MUTATIONS = [
      "*Ey = sy / (cs2 * tau_g);",
      "*Ey = sy / cs2;",
      "test_p9_linear_potential_between_electrodes"),
+    ("Eq. 63: the y weights of the bilinear sampler swapped",
+     "    return a * (1 - fy) + b * fy;",
+     "    return a * fy + b * (1 - fy);",
+     "test_deformation_sampler_is_exact_for_bilinear_fields"),
+    ("Eq. 63: the wrong end of the crossing interval in the interpolation",
+     "end = prev_t + (tt - prev_t) * (prev_v - 0.5) / (prev_v - v);",
+     "end = prev_t + (tt - prev_t) * (0.5 - v) / (prev_v - v);",
+     "test_deformation_factor_of_ellipses"),
+    ("the MRT source factor (I - S) instead of (I - S/2)",
+     "for (int k = 0; k < Q; ++k) m[k] *= (1.0 - 0.5 * s[k]);",
+     "for (int k = 0; k < Q; ++k) m[k] *= (1.0 - s[k]);",
+     "test_p4_momentum_and_ion_sources_exact_for_any_rates"),
+    ("Eq. 43: the other root of the quadratic for B < 0",
+     "c = (-B + disc) / (2.0 * lam0);",
+     "c = (-B - disc) / (2.0 * lam0);",
+     "test_p7_reaction_satisfies_eq41_with_eq5"),
+    ("the sweep residual without its square root",
+     "r = sp > 0.0 ? sqrt(sd / sp) : sqrt(sd);",
+     "r = sp > 0.0 ? sd / sp : sqrt(sd);",
+     "test_p9_linear_potential_between_electrodes"),
+    ("Eq. 32: eps instead of eps^2 in the regularised normal",
+     "double den = sqrt(gx * gx + gy * gy + eps * eps);",
+     "double den = sqrt(gx * gx + gy * gy + eps);",
+     "test_regularised_normal_is_the_unit_normal_away_from_flat_regions"),
     ("Eq. 55: cs2 dropped from the viscosity",
      "const double eta_v = cs2 * (P->tau_f - 0.5);",
      "const double eta_v = (P->tau_f - 0.5);",

@@ -596,6 +596,19 @@ def test_step_is_well_conditioned_with_the_regularised_normal():
 
 # ---- deformation factor (Eq. 63) ------------------------------------------------
 
+def test_deformation_sampler_is_exact_for_bilinear_fields():
+    # the extents of Eq. 63 sample phi by bilinear interpolation: exact for
+    # a + b x + c y + d x y at any interior point (x, y not on the periodic seam)
+    ny, nx = 24, 32
+    yy, xx = np.mgrid[0:ny, 0:nx].astype(float)
+    rng = np.random.default_rng(63)
+    a, b, c, d = rng.normal(size=4)
+    phi = a + b * xx + c * yy + d * xx * yy
+    for _ in range(50):
+        x, y = rng.uniform(0, nx - 1), rng.uniform(0, ny - 1)
+        assert abs(O.sample(phi, x, y) - (a + b * x + c * y + d * x * y)) < 1e-12
+
+
 def test_deformation_factor_of_ellipses():
     n = 96
     y, x = np.mgrid[0:n, 0:n].astype(float)
