@@ -189,6 +189,30 @@ MUTATIONS = [
      "double den = sqrt(gx * gx + gy * gy + eps * eps);",
      "double den = sqrt(gx * gx + gy * gy + eps);",
      "test_regularised_normal_is_the_unit_normal_away_from_flat_regions"),
+    ("Sec. 2.2: cation diffusivity without the Einstein scaling",
+     "double Dp = P->einstein_D ? P->D * mup / P->mu_v : P->D;",
+     "double Dp = P->D;",
+     "test_ion_diffusivities_follow_the_mobilities_inside_the_drop_phase"),
+    ("Eq. 61: the mobility interpolated with 1 - phi",
+     "double mup = P->mu_v * (1.0 + (P->mu_r - 1.0) * phi);",
+     "double mup = P->mu_v * (1.0 + (P->mu_r - 1.0) * (1.0 - phi));",
+     "test_ion_diffusivities_follow_the_mobilities_inside_the_drop_phase"),
+    ("anion mobility without the ratio m",
+     "double mum = P->m * mup;",
+     "double mum = mup;",
+     "test_ion_drift_moves_the_centroid_at_mobility_times_field"),
+    ("Eq. 58: sign of the Euler derivative of phi u",
+     "double dpux = phi * ux - c->phiu_prev[2 * k];",
+     "double dpux = c->phiu_prev[2 * k] - phi * ux;",
+     "test_side_walls_and_electrode_walls_act_alike_on_the_fluid"),
+    ("Eq. 37: the ion relaxation time without 1/cs2",
+     "rates_ion(P, Q, 0.5 + Dp / cs2, sqp);",
+     "rates_ion(P, Q, 0.5 + Dp, sqp);",
+     "test_ion_drift_moves_the_centroid_at_mobility_times_field"),
+    ("Eq. 37: the first-moment ion rates set to 1",
+     "    s[1] = s[2] = 1.0 / tau;\n}\n\n/* One",
+     "    s[1] = s[2] = 1.0;\n}\n\n/* One",
+     "test_ions_decay_in_the_slowest_mode_between_absorbing_electrodes"),
     ("Eq. 55: cs2 dropped from the viscosity",
      "const double eta_v = cs2 * (P->tau_f - 0.5);",
      "const double eta_v = (P->tau_f - 0.5);",

@@ -716,6 +716,26 @@ def test_ions_decay_in_the_slowest_mode_between_absorbing_electrodes(q):
     np.testing.assert_allclose(f["cm"][:, 0] / (0.5 * mode), decay, rtol=3e-3)
 
 
+def test_ion_diffusivities_follow_the_mobilities_inside_the_drop_phase():
+    # einstein_D (Sec. 2.2): D+ = D mu+ / mu_v and D- = D m mu+ / mu_v with
+    # mu+ = mu_v (1 + (mu_r - 1) phi) (Eq. 61); in a uniform phi = 1 medium
+    # with mu_r = 2, m = 1.5 the slowest mode between absorbing electrodes
+    # decays at 2 D (pi/ny)^2 for cations and 3 D (pi/ny)^2 for anions
+    nx, ny, steps, D = 4, 32, 2001, 0.01
+    o = O.Oracle(nx, ny, dict(QUIET, ion_bc=1, D=D, mu_r=2.0, m=1.5, einstein_D=1))
+    mode = np.sin(np.pi * (np.arange(ny) + 0.5) / ny)
+    s = _ion_state(o, 5, mode, mode)
+    s[:, :, 9:18] = W9[None, None, :]            # h at rest with phi = 1
+    o.set_state(s)
+    o.step(steps)
+    t = steps - 1
+    f = o.fields()
+    np.testing.assert_allclose(f["phi"], 1.0, atol=1e-12)
+    for key, scale in (("cp", 2.0), ("cm", 3.0)):
+        decay = np.exp(-scale * D * (np.pi / ny) ** 2 * t)
+        np.testing.assert_allclose(f[key][:, 0] / mode, decay, rtol=3e-3)
+
+
 @pytest.mark.parametrize("q", [5, 9])
 def test_uniform_ions_stay_uniform_at_zero_gradient_electrodes_and_side_walls(q):
     # Eq. 64: the attracted species takes the node's own value at its
