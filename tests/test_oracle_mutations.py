@@ -213,6 +213,18 @@ MUTATIONS = [
      "    s[1] = s[2] = 1.0 / tau;\n}\n\n/* One",
      "    s[1] = s[2] = 1.0;\n}\n\n/* One",
      "test_ions_decay_in_the_slowest_mode_between_absorbing_electrodes"),
+    ("Eq. 61: the density interpolated with 1 - phi",
+     "        double rho = 1.0 + (P->rho_ratio - 1.0) * phi;\n",
+     "        double rho = 1.0 + (P->rho_ratio - 1.0) * (1.0 - phi);\n",
+     "test_shear_wave_inside_the_drop_phase_decays_at_eta_over_rho"),
+    ("Eq. 61: the viscosity interpolated with 1 - phi",
+     "double eta = eta_v * (1.0 + (P->eta_ratio - 1.0) * phi);",
+     "double eta = eta_v * (1.0 + (P->eta_ratio - 1.0) * (1.0 - phi));",
+     "test_shear_wave_inside_the_drop_phase_decays_at_eta_over_rho"),
+    ("Eq. 55: the local tau_f without rho",
+     "double tau_f = 0.5 + eta / (rho * cs2);",
+     "double tau_f = 0.5 + eta / cs2;",
+     "test_shear_wave_inside_the_drop_phase_decays_at_eta_over_rho"),
     ("Eq. 55: cs2 dropped from the viscosity",
      "const double eta_v = cs2 * (P->tau_f - 0.5);",
      "const double eta_v = (P->tau_f - 0.5);",

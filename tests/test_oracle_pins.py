@@ -483,6 +483,29 @@ def test_shear_wave_decays_at_the_viscosity_of_tau_f():
     assert abs(rate / (nu * k * k) - 1) < 0.01, (rate, nu * k * k)
 
 
+def test_shear_wave_inside_the_drop_phase_decays_at_eta_over_rho():
+    # phi = 1 everywhere with rho_r = 2, eta_r = 3 (Eq. 61): the local tau_f
+    # of Eq. 55 gives the kinematic viscosity eta_v eta_r / rho_r
+    ny, tau, rr, er = 32, 0.8, 2.0, 3.0
+    o = O.Oracle(4, ny, dict(QUIET, tau_f=tau, rho_ratio=rr, eta_ratio=er))
+    s = o.state()
+    y = np.arange(ny)
+    k = np.pi / ny
+    mode = np.cos(k * (y + 0.5 - ny / 2))
+    for j in range(ny):
+        s[j, :, 0:9] = O.feq(0.0, rr, 1e-3 * mode[j], 0.0)
+    s[:, :, 9:18] = W9                            # h at rest with phi = 1
+    o.set_state(s)
+    amp = []
+    for n in (100, 400):
+        o.step(n - o.t)
+        ux = o.fields()["ux"][:, 0]
+        amp.append(ux @ mode / (mode @ mode))
+    nu = CS2 * (tau - 0.5) * er / rr
+    rate = -np.log(amp[1] / amp[0]) / 300
+    assert abs(rate / (nu * k * k) - 1) < 0.01, (rate, nu * k * k)
+
+
 # ---- polarization force (Eq. 14) on a flat dielectric layer ---------------------
 
 @pytest.mark.slow
