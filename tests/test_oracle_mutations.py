@@ -225,6 +225,10 @@ MUTATIONS = [
      "double tau_f = 0.5 + eta / (rho * cs2);",
      "double tau_f = 0.5 + eta / cs2;",
      "test_shear_wave_inside_the_drop_phase_decays_at_eta_over_rho"),
+    ("Eq. 54: d rho / dy taken from d phi / dx",
+     "double grx = (P->rho_ratio - 1.0) * gx, gry = (P->rho_ratio - 1.0) * gy;",
+     "double grx = (P->rho_ratio - 1.0) * gx, gry = (P->rho_ratio - 1.0) * gx;",
+     "test_flat_interface_translates_with_a_uniform_flow_along_it"),
     ("Eq. 55: cs2 dropped from the viscosity",
      "const double eta_v = cs2 * (P->tau_f - 0.5);",
      "const double eta_v = (P->tau_f - 0.5);",

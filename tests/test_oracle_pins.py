@@ -506,6 +506,28 @@ def test_shear_wave_inside_the_drop_phase_decays_at_eta_over_rho():
     assert abs(rate / (nu * k * k) - 1) < 0.01, (rate, nu * k * k)
 
 
+def test_flat_interface_translates_with_a_uniform_flow_along_it():
+    # u = (U, 0), p = 0 and a flat layer phi(y) solve Eq. 10-11 exactly for any
+    # rho(phi): the u grad(rho) terms of Eq. 54 keep the lattice on it.  The
+    # no-slip electrodes slow the flow only within a few sqrt(nu t) of the
+    # walls, so the middle half of the channel is checked after 20 steps.
+    nx, ny, U, rr, W = 4, 64, 0.02, 2.0, 8.0
+    o = O.Oracle(nx, ny, dict(QUIET, tau_f=0.8, rho_ratio=rr, eta_ratio=3.0, W=W))
+    s = o.state()
+    y = np.arange(ny)
+    phi = 0.5 * (1.0 + np.tanh(2.0 * (y - (ny - 1) / 2) / W))
+    for j in range(ny):
+        s[j, :, 0:9] = O.feq(0.0, 1.0 + (rr - 1.0) * phi[j], U, 0.0)
+        s[j, :, 9:18] = O.heq(phi[j], U, 0.0)
+        s[j, :, 33] = phi[j] * U                  # (phi u) of the previous step
+        s[j, :, 34] = 0.0
+    s[:, :, 18:28] = 0.0
+    o.set_state(s)
+    o.step(20)
+    ux = o.fields()["ux"][ny // 4:3 * ny // 4]
+    assert np.max(np.abs(ux - U)) < 5e-3 * U
+
+
 # ---- polarization force (Eq. 14) on a flat dielectric layer ---------------------
 
 @pytest.mark.slow
