@@ -763,6 +763,19 @@ template <typename T> __device__ __forceinline__ T fma_t(T a, T b, T c)
     else return __fma_rn(a, b, c);
 }
 
+// (a0 + c, a1 + c), each rounded once; one packed instruction on FP32.
+template <typename T> __device__ __forceinline__ void add_pair(T &d0, T &d1, T a0, T a1, T c)
+{
+    if constexpr (sizeof(T) == 4) {
+        const float2 v = __fadd2_rn(make_float2(a0, a1), make_float2(c, c));
+        d0 = v.x;
+        d1 = v.y;
+    } else {
+        d0 = a0 + c;
+        d1 = a1 + c;
+    }
+}
+
 // ---- register-blocked fused sweeps ----------------------------------------------
 
 // The NSW fused sweeps of tb_body on 64 x 8R regions, computed in registers
@@ -939,6 +952,44 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
 #pragma unroll
         for (int s = 0; s < NSW; ++s, ++sw) {
             T o1[R][2], o3[R][2], p2[R][2], p4[R][2];
+            if constexpr (sizeof(T) == 4) {
+                // The same collision on the lane's node pair with packed FP32
+                // operations (each element rounded once, as by the scalar
+                // form).  The signs sit on exact operands: n1 = g3 - g1 and
+                // n2 = g4 - g2 are -m1 and -m2 bit for bit, so every product
+                // and sum below equals its scalar counterpart.
+                const float2 K1 = make_float2(k1, k1), NK1 = make_float2(-k1, -k1);
+                const float2 KF = make_float2(kf, kf), KE = make_float2(ke, ke);
+                const float2 N1 = make_float2(-1.f, -1.f);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float2 G1 = make_float2(g1[r][0], g1[r][1]), G2 = make_float2(g2[r][0], g2[r][1]);
+                    const float2 G3 = make_float2(g3[r][0], g3[r][1]), G4 = make_float2(g4[r][0], g4[r][1]);
+                    const float2 n1 = __ffma2_rn(G1, N1, G3), n2 = __ffma2_rn(G2, N1, G4);
+                    const float2 m3 = __fadd2_rn(G1, G3), m4 = __fadd2_rn(G2, G4);
+                    const float2 m34 = __fadd2_rn(m3, m4);
+                    if (RESID) {
+                        const float2 pb = __fmul2_rn(make_float2(1.5f, 1.5f), m34);
+                        psi_before[r][0] = pb.x;
+                        psi_before[r][1] = pb.y;
+                    }
+                    const float2 X6 = __ffma2_rn(make_float2(chBy[r][0], chBy[r][1]), n2,
+                                                 __ffma2_rn(make_float2(chBx[r][0], chBx[r][1]), n1,
+                                                            make_float2(chA[r][0], chA[r][1])));
+                    const float2 e = __ffma2_rn(KE, m34, X6);
+                    const float2 h3 = __ffma2_rn(KF, m3, e), h4 = __ffma2_rn(KF, m4, e);
+                    const float2 O1 = __ffma2_rn(NK1, n1, h3), O3 = __ffma2_rn(K1, n1, h3);
+                    const float2 P2 = __ffma2_rn(NK1, n2, h4), P4 = __ffma2_rn(K1, n2, h4);
+                    o1[r][0] = O1.x;
+                    o1[r][1] = O1.y;
+                    o3[r][0] = O3.x;
+                    o3[r][1] = O3.y;
+                    p2[r][0] = P2.x;
+                    p2[r][1] = P2.y;
+                    p4[r][0] = P4.x;
+                    p4[r][1] = P4.y;
+                }
+            } else {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
 #pragma unroll
@@ -956,6 +1007,7 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
                     p4[r][j] = fma_t(-k1, m2, h4);
                 }
             }
+            }
             const int b = sw & 1;
             *reinterpret_cast<V2 *>(&xup[b][w][lx0]) = V2{p2[R - 1][0], p2[R - 1][1]};
             *reinterpret_cast<V2 *>(&xdn[b][w][lx0]) = V2{p4[0][0], p4[0][1]};
@@ -965,24 +1017,19 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
                 g1[r][0] = __shfl_up_sync(0xffffffffu, o1[r][1], 1);
                 g3[r][0] = o3[r][1];
                 g3[r][1] = __shfl_down_sync(0xffffffffu, o3[r][0], 1);
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    if (r > 0) g2[r][j] = p2[r - 1][j] - wG;
-                    if (r < R - 1) g4[r][j] = p4[r + 1][j] + wG;
-                }
+                if (r > 0) add_pair(g2[r][0], g2[r][1], p2[r - 1][0], p2[r - 1][1], -wG);
+                if (r < R - 1) add_pair(g4[r][0], g4[r][1], p4[r + 1][0], p4[r + 1][1], wG);
             }
             __syncthreads();
             if (w > 0) {
                 const V2 v = *reinterpret_cast<const V2 *>(&xup[b][w - 1][lx0]);
-                g2[0][0] = v.x - wG;
-                g2[0][1] = v.y - wG;
+                add_pair(g2[0][0], g2[0][1], v.x, v.y, -wG);
             } else {
                 g2[0][0] = g2[0][1] = T(0);   // below the region
             }
             if (w < NW - 1) {
                 const V2 v = *reinterpret_cast<const V2 *>(&xdn[b][w + 1][lx0]);
-                g4[R - 1][0] = v.x + wG;
-                g4[R - 1][1] = v.y + wG;
+                add_pair(g4[R - 1][0], g4[R - 1][1], v.x, v.y, wG);
             } else {
                 g4[R - 1][0] = g4[R - 1][1] = T(0);   // above the region
             }
