@@ -403,6 +403,21 @@ def test_p11_flat_interface_relaxes_to_tanh():
     assert e2 < e1 / 3.0, (e1, e2)
 
 
+def test_flat_interface_at_rest_has_no_pressure_bump():
+    # With beta = 12 sigma / W and kappa = 3 sigma W / 2 (Eq. 13) the tanh
+    # profile of width W makes mu of Eq. 12 vanish, so across a flat interface
+    # at rest the pressure (Eq. 56-57) stays flat.  A mismatched pair leaves
+    # p = f(phi) - kappa phi'^2 / 2 inside the interface, (beta / 16 -
+    # 3 sigma / (4 W)) at phi = 1/2; the lattice's own residue is ~0.05 sigma / W.
+    ny, W, sigma = 64, 6.0, 0.01
+    o = O.Oracle(4, ny, dict(QUIET, sigma=sigma, W=W, init_shape=1, yc=(ny - 1) / 2, R=ny / 4, xc=1.5))
+    o.step(400)
+    f = o.fields()
+    p, phi = f["p"][:, 0], f["phi"][:, 0]
+    bulk = np.where(phi > 0.5, np.median(p[phi > 0.99]), np.median(p[phi < 0.01]))
+    assert np.max(np.abs(p - bulk)) < 0.1 * sigma / W
+
+
 # ---- P12: Laplace law (Eq. 12-13, 56-57) ---------------------------------------
 
 @pytest.mark.slow
