@@ -379,14 +379,32 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // + dphi; both are written (phi for the potential, dphi for the stencils of
 // the main kernel).  With init_ctl the first thread also opens the step in
 // the control block.
-// Body of k_prep for the block at (bx, by) of the lattice's grid.
-template <typename T, typename S, int QI = 5>
+// VN consecutive values from an address aligned to VN elements, as one load.
+template <int VN, typename V> struct alignas(sizeof(V) * VN) VecN { V v[VN]; };
+template <int VN, typename V> __device__ __forceinline__ void ld_n(const V *a, V (&o)[VN])
+{
+    const VecN<VN, V> u = *reinterpret_cast<const VecN<VN, V> *>(a);
+#pragma unroll
+    for (int j = 0; j < VN; ++j) o[j] = u.v[j];
+}
+template <int VN, typename V> __device__ __forceinline__ void st_n(V *a, const V (&o)[VN])
+{
+    VecN<VN, V> u;
+#pragma unroll
+    for (int j = 0; j < VN; ++j) u.v[j] = o[j];
+    *reinterpret_cast<VecN<VN, V> *>(a) = u;
+}
+
+// Body of k_prep for the block at (bx, by) of the lattice's grid: each
+// thread takes VN consecutive nodes of a row (VN > 1 needs nx % VN == 0, so
+// every plane offset is aligned to VN elements), each node computed alone.
+template <typename T, typename S, int QI = 5, int VN = 1>
 __device__ __forceinline__ void prep_body(const DevP<T> &P, const S *__restrict__ h, const S *__restrict__ p,
                                           const S *__restrict__ n, const PhiRef<T> &R, T *__restrict__ phig,
                                           T *__restrict__ q, Control *ctl, int fixedK, int kmin, int kmax,
                                           int flips, int bx, int by)
 {
-    const int x = bx * blockDim.x + threadIdx.x;
+    const int x = (bx * blockDim.x + threadIdx.x) * VN;
     const int y = by * blockDim.y + threadIdx.y;
     if (bx == 0 && by == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
         if (fixedK >= 0) {
@@ -398,39 +416,53 @@ __device__ __forceinline__ void prep_body(const DevP<T> &P, const S *__restrict_
     }
     if (x >= P.nx || y >= P.ny) return;
     const long long nn = P.nn, k = (long long)y * P.nx + x;
-    S hv[9], pv[QI], nv[QI];
+    S hv[9][VN], pv[QI][VN], nv[QI][VN];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) hv[i] = h[i * nn + k];
+    for (int i = 0; i < 9; ++i) ld_n<VN>(h + i * nn + k, hv[i]);
 #pragma unroll
-    for (int i = 0; i < QI; ++i) { pv[i] = p[i * nn + k]; nv[i] = n[i * nn + k]; }
-    // pairwise: rest, axis pairs, diagonal pairs
-    T d = raw<S, T>(hv[0]) + ((((raw<S, T>(hv[1]) + raw<S, T>(hv[3])) + (raw<S, T>(hv[2]) + raw<S, T>(hv[4])))) +
-                              ((raw<S, T>(hv[5]) + raw<S, T>(hv[7])) + (raw<S, T>(hv[6]) + raw<S, T>(hv[8]))));
-    T sp = T(0), sn = T(0);
-#pragma unroll
-    for (int i = 0; i < QI; ++i) { sp += raw<S, T>(pv[i]); sn += raw<S, T>(nv[i]); }
-    T qv = sp - sn;   // the rest concentrations of stored p and n cancel
-    if constexpr (!kSame<S, T>) { d *= P.isc_h; qv *= P.isc_c; }
-    const long long gk = (long long)(y + 1) * P.nx + x;
-    const T phi = R.phir[gk] + d;
-    phig[gk] = phi;
-    R.dphig[gk] = d;
-    if (y == 0) { phig[x] = phi; R.dphig[x] = d; }
-    if (y == P.ny - 1) {
-        phig[(long long)(P.ny + 1) * P.nx + x] = phi;
-        R.dphig[(long long)(P.ny + 1) * P.nx + x] = d;
+    for (int i = 0; i < QI; ++i) {
+        ld_n<VN>(p + i * nn + k, pv[i]);
+        ld_n<VN>(n + i * nn + k, nv[i]);
     }
-    q[k] = qv;
+    const long long gk = (long long)(y + 1) * P.nx + x;
+    T pr[VN], ph[VN], dd[VN], qq[VN];
+    ld_n<VN>(R.phir + gk, pr);
+#pragma unroll
+    for (int j = 0; j < VN; ++j) {
+        // pairwise: rest, axis pairs, diagonal pairs
+        T d = raw<S, T>(hv[0][j]) +
+              ((((raw<S, T>(hv[1][j]) + raw<S, T>(hv[3][j])) + (raw<S, T>(hv[2][j]) + raw<S, T>(hv[4][j])))) +
+               ((raw<S, T>(hv[5][j]) + raw<S, T>(hv[7][j])) + (raw<S, T>(hv[6][j]) + raw<S, T>(hv[8][j]))));
+        T sp = T(0), sn = T(0);
+#pragma unroll
+        for (int i = 0; i < QI; ++i) { sp += raw<S, T>(pv[i][j]); sn += raw<S, T>(nv[i][j]); }
+        T qv = sp - sn;   // the rest concentrations of stored p and n cancel
+        if constexpr (!kSame<S, T>) { d *= P.isc_h; qv *= P.isc_c; }
+        dd[j] = d;
+        ph[j] = pr[j] + d;
+        qq[j] = qv;
+    }
+    st_n<VN>(phig + gk, ph);
+    st_n<VN>(R.dphig + gk, dd);
+    if (y == 0) {
+        st_n<VN>(phig + x, ph);
+        st_n<VN>(R.dphig + x, dd);
+    }
+    if (y == P.ny - 1) {
+        st_n<VN>(phig + (long long)(P.ny + 1) * P.nx + x, ph);
+        st_n<VN>(R.dphig + (long long)(P.ny + 1) * P.nx + x, dd);
+    }
+    st_n<VN>(q + k, qq);
 }
 
-// Launch: blockDim (64, 4) over the lattice.
-template <typename T, typename S, int QI = 5>
+// Launch: blockDim (64, 4) over the lattice, VN nodes per thread along x.
+template <typename T, typename S, int QI = 5, int VN = 1>
 __global__ void __launch_bounds__(256) k_prep(const DevP<T> P, const S *__restrict__ h,
                                               const S *__restrict__ p, const S *__restrict__ n,
                                               const PhiRef<T> R, T *__restrict__ phig, T *__restrict__ q,
                                               Control *ctl, int fixedK, int kmin, int kmax, int flips)
 {
-    prep_body<T, S, QI>(P, h, p, n, R, phig, q, ctl, fixedK, kmin, kmax, flips, blockIdx.x, blockIdx.y);
+    prep_body<T, S, QI, VN>(P, h, p, n, R, phig, q, ctl, fixedK, kmin, kmax, flips, blockIdx.x, blockIdx.y);
 }
 
 // One pseudo-time sweep of the potential (Eq. 44-50) at every node: E and

@@ -500,12 +500,25 @@ template <typename T, typename S = T> class Solver : public SolverBase {
 
     void launch_prep(int par, int fixedK, int kmin, int kmax, int flips)
     {
-        if (qi_ == 9)
-            k_prep<T, S, 9><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n, ref_,
-                                                                phig_, q_, ctl_, fixedK, kmin, kmax, flips);
-        else
-            k_prep<T, S, 5><<<grid_, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n, ref_,
-                                                                phig_, q_, ctl_, fixedK, kmin, kmax, flips);
+        // four nodes per thread (one vector load per plane) when rows split
+        // into aligned fours
+        const bool v4 = nx_ % 4 == 0;
+        const dim3 g = v4 ? dim3((nx_ / 4 + BX - 1) / BX, grid_.y) : grid_;
+        if (qi_ == 9) {
+            if (v4)
+                k_prep<T, S, 9, 4><<<g, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n,
+                                                                   ref_, phig_, q_, ctl_, fixedK, kmin, kmax, flips);
+            else
+                k_prep<T, S, 9, 1><<<g, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n,
+                                                                   ref_, phig_, q_, ctl_, fixedK, kmin, kmax, flips);
+        } else {
+            if (v4)
+                k_prep<T, S, 5, 4><<<g, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n,
+                                                                   ref_, phig_, q_, ctl_, fixedK, kmin, kmax, flips);
+            else
+                k_prep<T, S, 5, 1><<<g, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n,
+                                                                   ref_, phig_, q_, ctl_, fixedK, kmin, kmax, flips);
+        }
         ++launches_;
     }
 
