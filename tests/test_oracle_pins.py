@@ -305,6 +305,27 @@ def test_p9_linear_potential_between_electrodes():
     np.testing.assert_allclose(f["Ex"], 0.0, atol=1e-12)
 
 
+def test_p9_initial_linear_potential_is_exact_at_t0_and_a_fixed_point():
+    # The initial potential of the 2048^2 case (no initial sweeps): g at the
+    # equilibrium of Eq. 45 for the linear psi between the electrodes plus the
+    # first-order non-equilibrium part.  With that part Eq. 49 must return
+    # psi_lin and Eq. 50 E = -grad psi_lin exactly at t = 0, before any sweep;
+    # with q = 0 and a uniform eps the linear profile is the steady state of
+    # Eq. 44 with the electrode anti-bounce-back, so sweeps must leave it
+    # unchanged.  A wrong sign or factor of the non-equilibrium part gives a
+    # wrong E at t = 0 and a state that the first sweep moves.
+    nx, ny, pa, pc = 6, 20, 1.7, -0.3
+    o = O.Oracle(nx, ny, dict(QUIET, freeze_E=0, eps_r=1.0, Kq=0.0, psi_anode=pa, psi_cathode=pc,
+                              init_psi_zero=0, init_sweeps_fixed=0, sweeps_min=1, sweeps_max=1))
+    lin = np.tile((pa + (pc - pa) * (np.arange(ny) + 0.5) / ny)[:, None], (1, nx))
+    for steps in (0, 1, 5):
+        o.step(steps)
+        f = o.fields()
+        np.testing.assert_allclose(f["psi"], lin, rtol=0, atol=1e-13)
+        np.testing.assert_allclose(f["Ey"], (pa - pc) / ny, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(f["Ex"], 0.0, rtol=0, atol=1e-14)
+
+
 def test_p9_field_is_minus_grad_psi_for_a_charge_wave():
     # q = cos(2 pi x / nx) between grounded electrodes: E from the populations
     # (Eq. 50) against the central differences of the same psi (Eq. 49); both
