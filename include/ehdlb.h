@@ -307,8 +307,10 @@ int ehdlb_set_tuning(ehdlb_ctx *c, int sweeps_per_launch, int tile_shape, int ma
  * call's contents (the call resets what must start at zero), so calls whose
  * work overlaps on the GPU -- on different streams, or from different host
  * threads -- race and must be serialised by the caller.  The first call on a
- * device looks up the array's device address (with that device current); make
- * that first call before any stream capture begins.
+ * device looks up the array's device address (with that device current), and
+ * so does the first call after the device's context was replaced (by
+ * cudaDeviceReset, for instance); make that first call before any stream
+ * capture begins.
  * Returns EHDLB_EINVAL for a lattice above the maximum, nx or ny < 4, NULL
  * arrays, p->size != sizeof(ehdlb_params) or invalid potential parameters;
  * EHDLB_ECUDA if a launch or copy fails. */

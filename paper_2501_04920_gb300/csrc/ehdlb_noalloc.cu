@@ -1,16 +1,18 @@
 // ehdlb_noalloc.cu -- ehdlb_potential_noalloc: the potential solve for callers
 // that must not allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured, inside an allocator or memory-pool callback, or in a host
+// Some callers cannot call cudaMalloc: code inside an allocator or
+// memory-pool callback (an allocation there re-enters the allocator), a host
 // process whose device memory is owned and budgeted by another runtime that
-// forbids foreign allocations.  For them this entry point runs the pseudo-time
-// sweeps of the potential equation with every intermediate (the swept
-// populations, phi with its ghost rows, psi of the previous sweep, the block
-// partial sums of the residual and the sweep parity) in one file-scope device
-// array of fixed size.  Every GPU that loads this library reserves that array
-// until the process exits.  The caller provides the inputs (phi, q) and the
-// outputs (psi, E) in its own device memory.
+// forbids foreign allocations, or a latency-critical loop that must not risk
+// the implicit device synchronisation of an allocation.  For them this entry
+// point runs the pseudo-time sweeps of the potential equation with every
+// intermediate (the swept populations, phi with its ghost rows, psi of the
+// previous sweep, the block partial sums of the residual and the sweep
+// parity) in one file-scope device array of fixed size.  Every GPU that loads
+// this library reserves that array until the process exits.  The caller
+// provides the inputs (phi, q) and the outputs (psi, E) in its own device
+// memory.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -41,13 +43,53 @@ static_assert(sizeof(Control) <= kCtlDoubles * sizeof(double), "control block do
 // obtains the device address with cudaGetSymbolAddress (see scratch_ptr).
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
-// Per-device cache of the scratch array's device address.
+// Cache of the scratch array's device address, one entry per device.  The
+// address belongs to the device's current context: a context created anew
+// (after cudaDeviceReset, say) loads the module again, possibly elsewhere, so
+// each entry also records the unique id of the context it was looked up in,
+// read through the driver's cuCtxGetCurrent and cuCtxGetId.  If those two
+// cannot be resolved, the entry is keyed by the device alone.
 constexpr int kMaxDevices = 64;
-double *g_scratch_addr[kMaxDevices] = {};
+struct ScratchEntry {
+    double *addr = nullptr;
+    unsigned long long ctx_id = 0;
+};
+ScratchEntry g_scratch[kMaxDevices];
 std::mutex g_scratch_mu;
 
-// Address of the scratch array on the current device; looked up once per
-// device (with that device current) on the first call made on it.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+// Unique id of the calling thread's current context; 0 if no context is
+// current.  *known is false if the driver functions could not be resolved.
+unsigned long long current_ctx_id(bool *known)
+{
+    static CtxGetCurrentFn get_cur = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool resolved = false;
+    if (!resolved) {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess) {
+            get_cur = reinterpret_cast<CtxGetCurrentFn>(a);
+            get_id = reinterpret_cast<CtxGetIdFn>(b);
+        }
+        resolved = true;
+    }
+    *known = get_cur && get_id;
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (!*known || get_cur(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Address of the scratch array on the current device.  The set-up step: the
+// first call on a device (and the first after its context was replaced)
+// looks it up with cudaGetSymbolAddress, with that device current; later
+// calls reuse it.
 cudaError_t scratch_ptr(double **out)
 {
     int dev = 0;
@@ -55,13 +97,17 @@ cudaError_t scratch_ptr(double **out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    bool known = false;
+    const unsigned long long id = current_ctx_id(&known);
+    ScratchEntry &ent = g_scratch[dev];
+    if (!ent.addr || (known && (id == 0 || ent.ctx_id != id))) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);   // creates the context if none was current
         if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<double *>(p);
+        ent.addr = static_cast<double *>(p);
+        ent.ctx_id = current_ctx_id(&known);
     }
-    *out = g_scratch_addr[dev];
+    *out = ent.addr;
     return cudaSuccess;
 }
 
