@@ -56,6 +56,31 @@ def test_batched_cases_equal_the_same_cases_alone(precision, shape):
     b.close()
 
 
+# Uneven cases of the physical mapping (Sec. 3; R = nx / 5), each against the
+# oracle run alone on the same parameters, at the FP32 parity tolerance.
+ORACLE_CASES = [(96, 128, 1.2, 2.5, 2.0, 0.5), (128, 96, 0.8, 1.5, 0.5, 2.0), (64, 112, 1.6, 3.5, 4.0, 1.0)]
+
+
+def test_batched_uneven_cases_match_the_oracle():
+    from test_gpu_parity import FP32_TOL, FP32_U_TOL, field_errors
+    steps = 40
+    b = ehdlb.Batch(1 << 30, SWEEPS)
+    ids = [b.add(nx, ny, case_params(nx, ny, *c)) for nx, ny, *c in ORACLE_CASES]
+    _, st = b.step(steps)
+    assert st.cases == len(ORACLE_CASES) and st.unstable_cases == 0
+    for cid, (nx, ny, *c) in zip(ids, ORACLE_CASES):
+        prm = oracle.params_from_physical(nx, ny, *c)
+        prm.update(sweeps_min=SWEEPS, sweeps_max=SWEEPS)
+        orc = oracle.Oracle(nx, ny, prm)
+        orc.step(steps)
+        err = field_errors(b.fields(cid), orc.fields())
+        bad = {k: v for k, v in err.items() if k in ("phi", "psi", "q", "cp", "cm") and not v <= FP32_TOL}
+        if not err["u"] <= FP32_U_TOL:
+            bad["u"] = err["u"]
+        assert not bad, (nx, ny, bad, err)
+    b.close()
+
+
 def test_cases_join_and_leave_without_disturbing_the_others():
     b = ehdlb.Batch(2 << 30, SWEEPS)
     (nx0, ny0, *c0), (nx1, ny1, *c1), (nx2, ny2, *c2) = CASES[:3]
