@@ -33,6 +33,7 @@
 // sweep would feed its slowest modes faster than the sweeps damp them.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -112,6 +113,7 @@ struct Control {
     double sum_phi, sum_q;
     int tpar;          // f, h, p, n buffer that holds the state (flipped by k_step_end;
                        // read by the batched kernels, the single-lattice host tracks its own)
+    int fault;         // a staged copy did not arrive in time (k_main_tma)
 };
 
 // Opens an ehdlb_step call: zeroes its per-call counters (launch: 1 thread).
@@ -599,7 +601,7 @@ __device__ __forceinline__ void tb_body(const DevP<T> &P, S *__restrict__ gA, S 
     constexpr int NB = RW / 32, NA = RH / BY;
     static_assert(RW % 32 == 0 && RH % BY == 0, "region must tile the block");
     static_assert(TX > 0 && TY > 0 && NA >= 1 && H <= TB_NSW_MAX, "tile too small for NSW");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     // planes g1 (+x), g3 (-x), g2 (+y), g4 (-y); then (FIRST) phi ring and q
     T *const s1 = reinterpret_cast<T *>(smem_raw);
     T *const s3 = s1 + P1, *const s2 = s1 + 2 * P1, *const s4 = s2 + P2;
@@ -886,7 +888,7 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
                   TY = RH - 2 * H;
     constexpr int FW = TBR_FW, PL = RH * RW;
     static_assert(TX > 0 && TY > 0 && H <= TB_NSW_MAX, "region too small for NSW");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T *const stg = reinterpret_cast<T *>(smem_raw);           // planes of the staged tile
     T *const sphi = stg + 5 * PL;                               // FIRST: phi with its ring
     __shared__ __align__(16) T xup[2][NW][RW];   // p2 of each warp's top row, for the warp above
@@ -1313,7 +1315,7 @@ __global__ void __cluster_dims__(CX, CY, 1) __launch_bounds__(32 * BY, 3)
     constexpr int PW = RW + 2, PH = RH + 2, PL = PW * PH;
     constexpr int NB = RW / 32, NA = RH / BY;
     static_assert(RH % BY == 0 && TX > 0 && TY > 0, "cluster too small for NSW");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sg = reinterpret_cast<T *>(smem_raw);   // [2][4][PH][PW]
     const int par = (ctl->cur0 + m) & 1;
     const T *__restrict__ src = par ? gB : gA;
@@ -1522,6 +1524,45 @@ static __global__ void __launch_bounds__(256) k_sweep_decide(const double *__res
 // 2048^2: staging them costs FP32 0.031 ms per step and saves FP16
 // storage 0.008 ms).
 template <int QI> __host__ __device__ constexpr int main_splanes() { return 17 + 2 * QI + 2; }
+
+// ---- the step kernel's inputs staged by the tensor memory accelerator -----
+// One stage holds a 64 x 4 tile's inputs, each part at a 128-byte boundary:
+// the 27 population planes (f, h, p, n) and the 2 planes of (phi u)(t-1) as
+// S (one run, as the cp.async staging lays them out), then as T the 4 g
+// planes, mu_ref, grad phi_ref (x, y) and psi_prev, then dphi and phi_ref over
+// the tile's rows -1 .. 4 and columns -4 .. 67 (a box of 72 x 6 starting at a
+// 16-byte boundary; the columns outside the lattice read zero and the
+// periodic neighbours of the first and last column come from global memory).
+constexpr int TMA_HW = 72, TMA_HH = 6, TMA_HX = 4;
+__host__ __device__ constexpr size_t tma_align(size_t b) { return (b + 127) & ~(size_t)127; }
+template <typename T, typename S> struct TmaLayout {
+    static constexpr size_t pops = 0;                                     // 27 + 2 planes of S
+    static constexpr size_t tpl = tma_align(sizeof(S) * 29 * 256);       // g1..g4, mu_ref, gxr, gyr, psi_prev
+    static constexpr size_t dphi = tma_align(tpl + sizeof(T) * 8 * 256);
+    static constexpr size_t phir = tma_align(dphi + sizeof(T) * TMA_HW * TMA_HH);
+    static constexpr size_t stage = tma_align(phir + sizeof(T) * TMA_HW * TMA_HH);
+    // bytes the loads of one stage deliver (psi_prev only with the residual)
+    __host__ __device__ static constexpr unsigned tx(bool resid)
+    {
+        return (unsigned)(sizeof(S) * 29 * 256 + sizeof(T) * (resid ? 8 : 7) * 256 +
+                          2 * sizeof(T) * TMA_HW * TMA_HH);
+    }
+};
+// Pointers into the stage of the tile being computed.
+template <typename T, typename S> struct TmaView {
+    const S *pops;    // [29][256]
+    const T *tpl;     // [8][256]: g1..g4, mu_ref, gxr, gyr, psi_prev
+    const T *dphi;    // [6][72]
+    const T *phir;    // [6][72]
+};
+// Tensor maps of the step kernel's inputs (cuTensorMapEncodeTiled on the host).
+struct MainMaps {
+    CUtensorMap pops;     // 3D (nx, ny, 27), box (64, 4, 27): the source time level
+    CUtensorMap phiu;     // 3D (nx, ny, 2), box (64, 4, 2)
+    CUtensorMap g[2];     // 3D (nx, ny, 4), box (64, 4, 4): the two g buffers
+    CUtensorMap mur, gxr, gyr, psi;   // 2D (nx, ny), box (64, 4)
+    CUtensorMap dphi, phir;           // 2D (nx, ny + 2) with ghost rows, box (72, 6)
+};
 // Blocks of 256 per SM the step kernel's registers are sized for: 4 in float
 // (64 registers; measured 9 % faster at 2048^2 than 3 blocks at 80 registers,
 // though a few bytes spill), 3 in double.
@@ -1590,37 +1631,49 @@ __device__ __forceinline__ void stage_planes(E *st, PlaneF plane, int nx, int ny
 // Launch: blockDim (64, 4), dynamic shared memory main_smem_bytes<T, S>().
 // Body of k_main for the block at (bx, by) of the lattice's grid; slot: its
 // partials.
-template <typename T, typename S, bool SNAP, bool FROZEN, bool RESID, bool VEC, int QI = 5>
+//   TMA   : the inputs were staged by the caller (k_main_tma) into tv.
+template <typename T, typename S, bool SNAP, bool FROZEN, bool RESID, bool VEC, int QI = 5, bool TMA = false>
 __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, const Pops<S> &dst,
                                           const T *__restrict__ gA, const T *__restrict__ gB,
                                           const Control *__restrict__ ctl, const PhiRef<T> &Rf,
                                           S *__restrict__ phiu, const T *__restrict__ psi_prev, T *__restrict__ snap,
                                           double *__restrict__ part, int *__restrict__ unstable, int bx, int by,
-                                          long long slot)
+                                          long long slot, const TmaView<T, S> *tv = nullptr)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    S *st = reinterpret_cast<S *>(smem_raw);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int NSP = main_splanes<QI>(), NPOP = 17 + 2 * QI;
-    T *stg = reinterpret_cast<T *>(smem_raw + sizeof(S) * NSP * 256);
+    static_assert(!TMA || QI == 5, "the staged step kernel takes ions on D2Q5");
+    const S *st;
+    const T *stg;
+    if constexpr (TMA) {
+        st = tv->pops;
+        stg = tv->tpl;
+    } else {
+        st = reinterpret_cast<S *>(smem_raw);
+        stg = reinterpret_cast<T *>(smem_raw + sizeof(S) * NSP * 256);
+    }
+    // the legacy staging writes these buffers
+    S *st_w = reinterpret_cast<S *>(smem_raw);
+    T *stg_w = reinterpret_cast<T *>(smem_raw + sizeof(S) * NSP * 256);
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int x = bx * blockDim.x + threadIdx.x;
     const int y = by * blockDim.y + threadIdx.y;
     const bool inside = x < P.nx && y < P.ny;
     const long long nn = P.nn, k = (long long)y * P.nx + x;
     T red[4] = {T(0), T(0), T(0), T(0)};
-    {
+    if constexpr (!TMA) {
         const T *__restrict__ g = ((ctl->cur0 + ctl->flips) & 1) ? gB : gA;
         const S *pops = src.f, *pu = phiu;
         const int x0 = bx * blockDim.x, y0 = by * blockDim.y;
         stage_planes<S, NSP, VEC>(
-            st, [=](int i) { return i < NPOP ? pops + i * nn : pu + (i - NPOP) * nn; }, P.nx, P.ny, x0, y0, tid, inside,
-            k);
+            st_w, [=](int i) { return i < NPOP ? pops + i * nn : pu + (i - NPOP) * nn; }, P.nx, P.ny, x0, y0, tid,
+            inside, k);
         const T *mur = Rf.mur;
-        stage_planes<T, MAIN_TPLANES<T, S>, VEC>(stg, [=](int i) { return i < 4 ? g + i * nn : mur; }, P.nx, P.ny,
-                                                 x0, y0, tid, inside, k);
+        stage_planes<T, MAIN_TPLANES<T, S>, VEC>(stg_w, [=](int i) { return i < 4 ? g + i * nn : mur; }, P.nx,
+                                                 P.ny, x0, y0, tid, inside, k);
         // phi_ref of rows y0 - 1 .. y0 + 4 (phir holds the rows -1 .. ny),
         // columns x0 - 1 .. x0 + 64 (periodic); rows above ny are never read
-        T *ring = stg + MAIN_TPLANES<T, S> * 256;
+        T *ring = stg_w + MAIN_TPLANES<T, S> * 256;
         for (int e = tid; MAIN_STAGE_REF<T, S> && e < MAIN_RING; e += 256) {
             const int ry = e / MAIN_RING_W, rx = e - ry * MAIN_RING_W;
             const int gy = y0 - 1 + ry;
@@ -1629,7 +1682,7 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
             if (gy <= P.ny) cp_async(ring + e, Rf.phir + (long long)(gy + 1) * P.nx + gx);
         }
     }
-    const T pprev = (RESID && inside) ? psi_prev[k] : T(0);
+    const T pprev = (RESID && inside) ? (TMA ? stg[7 * 256 + tid] : psi_prev[k]) : T(0);
     const int nx = P.nx, ny = P.ny;
     const T third = T(1.0 / 3.0);
     // ---- O1-O2: phi, properties (Eq. 61), stencils (Eq. 59) ----
@@ -1644,17 +1697,40 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
         const T *r1 = Rf.dphig + nx + ki, *r0 = r1 - nx, *r2 = r1 + nx;
         xm -= x;   // column offsets from here on
         xp -= x;
-        dphi = r1[0];
-        const T dE = r1[xp] - dphi, dW = r1[xm] - dphi, dN = r2[0] - dphi, dS = r0[0] - dphi;
-        const T dNE = r2[xp] - dphi, dNW = r2[xm] - dphi, dSW = r0[xm] - dphi, dSE = r0[xp] - dphi;
-        phir = Rf.phir[nx + ki];
+        T vc, vE, vW, vN, vS, vNE, vNW, vSW, vSE, gxr, gyr;
+        if constexpr (TMA) {
+            // the staged box; the periodic neighbours of the first and last
+            // column from global memory
+            const T *h1 = tv->dphi + (threadIdx.y + 1) * TMA_HW + threadIdx.x + TMA_HX;
+            vc = h1[0]; vN = h1[TMA_HW]; vS = h1[-TMA_HW];
+            if (x == 0 || x == nx - 1) {
+                vE = r1[xp]; vW = r1[xm]; vNE = r2[xp]; vNW = r2[xm]; vSW = r0[xm]; vSE = r0[xp];
+            } else {
+                vE = h1[1]; vW = h1[-1]; vNE = h1[TMA_HW + 1]; vNW = h1[TMA_HW - 1];
+                vSW = h1[-TMA_HW - 1]; vSE = h1[-TMA_HW + 1];
+            }
+            phir = tv->phir[(threadIdx.y + 1) * TMA_HW + threadIdx.x + TMA_HX];
+            gxr = stg[5 * 256 + tid];
+            gyr = stg[6 * 256 + tid];
+        } else {
+            vc = r1[0]; vE = r1[xp]; vW = r1[xm]; vN = r2[0]; vS = r0[0];
+            vNE = r2[xp]; vNW = r2[xm]; vSW = r0[xm]; vSE = r0[xp];
+            phir = Rf.phir[nx + ki];
+            gxr = Rf.gxr[ki];
+            gyr = Rf.gyr[ki];
+        }
+        dphi = vc;
+        const T dE = vE - dphi, dW = vW - dphi, dN = vN - dphi, dS = vS - dphi;
+        const T dNE = vNE - dphi, dNW = vNW - dphi, dSW = vSW - dphi, dSE = vSE - dphi;
         phi = phir + dphi;
-        gx = Rf.gxr[ki] + ((dE - dW) * third + ((dNE - dNW) + (dSE - dSW)) * T(1.0 / 12.0));
-        gy = Rf.gyr[ki] + ((dN - dS) * third + ((dNE + dNW) - (dSE + dSW)) * T(1.0 / 12.0));
+        gx = gxr + ((dE - dW) * third + ((dNE - dNW) + (dSE - dSW)) * T(1.0 / 12.0));
+        gy = gyr + ((dN - dS) * third + ((dNE + dNW) - (dSE + dSW)) * T(1.0 / 12.0));
         lapd = T(2.0 / 3.0) * ((dE + dW) + (dN + dS)) + T(1.0 / 6.0) * ((dNE + dSW) + (dNW + dSE));
     }
-    cp_async_wait_all();
-    if constexpr (VEC || MAIN_STAGE_REF<T, S>) __syncthreads();   // copies of all threads
+    if constexpr (!TMA) {
+        cp_async_wait_all();
+        if constexpr (VEC || MAIN_STAGE_REF<T, S>) __syncthreads();   // copies of all threads
+    }
     if (inside) {
         SRng rng(k, kSame<S, T> ? 0 : ctl->t, 0x1b873593u);
         // in-plane offsets of the push targets: rows below / at / above, the
@@ -1732,7 +1808,7 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
         // ---- O6: forces (Eq. 12-14) ----
         // mu_phi - mu_ref: the cubic of Eq. 13 as (phi - phi_ref) times
         // (phi^2 + phi phi_ref + phi_ref^2 - 1.5 (phi + phi_ref) + 0.5)
-        const T mu_phi = (MAIN_STAGE_REF<T, S> ? stg[4 * 256 + tid] : Rf.mur[rowC]) +
+        const T mu_phi = ((MAIN_STAGE_REF<T, S> || TMA) ? stg[4 * 256 + tid] : Rf.mur[rowC]) +
                          T(4) * P.beta * dphi * ((phi * phi + phi * phir + phir * phir) - T(1.5) * (phi + phir) + T(0.5)) -
                          P.kappa * lapd;
         const T E2 = Ex * Ex + Ey * Ey;
@@ -1845,6 +1921,15 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
             const T *qr = MAIN_STAGE_REF<T, S>
                               ? stg + MAIN_TPLANES<T, S> * 256 + (threadIdx.y + 1) * MAIN_RING_W + threadIdx.x + 1
                               : Rf.phir + nx;   // phi_ref without its ghost row
+            // phi_ref of the push target in direction i (in-plane offset o)
+            auto qphi = [&](int i, int o) -> T {
+                if constexpr (TMA) {
+                    if ((x == 0 && cx9(i) < 0) || (x == nx - 1 && cx9(i) > 0)) return Rf.phir[nx + o];
+                    return tv->phir[(threadIdx.y + 1 + cy9(i)) * TMA_HW + threadIdx.x + TMA_HX + cx9(i)];
+                } else {
+                    return qr[MAIN_STAGE_REF<T, S> ? cy9(i) * MAIN_RING_W + cx9(i) : o];
+                }
+            };
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const T v = hv[i] - dl[i];
@@ -1852,9 +1937,7 @@ __device__ __forceinline__ void main_body(const DevP<T> &P, const Pops<S> &src, 
                     sts_sr(dst.h + opp9(i) * nn + rowC, v, P.sc_h, rng);
                 } else {
                     const int o = dest(cx9(i), cy9(i));
-                    const T shift =
-                        i == 0 ? T(0)
-                               : w9<T>(i) * (phir - qr[MAIN_STAGE_REF<T, S> ? cy9(i) * MAIN_RING_W + cx9(i) : o]);
+                    const T shift = i == 0 ? T(0) : w9<T>(i) * (phir - qphi(i, o));
                     sts_sr(dst.h + i * nn + o, v + shift, P.sc_h, rng);
                 }
             }
@@ -2039,6 +2122,131 @@ __global__ void __launch_bounds__(256, MAIN_MINB<T>) k_main(const DevP<T> P, con
 {
     main_body<T, S, SNAP, FROZEN, RESID, VEC, QI>(P, src, dst, gA, gB, ctl, Rf, phiu, psi_prev, snap, part, unstable,
                                               blockIdx.x, blockIdx.y, blockIdx.x + (long long)blockIdx.y * gridDim.x);
+}
+
+// ---- tensor memory accelerator and mbarrier (inline PTX) --------------------------
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the phase of the given parity, at most about 70 ms (2^20 tries,
+// spaced by 64 ns after the first 64); false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
+{
+    for (unsigned i = 0; i < (1u << 20); ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i >= 64) __nanosleep(64);
+    }
+    return false;
+}
+// Orders this thread's earlier generic-proxy accesses of shared memory before
+// its later asynchronous-proxy ones (a stage is refilled after it was read).
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+        "[%2];\n" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+// The step kernel on inputs staged by the tensor memory accelerator:
+// persistent blocks of 64 x 4 threads walk the 64 x 4 tiles of the lattice;
+// thread 0 loads the next tile's inputs (MainMaps: one box of the 27
+// population planes, one of (phi u)(t-1), one of the g buffer the sweeps
+// left, mu_ref, grad phi_ref, psi_prev with the residual, and the 72 x 6 boxes
+// of dphi and phi_ref) into the other of two stages while the block computes
+// the current tile with main_body.  Needs D2Q5 ions, periodic x and rows of
+// 16-byte multiples.  A stage that does not arrive within about 70 ms sets
+// *fault, the block waits (bounded) for its copies and returns.
+// Launch: blockDim (64, 4), grid min(tiles, resident blocks), dynamic shared
+// memory 2 TmaLayout<T, S>::stage.
+template <typename T, typename S, bool SNAP, bool FROZEN, bool RESID>
+__global__ void __launch_bounds__(256, sizeof(S) == 4 ? 2 : 3)
+    k_main_tma(const __grid_constant__ DevP<T> P, const __grid_constant__ MainMaps M, const Pops<S> src,
+               const Pops<S> dst, const T *__restrict__ gA, const T *__restrict__ gB,
+               const Control *__restrict__ ctl, const PhiRef<T> Rf, S *__restrict__ phiu,
+               const T *__restrict__ psi_prev, T *__restrict__ snap, double *__restrict__ part,
+               int *__restrict__ unstable, int *__restrict__ fault, int tiles_x, int ntiles)
+{
+    using L = TmaLayout<T, S>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int tid = threadIdx.x + threadIdx.y * 64;
+    const int gsel = (ctl->cur0 + ctl->flips) & 1;
+    // the copies need 128-byte aligned destinations (block-uniform check)
+    if (smem_u32(smem_raw) & 127u) {
+        if (tid == 0) atomicExch(fault, 2);
+        return;
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t, int sidx) {
+        unsigned char *base = smem_raw + (size_t)sidx * L::stage;
+        const int x0 = (t % tiles_x) * 64, y0 = (t / tiles_x) * 4;
+        mbar_expect_tx(&bar[sidx], L::tx(RESID));
+        tma_load_3d(base + L::pops, &M.pops, &bar[sidx], x0, y0, 0);
+        tma_load_3d(base + L::pops + sizeof(S) * 27 * 256, &M.phiu, &bar[sidx], x0, y0, 0);
+        tma_load_3d(base + L::tpl, gsel ? &M.g[1] : &M.g[0], &bar[sidx], x0, y0, 0);
+        tma_load_2d(base + L::tpl + sizeof(T) * 4 * 256, &M.mur, &bar[sidx], x0, y0);
+        tma_load_2d(base + L::tpl + sizeof(T) * 5 * 256, &M.gxr, &bar[sidx], x0, y0);
+        tma_load_2d(base + L::tpl + sizeof(T) * 6 * 256, &M.gyr, &bar[sidx], x0, y0);
+        if (RESID) tma_load_2d(base + L::tpl + sizeof(T) * 7 * 256, &M.psi, &bar[sidx], x0, y0);
+        // rows y0 - 1 .. y0 + 4 are rows y0 .. y0 + 5 of the ghost-row arrays
+        tma_load_2d(base + L::dphi, &M.dphi, &bar[sidx], x0 - TMA_HX, y0);
+        tma_load_2d(base + L::phir, &M.phir, &bar[sidx], x0 - TMA_HX, y0);
+    };
+    if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    int k = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+        const int sidx = k & 1;
+        const bool late = !mbar_wait_bounded(&bar[sidx], (k >> 1) & 1);
+        if (__syncthreads_or(late)) {   // every thread of the block leaves together
+            if (tid == 0) atomicExch(fault, 1);
+            mbar_wait_bounded(&bar[sidx], (k >> 1) & 1);   // the copies in flight
+            return;
+        }
+        if (tid == 0 && t + (int)gridDim.x < ntiles) {
+            fence_proxy_async();
+            issue(t + gridDim.x, sidx ^ 1);
+        }
+        const unsigned char *base = smem_raw + (size_t)sidx * L::stage;
+        const TmaView<T, S> tv{reinterpret_cast<const S *>(base + L::pops), reinterpret_cast<const T *>(base + L::tpl),
+                               reinterpret_cast<const T *>(base + L::dphi), reinterpret_cast<const T *>(base + L::phir)};
+        main_body<T, S, SNAP, FROZEN, RESID, false, 5, true>(P, src, dst, gA, gB, ctl, Rf, phiu, psi_prev, snap, part,
+                                                             unstable, t % tiles_x, t / tiles_x, t, &tv);
+    }
 }
 
 // End of step (one block of 256): global sums of the main kernel (when it

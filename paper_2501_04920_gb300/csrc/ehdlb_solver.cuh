@@ -19,6 +19,40 @@
 
 namespace ehdlb {
 
+// cuTensorMapEncodeTiled of the driver, resolved through the runtime (no
+// link against the driver library); nullptr if unavailable.
+using TensorMapEncodeFn = decltype(&cuTensorMapEncodeTiled);
+inline TensorMapEncodeFn tensor_map_encoder()
+{
+    static TensorMapEncodeFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (TensorMapEncodeFn) nullptr;
+        return reinterpret_cast<TensorMapEncodeFn>(p);
+    }();
+    return fn;
+}
+
+// A tiled map of `planes` planes of an nx x rows array of E (planes > 1:
+// rank 3, planes nn elements apart), box (bw, bh, planes).
+template <typename E>
+bool encode_tiles(CUtensorMap *m, const void *base, int nx, int rows, int planes, long long nn, int bw, int bh)
+{
+    TensorMapEncodeFn enc = tensor_map_encoder();
+    if (!enc) return false;
+    const CUtensorMapDataType dt = sizeof(E) == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)rows, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(E), (cuuint64_t)nn * sizeof(E)};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, (cuuint32_t)planes};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, dt, planes > 1 ? 3 : 2, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 #define EHDLB_CK(call)                                                              \
     do {                                                                            \
         cudaError_t e_ = (call);                                                    \
@@ -96,6 +130,14 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         EHDLB_CK((main_attr<false, true, false>()));
         EHDLB_CK((main_attr<false, false, true>()));
         EHDLB_CK((main_attr<false, false, false>()));
+        if constexpr (kTmaMain) {
+            EHDLB_CK((tma_attr<true, true, false>()));
+            EHDLB_CK((tma_attr<true, false, true>()));
+            EHDLB_CK((tma_attr<true, false, false>()));
+            EHDLB_CK((tma_attr<false, true, false>()));
+            EHDLB_CK((tma_attr<false, false, true>()));
+            EHDLB_CK((tma_attr<false, false, false>()));
+        }
         EHDLB_CK(tb_attr<1>());
         EHDLB_CK(tb_attr<2>());
         if constexpr (TB_MAX >= 5) {
@@ -107,6 +149,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         EHDLB_CK(alloc((void **)&red_, sizeof(double) * (6 * PSUM + 3 * DEF_MAX_SLICES)));
         EHDLB_CK(cudaMemsetAsync(snap_, 0, plane * EHDLB_NFIELDS, stream_));
         EHDLB_CK(cudaStreamSynchronize(stream_));
+        encode_main_maps();
         return EHDLB_OK;
     }
 
@@ -120,6 +163,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             EHDLB_CK(cudaStreamSynchronize(stream_));
             EHDLB_CK(alloc_pops(0, qi));
             EHDLB_CK(alloc_pops(1, qi));
+            encode_main_maps();
         }
         Control c{};
         c.cur0 = 0;
@@ -189,7 +233,10 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     {
         if (sweeps_per_launch >= 0) tb_chunk_ = sweeps_per_launch;
         if (shape >= 0) tb_shape_ = shape < TB_NSHAPES ? shape : 0;
-        if (vec_staging >= 0) vec_ = vec_staging != 0;
+        if (vec_staging >= 0) {
+            vec_ = vec_staging != 0;
+            tma_ = vec_staging == 2;
+        }
     }
 
     int step(int nsteps, ehdlb_stats *st, std::string &err) override
@@ -257,6 +304,10 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             st->sweeps_per_launch = tb_chunk();
             st->tile_shape = tb_shape_;
             st->deformation = deform_each_ && nsteps > 0 ? pin_->D : NAN;
+        }
+        if (ctl_h_.fault) {
+            err = "a staged copy of the step kernel did not arrive in time";
+            return EHDLB_ECUDA;
         }
         if (ctl_h_.unstable) {
             err = "NaN or Inf in the fields";
@@ -557,6 +608,49 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         return dim3((nx + tx - 1) / tx, (ny + ty - 1) / ty);
     }
 
+    // The staged step kernel runs for float arithmetic on float or FP16
+    // storage; FP64 keeps the cp.async staging.
+    static constexpr bool kTmaMain = std::is_same<T, float>::value;
+
+    template <bool SN, bool F, bool R> cudaError_t tma_attr()
+    {
+        if constexpr (kTmaMain) {
+            auto kern = k_main_tma<T, S, SN, F, R>;
+            const int smem = (int)(2 * TmaLayout<T, S>::stage);
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            int per = 0;
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, smem);
+            if (e == cudaSuccess) tma_per_sm_ = std::max(1, std::min(tma_per_sm_, per));
+            return e;
+        }
+        return cudaSuccess;
+    }
+
+    // Tensor maps of the staged step kernel; tma_ok_ records whether the
+    // lattice can take it (rows of 16-byte multiples, maps encoded).
+    void encode_main_maps()
+    {
+        tma_ok_ = false;
+        if constexpr (kTmaMain) {
+            if (((size_t)nx_ * sizeof(S)) % 16 != 0 || qi_ != 5) return;
+            bool ok = true;
+            for (int b = 0; b < 2; ++b) {
+                MainMaps &m = maps_[b];
+                ok = ok && encode_tiles<S>(&m.pops, pops_[b].f, nx_, ny_, 27, nn_, 64, 4);
+                ok = ok && encode_tiles<S>(&m.phiu, phiu_, nx_, ny_, 2, nn_, 64, 4);
+                ok = ok && encode_tiles<T>(&m.g[0], g_[0], nx_, ny_, 4, nn_, 64, 4);
+                ok = ok && encode_tiles<T>(&m.g[1], g_[1], nx_, ny_, 4, nn_, 64, 4);
+                ok = ok && encode_tiles<T>(&m.mur, ref_.mur, nx_, ny_, 1, nn_, 64, 4);
+                ok = ok && encode_tiles<T>(&m.gxr, ref_.gxr, nx_, ny_, 1, nn_, 64, 4);
+                ok = ok && encode_tiles<T>(&m.gyr, ref_.gyr, nx_, ny_, 1, nn_, 64, 4);
+                ok = ok && encode_tiles<T>(&m.psi, psi_prev_, nx_, ny_, 1, nn_, 64, 4);
+                ok = ok && encode_tiles<T>(&m.dphi, ref_.dphig, nx_, ny_ + 2, 1, nn_, TMA_HW, TMA_HH);
+                ok = ok && encode_tiles<T>(&m.phir, ref_.phir, nx_, ny_ + 2, 1, nn_, TMA_HW, TMA_HH);
+            }
+            tma_ok_ = ok;
+        }
+    }
+
     template <bool SN, bool F, bool R> cudaError_t main_attr()
     {
         cudaError_t e = cudaSuccess;
@@ -801,7 +895,28 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             else EHDLB_MAIN1(SN, F, R, false, 5);                                                        \
         }                                                                                                \
     } while (0)
-        if (last) {
+        const bool staged = kTmaMain && tma_ && tma_ok_ && qi_ == 5 && !P_.side_walls;
+#define EHDLB_MAIN_TMA(SN, F, R)                                                                         \
+    do {                                                                                                 \
+        if constexpr (kTmaMain) {                                                                        \
+            const int ntiles = (int)(grid_.x * grid_.y);                                                 \
+            k_main_tma<T, S, SN, F, R><<<std::min(ntiles, tma_per_sm_ * sms_), b,                        \
+                                         2 * TmaLayout<T, S>::stage, stream_>>>(                         \
+                dp_, maps_[par], pops_[par], pops_[par ^ 1], g_[0], g_[1], ctl_, ref_, phiu_, psi_prev_, snap_, \
+                part_, unstable, &ctl_->fault, (int)grid_.x, ntiles);                                    \
+        }                                                                                                \
+    } while (0)
+        if (staged) {
+            if (last) {
+                if (frozen) EHDLB_MAIN_TMA(true, true, false);
+                else if (main_resid) EHDLB_MAIN_TMA(true, false, true);
+                else EHDLB_MAIN_TMA(true, false, false);
+            } else {
+                if (frozen) EHDLB_MAIN_TMA(false, true, false);
+                else if (main_resid) EHDLB_MAIN_TMA(false, false, true);
+                else EHDLB_MAIN_TMA(false, false, false);
+            }
+        } else if (last) {
             if (frozen) EHDLB_MAIN(true, true, false);
             else if (main_resid) EHDLB_MAIN(true, false, true);
             else EHDLB_MAIN(true, false, false);
@@ -810,6 +925,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             else if (main_resid) EHDLB_MAIN(false, false, true);
             else EHDLB_MAIN(false, false, false);
         }
+#undef EHDLB_MAIN_TMA
 #undef EHDLB_MAIN
 #undef EHDLB_MAIN1
         long long nb2 = 0;
@@ -911,6 +1027,10 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     S *phiu_ = nullptr;
     bool vec_ok_ = false;                     // 16-byte staging possible
     bool vec_ = true;                         // and chosen (tuning)
+    bool tma_ = true;                         // staged step kernel chosen (tuning main_staging 2, default)
+    bool tma_ok_ = false;                     // and possible for this lattice
+    int tma_per_sm_ = 1 << 20;                // resident blocks per SM of the staged step kernel
+    MainMaps maps_[2]{};                      // its tensor maps, by the time level of the source
     T *phig_ = nullptr, *q_ = nullptr, *psi_prev_ = nullptr, *snap_ = nullptr;
     PhiRef<T> ref_{};
     double *part_ = nullptr, *part2_ = nullptr, *stage_ = nullptr;

@@ -16,13 +16,15 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 FP32_TOL = 1e-5
-# FP32 |u| bound.  Near equilibrium the surface-tension force is mu_phi
-# grad phi with mu_phi a small residual of kappa lap(phi) and a cubic of phi
-# ~ 1; the library stores h relative to a reference profile so that float
-# carries only the small deviation (the storage alone, emulated with the
-# oracle, then moves |u| by 9.4e-7 after 100 steps of the 256^2 case).  The
-# float arithmetic of the remaining terms leaves 1.2e-5 after 100 steps and
-# 8.2e-6 after 300 of that case; phi, psi and q stay below 1e-6.
+# FP32 |u| bound of the runs of 100 to 300 steps.  The contract's 1e-5 holds
+# for phi, psi, q, c+ and c- but not for |u|: |u| ~ 1e-4 is driven by small
+# residuals of the interfacial forces, and the float arithmetic of the step
+# kernel and the sweeps leaves 1.2e-5 after 100 steps of the 256^2 case and
+# 7.9e-6 after 300 (measured on a GB300).  For comparison, FP32 rounding of
+# the stored state alone (emulated on the oracle) gives 6.6e-7 after 1000
+# steps, and the oracle's response to one FP32 rounding of its initial state
+# decays (1.5e-6 after 100 steps, 2.6e-8 after 1000).  3e-5 guards against
+# regressions; it is not the contract.
 FP32_U_TOL = 3e-5
 
 
@@ -73,11 +75,12 @@ def test_fp64_droplet64_200_steps_matches():
     assert np.array_equal(lat.sweep_counts(200), counts)
 
 
-# Velocity bound after 2000 steps.  max|u| stays at 3e-4..8e-4 over the run,
-# and the GPU - oracle difference of |u| reaches 1.5e-12 of it (about 8e-16
-# absolute) while every other field stays below 5e-13: two FP64 codes with
-# different operation orders accumulate round-off in the small velocity, the
-# oracle's own response to a 1-ulp perturbation at every step being 1.1e-13.
+# Velocity bound after 2000 steps: the contract's 1e-12 holds for every field
+# but |u|.  max|u| stays at 3e-4..8e-4 over the run, and the GPU - oracle
+# difference of |u| reaches 1.5e-12 of it (about 8e-16 absolute) while every
+# other field stays below 5e-13: two FP64 codes with different operation
+# orders accumulate round-off in the small velocity.  3e-12 guards against
+# regressions; it is not the contract.
 FP64_TOL_U_2000 = 3e-12
 
 
@@ -169,6 +172,53 @@ def test_fp32_droplet256_matches_oracle():
     assert_close(err, FP32_U_TOL, keys=["u"])
 
 
+# The 256^2 copy of the 2048^2 case (R = 32, 20 sweeps per step) for the
+# 20000 steps of the 2048^2 run.  Measured on a GB300: phi 2.3e-6, psi 5.9e-7,
+# q 6.1e-6 (within the contract's 1e-5) and |u| 6.8e-5 (the contract misses
+# it; 1.2e-4 guards against regressions).  The oracle takes about 4 minutes on
+# 16 host cores.
+FP32_U_BOUND_20000 = 1.2e-4
+
+
+@pytest.mark.slow
+def test_fp32_droplet256_20000_steps_matches_oracle():
+    n, steps = 256, 20000
+    got, ref, *_ = run_pair(n, n, workloads.droplet(n), steps, precision=ehdlb.FP32)
+    err = field_errors(got, ref)
+    print("FP32 256^2 after 20000 steps: " + " ".join(f"{k} {v:.2e}" for k, v in sorted(err.items())))
+    assert_close(err, FP32_TOL, keys=["phi", "psi", "q", "cp", "cm"])
+    assert_close(err, FP32_U_BOUND_20000, keys=["u"])
+
+
+@pytest.mark.slow
+def test_fp32_droplet2048_from_a_developed_state_matches_oracle():
+    # The launch configuration the benchmark times, from a state with flow,
+    # charge layers and a displaced potential: the oracle's 128^2 copy of the
+    # case after 300 steps, each node repeated on a 16 x 16 block (a state of
+    # the 2048^2 lattice with R = 256), loaded into both codes and stepped twice.
+    small = oracle.Oracle(128, 128, workloads.droplet(128))
+    small.step(300)
+    s = np.repeat(np.repeat(small.state(), 16, axis=0), 16, axis=1)
+    small.close()
+    n, steps = 2048, 2
+    prm = workloads.droplet(n)
+    orc = oracle.Oracle(n, n, prm)
+    orc.set_state(s)
+    orc.step(steps)
+    ref = orc.fields()
+    orc.close()
+    lat = ehdlb.Lattice(n, n, prm, precision=ehdlb.FP32)
+    lat.set_state(s)
+    del s
+    lat.step(steps)
+    got = lat.fields()
+    lat.close()
+    assert np.max(np.hypot(ref["ux"], ref["uy"])) > 1e-5 and np.max(np.abs(ref["q"])) > 0.1
+    err = field_errors(got, ref)
+    assert_close(err, FP32_TOL, keys=["phi", "psi", "q", "cp", "cm"])
+    assert_close(err, FP32_U_TOL, keys=["u"])
+
+
 def test_fp32_side_walls_match_oracle():
     # the enclosure of Sec. 6: side walls (Eq. 64) instead of periodic x
     n, steps = 128, 100
@@ -234,7 +284,8 @@ def test_fp64_droplet256_matches_oracle():
 
 def test_fp32_every_sweep_tuning_matches_oracle():
     # sweeps fused per launch (0: one per launch) x region shapes of the fused
-    # kernel x staging of the step kernel, on a lattice that no tile divides
+    # kernel x staging of the step kernel (0: per node, 1: 16-byte copies,
+    # 2: tensor-memory-accelerator boxes), on a lattice that no tile divides
     nx, ny, steps = 136, 97, 12
     prm = workloads.droplet(128)
     prm.update(xc=(nx - 1) / 2, yc=(ny - 1) / 2, R=24.0, Kq=5.6893 / (nx * ny))
@@ -244,7 +295,7 @@ def test_fp32_every_sweep_tuning_matches_oracle():
     for shape in range(6):
         for spl in (0, 1, 2, 3, 4, 5):
             lat = ehdlb.Lattice(nx, ny, prm, precision=ehdlb.FP32)
-            ehdlb.ehdlb_set_tuning(lat.ctx, spl, shape, spl % 2)
+            ehdlb.ehdlb_set_tuning(lat.ctx, spl, shape, spl % 3)
             lat.step(steps)
             err = field_errors(lat.fields(), ref)
             try:
@@ -252,6 +303,28 @@ def test_fp32_every_sweep_tuning_matches_oracle():
                 assert_close(err, FP32_U_TOL, keys=["u"])
             except AssertionError as e:
                 raise AssertionError(f"shape {shape}, {spl} sweeps per launch: {e}") from None
+
+
+@pytest.mark.parametrize("precision", [ehdlb.FP32, ehdlb.FP16S])
+@pytest.mark.parametrize("nx,ny", [(128, 96), (200, 68), (64, 8)])
+def test_staged_step_kernel_equals_the_copy_staged_one(precision, nx, ny):
+    # the step kernel fed by tensor-memory-accelerator boxes (persistent,
+    # double-buffered) against the one that stages with cp.async: the same
+    # arithmetic on the same inputs, on lattices whose last tile column or row
+    # is partial and one narrower than a tile row of blocks
+    prm = workloads.droplet(128)
+    prm.update(xc=(nx - 1) / 2, yc=(ny - 1) / 2, R=min(nx, ny) / 4, Kq=5.6893 / (nx * ny))
+    out = []
+    for staging in (1, 2):
+        lat = ehdlb.Lattice(nx, ny, prm, precision=precision)
+        ehdlb.ehdlb_set_tuning(lat.ctx, -1, -1, staging)
+        status, _ = lat.step(25)
+        assert status == ehdlb.OK
+        out.append((lat.fields(), lat.state()))
+        lat.close()
+    (fa, sa), (fb, sb) = out
+    diff = max(float(np.max(np.abs(fa[k] - fb[k]))) for k in ehdlb.FIELDS)
+    assert np.array_equal(sa, sb) and diff == 0.0, diff
 
 
 @pytest.mark.parametrize("nx,ny", [(8, 8), (13, 7), (40, 70), (66, 45), (45, 66), (137, 50)])
@@ -348,7 +421,7 @@ def test_error_codes():
     assert L.ehdlb_set_params(h, ehdlb.C.byref(good)) == ehdlb.OK
     assert L.ehdlb_set_tuning(h, 6, 0, 0) == ehdlb.EINVAL
     assert L.ehdlb_set_tuning(h, 2, 6, 0) == ehdlb.EINVAL
-    assert L.ehdlb_set_tuning(h, 2, 0, 2) == ehdlb.EINVAL
+    assert L.ehdlb_set_tuning(h, 2, 0, 3) == ehdlb.EINVAL
     assert L.ehdlb_set_tuning(h, -1, -1, -1) == ehdlb.OK
     assert L.ehdlb_step(h, 2, ehdlb.C.byref(st)) == ehdlb.WNOTCONV
     assert st.not_converged == 2
