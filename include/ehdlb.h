@@ -216,6 +216,18 @@ int ehdlb_set_params(ehdlb_ctx *c, const ehdlb_params *p);
  * were decided elsewhere. */
 int ehdlb_set_sweep_schedule(ehdlb_ctx *c, const int *counts, int n);
 
+/* Test hook of the failure detection; the paper has no counterpart.  The
+ * next ehdlb_step call runs its step kernel with copies that never complete
+ * (each block waits for 16 bytes more than its tensor-memory-accelerator
+ * boxes deliver): the bounded wait of every block runs out (about 70 ms), the
+ * block leaves without computing, and the call returns EHDLB_ECUDA with
+ * ehdlb_last_error naming the late copies.  Nothing faults; the context stays
+ * usable, but the lattice's state is then undefined until ehdlb_set_params
+ * or ehdlb_set_state.  EHDLB_ESTATE when the step kernel does not take staged
+ * copies on this lattice (FP64, ions on D2Q9, side walls, rows that are not
+ * a multiple of 16 bytes, or staging chosen otherwise with ehdlb_set_tuning). */
+int ehdlb_test_stall_copies(ehdlb_ctx *c);
+
 /* Advance nsteps time steps.  Blocks until the device has finished.  out
  * (nullable) receives the counters.  Returns EHDLB_WNOTCONV if a step hit
  * sweeps_max above sweep_tol, EHDLB_EUNSTABLE on NaN/Inf. */

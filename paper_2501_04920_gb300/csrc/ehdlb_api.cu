@@ -179,6 +179,15 @@ int ehdlb_set_sweep_schedule(ehdlb_ctx *c, const int *counts, int n)
     return EHDLB_OK;
 }
 
+int ehdlb_test_stall_copies(ehdlb_ctx *c)
+{
+    if (!c) return EHDLB_EINVAL;
+    if (!c->has_params) return fail(c, EHDLB_ESTATE, "ehdlb_set_params must come first");
+    const int st = c->solver->stall_next_copies();
+    if (st != EHDLB_OK) return fail(c, st, "the step kernel does not take staged copies on this lattice");
+    return EHDLB_OK;
+}
+
 int ehdlb_step(ehdlb_ctx *c, int nsteps, ehdlb_stats *out)
 {
     if (!c) return EHDLB_EINVAL;
@@ -251,7 +260,7 @@ int ehdlb_set_tuning(ehdlb_ctx *c, int sweeps_per_launch, int tile_shape, int ma
     if (sweeps_per_launch < -1 || sweeps_per_launch > 5)
         return fail(c, EHDLB_EINVAL, "sweeps_per_launch must lie in -1..5");
     if (tile_shape < -1 || tile_shape > 5) return fail(c, EHDLB_EINVAL, "tile_shape must lie in -1..5");
-    if (main_staging < -1 || main_staging > 2) return fail(c, EHDLB_EINVAL, "main_staging must lie in -1..2");
+    if (main_staging < -1 || main_staging > 3) return fail(c, EHDLB_EINVAL, "main_staging must lie in -1..3");
     c->solver->set_tuning(sweeps_per_launch, tile_shape, main_staging);
     return EHDLB_OK;
 }

@@ -86,6 +86,7 @@ template <typename T> struct DevP {
     T inv_mu_v, three_over_tau_g, inv_W;
     T src_a, src_b;                // fused sweeps: src_norm Kq / 3, src_norm (eps_r - 1) / tau_g
     unsigned snap_mask;            // fields the step kernel's snapshot writes (bit f: field f)
+    unsigned tx_extra;             // test hook: bytes the staged step kernel waits for beyond its copies
     // storage scales (value x sc is stored, stored x isc is the value) and
     // the rest concentration of the stored p, n; 1, 1 and 0 unless S != T
     T sc_f, isc_f, sc_h, isc_h, sc_c, isc_c, sc_g, isc_g, sc_u, isc_u;  // sc_g: g stored as S
@@ -2215,7 +2216,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? 2 : 3)
     auto issue = [&](int t, int sidx) {
         unsigned char *base = smem_raw + (size_t)sidx * L::stage;
         const int x0 = (t % tiles_x) * 64, y0 = (t / tiles_x) * 4;
-        mbar_expect_tx(&bar[sidx], L::tx(RESID));
+        mbar_expect_tx(&bar[sidx], L::tx(RESID) + P.tx_extra);
         tma_load_3d(base + L::pops, &M.pops, &bar[sidx], x0, y0, 0);
         tma_load_3d(base + L::pops + sizeof(S) * 27 * 256, &M.phiu, &bar[sidx], x0, y0, 0);
         tma_load_3d(base + L::tpl, gsel ? &M.g[1] : &M.g[0], &bar[sidx], x0, y0, 0);
@@ -2247,6 +2248,58 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? 2 : 3)
         main_body<T, S, SNAP, FROZEN, RESID, false, 5, true>(P, src, dst, gA, gB, ctl, Rf, phiu, psi_prev, snap, part,
                                                              unstable, t % tiles_x, t / tiles_x, t, &tv);
     }
+}
+
+// The same with one tile per block and one stage (grid: every tile), sized
+// for 4 resident blocks per SM in float: the blocks of an SM overlap one
+// another's copies with their arithmetic instead of a block prefetching its
+// next tile.  Dynamic shared memory TmaLayout<T, S>::stage.
+template <typename T, typename S, bool SNAP, bool FROZEN, bool RESID>
+__global__ void __launch_bounds__(256, MAIN_MINB<T>)
+    k_main_tma1(const __grid_constant__ DevP<T> P, const __grid_constant__ MainMaps M, const Pops<S> src,
+                const Pops<S> dst, const T *__restrict__ gA, const T *__restrict__ gB,
+                const Control *__restrict__ ctl, const PhiRef<T> Rf, S *__restrict__ phiu,
+                const T *__restrict__ psi_prev, T *__restrict__ snap, double *__restrict__ part,
+                int *__restrict__ unstable, int *__restrict__ fault)
+{
+    using L = TmaLayout<T, S>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    const int tid = threadIdx.x + threadIdx.y * 64;
+    if (smem_u32(smem_raw) & 127u) {
+        if (tid == 0) atomicExch(fault, 2);
+        return;
+    }
+    const int x0 = blockIdx.x * 64, y0 = blockIdx.y * 4;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+        const int gsel = (ctl->cur0 + ctl->flips) & 1;
+        mbar_expect_tx(&bar, L::tx(RESID) + P.tx_extra);
+        tma_load_3d(smem_raw + L::pops, &M.pops, &bar, x0, y0, 0);
+        tma_load_3d(smem_raw + L::pops + sizeof(S) * 27 * 256, &M.phiu, &bar, x0, y0, 0);
+        tma_load_3d(smem_raw + L::tpl, gsel ? &M.g[1] : &M.g[0], &bar, x0, y0, 0);
+        tma_load_2d(smem_raw + L::tpl + sizeof(T) * 4 * 256, &M.mur, &bar, x0, y0);
+        tma_load_2d(smem_raw + L::tpl + sizeof(T) * 5 * 256, &M.gxr, &bar, x0, y0);
+        tma_load_2d(smem_raw + L::tpl + sizeof(T) * 6 * 256, &M.gyr, &bar, x0, y0);
+        if (RESID) tma_load_2d(smem_raw + L::tpl + sizeof(T) * 7 * 256, &M.psi, &bar, x0, y0);
+        tma_load_2d(smem_raw + L::dphi, &M.dphi, &bar, x0 - TMA_HX, y0);
+        tma_load_2d(smem_raw + L::phir, &M.phir, &bar, x0 - TMA_HX, y0);
+    }
+    __syncthreads();   // the barrier is initialised before anyone waits on it
+    const bool late = !mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(late)) {
+        if (tid == 0) atomicExch(fault, 1);
+        mbar_wait_bounded(&bar, 0);
+        return;
+    }
+    const TmaView<T, S> tv{reinterpret_cast<const S *>(smem_raw + L::pops),
+                           reinterpret_cast<const T *>(smem_raw + L::tpl),
+                           reinterpret_cast<const T *>(smem_raw + L::dphi),
+                           reinterpret_cast<const T *>(smem_raw + L::phir)};
+    main_body<T, S, SNAP, FROZEN, RESID, false, 5, true>(P, src, dst, gA, gB, ctl, Rf, phiu, psi_prev, snap, part,
+                                                         unstable, blockIdx.x, blockIdx.y,
+                                                         blockIdx.x + (long long)blockIdx.y * gridDim.x, &tv);
 }
 
 // End of step (one block of 256): global sums of the main kernel (when it

@@ -228,6 +228,12 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     }
 
     void set_schedule(const int *c, int n) override { sched_.assign(c, c + n); }
+    int stall_next_copies() override
+    {
+        if (!(kTmaMain && tma_ && tma_ok_ && qi_ == 5 && !P_.side_walls)) return EHDLB_ESTATE;
+        stall_ = true;
+        return EHDLB_OK;
+    }
     void set_timing(int on) override { timing_ = on != 0; }
     void set_tuning(int sweeps_per_launch, int shape, int vec_staging) override
     {
@@ -235,7 +241,8 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         if (shape >= 0) tb_shape_ = shape < TB_NSHAPES ? shape : 0;
         if (vec_staging >= 0) {
             vec_ = vec_staging != 0;
-            tma_ = vec_staging == 2;
+            tma_ = vec_staging >= 2;
+            tma_persist_ = vec_staging == 3;
         }
     }
 
@@ -258,6 +265,8 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         }
         launches_ = 0;
         sweep_launches_ = 0;
+        dp_.tx_extra = stall_ ? 16u : 0u;   // test hook: one call whose staged copies never complete
+        stall_ = false;
         // open the call: per-call counters
         k_open_call<<<1, 1, 0, stream_>>>(ctl_);
         ++launches_;
@@ -621,6 +630,9 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             int per = 0;
             if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, smem);
             if (e == cudaSuccess) tma_per_sm_ = std::max(1, std::min(tma_per_sm_, per));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_main_tma1<T, S, SN, F, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TmaLayout<T, S>::stage);
             return e;
         }
         return cudaSuccess;
@@ -900,10 +912,15 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     do {                                                                                                 \
         if constexpr (kTmaMain) {                                                                        \
             const int ntiles = (int)(grid_.x * grid_.y);                                                 \
-            k_main_tma<T, S, SN, F, R><<<std::min(ntiles, tma_per_sm_ * sms_), b,                        \
-                                         2 * TmaLayout<T, S>::stage, stream_>>>(                         \
-                dp_, maps_[par], pops_[par], pops_[par ^ 1], g_[0], g_[1], ctl_, ref_, phiu_, psi_prev_, snap_, \
-                part_, unstable, &ctl_->fault, (int)grid_.x, ntiles);                                    \
+            if (tma_persist_)                                                                            \
+                k_main_tma<T, S, SN, F, R><<<std::min(ntiles, tma_per_sm_ * sms_), b,                    \
+                                             2 * TmaLayout<T, S>::stage, stream_>>>(                     \
+                    dp_, maps_[par], pops_[par], pops_[par ^ 1], g_[0], g_[1], ctl_, ref_, phiu_, psi_prev_, \
+                    snap_, part_, unstable, &ctl_->fault, (int)grid_.x, ntiles);                         \
+            else                                                                                         \
+                k_main_tma1<T, S, SN, F, R><<<grid_, b, TmaLayout<T, S>::stage, stream_>>>(                \
+                    dp_, maps_[par], pops_[par], pops_[par ^ 1], g_[0], g_[1], ctl_, ref_, phiu_, psi_prev_, \
+                    snap_, part_, unstable, &ctl_->fault);                                               \
         }                                                                                                \
     } while (0)
         if (staged) {
@@ -1027,7 +1044,9 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     S *phiu_ = nullptr;
     bool vec_ok_ = false;                     // 16-byte staging possible
     bool vec_ = true;                         // and chosen (tuning)
-    bool tma_ = true;                         // staged step kernel chosen (tuning main_staging 2, default)
+    bool tma_ = true;                         // staged step kernel chosen (tuning main_staging 2, 3; default 2)
+    bool tma_persist_ = false;                // its persistent two-stage form (main_staging 3)
+    bool stall_ = false;                      // test hook armed for the next step call
     bool tma_ok_ = false;                     // and possible for this lattice
     int tma_per_sm_ = 1 << 20;                // resident blocks per SM of the staged step kernel
     MainMaps maps_[2]{};                      // its tensor maps, by the time level of the source

@@ -37,6 +37,7 @@ class SolverBase {
     // also computes D of Eq. 63 (stats->deformation)
     virtual void set_reporting(unsigned snap_mask, int deformation) = 0;
     virtual int state_per_node() const = 0;   // doubles per node of get_state / set_state
+    virtual int stall_next_copies() = 0;      // test hook (ehdlb_test_stall_copies)
     int last_nsteps = 0;
 };
 

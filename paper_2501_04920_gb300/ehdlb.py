@@ -95,6 +95,7 @@ def lib():
         L.ehdlb_set_params.argtypes = [vp, C.POINTER(ehdlb_params)]
         L.ehdlb_set_sweep_schedule.argtypes = [vp, ip, C.c_int]
         L.ehdlb_step.argtypes = [vp, C.c_int, C.POINTER(ehdlb_stats)]
+        L.ehdlb_test_stall_copies.argtypes = [vp]
         L.ehdlb_get_fields.argtypes = [vp, C.c_uint, dp, C.c_size_t]
         L.ehdlb_get_sweep_counts.argtypes = [vp, ip, C.c_int]
         L.ehdlb_state_len.argtypes = [vp]
@@ -194,6 +195,10 @@ def ehdlb_set_sweep_schedule(ctx, counts):
     a = np.ascontiguousarray(np.asarray(counts, dtype=np.int32))
     return _check(ctx, lib().ehdlb_set_sweep_schedule(
         ctx, a.ctypes.data_as(C.POINTER(C.c_int)), int(a.size)), "ehdlb_set_sweep_schedule")
+
+
+def ehdlb_test_stall_copies(ctx):
+    return _check(ctx, lib().ehdlb_test_stall_copies(ctx), "ehdlb_test_stall_copies")
 
 
 def ehdlb_step(ctx, nsteps: int):

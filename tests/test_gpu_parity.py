@@ -174,9 +174,12 @@ def test_fp32_droplet256_matches_oracle():
 
 # The 256^2 copy of the 2048^2 case (R = 32, 20 sweeps per step) for the
 # 20000 steps of the 2048^2 run.  Measured on a GB300: phi 2.3e-6, psi 5.9e-7,
-# q 6.1e-6 (within the contract's 1e-5) and |u| 6.8e-5 (the contract misses
-# it; 1.2e-4 guards against regressions).  The oracle takes about 4 minutes on
-# 16 host cores.
+# q 6.1e-6 (within the contract's 1e-5) and |u| 6.8e-5.  The contract's 1e-5
+# on |u| is out of reach of any FP32 storage: the oracle itself, with exact
+# FP64 arithmetic but its populations rounded to float after every step in the
+# library's storage form, ends 9.9e-5 from the unrounded oracle on |u| (phi
+# 8.8e-7, psi 6.0e-7, q 8.5e-6).  1.2e-4 guards against regressions.  The
+# oracle takes about 4 minutes on 16 host cores.
 FP32_U_BOUND_20000 = 1.2e-4
 
 
@@ -285,7 +288,8 @@ def test_fp64_droplet256_matches_oracle():
 def test_fp32_every_sweep_tuning_matches_oracle():
     # sweeps fused per launch (0: one per launch) x region shapes of the fused
     # kernel x staging of the step kernel (0: per node, 1: 16-byte copies,
-    # 2: tensor-memory-accelerator boxes), on a lattice that no tile divides
+    # 2: tensor-memory-accelerator boxes, 3: the same, persistent with two
+    # stages), on a lattice that no tile divides
     nx, ny, steps = 136, 97, 12
     prm = workloads.droplet(128)
     prm.update(xc=(nx - 1) / 2, yc=(ny - 1) / 2, R=24.0, Kq=5.6893 / (nx * ny))
@@ -295,7 +299,7 @@ def test_fp32_every_sweep_tuning_matches_oracle():
     for shape in range(6):
         for spl in (0, 1, 2, 3, 4, 5):
             lat = ehdlb.Lattice(nx, ny, prm, precision=ehdlb.FP32)
-            ehdlb.ehdlb_set_tuning(lat.ctx, spl, shape, spl % 3)
+            ehdlb.ehdlb_set_tuning(lat.ctx, spl, shape, spl % 4)
             lat.step(steps)
             err = field_errors(lat.fields(), ref)
             try:
@@ -308,23 +312,25 @@ def test_fp32_every_sweep_tuning_matches_oracle():
 @pytest.mark.parametrize("precision", [ehdlb.FP32, ehdlb.FP16S])
 @pytest.mark.parametrize("nx,ny", [(128, 96), (200, 68), (64, 8)])
 def test_staged_step_kernel_equals_the_copy_staged_one(precision, nx, ny):
-    # the step kernel fed by tensor-memory-accelerator boxes (persistent,
-    # double-buffered) against the one that stages with cp.async: the same
+    # the step kernel fed by tensor-memory-accelerator boxes (one tile per
+    # block, and persistent with two stages) against the one that stages with
+    # cp.async: the same
     # arithmetic on the same inputs, on lattices whose last tile column or row
     # is partial and one narrower than a tile row of blocks
     prm = workloads.droplet(128)
     prm.update(xc=(nx - 1) / 2, yc=(ny - 1) / 2, R=min(nx, ny) / 4, Kq=5.6893 / (nx * ny))
     out = []
-    for staging in (1, 2):
+    for staging in (1, 2, 3):
         lat = ehdlb.Lattice(nx, ny, prm, precision=precision)
         ehdlb.ehdlb_set_tuning(lat.ctx, -1, -1, staging)
         status, _ = lat.step(25)
         assert status == ehdlb.OK
         out.append((lat.fields(), lat.state()))
         lat.close()
-    (fa, sa), (fb, sb) = out
-    diff = max(float(np.max(np.abs(fa[k] - fb[k]))) for k in ehdlb.FIELDS)
-    assert np.array_equal(sa, sb) and diff == 0.0, diff
+    fa, sa = out[0]
+    for staging, (fb, sb) in zip((2, 3), out[1:]):
+        diff = max(float(np.max(np.abs(fa[k] - fb[k]))) for k in ehdlb.FIELDS)
+        assert np.array_equal(sa, sb) and diff == 0.0, (staging, diff)
 
 
 @pytest.mark.parametrize("nx,ny", [(8, 8), (13, 7), (40, 70), (66, 45), (45, 66), (137, 50)])
@@ -406,6 +412,32 @@ def test_oracle_state_imported_steps_identically():
     assert_close(field_errors(lat.fields(), orc.fields()), FP64_TOL)
 
 
+@pytest.mark.parametrize("staging", [2, 3])
+def test_late_staged_copies_are_reported_and_the_context_recovers(staging):
+    # failure detection of the step kernel's bounded waits, injected on the
+    # host: the copies of one call never complete, every block gives up after
+    # its wait limit and the call reports it; nothing faults, and the context
+    # steps normally once the lattice is set up again
+    prm = workloads.droplet(64)
+    lat = ehdlb.Lattice(64, 64, prm, precision=ehdlb.FP32)
+    ehdlb.ehdlb_set_tuning(lat.ctx, -1, -1, staging)
+    ref = ehdlb.Lattice(64, 64, prm, precision=ehdlb.FP32)
+    ref.step(3)
+    ehdlb.ehdlb_test_stall_copies(lat.ctx)
+    st = ehdlb.ehdlb_stats()
+    assert ehdlb.lib().ehdlb_step(lat.ctx, 1, ehdlb.C.byref(st)) == ehdlb.ECUDA
+    assert "did not arrive" in ehdlb.ehdlb_last_error(lat.ctx)
+    ehdlb.ehdlb_set_params(lat.ctx, lat.params)
+    status, _ = lat.step(3)
+    assert status == ehdlb.OK
+    got, want = lat.fields(), ref.fields()
+    for k in ehdlb.FIELDS:
+        assert np.array_equal(got[k], want[k]), k
+    side = ehdlb.Lattice(64, 64, dict(prm, side_walls=1), precision=ehdlb.FP32)
+    assert ehdlb.lib().ehdlb_test_stall_copies(side.ctx) == ehdlb.ESTATE
+    lat.close(); ref.close(); side.close()
+
+
 def test_error_codes():
     L = ehdlb.lib()
     h = ehdlb.ehdlb_create(16, 16, ehdlb.FP32)
@@ -421,7 +453,7 @@ def test_error_codes():
     assert L.ehdlb_set_params(h, ehdlb.C.byref(good)) == ehdlb.OK
     assert L.ehdlb_set_tuning(h, 6, 0, 0) == ehdlb.EINVAL
     assert L.ehdlb_set_tuning(h, 2, 6, 0) == ehdlb.EINVAL
-    assert L.ehdlb_set_tuning(h, 2, 0, 3) == ehdlb.EINVAL
+    assert L.ehdlb_set_tuning(h, 2, 0, 4) == ehdlb.EINVAL
     assert L.ehdlb_set_tuning(h, -1, -1, -1) == ehdlb.OK
     assert L.ehdlb_step(h, 2, ehdlb.C.byref(st)) == ehdlb.WNOTCONV
     assert st.not_converged == 2
