@@ -859,6 +859,10 @@ template <typename T> struct TbrTile {
     double *part;
     long long slot;
     int x0, y0;
+    // fused prep (the first launch computes phi and q itself): the h, p, n
+    // planes of the time level, phi_ref and dphi (both with ghost rows)
+    const T *h, *pp, *pn, *phir;
+    T *dphig;
 };
 
 // The tiles of one lattice, tiles_x per row, row by row; src / dst: the g
@@ -871,17 +875,25 @@ template <typename T> struct TbrLatticeTiles {
     T *coef;
     double *part;
     int tiles_x, ntiles;
+    const T *h = nullptr, *pp = nullptr, *pn = nullptr, *phir = nullptr;
+    T *dphig = nullptr;
     __device__ int count() const { return ntiles; }
     __device__ TbrTile<T> tile(int t, int TX, int TY) const
     {
-        return TbrTile<T>{P, src, dst, phig, q, coef, part, t, (t % tiles_x) * TX, (t / tiles_x) * TY};
+        return TbrTile<T>{P,    src, dst, phig, q,  coef, part, t, (t % tiles_x) * TX, (t / tiles_x) * TY,
+                          h,    pp,  pn,  phir, dphig};
     }
 };
 
 // The persistent loop over the tiles J gives (count(), tile(i, TX, TY)).
 // Launch: blockDim (32, NW), dynamic shared memory tbr_smem_bytes<T, R, NW>(FIRST),
 // grid = min(tiles, resident blocks).
-template <typename T, int NSW, int R, int NW, bool FIRST, bool RESID, typename Tiles>
+// FPREP (with FIRST): the launch also does the prep pass of the step for its
+// tiles: phi = phi_ref + sum h (Eq. 33) and q = sum p - sum n of every region
+// node and of the one-node ring from the populations, in the order prep_body
+// sums them (so the coefficients are the same bits), and writes dphi of its
+// output nodes (with the mirrored ghost rows).
+template <typename T, int NSW, int R, int NW, bool FIRST, bool RESID, bool FPREP = false, typename Tiles>
 __device__ __forceinline__ void tbr_run(const Tiles &J)
 {
     using V2 = typename Vec2T<T>::type;
@@ -896,7 +908,8 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
     __shared__ __align__(16) T xdn[2][NW][RW];   // p4 of each warp's bottom row, for the warp below
     const int lane = threadIdx.x, w = threadIdx.y;
     const int lx0 = 2 * lane, ly0 = w * R;
-    constexpr int NPL = FIRST ? 5 : 7;
+    static_assert(!FPREP || FIRST, "the prep pass is fused into the first launch of a step");
+    constexpr int NPL = FIRST ? (FPREP ? 4 : 5) : 7;
 
     // copy tile tl to the stage: this thread's own cells (zeros outside the
     // lattice rows), and (FIRST) a share of phi with its ring
@@ -934,7 +947,7 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
                 }
             }
         }
-        if (FIRST) {
+        if (FIRST && !FPREP) {
             // phi (phig holds the rows -1 .. ny): this thread's node pairs,
             // then the ring (rows -1 and RH, columns -1 and 64) by all
 #pragma unroll
@@ -1102,9 +1115,91 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
         const int x0 = cur.x0, y0 = cur.y0;
         const int gy0 = y0 - H + ly0;   // lattice row of this thread's row 0
         cp_async_wait_all();
-        if (FIRST) __syncthreads();      // phi was copied by all threads
-
         T g1[R][2], g2[R][2], g3[R][2], g4[R][2], cA[R][2], cBx[R][2], cBy[R][2];
+        if constexpr (FPREP) {
+            // phi of the region and its ring from the populations
+            const bool wide = nx >= RW + 2;
+            auto node = [&](int gy, int gx, T &d, T &qv) {
+                const long long kk = (long long)gy * nx + gx;
+                const T *hp = cur.h + kk;
+                d = hp[0] + ((((hp[nn] + hp[3 * nn]) + (hp[2 * nn] + hp[4 * nn]))) +
+                             ((hp[5 * nn] + hp[7 * nn]) + (hp[6 * nn] + hp[8 * nn])));
+                T sp = T(0), sn = T(0);
+#pragma unroll
+                for (int i = 0; i < 5; ++i) { sp += cur.pp[i * nn + kk]; sn += cur.pn[i * nn + kk]; }
+                qv = sp - sn;
+            };
+            const int gxA = wrap_x(x0 - HL + lx0, nx, wide);
+            const int gxB = pairs ? gxA + 1 : wrap_x(x0 - HL + lx0 + 1, nx, wide);
+            const int gxo = x0 - HL + lx0;
+            const bool xout = lx0 >= HL && lx0 < HL + TX && gxo < nx;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int gy = gy0 + r, ly = ly0 + r;
+                T *c = sphi + (ly + 1) * TBR_FW + lx0 + 2;
+                T qA = T(0), qB = T(0);
+                if (gy >= -1 && gy <= ny) {
+                    const int ry = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);   // the ghost rows mirror
+                    T dA, dB, qa, qb;
+                    node(ry, gxA, dA, qa);
+                    node(ry, gxB, dB, qb);
+                    const T *pr = cur.phir + (long long)(gy + 1) * nx;
+                    c[0] = pr[gxA] + dA;
+                    c[1] = pr[gxB] + dB;
+                    if (gy >= 0 && gy < ny) {
+                        qA = qa;
+                        qB = qb;
+                        if (xout && ly >= H && ly < H + TY) {
+                            // dphi of the output nodes and of the ghost rows they mirror into
+                            T *drow = cur.dphig + (long long)(gy + 1) * nx;
+                            drow[gxo] = dA;
+                            if (gxo + 1 < nx) drow[gxo + 1] = dB;
+                            if (gy == 0) {
+                                cur.dphig[gxo] = dA;
+                                if (gxo + 1 < nx) cur.dphig[gxo + 1] = dB;
+                            }
+                            if (gy == ny - 1) {
+                                T *top = cur.dphig + (long long)(ny + 1) * nx;
+                                top[gxo] = dA;
+                                if (gxo + 1 < nx) top[gxo + 1] = dB;
+                            }
+                        }
+                    }
+                } else {
+                    c[0] = T(0);
+                    c[1] = T(0);
+                }
+                cA[r][0] = qA;
+                cA[r][1] = qB;
+            }
+            constexpr int NRING = 2 * (RW + 2) + 2 * RH;
+            for (int e = lane + 32 * w; e < NRING; e += 32 * NW) {
+                int ly, lx;
+                if (e < 2 * (RW + 2)) {
+                    ly = e < RW + 2 ? -1 : RH;
+                    lx = (e < RW + 2 ? e : e - (RW + 2)) - 1;
+                } else {
+                    const int c = e - 2 * (RW + 2);
+                    ly = c < RH ? c : c - RH;
+                    lx = c < RH ? -1 : RW;
+                }
+                const int gy = y0 - H + ly;
+                T *dd = sphi + (ly + 1) * TBR_FW + lx + 2;
+                if (gy >= -1 && gy <= ny) {
+                    const int ry = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
+                    const int gx = wrap_x(x0 - HL + lx, nx, wide);
+                    T d, qv;
+                    node(ry, gx, d, qv);
+                    *dd = cur.phir[(long long)(gy + 1) * nx + gx] + d;
+                } else {
+                    *dd = T(0);
+                }
+            }
+            __syncthreads();      // phi of the region and ring written by all
+        } else if (FIRST) {
+            __syncthreads();      // phi was copied by all threads
+        }
+
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const T *c = stg + (ly0 + r) * RW + lx0;
@@ -1118,7 +1213,7 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
             ld2(2, g3);
             ld2(3, g4);
             if (FIRST) {
-                ld2(4, cA);   // q until the coefficients are formed
+                if (!FPREP) ld2(4, cA);   // q until the coefficients are formed
             } else {
                 ld2(4, cA);
                 ld2(5, cBx);
@@ -1241,6 +1336,32 @@ __global__ void __launch_bounds__(32 * NW, MINB)
     const int par = (ctl->cur0 + m) & 1;
     const TbrLatticeTiles<T> J{&P, par ? gB : gA, par ? gA : gB, phig, q, coef, part, tiles_x, ntiles};
     tbr_run<T, NSW, R, NW, FIRST, RESID>(J);
+}
+
+// The first sweep launch of a step with the prep pass fused (tbr_run FPREP):
+// reads h, p, n of the step's time level instead of the prep kernel's phi
+// and q, writes dphi for the step kernel, and opens the step in the control
+// block (fixed sweep count K, flips g buffer swaps) as the prep kernel does.
+template <typename T, int NSW, int R, int NW, int MINB, bool RESID>
+__global__ void __launch_bounds__(32 * NW, MINB)
+    k_sweep_tbr_fp(const __grid_constant__ DevP<T> P, T *__restrict__ gA, T *__restrict__ gB,
+                   const T *__restrict__ h, const T *__restrict__ pp, const T *__restrict__ pn,
+                   const T *__restrict__ phir, T *__restrict__ dphig, T *__restrict__ coef,
+                   double *__restrict__ part, Control *__restrict__ ctl, int tiles_x, int ntiles, int fixedK,
+                   int flips)
+{
+    const int par = ctl->cur0 & 1;   // the first launch of the step (m = 0)
+    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        ctl->K = fixedK; ctl->flips = flips; ctl->done = 1; ctl->converge = 0;
+        ctl->kmin = fixedK; ctl->kmax = fixedK; ctl->early = 0; ctl->r_last = nan("");
+    }
+    TbrLatticeTiles<T> J{&P, par ? gB : gA, par ? gA : gB, nullptr, nullptr, coef, part, tiles_x, ntiles};
+    J.h = h;
+    J.pp = pp;
+    J.pn = pn;
+    J.phir = phir;
+    J.dphig = dphig;
+    tbr_run<T, NSW, R, NW, true, RESID, true>(J);
 }
 
 // ---- thread-block clusters -------------------------------------------------------

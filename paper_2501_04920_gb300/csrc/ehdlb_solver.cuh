@@ -591,7 +591,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     // float: shape 2 is the cluster kernel (k_sweep_cl), 2 x 4 CTAs of 64 x 32;
     // shapes 4 and 5 are register-blocked (by = warps, r = rows per warp),
     // 64 x 32 and 64 x 40
-    static constexpr int TB_NSHAPES = sizeof(T) == 4 ? 6 : 1;
+    static constexpr int TB_NSHAPES = sizeof(T) == 4 ? 7 : 1;
     static constexpr int CL_X = 2, CL_Y = 4, CL_BY = 16;
     static constexpr TbShape tb_shape(int i)
     {
@@ -601,6 +601,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         case 3: return TbShape{64, 64, 16, 2, 0};
         case 4: return TbShape{64, 32, 8, 2, 4};
         case 5: return TbShape{64, 40, 8, 2, 5};
+        case 6: return TbShape{64, 40, 8, 2, 5};   // shape 5 with the prep pass in its first launch
         default: return TbShape{64, 32, 16, 3, 0};
         }
     }
@@ -710,6 +711,8 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             if (e == cudaSuccess) e = tb_attr1<NSW, 3>();
             if (e == cudaSuccess) e = tbr_attr1<NSW, 4>();
             if (e == cudaSuccess) e = tbr_attr1<NSW, 5>();
+            if (e == cudaSuccess) e = tbr_fp_attr<NSW, false>();
+            if (e == cudaSuccess) e = tbr_fp_attr<NSW, true>();
             if (e == cudaSuccess) e = cl_attr2<NSW, false, false>();
             if (e == cudaSuccess) e = cl_attr2<NSW, false, true>();
             if (e == cudaSuccess) e = cl_attr2<NSW, true, false>();
@@ -747,6 +750,43 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         // persistent grid: the fewest resident blocks per SM of any variant
         if (e == cudaSuccess) tbr_per_sm_[SH - 4] = std::max(1, std::min(tbr_per_sm_[SH - 4], per));
         return e;
+    }
+
+    // the first launch with the prep pass fused (shape 6, float storage)
+    template <int NSW, bool RESID> cudaError_t tbr_fp_attr()
+    {
+        if constexpr (kSame<S, T>) {
+            constexpr TbShape sh = tb_shape(6);
+            const size_t smem = tbr_smem_bytes<T, sh.r, sh.by>(true);
+            auto kern = k_sweep_tbr_fp<T, NSW, sh.r, sh.by, sh.minb, RESID>;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int per = 0;
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * sh.by, smem);
+            if (e == cudaSuccess) tbr_per_sm_[1] = std::max(1, std::min(tbr_per_sm_[1], per));
+            return e;
+        }
+        return cudaSuccess;
+    }
+
+    // prep fused into the first sweep launch of a fixed-count step
+    bool fprep() const
+    {
+        return kSame<S, T> && sizeof(T) == 4 && tb_shape_ == 6 && qi_ == 5 && !P_.side_walls;
+    }
+
+    template <int NSW, bool RESID> void tbr_fp_launch(int fixedK, int flips)
+    {
+        if constexpr (kSame<S, T> && TB_NSHAPES > 6) {
+            constexpr TbShape sh = tb_shape(6);
+            const dim3 g = tb_grid(NSW, 6, nx_, ny_);
+            const int ntiles = (int)(g.x * g.y);
+            const int grid = std::min(ntiles, tbr_per_sm_[1] * sms_);
+            const Pops<S> &pp = pops_[tpar_];
+            k_sweep_tbr_fp<T, NSW, sh.r, sh.by, sh.minb, RESID>
+                <<<grid, dim3(32, sh.by), tbr_smem_bytes<T, sh.r, sh.by>(true), stream_>>>(
+                    dp_, g_[0], g_[1], pp.h, pp.p, pp.n, ref_.phir, ref_.dphig, coef_, part2_, ctl_, (int)g.x,
+                    ntiles, fixedK, flips);
+        }
     }
 
     template <int NSW, int SH> cudaError_t tbr_attr1()
@@ -810,8 +850,13 @@ template <typename T, typename S = T> class Solver : public SolverBase {
                 tb_launch1<NSW, 3>(first, resid);
             } else if (tb_shape_ == 4) {
                 tbr_launch1<NSW, 4>(first, resid);
-            } else if (tb_shape_ == 5) {
-                tbr_launch1<NSW, 5>(first, resid);
+            } else if (tb_shape_ == 5 || tb_shape_ == 6) {
+                if (first && fprep()) {
+                    if (resid) tbr_fp_launch<NSW, true>(fp_fixedK_, fp_flips_);
+                    else tbr_fp_launch<NSW, false>(fp_fixedK_, fp_flips_);
+                } else {
+                    tbr_launch1<NSW, 5>(first, resid);
+                }
 
             } else {
                 tb_launch1<NSW, 0>(first, resid);
@@ -871,7 +916,13 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         const bool fused = !converge && fixedK > 0 && chunk > 0 && !P_.side_walls;
         const int nk = fused ? (fixedK + chunk - 1) / chunk : (converge ? 0 : fixedK);
         if (timing_) cudaEventRecord(events_[4 * s], stream_);
-        launch_prep(par, fixedK, kmin, kmax, nk);
+        const bool fp = fused && fprep();
+        if (fp) {
+            fp_fixedK_ = fixedK;   // the first sweep launch does the prep pass
+            fp_flips_ = nk;
+        } else {
+            launch_prep(par, fixedK, kmin, kmax, nk);
+        }
         if (timing_) cudaEventRecord(events_[4 * s + 1], stream_);
         if (fused) {
             for (int m = 0, done = 0; m < nk; ++m) {
@@ -1047,6 +1098,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     bool tma_ = true;                         // staged step kernel chosen (tuning main_staging 2, 3; default 2)
     bool tma_persist_ = false;                // its persistent two-stage form (main_staging 3)
     bool stall_ = false;                      // test hook armed for the next step call
+    int fp_fixedK_ = 0, fp_flips_ = 0;        // the step the fused prep pass opens
     bool tma_ok_ = false;                     // and possible for this lattice
     int tma_per_sm_ = 1 << 20;                // resident blocks per SM of the staged step kernel
     MainMaps maps_[2]{};                      // its tensor maps, by the time level of the source

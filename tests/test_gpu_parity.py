@@ -296,7 +296,7 @@ def test_fp32_every_sweep_tuning_matches_oracle():
     orc = oracle.Oracle(nx, ny, prm)
     orc.step(steps)
     ref = orc.fields()
-    for shape in range(6):
+    for shape in range(7):
         for spl in (0, 1, 2, 3, 4, 5):
             lat = ehdlb.Lattice(nx, ny, prm, precision=ehdlb.FP32)
             ehdlb.ehdlb_set_tuning(lat.ctx, spl, shape, spl % 4)
@@ -307,6 +307,30 @@ def test_fp32_every_sweep_tuning_matches_oracle():
                 assert_close(err, FP32_U_TOL, keys=["u"])
             except AssertionError as e:
                 raise AssertionError(f"shape {shape}, {spl} sweeps per launch: {e}") from None
+
+
+@pytest.mark.parametrize("nx,ny", [(256, 256), (136, 97), (45, 66), (66, 45), (13, 7), (8, 8)])
+def test_prep_fused_into_the_first_sweep_launch_gives_the_same_bits(nx, ny):
+    # tile shape 6: the first register-blocked sweep launch of a step forms
+    # phi and q from the populations itself (no prep kernel) and writes dphi
+    # for the step kernel; against shape 5 with the prep kernel, on lattices
+    # with odd widths, fewer rows than a region and regions wider than the
+    # lattice, over steps that report (residual, sums) and steps that do not
+    prm = workloads.droplet(128)
+    prm.update(xc=(nx - 1) / 2, yc=(ny - 1) / 2, R=min(nx, ny) / 4, Kq=5.6893 / (nx * ny))
+    out = []
+    for shape in (5, 6):
+        lat = ehdlb.Lattice(nx, ny, prm, precision=ehdlb.FP32)
+        ehdlb.ehdlb_set_tuning(lat.ctx, 5, shape, -1)
+        _, a = lat.step(7)
+        _, b = lat.step(1)
+        out.append((lat.fields(), lat.state(), a.last_residual, b.sum_phi, b.launches))
+        lat.close()
+    (fa, sa, ra, pa, la), (fb, sb, rb, pb, lb) = out
+    for k in ehdlb.FIELDS:
+        assert np.array_equal(fa[k], fb[k]), k
+    assert np.array_equal(sa, sb) and ra == rb and pa == pb
+    assert lb == la - 1   # one launch fewer per step: no prep kernel
 
 
 @pytest.mark.parametrize("precision", [ehdlb.FP32, ehdlb.FP16S])
@@ -345,7 +369,7 @@ def test_fp32_register_blocked_sweeps_on_narrow_lattices(nx, ny):
     orc = oracle.Oracle(nx, ny, prm)
     orc.step(steps)
     ref = orc.fields()
-    for shape in (1, 4, 5):
+    for shape in (1, 4, 5, 6):
         lat = ehdlb.Lattice(nx, ny, prm, precision=ehdlb.FP32)
         ehdlb.ehdlb_set_tuning(lat.ctx, 5, shape, -1)
         lat.step(steps)
@@ -452,7 +476,7 @@ def test_error_codes():
                                            sweep_tol=0.0, init_sweeps_max=10))
     assert L.ehdlb_set_params(h, ehdlb.C.byref(good)) == ehdlb.OK
     assert L.ehdlb_set_tuning(h, 6, 0, 0) == ehdlb.EINVAL
-    assert L.ehdlb_set_tuning(h, 2, 6, 0) == ehdlb.EINVAL
+    assert L.ehdlb_set_tuning(h, 2, 7, 0) == ehdlb.EINVAL
     assert L.ehdlb_set_tuning(h, 2, 0, 4) == ehdlb.EINVAL
     assert L.ehdlb_set_tuning(h, -1, -1, -1) == ehdlb.OK
     assert L.ehdlb_step(h, 2, ehdlb.C.byref(st)) == ehdlb.WNOTCONV
