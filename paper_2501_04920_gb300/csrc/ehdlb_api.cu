@@ -259,7 +259,7 @@ int ehdlb_set_tuning(ehdlb_ctx *c, int sweeps_per_launch, int tile_shape, int ma
     if (!c) return EHDLB_EINVAL;
     if (sweeps_per_launch < -1 || sweeps_per_launch > 5)
         return fail(c, EHDLB_EINVAL, "sweeps_per_launch must lie in -1..5");
-    if (tile_shape < -1 || tile_shape > 6) return fail(c, EHDLB_EINVAL, "tile_shape must lie in -1..6");
+    if (tile_shape < -1 || tile_shape > 7) return fail(c, EHDLB_EINVAL, "tile_shape must lie in -1..7");
     if (main_staging < -1 || main_staging > 3) return fail(c, EHDLB_EINVAL, "main_staging must lie in -1..3");
     c->solver->set_tuning(sweeps_per_launch, tile_shape, main_staging);
     return EHDLB_OK;

@@ -186,12 +186,15 @@ template <typename T, typename S> struct TbrBatchTiles {
     const WorkItem *items;
     int n, m;
     __device__ int count() const { return n; }
-    __device__ TbrTile<T> tile(int i, int TX, int TY) const
+    __device__ TbrTile<T> tile(int i, int TX, int TY, int H) const
     {
         const WorkItem w = items[i];
         const CaseDev<T, S> &C = cases[w.x];
         const int par = (C.ctl->cur0 + m) & 1;
-        return TbrTile<T>{&C.P, C.g[par], C.g[par ^ 1], C.phig, C.q, C.coef, C.part2, w.w, w.y * TX, w.z * TY};
+        TbrTile<T> t{&C.P, C.g[par], C.g[par ^ 1], C.phig, C.q, C.coef, C.part2, w.w, w.y * TX, w.z * TY};
+        t.ry0 = t.y0 - H;   // regions with a halo on both sides
+        t.oy1 = min(t.y0 + TY, C.P.ny);
+        return t;
     }
 };
 
@@ -202,7 +205,7 @@ __global__ void __launch_bounds__(256, 2) kb_sweep_r(const CaseDev<T, S> *__rest
                                                      const WorkItem *__restrict__ items,
                                                      const int *__restrict__ nitems, int m)
 {
-    const TbrBatchTiles<T, S> J{cases, items, *nitems, m};
+    TbrBatchTiles<T, S> J{cases, items, *nitems, m};
     tbr_run<T, NSW, R, 8, FIRST, false>(J);
 }
 

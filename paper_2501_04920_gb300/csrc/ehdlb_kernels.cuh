@@ -863,6 +863,106 @@ template <typename T> struct TbrTile {
     // planes of the time level, phi_ref and dphi (both with ghost rows)
     const T *h, *pp, *pn, *phir;
     T *dphig;
+    int ry0;   // lattice row of the region's first row
+    int oy1;   // end of the output rows [y0, oy1)
+    int carry; // walk: the row below the region was the previous tile's (its upward flux is carried)
+};
+
+// Rows of tile row ty of a lattice of ny rows for regions of RH rows and H
+// sweeps.  An edge of a region that lies on an electrode wall needs no halo
+// (the wall links are exact inside the region), so the first tile row takes
+// the region [0, RH) and outputs [0, RH - H), the last [ny - RH, ny) and
+// outputs its last rows, and the rows between take TY = RH - 2 H rows of
+// output from regions with H rows of halo on both sides; a lattice of at
+// most RH rows is one region.  Returns the region's first row and sets the
+// output rows [*oy0, *oy1).
+__host__ __device__ inline int tbr_rows(int ty, int ny, int RH, int H, int *oy0, int *oy1)
+{
+    const int TY = RH - 2 * H;
+    if (ny <= RH) {
+        *oy0 = 0;
+        *oy1 = ny;
+        return 0;
+    }
+    const int edge = RH - H, mid = ny - 2 * edge > 0 ? (ny - 2 * edge + TY - 1) / TY : 0;
+    if (ty == 0) {
+        *oy0 = 0;
+        *oy1 = edge;
+        return 0;
+    }
+    if (ty <= mid) {
+        *oy0 = edge + (ty - 1) * TY;
+        *oy1 = *oy0 + TY;
+        return *oy0 - H;
+    }
+    *oy0 = edge + mid * TY;
+    *oy1 = ny;
+    return ny - RH;
+}
+// Tile rows of that partition.
+__host__ __device__ inline int tbr_tile_rows(int ny, int RH, int H)
+{
+    const int TY = RH - 2 * H, edge = RH - H;
+    if (ny <= RH) return 1;
+    return 2 + (ny - 2 * edge > 0 ? (ny - 2 * edge + TY - 1) / TY : 0);
+}
+
+// Walking order of the register-blocked sweeps: the lattice is cut into
+// strips of TX output columns, and the strips, bottom to top and one after
+// another, form one sequence of nstrips x ny rows, of which block b of G
+// takes the rows [b T / G, (b + 1) T / G).  A block walks its rows upward in
+// regions of RH rows.  Potential populations cross a row upward only through
+// g2 (Eq. 44-50, D2Q5), so a region that starts right above the rows the
+// previous region output needs no halo below: the post-collision g2 of the
+// row under it, at every sweep, is the one the previous region computed
+// there (valid at every sweep, H rows below that region's top), carried in
+// shared memory.  Such a region outputs its RH - H lowest rows; a region
+// that starts at the electrode wall needs no halo below either; a block's
+// first region elsewhere takes a halo of H rows below and outputs RH - 2 H
+// rows; a region that reaches the top wall outputs up to it.  Each tile
+// reports its partials of the residual into the block's slot.
+template <typename T> struct TbrWalkTiles {
+    const DevP<T> *P;
+    const T *src;
+    T *dst;
+    const T *phig, *q;
+    T *coef;
+    double *part;
+    int nstrips;
+    int RH, H, TX;
+    long long p1;   // end of this block's rows in the sequence
+    __device__ void at(TbrTile<T> &t, int strip, int row, bool carry) const
+    {
+        t = TbrTile<T>{P, src, dst, phig, q, coef, part, (long long)blockIdx.x, strip * TX, row};
+        const int ny = P->ny;
+        t.carry = carry;
+        t.ry0 = carry ? row : (row > H ? row - H : 0);   // at most H rows from the wall: start at it
+        int oy1 = t.ry0 + RH >= ny ? ny : t.ry0 + RH - H;
+        const long long pend = p1 - (long long)strip * ny;   // the block's end in this strip's rows
+        if (pend < oy1) oy1 = (int)pend;
+        t.oy1 = oy1;
+    }
+    __device__ bool begin(TbrTile<T> &t)
+    {
+        const int ny = P->ny;
+        const long long T_ = (long long)nstrips * ny;
+        const long long p0 = T_ * blockIdx.x / gridDim.x;
+        p1 = T_ * (blockIdx.x + 1) / gridDim.x;
+        if (p0 >= p1) return false;
+        at(t, (int)(p0 / ny), (int)(p0 % ny), false);
+        return true;
+    }
+    // the tile after t (which it overwrites); false at the block's end
+    __device__ bool next(TbrTile<T> &t) const
+    {
+        const int ny = P->ny;
+        const int strip = t.x0 / TX;
+        const long long pe = (long long)strip * ny + t.oy1;
+        if (pe >= p1) return false;
+        if (t.oy1 >= ny) at(t, strip + 1, 0, false);
+        else at(t, strip, t.oy1, true);
+        return true;
+    }
 };
 
 // The tiles of one lattice, tiles_x per row, row by row; src / dst: the g
@@ -878,10 +978,12 @@ template <typename T> struct TbrLatticeTiles {
     const T *h = nullptr, *pp = nullptr, *pn = nullptr, *phir = nullptr;
     T *dphig = nullptr;
     __device__ int count() const { return ntiles; }
-    __device__ TbrTile<T> tile(int t, int TX, int TY) const
+    __device__ TbrTile<T> tile(int t, int TX, int TY, int H) const
     {
-        return TbrTile<T>{P,    src, dst, phig, q,  coef, part, t, (t % tiles_x) * TX, (t / tiles_x) * TY,
-                          h,    pp,  pn,  phir, dphig};
+        int oy0, oy1;
+        const int ry0 = tbr_rows(t / tiles_x, P->ny, TY + 2 * H, H, &oy0, &oy1);
+        return TbrTile<T>{P, src, dst,  phig, q,     coef, part, t,   (t % tiles_x) * TX, oy0,
+                          h, pp,  pn,   phir, dphig, ry0,  oy1};
     }
 };
 
@@ -893,8 +995,9 @@ template <typename T> struct TbrLatticeTiles {
 // node and of the one-node ring from the populations, in the order prep_body
 // sums them (so the coefficients are the same bits), and writes dphi of its
 // output nodes (with the mirrored ghost rows).
-template <typename T, int NSW, int R, int NW, bool FIRST, bool RESID, bool FPREP = false, typename Tiles>
-__device__ __forceinline__ void tbr_run(const Tiles &J)
+template <typename T, int NSW, int R, int NW, bool FIRST, bool RESID, bool FPREP = false, bool WALK = false,
+          typename Tiles>
+__device__ __forceinline__ void tbr_run(Tiles &J)
 {
     using V2 = typename Vec2T<T>::type;
     constexpr int H = NSW, HL = tbr_halo_x(NSW), RW = 64, RH = NW * R, TX = RW - 2 * HL,
@@ -906,6 +1009,9 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
     T *const sphi = stg + 5 * PL;                               // FIRST: phi with its ring
     __shared__ __align__(16) T xup[2][NW][RW];   // p2 of each warp's top row, for the warp above
     __shared__ __align__(16) T xdn[2][NW][RW];   // p4 of each warp's bottom row, for the warp below
+    // walk: p2 of the carried row (local row RH - H - 1) at each sweep, by tile parity
+    __shared__ __align__(16) T carry[WALK ? 2 : 1][WALK ? NSW : 1][RW];
+    constexpr int CW = (RH - H - 1) / R, CR = (RH - H - 1) % R;   // its warp and row in the warp
     const int lane = threadIdx.x, w = threadIdx.y;
     const int lx0 = 2 * lane, ly0 = w * R;
     static_assert(!FPREP || FIRST, "the prep pass is fused into the first launch of a step");
@@ -923,12 +1029,12 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
         auto plane = [&](int pl) -> const T * {
             return pl < 4 ? tl.src + pl * nn : (FIRST ? tl.q : tl.coef + (pl - 4) * nn);
         };
-        const int x0 = tl.x0, y0 = tl.y0;
+        const int x0 = tl.x0, ry = tl.ry0;
         const int gx = wrap_x(x0 - HL + lx0, nx, wide);
         const int gx1 = pairs ? gx + 1 : wrap_x(x0 - HL + lx0 + 1, nx, wide);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int gy = y0 - H + ly0 + r;
+            const int gy = ry + ly0 + r;
             T *c = stg + (ly0 + r) * RW + lx0;
             if (gy < 0 || gy >= ny) {
 #pragma unroll
@@ -952,7 +1058,7 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
             // then the ring (rows -1 and RH, columns -1 and 64) by all
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int gy = y0 - H + ly0 + r;
+                const int gy = ry + ly0 + r;
                 T *c = sphi + (ly0 + r + 1) * FW + lx0 + 2;
                 if (gy < -1 || gy > ny) {
                     *reinterpret_cast<V2 *>(c) = V2{T(0), T(0)};
@@ -977,7 +1083,7 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
                     ly = c < RH ? c : c - RH;
                     lx = c < RH ? -1 : RW;
                 }
-                const int gy = y0 - H + ly;
+                const int gy = ry + ly;
                 T *d = sphi + (ly + 1) * FW + lx + 2;
                 if (gy >= -1 && gy <= ny)
                     cp_async(d, phig + (long long)(gy + 1) * nx + wrap_x(x0 - HL + lx, nx, wide));
@@ -995,7 +1101,8 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
     // electrode row (block-uniform), which adds the wall links.  ch = half of
     // the coefficients A, Bx, By (exact), so X/6 = chA - chBx m1 - chBy m2.
     auto sweeps = [&](auto edge, int gy0, T (&g1)[R][2], T (&g2)[R][2], T (&g3)[R][2], T (&g4)[R][2],
-                      const T (&chA)[R][2], const T (&chBx)[R][2], const T (&chBy)[R][2], T (&psi_before)[R][2]) {
+                      const T (&chA)[R][2], const T (&chBx)[R][2], const T (&chBy)[R][2], T (&psi_before)[R][2],
+                      bool carry_in, int cpar) {
         constexpr bool EDGE = decltype(edge)::value;
 #pragma unroll
         for (int s = 0; s < NSW; ++s, ++sw) {
@@ -1058,6 +1165,9 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
             }
             const int b = sw & 1;
             *reinterpret_cast<V2 *>(&xup[b][w][lx0]) = V2{p2[R - 1][0], p2[R - 1][1]};
+            if constexpr (WALK) {
+                if (w == CW) *reinterpret_cast<V2 *>(&carry[cpar][s][lx0]) = V2{p2[CR][0], p2[CR][1]};
+            }
             *reinterpret_cast<V2 *>(&xdn[b][w][lx0]) = V2{p4[0][0], p4[0][1]};
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -1071,6 +1181,9 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
             __syncthreads();
             if (w > 0) {
                 const V2 v = *reinterpret_cast<const V2 *>(&xup[b][w - 1][lx0]);
+                add_pair(g2[0][0], g2[0][1], v.x, v.y, -wG);
+            } else if (WALK && carry_in) {   // the previous tile's row below, at this sweep
+                const V2 v = *reinterpret_cast<const V2 *>(&carry[cpar ^ 1][s][lx0]);
                 add_pair(g2[0][0], g2[0][1], v.x, v.y, -wG);
             } else {
                 g2[0][0] = g2[0][1] = T(0);   // below the region
@@ -1096,13 +1209,19 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
         }
     };
 
-    const int ntiles = J.count();
     TbrTile<T> cur;
-    if ((int)blockIdx.x < ntiles) {
-        cur = J.tile(blockIdx.x, TX, TY);
-        issue(cur);
+    bool have;
+    int t = blockIdx.x, ntiles = 0;
+    if constexpr (WALK) {
+        have = J.begin(cur);
+    } else {
+        ntiles = J.count();
+        have = t < ntiles;
+        if (have) cur = J.tile(t, TX, TY, H);
     }
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if (have) issue(cur);
+    T racc[2] = {T(0), T(0)};   // walk: the block's residual partials over its tiles
+    for (int ck = 0; have; ++ck) {
         const DevP<T> &P = *cur.P;
         const int nx = P.nx;
         const long long nn = P.nn;
@@ -1112,8 +1231,8 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
         kf = T(0.5) * (T(1) - P.s_free_g);
         ke = T(0.25) * P.s_free_g;
         wG = P.wG;
-        const int x0 = cur.x0, y0 = cur.y0;
-        const int gy0 = y0 - H + ly0;   // lattice row of this thread's row 0
+        const int x0 = cur.x0, ry = cur.ry0, oy0 = cur.y0, oy1 = cur.oy1;
+        const int gy0 = ry + ly0;   // lattice row of this thread's row 0
         cp_async_wait_all();
         T g1[R][2], g2[R][2], g3[R][2], g4[R][2], cA[R][2], cBx[R][2], cBy[R][2];
         if constexpr (FPREP) {
@@ -1149,7 +1268,7 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
                     if (gy >= 0 && gy < ny) {
                         qA = qa;
                         qB = qb;
-                        if (xout && ly >= H && ly < H + TY) {
+                        if (xout && gy >= oy0 && gy < oy1) {
                             // dphi of the output nodes and of the ghost rows they mirror into
                             T *drow = cur.dphig + (long long)(gy + 1) * nx;
                             drow[gxo] = dA;
@@ -1183,7 +1302,7 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
                     ly = c < RH ? c : c - RH;
                     lx = c < RH ? -1 : RW;
                 }
-                const int gy = y0 - H + ly;
+                const int gy = ry + ly;
                 T *dd = sphi + (ly + 1) * TBR_FW + lx + 2;
                 if (gy >= -1 && gy <= ny) {
                     const int ry = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
@@ -1260,10 +1379,14 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
             __syncthreads();      // phi read by all before it is refilled
         }
         TbrTile<T> nxt = cur;
-        if (t + (int)gridDim.x < ntiles) {
-            nxt = J.tile(t + gridDim.x, TX, TY);
-            issue(nxt);
+        bool more;
+        if constexpr (WALK) {
+            more = J.next(nxt);
+        } else {
+            more = t + (int)gridDim.x < ntiles;
+            if (more) nxt = J.tile(t + gridDim.x, TX, TY, H);
         }
+        if (more) issue(nxt);
 
         // halves of the coefficients (exact); the first launch stores them
         // so that the later ones load halves
@@ -1277,10 +1400,11 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
                 chBx[r][j] = f * cBx[r][j];
                 chBy[r][j] = f * cBy[r][j];
             }
-        if (y0 - H <= 0 || y0 - H + RH >= ny)
-            sweeps(std::true_type{}, gy0, g1, g2, g3, g4, chA, chBx, chBy, psi_before);
+        const bool cin = WALK && cur.carry;
+        if (ry <= 0 || ry + RH >= ny)
+            sweeps(std::true_type{}, gy0, g1, g2, g3, g4, chA, chBx, chBy, psi_before, cin, ck & 1);
         else
-            sweeps(std::false_type{}, gy0, g1, g2, g3, g4, chA, chBx, chBy, psi_before);
+            sweeps(std::false_type{}, gy0, g1, g2, g3, g4, chA, chBx, chBy, psi_before, cin, ck & 1);
 
         // ---- the output tile (and, FIRST, its coefficients); lx0 and HL
         // are even, so a lane's two nodes are both in the tile or both out ----
@@ -1290,7 +1414,7 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int ly = ly0 + r, gy = gy0 + r;
-            if (!xin || ly < H || ly >= H + TY || gy >= ny) continue;
+            if (!xin || gy < oy0 || gy >= oy1 || gy >= ny) continue;
             const int k = gy * nx + gxo;
             auto st2 = [&](T *base, const T(&v)[R][2]) {
                 if (pairs) {
@@ -1321,9 +1445,19 @@ __device__ __forceinline__ void tbr_run(const Tiles &J)
                 }
             }
         }
-        if (RESID) block_sum_store_at<T, 2>(red, cur.part, cur.slot);
+        if constexpr (RESID) {
+            if constexpr (WALK) {
+                racc[0] += red[0];
+                racc[1] += red[1];
+            } else {
+                block_sum_store_at<T, 2>(red, cur.part, cur.slot);
+            }
+        }
         cur = nxt;
+        have = more;
+        t += gridDim.x;
     }
+    if constexpr (WALK && RESID) block_sum_store_at<T, 2>(racc, J.part, (long long)blockIdx.x);
     cp_async_wait_all();
 }
 
@@ -1334,8 +1468,23 @@ __global__ void __launch_bounds__(32 * NW, MINB)
                 double *__restrict__ part, const Control *__restrict__ ctl, int m, int tiles_x, int ntiles)
 {
     const int par = (ctl->cur0 + m) & 1;
-    const TbrLatticeTiles<T> J{&P, par ? gB : gA, par ? gA : gB, phig, q, coef, part, tiles_x, ntiles};
+    TbrLatticeTiles<T> J{&P, par ? gB : gA, par ? gA : gB, phig, q, coef, part, tiles_x, ntiles};
     tbr_run<T, NSW, R, NW, FIRST, RESID>(J);
+}
+
+// The register-blocked sweeps in the walking order (TbrWalkTiles): grid =
+// resident blocks, each walking its share of the strip rows; residual
+// partials in one slot per block.
+template <typename T, int NSW, int R, int NW, int MINB, bool FIRST, bool RESID>
+__global__ void __launch_bounds__(32 * NW, MINB)
+    k_sweep_tbw(const __grid_constant__ DevP<T> P, T *__restrict__ gA, T *__restrict__ gB,
+                const T *__restrict__ phig, const T *__restrict__ q, T *__restrict__ coef,
+                double *__restrict__ part, const Control *__restrict__ ctl, int m, int nstrips)
+{
+    const int par = (ctl->cur0 + m) & 1;
+    constexpr int H = NSW, HL = tbr_halo_x(NSW), RH = NW * R;
+    TbrWalkTiles<T> J{&P, par ? gB : gA, par ? gA : gB, phig, q, coef, part, nstrips, RH, H, 64 - 2 * HL, 0};
+    tbr_run<T, NSW, R, NW, FIRST, RESID, false, true>(J);
 }
 
 // The first sweep launch of a step with the prep pass fused (tbr_run FPREP):

@@ -591,7 +591,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     // float: shape 2 is the cluster kernel (k_sweep_cl), 2 x 4 CTAs of 64 x 32;
     // shapes 4 and 5 are register-blocked (by = warps, r = rows per warp),
     // 64 x 32 and 64 x 40
-    static constexpr int TB_NSHAPES = sizeof(T) == 4 ? 7 : 1;
+    static constexpr int TB_NSHAPES = sizeof(T) == 4 ? 8 : 1;
     static constexpr int CL_X = 2, CL_Y = 4, CL_BY = 16;
     static constexpr TbShape tb_shape(int i)
     {
@@ -602,6 +602,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         case 4: return TbShape{64, 32, 8, 2, 4};
         case 5: return TbShape{64, 40, 8, 2, 5};
         case 6: return TbShape{64, 40, 8, 2, 5};   // shape 5 with the prep pass in its first launch
+        case 7: return TbShape{64, 40, 8, 2, 5};   // shape 5 in the walking order (TbrWalkTiles)
         default: return TbShape{64, 32, 16, 3, 0};
         }
     }
@@ -615,7 +616,8 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         }
         const TbShape sh = tb_shape(shape);
         const int tx = sh.rw - 2 * (sh.r ? tbr_halo_x(nsw) : nsw), ty = sh.rh - 2 * nsw;
-        return dim3((nx + tx - 1) / tx, (ny + ty - 1) / ty);
+        // register-blocked regions need no halo at the electrode walls (tbr_rows)
+        return dim3((nx + tx - 1) / tx, sh.r ? tbr_tile_rows(ny, sh.rh, nsw) : (ny + ty - 1) / ty);
     }
 
     // The staged step kernel runs for float arithmetic on float or FP16
@@ -711,6 +713,10 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             if (e == cudaSuccess) e = tb_attr1<NSW, 3>();
             if (e == cudaSuccess) e = tbr_attr1<NSW, 4>();
             if (e == cudaSuccess) e = tbr_attr1<NSW, 5>();
+            if (e == cudaSuccess) e = tbw_attr2<NSW, false, false>();
+            if (e == cudaSuccess) e = tbw_attr2<NSW, false, true>();
+            if (e == cudaSuccess) e = tbw_attr2<NSW, true, false>();
+            if (e == cudaSuccess) e = tbw_attr2<NSW, true, true>();
             if (e == cudaSuccess) e = tbr_fp_attr<NSW, false>();
             if (e == cudaSuccess) e = tbr_fp_attr<NSW, true>();
             if (e == cudaSuccess) e = cl_attr2<NSW, false, false>();
@@ -766,6 +772,41 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             return e;
         }
         return cudaSuccess;
+    }
+
+    // the walking order (shape 7)
+    template <int NSW, bool FIRST, bool RESID> cudaError_t tbw_attr2()
+    {
+        if constexpr (TB_NSHAPES > 7) {
+            constexpr TbShape sh = tb_shape(7);
+            const size_t smem = tbr_smem_bytes<T, sh.r, sh.by>(FIRST);
+            auto kern = k_sweep_tbw<T, NSW, sh.r, sh.by, sh.minb, FIRST, RESID>;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int per = 0;
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * sh.by, smem);
+            if (e == cudaSuccess) tbr_per_sm_[1] = std::max(1, std::min(tbr_per_sm_[1], per));
+            return e;
+        }
+        return cudaSuccess;
+    }
+
+    // blocks of a walking launch of nsw sweeps: the resident blocks, at most
+    // the tiles of shape 5 (whose partial slots are allocated)
+    int tbw_blocks(int nsw) const
+    {
+        const dim3 g = tb_grid(nsw, 5, nx_, ny_);
+        return std::max(1, std::min((int)(g.x * g.y), tbr_per_sm_[1] * sms_));
+    }
+
+    template <int NSW, bool FIRST, bool RESID> void tbw_launch2()
+    {
+        if constexpr (TB_NSHAPES > 7) {
+            constexpr TbShape sh = tb_shape(7);
+            const int tx = 64 - 2 * tbr_halo_x(NSW);
+            k_sweep_tbw<T, NSW, sh.r, sh.by, sh.minb, FIRST, RESID>
+                <<<tbw_blocks(NSW), dim3(32, sh.by), tbr_smem_bytes<T, sh.r, sh.by>(FIRST), stream_>>>(
+                    dp_, g_[0], g_[1], phig_, q_, coef_, part2_, ctl_, tb_m_, (nx_ + tx - 1) / tx);
+        }
     }
 
     // prep fused into the first sweep launch of a fixed-count step
@@ -850,6 +891,14 @@ template <typename T, typename S = T> class Solver : public SolverBase {
                 tb_launch1<NSW, 3>(first, resid);
             } else if (tb_shape_ == 4) {
                 tbr_launch1<NSW, 4>(first, resid);
+            } else if (tb_shape_ == 7) {
+                if (first) {
+                    if (resid) tbw_launch2<NSW, true, true>();
+                    else tbw_launch2<NSW, true, false>();
+                } else {
+                    if (resid) tbw_launch2<NSW, false, true>();
+                    else tbw_launch2<NSW, false, false>();
+                }
             } else if (tb_shape_ == 5 || tb_shape_ == 6) {
                 if (first && fprep()) {
                     if (resid) tbr_fp_launch<NSW, true>(fp_fixedK_, fp_flips_);
@@ -998,8 +1047,9 @@ template <typename T, typename S = T> class Solver : public SolverBase {
 #undef EHDLB_MAIN1
         long long nb2 = 0;
         if (resid_mode == 2) {
-            const dim3 g = tb_grid(std::min(chunk, fixedK - (nk - 1) * chunk), tb_shape_, nx_, ny_);
-            nb2 = (long long)g.x * g.y;
+            const int nsw = std::min(chunk, fixedK - (nk - 1) * chunk);
+            const dim3 g = tb_grid(nsw, tb_shape_, nx_, ny_);
+            nb2 = tb_shape_ == 7 ? tbw_blocks(nsw) : (long long)g.x * g.y;
         }
         // sums of the block partials in two stages (PSUM blocks, then one)
         const double *p4 = part_, *p2 = part2_;

@@ -296,7 +296,7 @@ def test_fp32_every_sweep_tuning_matches_oracle():
     orc = oracle.Oracle(nx, ny, prm)
     orc.step(steps)
     ref = orc.fields()
-    for shape in range(7):
+    for shape in range(8):
         for spl in (0, 1, 2, 3, 4, 5):
             lat = ehdlb.Lattice(nx, ny, prm, precision=ehdlb.FP32)
             ehdlb.ehdlb_set_tuning(lat.ctx, spl, shape, spl % 4)
@@ -307,6 +307,27 @@ def test_fp32_every_sweep_tuning_matches_oracle():
                 assert_close(err, FP32_U_TOL, keys=["u"])
             except AssertionError as e:
                 raise AssertionError(f"shape {shape}, {spl} sweeps per launch: {e}") from None
+
+
+@pytest.mark.parametrize("nx,ny", [(136, 97), (64, 41), (48, 70), (40, 71), (66, 40)])
+def test_sweep_kernels_give_the_same_bits(nx, ny):
+    # the shared-memory, register-blocked (regions of 64 x 32 and 64 x 40,
+    # the latter without halo rows at the electrode walls), fused-prep and
+    # walking (two and five sweeps per launch) sweep kernels do the same
+    # arithmetic per node, so the same bits; ny around the region heights and
+    # their multiples minus the wall rows
+    prm = workloads.droplet(128)
+    prm.update(xc=(nx - 1) / 2, yc=(ny - 1) / 2, R=min(nx, ny) / 4, Kq=5.6893 / (nx * ny))
+    out = {}
+    for shape in (1, 4, 5, 6, 7):
+        for spl in ((2, 5) if shape == 7 else (5,)):
+            lat = ehdlb.Lattice(nx, ny, prm, precision=ehdlb.FP32)
+            ehdlb.ehdlb_set_tuning(lat.ctx, spl, shape, -1)
+            lat.step(6)
+            out[shape, spl] = lat.state()
+            lat.close()
+    for key in out:
+        assert np.array_equal(out[key], out[1, 5]), key
 
 
 @pytest.mark.parametrize("nx,ny", [(256, 256), (136, 97), (45, 66), (66, 45), (13, 7), (8, 8)])
@@ -369,7 +390,7 @@ def test_fp32_register_blocked_sweeps_on_narrow_lattices(nx, ny):
     orc = oracle.Oracle(nx, ny, prm)
     orc.step(steps)
     ref = orc.fields()
-    for shape in (1, 4, 5, 6):
+    for shape in (1, 4, 5, 6, 7):
         lat = ehdlb.Lattice(nx, ny, prm, precision=ehdlb.FP32)
         ehdlb.ehdlb_set_tuning(lat.ctx, 5, shape, -1)
         lat.step(steps)
@@ -476,7 +497,7 @@ def test_error_codes():
                                            sweep_tol=0.0, init_sweeps_max=10))
     assert L.ehdlb_set_params(h, ehdlb.C.byref(good)) == ehdlb.OK
     assert L.ehdlb_set_tuning(h, 6, 0, 0) == ehdlb.EINVAL
-    assert L.ehdlb_set_tuning(h, 2, 7, 0) == ehdlb.EINVAL
+    assert L.ehdlb_set_tuning(h, 2, 8, 0) == ehdlb.EINVAL
     assert L.ehdlb_set_tuning(h, 2, 0, 4) == ehdlb.EINVAL
     assert L.ehdlb_set_tuning(h, -1, -1, -1) == ehdlb.OK
     assert L.ehdlb_step(h, 2, ehdlb.C.byref(st)) == ehdlb.WNOTCONV
