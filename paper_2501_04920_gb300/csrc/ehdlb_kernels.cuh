@@ -866,6 +866,7 @@ template <typename T> struct TbrTile {
     int ry0;   // lattice row of the region's first row
     int oy1;   // end of the output rows [y0, oy1)
     int carry; // walk: the row below the region was the previous tile's (its upward flux is carried)
+    int strip; // walk: the tile's strip of columns
 };
 
 // Rows of tile row ty of a lattice of ny rows for regions of RH rows and H
@@ -930,37 +931,37 @@ template <typename T> struct TbrWalkTiles {
     double *part;
     int nstrips;
     int RH, H, TX;
-    long long p1;   // end of this block's rows in the sequence
+    int p1;   // end of this block's rows in the sequence (nstrips ny < 2^31)
     __device__ void at(TbrTile<T> &t, int strip, int row, bool carry) const
     {
         t = TbrTile<T>{P, src, dst, phig, q, coef, part, (long long)blockIdx.x, strip * TX, row};
         const int ny = P->ny;
         t.carry = carry;
+        t.strip = strip;
         t.ry0 = carry ? row : (row > H ? row - H : 0);   // at most H rows from the wall: start at it
         int oy1 = t.ry0 + RH >= ny ? ny : t.ry0 + RH - H;
-        const long long pend = p1 - (long long)strip * ny;   // the block's end in this strip's rows
-        if (pend < oy1) oy1 = (int)pend;
+        const int pend = p1 - strip * ny;   // the block's end in this strip's rows
+        if (pend < oy1) oy1 = pend;
         t.oy1 = oy1;
     }
     __device__ bool begin(TbrTile<T> &t)
     {
         const int ny = P->ny;
         const long long T_ = (long long)nstrips * ny;
-        const long long p0 = T_ * blockIdx.x / gridDim.x;
-        p1 = T_ * (blockIdx.x + 1) / gridDim.x;
+        const int p0 = (int)(T_ * blockIdx.x / gridDim.x);
+        p1 = (int)(T_ * (blockIdx.x + 1) / gridDim.x);
         if (p0 >= p1) return false;
-        at(t, (int)(p0 / ny), (int)(p0 % ny), false);
+        const int strip = p0 / ny;
+        at(t, strip, p0 - strip * ny, false);
         return true;
     }
     // the tile after t (which it overwrites); false at the block's end
     __device__ bool next(TbrTile<T> &t) const
     {
         const int ny = P->ny;
-        const int strip = t.x0 / TX;
-        const long long pe = (long long)strip * ny + t.oy1;
-        if (pe >= p1) return false;
-        if (t.oy1 >= ny) at(t, strip + 1, 0, false);
-        else at(t, strip, t.oy1, true);
+        if (t.strip * ny + t.oy1 >= p1) return false;
+        if (t.oy1 >= ny) at(t, t.strip + 1, 0, false);
+        else at(t, t.strip, t.oy1, true);
         return true;
     }
 };
