@@ -406,8 +406,8 @@ def run_ours(args):
     sweeps_per_launch = SWEEPS / sweep_launches_per_step
 
     # Every kernel class of a step.  hbm: bytes per node of the byte model
-    # (56 s + 24 for the f, h, p, n update and the carried
-    # scalars; 10 s + 8 per potential sweep) and the DRAM bytes ncu measured
+    # (56 s + 24 for the f, h, p, n update and the carried scalars, s the
+    # storage bytes of a population; 10 s + 8 per potential sweep) and the DRAM bytes ncu measured
     # for the current kernel source, each over the class's device time per
     # step, against the measured copy bandwidth.  The fused sweeps keep five
     # sweeps on chip per DRAM round trip, so their model bytes are no floor

@@ -281,12 +281,20 @@ int ehdlb_set_timing(ehdlb_ctx *c, int on);
  *     (512 threads), 4: 64 x 32 and 5: 64 x 40 (persistent blocks of 256
  *     threads, each thread holding the populations of 2 x 4 or 2 x 5 nodes
  *     in registers; populations cross lanes by warp shuffles and warps
- *     through shared memory; 5 is the default for float); 1 to 5 float
- *     only;
+ *     through shared memory; 5 is the default for float), 6: shape 5 with
+ *     the pass that forms phi, grad phi and q fused into the first sweep
+ *     launch of a step (float storage, D2Q5 ions, no side walls and a fixed
+ *     sweep count; else shape 5), 7: shape 5 with each block walking its
+ *     tiles down a column strip and keeping the upward flux of the row
+ *     under a region in shared memory; 1 to 7 float only;
  *   main_staging: how the step kernel copies its block's populations to
  *     shared memory, 0: one asynchronous copy per node and plane, 1: 16-byte
- *     copies of row segments (default; used only when nx times the element
- *     size is a multiple of 16 bytes, else 0).
+ *     copies of row segments (used only when nx times the element size is a
+ *     multiple of 16 bytes, else 0; default for double), 2: tensor-memory-
+ *     accelerator loads of the block's tile behind one mbarrier, one tile
+ *     per block (default for float), 3: the same in persistent blocks with
+ *     two stages; 2 and 3 need float compute, D2Q5 ions, no side walls and
+ *     nx times the element size a multiple of 16 bytes, else 1.
  * -1 keeps a setting.  EINVAL outside these ranges. */
 int ehdlb_set_tuning(ehdlb_ctx *c, int sweeps_per_launch, int tile_shape, int main_staging);
 
