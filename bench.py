@@ -72,6 +72,8 @@ SWEEP_KERNELS = {
     3: ("k_sweep_tb", "potential sweeps fused in shared memory, 64 x 64 regions"),
     4: ("k_sweep_tbr", "potential sweeps fused in registers, persistent, 64 x 32 regions"),
     5: ("k_sweep_tbr", "potential sweeps fused in registers, persistent, 64 x 40 regions"),
+    6: ("k_sweep_tbr_fp", "potential sweeps fused in registers, 64 x 40 regions, the prep pass in the first launch"),
+    7: ("k_sweep_tbw", "potential sweeps fused in registers, 64 x 40 regions walked down column strips"),
 }
 
 PRECISIONS = {"fp32": ("FP32", 4, "f32"), "fp16s": ("FP16 storage, FP32 arithmetic", 2, "f32"),
