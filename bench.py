@@ -119,32 +119,53 @@ def dist_info():
 
 
 class ClockSampler:
-    """nvidia-smi clock and throttle sampling during the timed region."""
+    """nvidia-smi clock and throttle sampling around the timed region: the
+    sampler runs every 50 ms from before the region (its first sample read
+    before the region starts) to after it; the summary takes the samples
+    received inside the region, or, for a region shorter than the sampling
+    period, the last one before it and the first one after it."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
 
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
-        self.lines: list[str] = []
+        self.lines: list[tuple[float, str]] = []
         self.proc = None
+        self.first = threading.Event()
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            self.first.wait(timeout=10.0)
         except OSError:
             self.proc = None
         return self
 
+    def start(self):
+        """Mark the start of the timed region."""
+        self.t0 = time.monotonic()
+
+    def stop(self):
+        """Mark its end; let one more sample arrive."""
+        self.t1 = time.monotonic()
+        if self.proc:
+            deadline = self.t1 + 3 * self.PERIOD_MS / 1e3
+            while time.monotonic() < deadline and not any(t > self.t1 for t, _ in self.lines[-2:]):
+                time.sleep(0.005)
+
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+            self.first.set()
 
     def __exit__(self, *a):
         if self.proc:
@@ -154,10 +175,21 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
+    def _chosen(self):
+        if self.t0 is None or self.t1 is None:
+            return [ln for _, ln in self.lines], "all"
+        inside = [ln for t, ln in self.lines if self.t0 <= t <= self.t1]
+        if inside:
+            return inside, "inside"
+        before = [ln for t, ln in self.lines if t < self.t0][-1:]
+        after = [ln for t, ln in self.lines if t > self.t1][:1]
+        return before + after, "bracketing"
+
     def summary(self):
         mhz, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines, how = self._chosen()
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -169,8 +201,11 @@ class ClockSampler:
             for nm, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
+        region_ms = (self.t1 - self.t0) * 1e3 if self.t0 is not None and self.t1 is not None else None
         return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(mhz)}
+                "reasons": sorted(reasons), "samples": len(mhz), "samples_taken": how,
+                "period_ms": self.PERIOD_MS,
+                "region_ms": round(region_ms, 1) if region_ms is not None else None}
 
 
 def reduce_max(value: float, device) -> float:
@@ -388,10 +423,12 @@ def run_ours(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize(dev)
+        clk.start()
         ev0.record(stream)
         status, st = lat.step(args.steps)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
+        clk.stop()
     barrier()
     ms = reduce_max(ev0.elapsed_time(ev1), dev)
     value = replica_value(nn, args.steps, world, ms / 1e3)

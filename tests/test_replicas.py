@@ -2,7 +2,8 @@
 
 The method runs one lattice per GPU with no exchange between them (replicas),
 so the only multi-rank logic is the max-over-ranks time and the whole-job
-value; both are checked here with world_size 2 over gloo.
+value; both are checked here with world_size 2 over gloo.  Also on CPU: which
+clock samples the bench reports for its timed region.
 """
 import os
 import socket
@@ -49,3 +50,29 @@ def test_two_replicas_take_the_slowest_rank():
         assert slowest == 15.0
         assert value == pytest.approx(2048 * 2048 * 100 * 2 / 0.015 / 1e6)
 
+
+
+def _clock_line(mhz, *reasons):
+    flags = ["Active" if nm in reasons else "Not Active"
+             for nm in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")]
+    return ", ".join(["0", str(mhz), "2070", "900.0", "0x0"] + flags)
+
+
+def test_clock_summary_takes_the_samples_of_the_timed_region():
+    # samples inside [start, stop] when there are any; for a region shorter
+    # than the sampling period the samples just before and just after it;
+    # throttle reasons from those samples only
+    import bench
+    clk = bench.ClockSampler(0)
+    clk.lines = [(0.0, _clock_line(1200, "hw_slowdown")), (1.0, _clock_line(2070)),
+                 (1.1, _clock_line(2040, "sw_power_cap")), (1.2, _clock_line(2070)),
+                 (2.0, _clock_line(900, "hw_thermal_slowdown"))]
+    clk.t0, clk.t1 = 0.95, 1.15
+    s = clk.summary()
+    assert s["samples"] == 2 and s["samples_taken"] == "inside"
+    assert s["sm_mhz"] == 2055.0 and s["reasons"] == ["sw_power_cap"]
+    clk.t0, clk.t1 = 1.15, 1.16
+    s = clk.summary()
+    assert s["samples_taken"] == "bracketing" and s["samples"] == 2
+    assert s["sm_mhz"] == 2055.0 and s["reasons"] == ["sw_power_cap"]
+    assert abs(s["region_ms"] - 10.0) < 1e-6
