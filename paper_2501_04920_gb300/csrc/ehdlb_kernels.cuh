@@ -1468,6 +1468,11 @@ __global__ void __launch_bounds__(32 * NW, MINB)
                 const T *__restrict__ phig, const T *__restrict__ q, T *__restrict__ coef,
                 double *__restrict__ part, const Control *__restrict__ ctl, int m, int tiles_x, int ntiles)
 {
+    // launched as a programmatic dependent of the previous sweep launch: wait
+    // for it (all its memory operations) before touching memory, and let the
+    // next launch be scheduled while this one runs
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int par = (ctl->cur0 + m) & 1;
     TbrLatticeTiles<T> J{&P, par ? gB : gA, par ? gA : gB, phig, q, coef, part, tiles_x, ntiles};
     tbr_run<T, NSW, R, NW, FIRST, RESID>(J);

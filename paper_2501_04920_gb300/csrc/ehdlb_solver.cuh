@@ -845,9 +845,22 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         const dim3 g = tb_grid(NSW, SH, nx_, ny_);
         const int ntiles = (int)(g.x * g.y);
         const int grid = std::min(ntiles, tbr_per_sm_[SH - 4] * sms_);
-        k_sweep_tbr<T, NSW, sh.r, sh.by, sh.minb, FIRST, RESID>
-            <<<grid, dim3(32, sh.by), tbr_smem_bytes<T, sh.r, sh.by>(FIRST), stream_>>>(
-                dp_, g_[0], g_[1], phig_, q_, coef_, part2_, ctl_, tb_m_, (int)g.x, ntiles);
+        // a later launch of the step follows the previous sweep launch
+        // directly: it may be scheduled while that one drains (programmatic
+        // dependent launch); the kernel waits for it before any memory access
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(32, sh.by);
+        cfg.dynamicSmemBytes = tbr_smem_bytes<T, sh.r, sh.by>(FIRST);
+        cfg.stream = stream_;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = FIRST ? 0 : 1;
+        (void)cudaLaunchKernelEx(&cfg, k_sweep_tbr<T, NSW, sh.r, sh.by, sh.minb, FIRST, RESID>, dp_, g_[0], g_[1],
+                                 (const T *)phig_, (const T *)q_, coef_, part2_, (const Control *)ctl_, tb_m_,
+                                 (int)g.x, ntiles);
     }
 
     template <int NSW, int SH> void tbr_launch1(bool first, bool resid)
