@@ -157,7 +157,8 @@ typedef struct ehdlb_stats {
     double seconds;           /* wall time of the call */
     double mlups;             /* nx ny steps / seconds / 1e6 */
     double ms_prep, ms_sweeps, ms_main;  /* device time per kernel class when
-                                            timing is on (ehdlb_set_timing) */
+                                            timing is on (ehdlb_set_timing),
+                                            over all steps of the call */
     long long launches;       /* kernels launched by the call */
     long long sweep_launches; /* of which potential-sweep kernels */
     int sweeps_per_launch;    /* fused sweeps per launch (0: one sweep per launch) */
@@ -266,8 +267,14 @@ size_t ehdlb_state_len(const ehdlb_ctx *c);
 int ehdlb_get_state(ehdlb_ctx *c, double *dst, size_t len);
 int ehdlb_set_state(ehdlb_ctx *c, const double *src, size_t len);
 
-/* Record device time per kernel class in ehdlb_stats (1) or not (0). */
-int ehdlb_set_timing(ehdlb_ctx *c, int on);
+/* Device time per kernel class in ehdlb_stats (ms_prep, ms_sweeps, ms_main):
+ * every > 0 records CUDA events around the kernel classes of every every-th
+ * step of a call (its first step, then every every-th) and scales their sums
+ * to all the call's steps; 0 records none (the default).  A recorded step
+ * runs a few microseconds longer: its events stand between kernels that
+ * otherwise start as programmatic dependents of their predecessors.
+ * EINVAL if every < 0. */
+int ehdlb_set_timing(ehdlb_ctx *c, int every);
 
 /* Performance knobs; none changes the result beyond round-off.
  *   sweeps_per_launch: potential sweeps the fused sweep kernel computes in

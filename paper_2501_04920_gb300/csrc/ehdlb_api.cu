@@ -238,10 +238,11 @@ int ehdlb_set_state(ehdlb_ctx *c, const double *src, size_t len)
     return c->solver->set_state(src, c->err);
 }
 
-int ehdlb_set_timing(ehdlb_ctx *c, int on)
+int ehdlb_set_timing(ehdlb_ctx *c, int every)
 {
     if (!c) return EHDLB_EINVAL;
-    c->solver->set_timing(on);
+    if (every < 0) return fail(c, EHDLB_EINVAL, "timing stride must be >= 0");
+    c->solver->set_timing(every);
     return EHDLB_OK;
 }
 

@@ -117,6 +117,17 @@ struct Control {
     int fault;         // a staged copy did not arrive in time (k_main_tma)
 };
 
+// Programmatic dependent launch: a kernel launched as a dependent of the
+// previous kernel in its stream may be scheduled before that one finishes; it
+// waits here for it (and all its memory operations) before touching memory,
+// then lets its own dependents be scheduled.  In a kernel launched without
+// that attribute both instructions have no effect.
+__device__ __forceinline__ void griddep_begin()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Opens an ehdlb_step call: zeroes its per-call counters (launch: 1 thread).
 static __global__ void k_open_call(Control *c)
 {
@@ -465,6 +476,7 @@ __global__ void __launch_bounds__(256) k_prep(const DevP<T> P, const S *__restri
                                               const PhiRef<T> R, T *__restrict__ phig, T *__restrict__ q,
                                               Control *ctl, int fixedK, int kmin, int kmax, int flips)
 {
+    griddep_begin();
     prep_body<T, S, QI, VN>(P, h, p, n, R, phig, q, ctl, fixedK, kmin, kmax, flips, blockIdx.x, blockIdx.y);
 }
 
@@ -1468,11 +1480,7 @@ __global__ void __launch_bounds__(32 * NW, MINB)
                 const T *__restrict__ phig, const T *__restrict__ q, T *__restrict__ coef,
                 double *__restrict__ part, const Control *__restrict__ ctl, int m, int tiles_x, int ntiles)
 {
-    // launched as a programmatic dependent of the previous sweep launch: wait
-    // for it (all its memory operations) before touching memory, and let the
-    // next launch be scheduled while this one runs
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    griddep_begin();
     const int par = (ctl->cur0 + m) & 1;
     TbrLatticeTiles<T> J{&P, par ? gB : gA, par ? gA : gB, phig, q, coef, part, tiles_x, ntiles};
     tbr_run<T, NSW, R, NW, FIRST, RESID>(J);
@@ -2538,6 +2546,7 @@ __global__ void __launch_bounds__(256, MAIN_MINB<T>)
                 const T *__restrict__ psi_prev, T *__restrict__ snap, double *__restrict__ part,
                 int *__restrict__ unstable, int *__restrict__ fault)
 {
+    griddep_begin();
     using L = TmaLayout<T, S>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -2589,6 +2598,7 @@ __global__ void __launch_bounds__(256, MAIN_MINB<T>)
 template <int NV>
 __global__ void __launch_bounds__(256) k_partials(const double *__restrict__ part, long long nb, double *out)
 {
+    griddep_begin();
     __shared__ double red[256][NV];
     double acc[NV];
 #pragma unroll
@@ -2650,6 +2660,7 @@ static __global__ void __launch_bounds__(256) k_step_end(const double *__restric
                                                          const double *__restrict__ part2, long long nb2,
                                                          Control *ctl, int *counts, int resid, int sums)
 {
+    griddep_begin();
     step_end_body(part, nb, part2, nb2, ctl, counts, resid, sums);
 }
 

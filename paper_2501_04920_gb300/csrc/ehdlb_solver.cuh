@@ -234,7 +234,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         stall_ = true;
         return EHDLB_OK;
     }
-    void set_timing(int on) override { timing_ = on != 0; }
+    void set_timing(int every) override { timing_ = every > 0 ? every : 0; }
     void set_tuning(int sweeps_per_launch, int shape, int vec_staging) override
     {
         if (sweeps_per_launch >= 0) tb_chunk_ = sweeps_per_launch;
@@ -298,7 +298,9 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             st->mlups = secs > 0 ? (double)nn_ * nsteps / secs / 1e6 : 0.0;
             st->ms_prep = st->ms_sweeps = st->ms_main = 0.0;
             if (timing_) {
-                for (int s = 0; s < nsteps; ++s) {
+                // the recorded steps, scaled to all steps of the call
+                int nrec = 0;
+                for (int s = 0; s < nsteps; s += timing_) {
                     float a = 0, b = 0, c = 0;
                     cudaEventElapsedTime(&a, events_[4 * s], events_[4 * s + 1]);
                     cudaEventElapsedTime(&b, events_[4 * s + 1], events_[4 * s + 2]);
@@ -306,6 +308,13 @@ template <typename T, typename S = T> class Solver : public SolverBase {
                     st->ms_prep += a;
                     st->ms_sweeps += b;
                     st->ms_main += c;
+                    ++nrec;
+                }
+                if (nrec > 0) {
+                    const double f = (double)nsteps / nrec;
+                    st->ms_prep *= f;
+                    st->ms_sweeps *= f;
+                    st->ms_main *= f;
                 }
             }
             st->launches = launches_;
@@ -558,26 +567,39 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         dp_ = d;
     }
 
+    // launch kernel k on the solver's stream; dep: as a programmatic
+    // dependent of the previous kernel in the stream (k waits for it first
+    // thing, griddep_begin), so that it may be scheduled while that one drains
+    template <typename... P, typename... A>
+    void launch_k(void (*k)(P...), dim3 grid, dim3 block, size_t smem, bool dep, A &&...args)
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = stream_;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = dep ? 1 : 0;
+        (void)cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+    }
+
     void launch_prep(int par, int fixedK, int kmin, int kmax, int flips)
     {
         // four nodes per thread (one vector load per plane) when rows split
         // into aligned fours
         const bool v4 = nx_ % 4 == 0;
         const dim3 g = v4 ? dim3((nx_ / 4 + BX - 1) / BX, grid_.y) : grid_;
+        const Pops<S> &pp = pops_[par];
+        const dim3 b(BX, BY);
         if (qi_ == 9) {
-            if (v4)
-                k_prep<T, S, 9, 4><<<g, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n,
-                                                                   ref_, phig_, q_, ctl_, fixedK, kmin, kmax, flips);
-            else
-                k_prep<T, S, 9, 1><<<g, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n,
-                                                                   ref_, phig_, q_, ctl_, fixedK, kmin, kmax, flips);
+            if (v4) launch_k(k_prep<T, S, 9, 4>, g, b, 0, true, dp_, pp.h, pp.p, pp.n, ref_, phig_, q_, ctl_, fixedK, kmin, kmax, flips);
+            else launch_k(k_prep<T, S, 9, 1>, g, b, 0, true, dp_, pp.h, pp.p, pp.n, ref_, phig_, q_, ctl_, fixedK, kmin, kmax, flips);
         } else {
-            if (v4)
-                k_prep<T, S, 5, 4><<<g, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n,
-                                                                   ref_, phig_, q_, ctl_, fixedK, kmin, kmax, flips);
-            else
-                k_prep<T, S, 5, 1><<<g, dim3(BX, BY), 0, stream_>>>(dp_, pops_[par].h, pops_[par].p, pops_[par].n,
-                                                                   ref_, phig_, q_, ctl_, fixedK, kmin, kmax, flips);
+            if (v4) launch_k(k_prep<T, S, 5, 4>, g, b, 0, true, dp_, pp.h, pp.p, pp.n, ref_, phig_, q_, ctl_, fixedK, kmin, kmax, flips);
+            else launch_k(k_prep<T, S, 5, 1>, g, b, 0, true, dp_, pp.h, pp.p, pp.n, ref_, phig_, q_, ctl_, fixedK, kmin, kmax, flips);
         }
         ++launches_;
     }
@@ -845,22 +867,9 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         const dim3 g = tb_grid(NSW, SH, nx_, ny_);
         const int ntiles = (int)(g.x * g.y);
         const int grid = std::min(ntiles, tbr_per_sm_[SH - 4] * sms_);
-        // a later launch of the step follows the previous sweep launch
-        // directly: it may be scheduled while that one drains (programmatic
-        // dependent launch); the kernel waits for it before any memory access
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(grid);
-        cfg.blockDim = dim3(32, sh.by);
-        cfg.dynamicSmemBytes = tbr_smem_bytes<T, sh.r, sh.by>(FIRST);
-        cfg.stream = stream_;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        at[0].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = FIRST ? 0 : 1;
-        (void)cudaLaunchKernelEx(&cfg, k_sweep_tbr<T, NSW, sh.r, sh.by, sh.minb, FIRST, RESID>, dp_, g_[0], g_[1],
-                                 (const T *)phig_, (const T *)q_, coef_, part2_, (const Control *)ctl_, tb_m_,
-                                 (int)g.x, ntiles);
+        launch_k(k_sweep_tbr<T, NSW, sh.r, sh.by, sh.minb, FIRST, RESID>, dim3(grid), dim3(32, sh.by),
+                 tbr_smem_bytes<T, sh.r, sh.by>(FIRST), true, dp_, g_[0], g_[1], phig_, q_, coef_, part2_, ctl_,
+                 tb_m_, (int)g.x, ntiles);
     }
 
     template <int NSW, int SH> void tbr_launch1(bool first, bool resid)
@@ -977,7 +986,8 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         // cases; with side walls every sweep is its own launch
         const bool fused = !converge && fixedK > 0 && chunk > 0 && !P_.side_walls;
         const int nk = fused ? (fixedK + chunk - 1) / chunk : (converge ? 0 : fixedK);
-        if (timing_) cudaEventRecord(events_[4 * s], stream_);
+        const bool tev = timing_ > 0 && s % timing_ == 0;   // this step's kernel classes are timed
+        if (tev) cudaEventRecord(events_[4 * s], stream_);
         const bool fp = fused && fprep();
         if (fp) {
             fp_fixedK_ = fixedK;   // the first sweep launch does the prep pass
@@ -985,7 +995,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         } else {
             launch_prep(par, fixedK, kmin, kmax, nk);
         }
-        if (timing_) cudaEventRecord(events_[4 * s + 1], stream_);
+        if (tev) cudaEventRecord(events_[4 * s + 1], stream_);
         if (fused) {
             for (int m = 0, done = 0; m < nk; ++m) {
                 const int nsw = std::min(chunk, fixedK - done);
@@ -1001,7 +1011,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
                 ++launches_;
             }
         }
-        if (timing_) cudaEventRecord(events_[4 * s + 2], stream_);
+        if (tev) cudaEventRecord(events_[4 * s + 2], stream_);
         const bool main_resid = !frozen && !fused && kmax >= 1 && (converge || last);
         const int resid_mode = main_resid ? 1 : ((fused && last) ? 2 : 0);
         const dim3 b(BX, BY);
@@ -1031,9 +1041,9 @@ template <typename T, typename S = T> class Solver : public SolverBase {
                     dp_, maps_[par], pops_[par], pops_[par ^ 1], g_[0], g_[1], ctl_, ref_, phiu_, psi_prev_, \
                     snap_, part_, unstable, &ctl_->fault, (int)grid_.x, ntiles);                         \
             else                                                                                         \
-                k_main_tma1<T, S, SN, F, R><<<grid_, b, TmaLayout<T, S>::stage, stream_>>>(                \
-                    dp_, maps_[par], pops_[par], pops_[par ^ 1], g_[0], g_[1], ctl_, ref_, phiu_, psi_prev_, \
-                    snap_, part_, unstable, &ctl_->fault);                                               \
+                launch_k(k_main_tma1<T, S, SN, F, R>, grid_, b, TmaLayout<T, S>::stage, true, dp_, maps_[par], \
+                         pops_[par], pops_[par ^ 1], g_[0], g_[1], ctl_, ref_, phiu_, psi_prev_, snap_, part_,   \
+                         unstable, &ctl_->fault);                                                        \
         }                                                                                                \
     } while (0)
         if (staged) {
@@ -1068,20 +1078,20 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         const double *p4 = part_, *p2 = part2_;
         long long n4 = nb_, n2 = nb2;
         if ((resid_mode == 1 || last) && nb_ > PSUM) {
-            k_partials<4><<<PSUM, 256, 0, stream_>>>(part_, nb_, red_);
+            launch_k(k_partials<4>, dim3(PSUM), dim3(256), 0, true, part_, nb_, red_);
             p4 = red_;
             n4 = PSUM;
             ++launches_;
         }
         if (resid_mode == 2 && nb2 > PSUM) {
-            k_partials<2><<<PSUM, 256, 0, stream_>>>(part2_, nb2, red_ + 4 * PSUM);
+            launch_k(k_partials<2>, dim3(PSUM), dim3(256), 0, true, part2_, nb2, red_ + 4 * PSUM);
             p2 = red_ + 4 * PSUM;
             n2 = PSUM;
             ++launches_;
         }
-        k_step_end<<<1, 256, 0, stream_>>>(p4, n4, p2, n2, ctl_, counts_, resid_mode, last ? 1 : 0);
+        launch_k(k_step_end, dim3(1), dim3(256), 0, true, p4, n4, p2, n2, ctl_, counts_, resid_mode, last ? 1 : 0);
         launches_ += 2;
-        if (timing_) cudaEventRecord(events_[4 * s + 3], stream_);
+        if (tev) cudaEventRecord(events_[4 * s + 3], stream_);
         tpar_ ^= 1;
         ++t_;
     }
@@ -1197,7 +1207,7 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     int tpar_ = 0;
     long long t_ = 0;
     int init_sweeps_ = 0;
-    bool timing_ = false;
+    int timing_ = 0;   // record the kernel classes of every timing_-th step (0: none)
     long long launches_ = 0;
     long long sweep_launches_ = 0;
 };

@@ -30,7 +30,7 @@ class SolverBase {
     virtual int get_state(double *dst, std::string &err) = 0;
     virtual int set_state(const double *src, std::string &err) = 0;
     virtual void set_schedule(const int *c, int n) = 0;
-    virtual void set_timing(int on) = 0;
+    virtual void set_timing(int every) = 0;
     virtual void set_tuning(int sweeps_per_launch, int shape, int vec_staging) = 0;
     virtual int deformation(double *out, std::string &err) = 0;
     // fields the last step of each call captures, and whether each call

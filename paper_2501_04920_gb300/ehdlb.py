@@ -233,8 +233,10 @@ def ehdlb_set_state(ctx, src: np.ndarray):
     return _check(ctx, lib().ehdlb_set_state(ctx, _dp(src), src.size), "ehdlb_set_state")
 
 
-def ehdlb_set_timing(ctx, on: bool):
-    return _check(ctx, lib().ehdlb_set_timing(ctx, 1 if on else 0), "ehdlb_set_timing")
+def ehdlb_set_timing(ctx, every):
+    """every: True / False, or record every n-th step (n >= 1; 0 off)."""
+    n = (1 if every else 0) if isinstance(every, bool) else int(every)
+    return _check(ctx, lib().ehdlb_set_timing(ctx, n), "ehdlb_set_timing")
 
 
 def ehdlb_potential_noalloc(nx, ny, p: ehdlb_params, phi_dev: int, q_dev: int, nsweeps: int,
