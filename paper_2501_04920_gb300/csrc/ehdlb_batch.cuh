@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(256) kb_prep(const CaseDev<T, S> *__restrict__
                                                const WorkItem *__restrict__ items, const int *__restrict__ nitems,
                                                int fixedK, int flips)
 {
+    griddep_begin();
     __shared__ CaseDev<T, S> C;
     const int n = *nitems;
     for (int it = blockIdx.x; it < n; it += gridDim.x) {
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(32 * BY, MINB) kb_sweep(const CaseDev<T, S> *_
                                                            const WorkItem *__restrict__ items,
                                                            const int *__restrict__ nitems, int m)
 {
+    griddep_begin();
     __shared__ CaseDev<T, S> C;
     const int n = *nitems;
     for (int it = blockIdx.x; it < n; it += gridDim.x) {
@@ -205,6 +207,7 @@ __global__ void __launch_bounds__(256, 2) kb_sweep_r(const CaseDev<T, S> *__rest
                                                      const WorkItem *__restrict__ items,
                                                      const int *__restrict__ nitems, int m)
 {
+    griddep_begin();
     TbrBatchTiles<T, S> J{cases, items, *nitems, m};
     tbr_run<T, NSW, R, 8, FIRST, false>(J);
 }
@@ -214,6 +217,7 @@ template <typename T, typename S, bool SNAP>
 __global__ void __launch_bounds__(256, MAIN_MINB<T>) kb_main(const CaseDev<T, S> *__restrict__ cases,
                                                   const WorkItem *__restrict__ items, const int *__restrict__ nitems)
 {
+    griddep_begin();
     __shared__ CaseDev<T, S> C;
     const int n = *nitems;
     for (int it = blockIdx.x; it < n; it += gridDim.x) {
@@ -236,6 +240,7 @@ template <typename T, typename S>
 __global__ void __launch_bounds__(256) kb_step_end(const CaseDev<T, S> *__restrict__ cases, const int *__restrict__ ncases,
                                                    int sums)
 {
+    griddep_begin();
     const int n = *ncases;
     for (int c = blockIdx.x; c < n; c += gridDim.x) {
         const CaseDev<T, S> *C = cases + c;
@@ -555,12 +560,12 @@ template <typename T, typename S> class Batch : public BatchBase {
         const int items = host_nitems_[NSW];
         if (m == 0) {
             const int g = pgrid(kb_sweep<T, S, NSW, BY, MINB, true>, 32 * BY, sm, items);
-            kb_sweep<T, S, NSW, BY, MINB, true><<<g, dim3(32, BY), sm, stream_>>>(d_cases_, d_items_tb_[NSW],
-                                                                                 d_nitems_ + NSW, m);
+            launch_k(stream_, kb_sweep<T, S, NSW, BY, MINB, true>, dim3(g), dim3(32, BY), sm, true, d_cases_,
+                     d_items_tb_[NSW], d_nitems_ + NSW, m);
         } else {
             const int g = pgrid(kb_sweep<T, S, NSW, BY, MINB, false>, 32 * BY, sm, items);
-            kb_sweep<T, S, NSW, BY, MINB, false><<<g, dim3(32, BY), sm, stream_>>>(d_cases_, d_items_tb_[NSW],
-                                                                                  d_nitems_ + NSW, m);
+            launch_k(stream_, kb_sweep<T, S, NSW, BY, MINB, false>, dim3(g), dim3(32, BY), sm, true, d_cases_,
+                     d_items_tb_[NSW], d_nitems_ + NSW, m);
         }
     }
 
@@ -570,12 +575,12 @@ template <typename T, typename S> class Batch : public BatchBase {
         const int items = host_nitems_[8 + NSW];
         if (m == 0) {
             const int g = pgrid(kb_sweep_r<T, S, NSW, TBR_R, true>, 256, sm, items);
-            kb_sweep_r<T, S, NSW, TBR_R, true><<<g, dim3(32, 8), sm, stream_>>>(d_cases_, d_items_tbr_[NSW],
-                                                                               d_nitems_ + 8 + NSW, m);
+            launch_k(stream_, kb_sweep_r<T, S, NSW, TBR_R, true>, dim3(g), dim3(32, 8), sm, true, d_cases_,
+                     d_items_tbr_[NSW], d_nitems_ + 8 + NSW, m);
         } else {
             const int g = pgrid(kb_sweep_r<T, S, NSW, TBR_R, false>, 256, sm, items);
-            kb_sweep_r<T, S, NSW, TBR_R, false><<<g, dim3(32, 8), sm, stream_>>>(d_cases_, d_items_tbr_[NSW],
-                                                                                d_nitems_ + 8 + NSW, m);
+            launch_k(stream_, kb_sweep_r<T, S, NSW, TBR_R, false>, dim3(g), dim3(32, 8), sm, true, d_cases_,
+                     d_items_tbr_[NSW], d_nitems_ + 8 + NSW, m);
         }
     }
 
@@ -590,8 +595,8 @@ template <typename T, typename S> class Batch : public BatchBase {
     {
         const int nk = (S_ + chunk_ - 1) / chunk_;
         const int items = host_nitems_[0];
-        kb_prep<T, S><<<pgrid(kb_prep<T, S>, 256, 0, items), dim3(64, 4), 0, stream_>>>(d_cases_, d_items_node_,
-                                                                                       d_nitems_, S_, nk);
+        launch_k(stream_, kb_prep<T, S>, dim3(pgrid(kb_prep<T, S>, 256, 0, items)), dim3(64, 4), 0, true, d_cases_,
+                 d_items_node_, d_nitems_, S_, nk);
         for (int m = 0, done = 0; m < nk; ++m) {
             const int nsw = std::min(chunk_, S_ - done);
             switch (nsw) {
@@ -605,12 +610,13 @@ template <typename T, typename S> class Batch : public BatchBase {
         }
         const size_t msm = main_smem_bytes<T, S>();
         if (last)
-            kb_main<T, S, true><<<pgrid(kb_main<T, S, true>, 256, msm, items), dim3(64, 4), msm, stream_>>>(
-                d_cases_, d_items_node_, d_nitems_);
+            launch_k(stream_, kb_main<T, S, true>, dim3(pgrid(kb_main<T, S, true>, 256, msm, items)), dim3(64, 4), msm,
+                     true, d_cases_, d_items_node_, d_nitems_);
         else
-            kb_main<T, S, false><<<pgrid(kb_main<T, S, false>, 256, msm, items), dim3(64, 4), msm, stream_>>>(
-                d_cases_, d_items_node_, d_nitems_);
-        kb_step_end<T, S><<<std::min(ncases_, 4 * sms_), 256, 0, stream_>>>(d_cases_, d_nitems_ + 6, last ? 1 : 0);
+            launch_k(stream_, kb_main<T, S, false>, dim3(pgrid(kb_main<T, S, false>, 256, msm, items)), dim3(64, 4),
+                     msm, true, d_cases_, d_items_node_, d_nitems_);
+        launch_k(stream_, kb_step_end<T, S>, dim3(std::min(ncases_, 4 * sms_)), dim3(256), 0, true, d_cases_,
+                 d_nitems_ + 6, last ? 1 : 0);
         launches_ += per_step_launches();
     }
 

@@ -40,6 +40,7 @@
 #include <stdint.h>
 
 #include <type_traits>
+#include <utility>
 
 namespace ehdlb {
 
@@ -126,6 +127,27 @@ __device__ __forceinline__ void griddep_begin()
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Host: launch kernel k on stream st; dep: as a programmatic dependent of the
+// previous kernel in the stream (k must call griddep_begin first), so that it
+// may be scheduled while that one drains.  Captured into a graph, the
+// dependency becomes a programmatic edge.
+template <typename... P, typename... A>
+inline cudaError_t launch_k(cudaStream_t st, void (*k)(P...), dim3 grid, dim3 block, size_t smem, bool dep,
+                            A &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = dep ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
 }
 
 // Opens an ehdlb_step call: zeroes its per-call counters (launch: 1 thread).

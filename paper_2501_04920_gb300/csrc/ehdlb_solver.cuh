@@ -567,23 +567,11 @@ template <typename T, typename S = T> class Solver : public SolverBase {
         dp_ = d;
     }
 
-    // launch kernel k on the solver's stream; dep: as a programmatic
-    // dependent of the previous kernel in the stream (k waits for it first
-    // thing, griddep_begin), so that it may be scheduled while that one drains
+    // launch kernel k on the solver's stream (dep: as a programmatic dependent)
     template <typename... P, typename... A>
     void launch_k(void (*k)(P...), dim3 grid, dim3 block, size_t smem, bool dep, A &&...args)
     {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = grid;
-        cfg.blockDim = block;
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = stream_;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        at[0].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = dep ? 1 : 0;
-        (void)cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+        (void)ehdlb::launch_k(stream_, k, grid, block, smem, dep, std::forward<A>(args)...);
     }
 
     void launch_prep(int par, int fixedK, int kmin, int kmax, int flips)
