@@ -483,6 +483,33 @@ def test_late_staged_copies_are_reported_and_the_context_recovers(staging):
     lat.close(); ref.close(); side.close()
 
 
+def test_kernel_class_timing_every_nth_step_and_same_bits():
+    # ehdlb_set_timing(c, n): CUDA events around the kernel classes of every
+    # n-th step, their sums scaled to all steps; the recorded steps' events
+    # stand between kernels that otherwise start as programmatic dependents,
+    # which changes the timing, not the results
+    n, steps = 256, 24
+    prm = workloads.droplet(n)
+    out = {}
+    for every in (0, 1, 5):
+        lat = ehdlb.Lattice(n, n, prm, precision=ehdlb.FP32)
+        ehdlb.ehdlb_set_timing(lat.ctx, every)
+        status, st = lat.step(steps)
+        assert status == ehdlb.OK
+        classes = st.ms_prep + st.ms_sweeps + st.ms_main
+        if every == 0:
+            assert classes == 0.0
+        else:
+            assert st.ms_prep > 0 and st.ms_sweeps > 0 and st.ms_main > 0
+            assert classes < 1e3 * st.seconds   # device time of the classes within the call's wall time
+        out[every] = lat.state()
+        lat.close()
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[5])
+    lat = ehdlb.Lattice(16, 16, workloads.droplet(16), precision=ehdlb.FP32)
+    assert ehdlb.lib().ehdlb_set_timing(lat.ctx, -1) == ehdlb.EINVAL
+    lat.close()
+
+
 def test_error_codes():
     L = ehdlb.lib()
     h = ehdlb.ehdlb_create(16, 16, ehdlb.FP32)
