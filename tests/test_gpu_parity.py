@@ -501,7 +501,9 @@ def test_kernel_class_timing_every_nth_step_and_same_bits():
             assert classes == 0.0
         else:
             assert st.ms_prep > 0 and st.ms_sweeps > 0 and st.ms_main > 0
-            assert classes < 1e3 * st.seconds   # device time of the classes within the call's wall time
+            # the classes' device time against the call's wall time; scaled up
+            # from the recorded steps, which their events make a little slower
+            assert classes < (1.0 if every == 1 else 1.5) * 1e3 * st.seconds
         out[every] = lat.state()
         lat.close()
     assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[5])
