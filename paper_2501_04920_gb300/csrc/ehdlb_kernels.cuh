@@ -2979,55 +2979,34 @@ __device__ __forceinline__ void deform_slice_sums(const T *__restrict__ phi, int
 }
 
 // End of the phi >= 1/2 run through (xc, yc) in direction sgn along y or x,
-// searched by one warp 128 samples at a time (four consecutive ones per
-// lane, loaded together): the first s = 1 .. lim-1 whose sample drops below
-// 1/2 after one at or above it, interpolated linearly between the two;
-// sgn * lim when there is none.
+// searched by one warp 32 samples at a time: the first s = 1 .. lim-1 whose
+// sample drops below 1/2 after one at or above it, interpolated linearly
+// between the two; sgn * lim when there is none.
 template <typename T>
 __device__ __forceinline__ double phi_run_end(const T *phi, int nx, int ny, double xc, double yc, bool along_y,
                                               double sgn)
 {
-    constexpr int K = 4;
     const int lane = threadIdx.x & 31, lim = along_y ? ny : nx;
     double carry = phi_sample(phi, nx, ny, xc, yc);
-    for (int base = 1; base < lim; base += 32 * K) {
-        const int s0 = base + lane * K;
-        double v[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const int s = s0 + k;
-            const double tt = sgn * (double)s;
-            v[k] = 0.0;
-            if (s < lim) v[k] = along_y ? phi_sample(phi, nx, ny, xc, yc + tt) : phi_sample(phi, nx, ny, xc + tt, yc);
-        }
-        double pv0 = __shfl_up_sync(0xffffffffu, v[K - 1], 1);   // the sample before this lane's first
-        if (lane == 0) pv0 = carry;
-        int hk = -1;
-#pragma unroll
-        for (int k = K - 1; k >= 0; --k) {
-            const double pv = k == 0 ? pv0 : v[k > 0 ? k - 1 : 0];
-            if (s0 + k < lim && pv >= 0.5 && v[k] < 0.5) hk = k;
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, hk >= 0);
+    for (int base = 1; base < lim; base += 32) {
+        const int s = base + lane;
+        const double tt = sgn * (double)s;
+        double v = 0.0;
+        if (s < lim) v = along_y ? phi_sample(phi, nx, ny, xc, yc + tt) : phi_sample(phi, nx, ny, xc + tt, yc);
+        double pv = __shfl_up_sync(0xffffffffu, v, 1);
+        if (lane == 0) pv = carry;
+        const bool hit = s < lim && pv >= 0.5 && v < 0.5;
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
         if (m) {
             const int first = __ffs(m) - 1;
             double end = 0.0;
             if (lane == first) {
-                double pv = pv0, vk = v[0];
-#pragma unroll
-                for (int k = 1; k < K; ++k)
-                    if (k == hk) {
-                        pv = v[k - 1];
-                        vk = v[k];
-                    }
-                const int s = s0 + hk;
-                const double tt = sgn * (double)s;
                 const double pt = s == 1 ? 0.0 : sgn * (double)(s - 1);
-                end = pt + (tt - pt) * (pv - 0.5) / (pv - vk);
+                end = pt + (tt - pt) * (pv - 0.5) / (pv - v);
             }
             return __shfl_sync(0xffffffffu, end, first);
         }
-        carry = __shfl_sync(0xffffffffu, v[K - 1], 31);
+        carry = __shfl_sync(0xffffffffu, v, 31);
     }
     return sgn * lim;
 }
