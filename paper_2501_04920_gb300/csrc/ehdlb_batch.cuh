@@ -138,9 +138,10 @@ __device__ __forceinline__ void load_case(CaseDev<T, S> &dst, const CaseDev<T, S
     for (int i = tid; i < (int)(sizeof(CaseDev<T, S>) / 4); i += nt) d[i] = src[i];
 }
 
-// ---- persistent kernels of a batch step ----------------------------------------------------
+// ---- kernels of a batch step -----------------------------------------------------------------
 
-// O1-O3 of every case.  blockDim (64, 4).
+// O1-O3 of every case, one 64 x 4 tile per block: block (i, r) takes block
+// row z + r of work item i (grid: items x KB_ROWS; blockDim (64, 4)).
 template <typename T, typename S>
 __global__ void __launch_bounds__(256) kb_prep(const CaseDev<T, S> *__restrict__ cases,
                                                const WorkItem *__restrict__ items, const int *__restrict__ nitems,
@@ -148,18 +149,14 @@ __global__ void __launch_bounds__(256) kb_prep(const CaseDev<T, S> *__restrict__
 {
     griddep_begin();
     __shared__ CaseDev<T, S> C;
-    const int n = *nitems;
-    for (int it = blockIdx.x; it < n; it += gridDim.x) {
-        const WorkItem w = items[it];
-        load_case(C, cases, w.x);
-        __syncthreads();
-        const Pops<S> &cur = C.pops[C.ctl->tpar & 1];
-        const int by1 = min(w.z + KB_ROWS, C.gym);
-        for (int by = w.z; by < by1; ++by)
-            prep_body<T, S>(C.P, cur.h, cur.p, cur.n, C.ref, C.phig, C.q, C.ctl, fixedK, fixedK, fixedK, flips, w.y,
-                            by);
-        __syncthreads();
-    }
+    if ((int)blockIdx.x >= *nitems) return;
+    const WorkItem w = items[blockIdx.x];
+    load_case(C, cases, w.x);
+    __syncthreads();
+    const int by = w.z + (int)blockIdx.y;
+    if (by >= min(w.z + KB_ROWS, C.gym)) return;
+    const Pops<S> &cur = C.pops[C.ctl->tpar & 1];
+    prep_body<T, S>(C.P, cur.h, cur.p, cur.n, C.ref, C.phig, C.q, C.ctl, fixedK, fixedK, fixedK, flips, w.y, by);
 }
 
 // Sweep launch m of every case (NSW sweeps fused).  blockDim (32, BY).
@@ -212,27 +209,27 @@ __global__ void __launch_bounds__(256, 2) kb_sweep_r(const CaseDev<T, S> *__rest
     tbr_run<T, NSW, R, 8, FIRST, false>(J);
 }
 
-// O5-O11 of every case.  blockDim (64, 4), dynamic shared memory main_smem_bytes<T, S>().
+// O5-O11 of every case, one 64 x 4 tile per block: block (i, r) takes block
+// row z + r of work item i (grid: items x KB_ROWS; blockDim (64, 4), dynamic
+// shared memory main_smem_bytes<T, S>()), so that many blocks per SM hide the
+// latency of each one's staged copies (a persistent loop over the items
+// moved the same bytes at 0.61 of the copy bandwidth).
 template <typename T, typename S, bool SNAP>
 __global__ void __launch_bounds__(256, MAIN_MINB<T>) kb_main(const CaseDev<T, S> *__restrict__ cases,
-                                                  const WorkItem *__restrict__ items, const int *__restrict__ nitems)
+                                                   const WorkItem *__restrict__ items, const int *__restrict__ nitems)
 {
     griddep_begin();
     __shared__ CaseDev<T, S> C;
-    const int n = *nitems;
-    for (int it = blockIdx.x; it < n; it += gridDim.x) {
-        const WorkItem w = items[it];
-        load_case(C, cases, w.x);
-        __syncthreads();
-        const int par = C.ctl->tpar & 1;
-        const int by1 = min(w.z + KB_ROWS, C.gym);
-        for (int by = w.z; by < by1; ++by) {
-            main_body<T, S, SNAP, false, false, true>(C.P, C.pops[par], C.pops[par ^ 1], C.g[0], C.g[1], C.ctl,
-                                                      C.ref, C.phiu, C.psi_prev, C.snap, C.part, &C.ctl->unstable,
-                                                      w.y, by, (long long)by * C.gxm + w.y);
-            __syncthreads();
-        }
-    }
+    if ((int)blockIdx.x >= *nitems) return;
+    const WorkItem w = items[blockIdx.x];
+    load_case(C, cases, w.x);
+    __syncthreads();
+    const int by = w.z + (int)blockIdx.y;
+    if (by >= min(w.z + KB_ROWS, C.gym)) return;
+    const int par = C.ctl->tpar & 1;
+    main_body<T, S, SNAP, false, false, true>(C.P, C.pops[par], C.pops[par ^ 1], C.g[0], C.g[1], C.ctl, C.ref,
+                                              C.phiu, C.psi_prev, C.snap, C.part, &C.ctl->unstable, w.y, by,
+                                              (long long)by * C.gxm + w.y);
 }
 
 // End of step of every case (one block of 256 per case at a time).
@@ -595,7 +592,7 @@ template <typename T, typename S> class Batch : public BatchBase {
     {
         const int nk = (S_ + chunk_ - 1) / chunk_;
         const int items = host_nitems_[0];
-        launch_k(stream_, kb_prep<T, S>, dim3(pgrid(kb_prep<T, S>, 256, 0, items)), dim3(64, 4), 0, true, d_cases_,
+        launch_k(stream_, kb_prep<T, S>, dim3(std::max(1, items), KB_ROWS), dim3(64, 4), 0, true, d_cases_,
                  d_items_node_, d_nitems_, S_, nk);
         for (int m = 0, done = 0; m < nk; ++m) {
             const int nsw = std::min(chunk_, S_ - done);
@@ -610,11 +607,11 @@ template <typename T, typename S> class Batch : public BatchBase {
         }
         const size_t msm = main_smem_bytes<T, S>();
         if (last)
-            launch_k(stream_, kb_main<T, S, true>, dim3(pgrid(kb_main<T, S, true>, 256, msm, items)), dim3(64, 4), msm,
-                     true, d_cases_, d_items_node_, d_nitems_);
+            launch_k(stream_, kb_main<T, S, true>, dim3(std::max(1, items), KB_ROWS), dim3(64, 4), msm, true,
+                     d_cases_, d_items_node_, d_nitems_);
         else
-            launch_k(stream_, kb_main<T, S, false>, dim3(pgrid(kb_main<T, S, false>, 256, msm, items)), dim3(64, 4),
-                     msm, true, d_cases_, d_items_node_, d_nitems_);
+            launch_k(stream_, kb_main<T, S, false>, dim3(std::max(1, items), KB_ROWS), dim3(64, 4), msm, true,
+                     d_cases_, d_items_node_, d_nitems_);
         launch_k(stream_, kb_step_end<T, S>, dim3(std::min(ncases_, 4 * sms_)), dim3(256), 0, true, d_cases_,
                  d_nitems_ + 6, last ? 1 : 0);
         launches_ += per_step_launches();
