@@ -3054,6 +3054,7 @@ __device__ __forceinline__ void deform_finish(const T *__restrict__ phi, int nx,
 template <typename T>
 __global__ void __launch_bounds__(256) k_deform_sums(const T *__restrict__ phi, int nx, int ny, double *parts)
 {
+    griddep_begin();
     __shared__ double red[256][3];
     deform_slice_sums(phi, nx, ny, blockIdx.x, gridDim.x, red, parts + 3 * blockIdx.x);
 }
@@ -3063,6 +3064,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_deform_finish(const T *__restrict__ phi, int nx, int ny,
                                                        const double *__restrict__ parts, double *out)
 {
+    griddep_begin();
     __shared__ double red[256][3];
     deform_finish(phi, nx, ny, parts, red, out);
 }

@@ -393,8 +393,8 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     cudaError_t enqueue_deformation()
     {
         double *parts = red_ + 6 * PSUM;
-        k_deform_sums<T><<<deform_slices(nx_, ny_), 256, 0, stream_>>>(snap_, nx_, ny_, parts);
-        k_deform_finish<T><<<1, 256, 0, stream_>>>(snap_, nx_, ny_, parts, stage_);
+        launch_k(k_deform_sums<T>, dim3(deform_slices(nx_, ny_)), dim3(256), 0, true, snap_, nx_, ny_, parts);
+        launch_k(k_deform_finish<T>, dim3(1), dim3(256), 0, true, snap_, nx_, ny_, parts, stage_);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(&pin_->D, stage_, sizeof(double), cudaMemcpyDeviceToHost, stream_);
         return e;
