@@ -1535,6 +1535,7 @@ __global__ void __launch_bounds__(32 * NW, MINB)
                    double *__restrict__ part, Control *__restrict__ ctl, int tiles_x, int ntiles, int fixedK,
                    int flips)
 {
+    griddep_begin();
     const int par = ctl->cur0 & 1;   // the first launch of the step (m = 0)
     if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
         ctl->K = fixedK; ctl->flips = flips; ctl->done = 1; ctl->converge = 0;

@@ -833,10 +833,9 @@ template <typename T, typename S = T> class Solver : public SolverBase {
             const int ntiles = (int)(g.x * g.y);
             const int grid = std::min(ntiles, tbr_per_sm_[1] * sms_);
             const Pops<S> &pp = pops_[tpar_];
-            k_sweep_tbr_fp<T, NSW, sh.r, sh.by, sh.minb, RESID>
-                <<<grid, dim3(32, sh.by), tbr_smem_bytes<T, sh.r, sh.by>(true), stream_>>>(
-                    dp_, g_[0], g_[1], pp.h, pp.p, pp.n, ref_.phir, ref_.dphig, coef_, part2_, ctl_, (int)g.x,
-                    ntiles, fixedK, flips);
+            launch_k(k_sweep_tbr_fp<T, NSW, sh.r, sh.by, sh.minb, RESID>, dim3(grid), dim3(32, sh.by),
+                     tbr_smem_bytes<T, sh.r, sh.by>(true), true, dp_, g_[0], g_[1], pp.h, pp.p, pp.n, ref_.phir,
+                     ref_.dphig, coef_, part2_, ctl_, (int)g.x, ntiles, fixedK, flips);
         }
     }
 
