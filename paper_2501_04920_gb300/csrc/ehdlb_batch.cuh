@@ -232,6 +232,67 @@ __global__ void __launch_bounds__(256, MAIN_MINB<T>) kb_main(const CaseDev<T, S>
                                               (long long)by * C.gxm + w.y);
 }
 
+// The same with the tile staged by the tensor memory accelerator through the
+// case's tensor maps (maps[2 c + parity], in device memory; every case's
+// rows a multiple of 16 bytes): one thread issues the nine loads of the
+// single-lattice staged kernel behind one mbarrier and the block waits for
+// them (bounded: a late copy sets the case's Control::fault and the block
+// returns).  Dynamic shared memory TmaLayout<T, S>::stage.
+template <typename T, typename S, bool SNAP>
+__global__ void __launch_bounds__(256, MAIN_MINB<T>) kb_main_tma(const CaseDev<T, S> *__restrict__ cases,
+                                                      const MainMaps *__restrict__ maps,
+                                                      const WorkItem *__restrict__ items,
+                                                      const int *__restrict__ nitems)
+{
+    griddep_begin();
+    using L = TmaLayout<T, S>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ CaseDev<T, S> C;
+    const int tid = threadIdx.x + threadIdx.y * 64;
+    if ((int)blockIdx.x >= *nitems) return;
+    const WorkItem w = items[blockIdx.x];
+    load_case(C, cases, w.x);
+    __syncthreads();
+    const int by = w.z + (int)blockIdx.y;
+    if (by >= min(w.z + KB_ROWS, C.gym)) return;
+    if (smem_u32(smem_raw) & 127u) {
+        if (tid == 0) atomicExch(&C.ctl->fault, 2);
+        return;
+    }
+    const int par = C.ctl->tpar & 1;
+    const MainMaps *M = maps + 2 * w.x + par;
+    const int x0 = w.y * 64, y0 = by * 4;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+        const int gsel = (C.ctl->cur0 + C.ctl->flips) & 1;
+        mbar_expect_tx(&bar, L::tx(false) + C.P.tx_extra);
+        tma_load_3d(smem_raw + L::pops, &M->pops, &bar, x0, y0, 0);
+        tma_load_3d(smem_raw + L::pops + sizeof(S) * 27 * 256, &M->phiu, &bar, x0, y0, 0);
+        tma_load_3d(smem_raw + L::tpl, gsel ? &M->g[1] : &M->g[0], &bar, x0, y0, 0);
+        tma_load_2d(smem_raw + L::tpl + sizeof(T) * 4 * 256, &M->mur, &bar, x0, y0);
+        tma_load_2d(smem_raw + L::tpl + sizeof(T) * 5 * 256, &M->gxr, &bar, x0, y0);
+        tma_load_2d(smem_raw + L::tpl + sizeof(T) * 6 * 256, &M->gyr, &bar, x0, y0);
+        tma_load_2d(smem_raw + L::dphi, &M->dphi, &bar, x0 - TMA_HX, y0);
+        tma_load_2d(smem_raw + L::phir, &M->phir, &bar, x0 - TMA_HX, y0);
+    }
+    __syncthreads();   // the barrier is initialised before anyone waits on it
+    const bool late = !mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(late)) {
+        if (tid == 0) atomicExch(&C.ctl->fault, 1);
+        mbar_wait_bounded(&bar, 0);
+        return;
+    }
+    const TmaView<T, S> tv{reinterpret_cast<const S *>(smem_raw + L::pops),
+                           reinterpret_cast<const T *>(smem_raw + L::tpl),
+                           reinterpret_cast<const T *>(smem_raw + L::dphi),
+                           reinterpret_cast<const T *>(smem_raw + L::phir)};
+    main_body<T, S, SNAP, false, false, false, 5, true>(C.P, C.pops[par], C.pops[par ^ 1], C.g[0], C.g[1], C.ctl,
+                                                        C.ref, C.phiu, C.psi_prev, C.snap, C.part,
+                                                        &C.ctl->unstable, w.y, by, (long long)by * C.gxm + w.y, &tv);
+}
+
 // End of step of every case (one block of 256 per case at a time).
 template <typename T, typename S>
 __global__ void __launch_bounds__(256) kb_step_end(const CaseDev<T, S> *__restrict__ cases, const int *__restrict__ ncases,
@@ -328,6 +389,10 @@ template <typename T, typename S> class Batch : public BatchBase {
                                       (int)main_smem_bytes<T, S>()));
         EHDLB_CK(cudaFuncSetAttribute(kb_main<T, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)main_smem_bytes<T, S>()));
+        EHDLB_CK(cudaFuncSetAttribute(kb_main_tma<T, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)TmaLayout<T, S>::stage));
+        EHDLB_CK(cudaFuncSetAttribute(kb_main_tma<T, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)TmaLayout<T, S>::stage));
         EHDLB_CK(sweep_attr<1>());
         EHDLB_CK(sweep_attr<2>());
         EHDLB_CK(sweep_attr<3>());
@@ -408,12 +473,15 @@ template <typename T, typename S> class Batch : public BatchBase {
         EHDLB_CK(cudaEventElapsedTime(&ms, ev0_, ev1_));
         const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         // per-case control blocks: instability
-        int unstable = 0;
+        int unstable = 0, fault = 0;
         std::vector<Control> ctl(ncases_);
         for (int c = 0; c < ncases_; ++c)
             EHDLB_CK(cudaMemcpyAsync(&ctl[c], host_cases_[c].ctl, sizeof(Control), cudaMemcpyDeviceToHost, stream_));
         EHDLB_CK(cudaStreamSynchronize(stream_));
-        for (int c = 0; c < ncases_; ++c) unstable += ctl[c].unstable != 0;
+        for (int c = 0; c < ncases_; ++c) {
+            unstable += ctl[c].unstable != 0;
+            fault += ctl[c].fault != 0;
+        }
         if (st) {
             st->steps = nsteps;
             st->cases = ncases_;
@@ -425,6 +493,7 @@ template <typename T, typename S> class Batch : public BatchBase {
             st->sweeps_per_launch = chunk_;
             st->tile_shape = shape_;
         }
+        if (fault) { err = "a staged copy of the step kernel did not arrive in time"; return EHDLB_ECUDA; }
         if (unstable) { err = "NaN or Inf in a case"; return EHDLB_EUNSTABLE; }
         return EHDLB_OK;
     }
@@ -606,12 +675,20 @@ template <typename T, typename S> class Batch : public BatchBase {
             done += nsw;
         }
         const size_t msm = main_smem_bytes<T, S>();
-        if (last)
-            launch_k(stream_, kb_main<T, S, true>, dim3(std::max(1, items), KB_ROWS), dim3(64, 4), msm, true,
-                     d_cases_, d_items_node_, d_nitems_);
-        else
-            launch_k(stream_, kb_main<T, S, false>, dim3(std::max(1, items), KB_ROWS), dim3(64, 4), msm, true,
-                     d_cases_, d_items_node_, d_nitems_);
+        const dim3 mg(std::max(1, items), KB_ROWS), mb(64, 4);
+        if (tma_) {   // every case's tile staged through its tensor maps
+            const size_t tsm = TmaLayout<T, S>::stage;
+            if (last)
+                launch_k(stream_, kb_main_tma<T, S, true>, mg, mb, tsm, true, d_cases_, d_maps_, d_items_node_,
+                         d_nitems_);
+            else
+                launch_k(stream_, kb_main_tma<T, S, false>, mg, mb, tsm, true, d_cases_, d_maps_, d_items_node_,
+                         d_nitems_);
+        } else if (last) {
+            launch_k(stream_, kb_main<T, S, true>, mg, mb, msm, true, d_cases_, d_items_node_, d_nitems_);
+        } else {
+            launch_k(stream_, kb_main<T, S, false>, mg, mb, msm, true, d_cases_, d_items_node_, d_nitems_);
+        }
         launch_k(stream_, kb_step_end<T, S>, dim3(std::min(ncases_, 4 * sms_)), dim3(256), 0, true, d_cases_,
                  d_nitems_ + 6, last ? 1 : 0);
         launches_ += per_step_launches();
@@ -658,6 +735,8 @@ template <typename T, typename S> class Batch : public BatchBase {
         index_of_.clear();
         std::vector<WorkItem> node;
         std::vector<WorkItem> tb[TBMAX + 1], tbr[TBMAX + 1];
+        std::vector<MainMaps> maps;   // two per case: its time levels
+        bool all_maps = true;
         nodes_ = 0;
         int c = 0;
         for (auto &kv : cases_) {
@@ -672,6 +751,10 @@ template <typename T, typename S> class Batch : public BatchBase {
             d.gxm = gx;
             d.gym = gy;
             host_cases_.push_back(d);
+            MainMaps m[2] = {};
+            all_maps = sv.main_maps(m) && all_maps;
+            maps.push_back(m[0]);
+            maps.push_back(m[1]);
             index_of_[kv.first] = c;
             for (int by = 0; by < gy; by += KB_ROWS)
                 for (int bx = 0; bx < gx; ++bx) node.push_back(make_int4(c, bx, by, by * gx + bx));
@@ -693,6 +776,8 @@ template <typename T, typename S> class Batch : public BatchBase {
         EHDLB_CK(ensure(d_D_, cap_D_, host_cases_.size()));
         EHDLB_CK(ensure(d_Dpart_, cap_Dpart_, host_cases_.size() * 3 * DEF_MAX_SLICES));
         EHDLB_CK(ensure(d_items_node_, cap_node_, node.size()));
+        EHDLB_CK(ensure(d_maps_, cap_maps_, maps.size()));
+        tma_ = all_maps && !maps.empty();
         for (int nsw = 1; nsw <= TBMAX; ++nsw) {
             EHDLB_CK(ensure(d_items_tb_[nsw], cap_tb_[nsw], tb[nsw].size()));
             EHDLB_CK(ensure(d_items_tbr_[nsw], cap_tbr_[nsw], tbr[nsw].size()));
@@ -701,6 +786,9 @@ template <typename T, typename S> class Batch : public BatchBase {
                                  cudaMemcpyHostToDevice, stream_));
         EHDLB_CK(cudaMemcpyAsync(d_items_node_, node.data(), sizeof(WorkItem) * node.size(), cudaMemcpyHostToDevice,
                                  stream_));
+        if (!maps.empty())
+            EHDLB_CK(cudaMemcpyAsync(d_maps_, maps.data(), sizeof(MainMaps) * maps.size(), cudaMemcpyHostToDevice,
+                                     stream_));
         for (int nsw = 1; nsw <= TBMAX; ++nsw)
             EHDLB_CK(cudaMemcpyAsync(d_items_tbr_[nsw], tbr[nsw].data(), sizeof(WorkItem) * tbr[nsw].size(),
                                      cudaMemcpyHostToDevice, stream_));
@@ -742,6 +830,9 @@ template <typename T, typename S> class Batch : public BatchBase {
     double *d_D_ = nullptr;
     double *d_Dpart_ = nullptr;   // slice sums of the deformation factor
     WorkItem *d_items_node_ = nullptr;
+    MainMaps *d_maps_ = nullptr;   // tensor maps of the staged step kernel, two per case
+    size_t cap_maps_ = 0;
+    bool tma_ = false;             // every case takes the staged step kernel (kb_main_tma)
     WorkItem *d_items_tb_[TBMAX + 1] = {};
     WorkItem *d_items_tbr_[TBMAX + 1] = {};   // tiles of the register-blocked sweeps
     int *d_nitems_ = nullptr;   // [0] node items, [1..5] sweep items by NSW, [6] cases, [9..13] register-blocked sweep items

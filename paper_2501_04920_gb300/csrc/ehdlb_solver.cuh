@@ -228,6 +228,15 @@ template <typename T, typename S = T> class Solver : public SolverBase {
     }
 
     void set_schedule(const int *c, int n) override { sched_.assign(c, c + n); }
+    // the tensor maps of the staged step kernel for the two time levels
+    // (false if this lattice cannot take it)
+    bool main_maps(MainMaps (&m)[2]) const
+    {
+        if (!(kTmaMain && tma_ok_ && qi_ == 5 && !P_.side_walls)) return false;
+        m[0] = maps_[0];
+        m[1] = maps_[1];
+        return true;
+    }
     int stall_next_copies() override
     {
         if (!(kTmaMain && tma_ && tma_ok_ && qi_ == 5 && !P_.side_walls)) return EHDLB_ESTATE;
