@@ -3,7 +3,8 @@
 The method runs one lattice per GPU with no exchange between them (replicas),
 so the only multi-rank logic is the max-over-ranks time and the whole-job
 value; both are checked here with world_size 2 over gloo.  Also on CPU: which
-clock samples the bench reports for its timed region.
+clock samples the bench reports for its timed region, and that it reports ncu
+records only for the kernel source they were taken on.
 """
 import os
 import socket
@@ -76,3 +77,27 @@ def test_clock_summary_takes_the_samples_of_the_timed_region():
     assert s["samples_taken"] == "bracketing" and s["samples"] == 2
     assert s["sm_mhz"] == 2055.0 and s["reasons"] == ["sw_power_cap"]
     assert abs(s["region_ms"] - 10.0) < 1e-6
+
+
+def test_profile_records_are_reported_only_for_the_source_they_were_taken_on(tmp_path, monkeypatch):
+    # the bench's DRAM and instruction figures per node come from ncu records
+    # that name the kernel source they were measured on; a different source
+    # gives no figure (the line reports null rather than a stale number)
+    import hashlib
+    import json
+    import bench
+    csrc = tmp_path / "paper_2501_04920_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    src = b"// kernels\n"
+    (csrc / "ehdlb_kernels.cuh").write_bytes(src)
+    digest = hashlib.sha256(src).hexdigest()[:16]
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(
+        {"k_main": {"dram_bytes_per_node": 256.4, "source_sha256_16": digest}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profile_record("k_main", "dram_bytes_per_node") == 256.4
+    assert bench.measured_traffic("k_main", 2048) == 256.4 * 2048 * 2048
+    assert bench.profile_record("k_prep", "dram_bytes_per_node") is None
+    (csrc / "ehdlb_kernels.cuh").write_bytes(src + b"// changed\n")
+    assert bench.profile_record("k_main", "dram_bytes_per_node") is None
+    assert bench.measured_traffic("k_main", 2048) is None
